@@ -1,0 +1,15 @@
+import os
+import sys
+
+# triton is only used as an independent CPU implementation of Philox (interpreter mode);
+# the flag must be set before anything imports triton.
+os.environ.setdefault("TRITON_INTERPRET", "1")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300, sm_103a) and the built library")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
