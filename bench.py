@@ -1,0 +1,302 @@
+"""Benchmark: time to 1e-6 relative suboptimality of sketched-preconditioned SVRG (Alg. 3) on one GB300.
+
+Workload: n = 65536, d = 1024 FP32 rows with power-law spectrum j^-2 in a random basis,
+y = X w_gen + 0.05 N(0,1), lambda = 1e-5, CountSketch (s = 4096) then Gaussian sketch of rank 64,
+importance-sampled SVRG with m = 2n, eta = 1/beta_hat.  One step = one full solve from the
+device-resident (X, y) to w: sketch, precondition, every epoch needed to reach 1e-6.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {rs,reference}]
+
+Prints one JSON line.  `--impl reference` times the CPU oracle (the slow FP64 reference) on a
+bounded sample of the same workload and extrapolates to one solve.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+TARGET = 1e-6
+WORKLOAD = "fp32_n65536_d1024"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _clock_sampler(out_path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(out_path, "w")
+        dev = os.environ.get("LOCAL_RANK", "0")
+        return subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def _clock_summary(path):
+    try:
+        rows = [r.split(",") for r in open(path).read().strip().splitlines() if r.strip()]
+    except Exception:
+        return None
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+    reasons = set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        if len(r) < 9:
+            continue
+        for nm, v in zip(names, r[5:9]):
+            if "Active" in v and "Not" not in v:
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        return dist, rank, ws
+    return None, rank, ws
+
+
+def max_over_ranks(dist, value):
+    """Largest value over all ranks (the slowest replica sets the time)."""
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_rs(args):
+    import paper_1602_02350_gb300 as rs
+    from paper_1602_02350_gb300 import synth
+
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    cfg = synth.CONFIGS[WORKLOAD]
+    X, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.float32)
+    y = y64.float().contiguous()
+    n, d, k, lam = cfg.n, cfg.d, cfg.k, cfg.lam
+    m = 2 * n
+    eta_mult = 1.0
+    stream = torch.cuda.current_stream()
+    ctx = rs.Context(local, stream)
+
+    # reference minimiser for the accuracy target (double Cholesky; measurement only, untimed)
+    Xd = X.double()
+    A = Xd.T @ Xd / n + lam * torch.eye(d, dtype=torch.float64, device="cuda")
+    w_star64 = torch.cholesky_solve((Xd.T @ y64.cuda().double() / n)[:, None], torch.linalg.cholesky(A))[:, 0]
+    del Xd, A
+    w_star = w_star64.float()
+    L_star, _ = rs.rs_objective(ctx, X, y, lam, w_star)
+
+    def rel(w):
+        return rs.rs_objective(ctx, X, y, lam, w, w_star)[1] / L_star
+
+    # calibration (untimed): epochs needed to reach the target
+    max_ep = 20
+    _, info = rs.rs_solve(ctx, X, y, k, lam, max_ep, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
+                          eta_mult=eta_mult, snapshots=True)
+    hist = [rel(s) for s in info["snapshots"]]
+    reach = [i for i, r in enumerate(hist) if r <= TARGET]
+    epochs = (reach[0] + 1) if reach else max_ep
+
+    def step():
+        return rs.rs_solve(ctx, X, y, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
+                           eta_mult=eta_mult)[0]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    cpath = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    os.makedirs(os.path.dirname(cpath), exist_ok=True)
+    sampler, fh = _clock_sampler(cpath)
+    time.sleep(0.3)
+    l0 = ctx.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        w = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launches - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+        fh.close()
+    final_rel = rel(w)
+    ms = max_over_ranks(dist, ms)
+
+    # end to end through the public call with host buffers (pinned), copies inside the timed region
+    Xh = X.cpu().pin_memory()
+    yh = y.cpu().pin_memory()
+    wh = torch.empty(d, dtype=torch.float32).pin_memory()
+    rs.rs_solve(ctx, Xh, yh, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
+                eta_mult=eta_mult, w_out=wh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rs.rs_solve(ctx, Xh, yh, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
+                    eta_mult=eta_mult, w_out=wh)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / args.steps)
+
+    # dominant data pass: the full-gradient stream over the n + d component rows (same kernel the
+    # solve launches once per epoch), timed alone with events on the library's stream
+    V, s2 = rs.rs_sketch(ctx, X, k, cfg.seed_sketch, kind=cfg.kind, s=cfg.s)
+    Z, beta, bh = rs.rs_precondition(ctx, X, V, s2, lam)
+    wt = torch.zeros(d, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        rs.rs_full_gradient(ctx, Z, y, n, lam, wt)
+    reps = 20
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    f0.record(stream)
+    for _ in range(reps):
+        rs.rs_full_gradient(ctx, Z, y, n, lam, wt)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fg_ms = f0.elapsed_time(f1) / reps
+    fg_bytes = (n + d) * d * 4 + n * 4          # algorithmic: every component row and label read once
+    peak, peak_kind = _peaks()
+    achieved = fg_bytes / (fg_ms * 1e-3) / 1e9
+
+    # per-epoch split of the solve (events recorded by the library between epochs)
+    _, info2 = rs.rs_solve(ctx, X, y, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
+                           eta_mult=eta_mult)
+    ems = info2["epoch_ms"]
+    per_epoch = (ems[-1] - ems[0]) / max(1, len(ems) - 1) if len(ems) > 1 else (ems[0] if ems else None)
+
+    out = {
+        "metric": "time-to-1e-6 relative suboptimality", "value": ms / 1e3, "unit": "s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: n=65536 d=1024 fp32, spectrum j^-2, lambda=1e-5, "
+                               "CountSketch s=4096 -> Gaussian k=64, SVRG m=2n eta=1/beta_hat",
+                   "n": n, "d": d, "k": k, "lambda": lam, "m": m, "eta_mult": eta_mult, "epochs": epochs,
+                   "rel_subopt_per_epoch": [float(f"{h:.3e}") for h in hist[:epochs]],
+                   "final_rel_subopt": final_rel, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs exceed L2 (X 268 MB, components 272 MB vs 129 MB L2); no flush"},
+        "roofline": {"kernel": "fullgrad (data pass over the n+d component rows)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": None, "ms_per_launch": fg_ms},
+        "inner_loop": {"ms_per_epoch": per_epoch, "ns_per_step": per_epoch * 1e6 / m if per_epoch else None,
+                       "steps_per_s": m / (per_epoch * 1e-3) if per_epoch else None},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * d * 4 + n * 4, "d2h_bytes_per_step": d * 4},
+        "gpu_launches": launches,
+        "clocks": _clock_summary(cpath),
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline_sample(budget_s=args.cpu_budget) if args.cpu_budget > 0 else None
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+
+
+def cpu_baseline_sample(budget_s=20.0, epochs=None):
+    """Time the FP64 oracle on host cores on a bounded sample of the workload and extrapolate
+    to one solve: (sketch + precondition) once, plus epochs x (full gradient + m steps)."""
+    from oracle import precond, sketch, svrg
+    from paper_1602_02350_gb300 import synth
+    cfg = synth.CONFIGS[WORKLOAD]
+    X, y, _ = synth.config_problem(cfg, dtype=torch.float32)
+    Xn = X.double().numpy()
+    yn = y.float().double().numpy()
+    n, d, lam = cfg.n, cfg.d, cfg.lam
+    m = 2 * n
+    epochs = epochs or 4
+    t0 = time.perf_counter()
+    V, s2 = sketch.block_lanczos(Xn, cfg.k, cfg.seed_sketch, kind=cfg.kind, s=cfg.s)
+    M = precond.m_matrix(V, s2, lam)
+    Z, yz, g = precond.components(*precond.transform(Xn, M), yn, lam)
+    beta = precond.smoothness(Z, g)
+    t_prep = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    wbar = np.zeros(d)
+    mu = svrg.full_gradient_fast(Z, yz, g, wbar)
+    t_fg = time.perf_counter() - t1
+    W, cum, q = svrg.sampling_table(beta)
+    from oracle import streams
+    steps = int(min(m, max(2000, (budget_s - t_prep - t_fg) / 20e-6)))
+    idx = streams.sample_indices(cum, cfg.seed_svrg, 0, steps)
+    t2 = time.perf_counter()
+    svrg.epoch(Z, yz, g, wbar, idx, q, 1.0 / precond.beta_hat(beta), v_bar=mu)
+    t_step = (time.perf_counter() - t2) / steps
+    total = t_prep + epochs * (t_fg + m * t_step)
+    return {"value": total, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"sketch+precondition once ({t_prep:.1f} s), one full-gradient pass ({t_fg:.2f} s) and "
+                      f"{steps} inner steps ({t_step * 1e6:.1f} us/step) of the {WORKLOAD} workload, "
+                      f"extrapolated to {epochs} epochs of m={m}; numpy BLAS threads for the dense steps, "
+                      f"one thread for the sequential inner loop"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on host cores, same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    cb = None
+    for _ in range(max(0, args.warmup)):
+        pass   # the oracle has no warm-up state; a warm-up pass would only double the run time
+    for _ in range(args.steps):
+        cb = cpu_baseline_sample(budget_s=args.cpu_budget if args.cpu_budget > 0 else 15.0)
+        vals.append(cb["value"])
+    v = statistics.mean(vals)
+    out = {"impl": "reference", "metric": "time-to-1e-6 relative suboptimality", "value": v, "unit": "s",
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{WORKLOAD} (bounded sample, extrapolated)", "parallelism": "cpu"},
+           "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rs", choices=["rs", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle work for the cpu_baseline sample (0 = skip)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_rs(args)
+
+
+if __name__ == "__main__":
+    main()

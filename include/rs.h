@@ -1,0 +1,255 @@
+/*
+ * rs.h -- C ABI of the GB300 (sm_103a) library for ridge regression by sketched
+ * preconditioned SVRG (Gonen, Orabona, Shalev-Shwartz, "Solving Ridge Regression
+ * using Sketched Preconditioned SVRG").
+ *
+ * Problem (Eq. (1)):  min_w  L(w) = (1/n) sum_i 1/2 (w^T x_i - y_i)^2 + (lam/2) ||w||^2.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major; row i of X is the example x_i.  ``ld`` is the row
+ *     stride in elements; ld * sizeof(element) and the base address must be
+ *     multiples of 16 bytes (vectorised and asynchronous copies), else RS_EINVAL.
+ *   - Every array argument is a caller-owned DEVICE pointer unless its comment
+ *     says "host".  The library never frees caller memory.
+ *   - "T" below is the compute type of the call: double when the data matrix is
+ *     RS_F64, float otherwise.  Vectors and small matrices (y, w, mu, V, Q, ...)
+ *     are T unless stated.
+ *   - Calls are ordered on the context's CUDA stream and return without a host
+ *     synchronisation unless stated; a status of RS_OK means the work was
+ *     enqueued.  rs_svrg_solve, rs_solve and rs_objective synchronise.
+ *   - On a non-zero status nothing is guaranteed about outputs; the message is
+ *     available from rs_last_error() (per host thread).  No C++ exception
+ *     crosses this boundary, and there is no CPU fallback: without a CUDA
+ *     device every compute call returns RS_ECUDA.
+ *   - The context owns scratch memory (grown on demand with cudaMalloc, kept
+ *     until rs_destroy) and a device status word that kernels use to report
+ *     non-finite data.
+ *   - Random draws come from the counter-based Philox4x32-10 generator (Salmon
+ *     et al., SC'11), key = the 64-bit seed, counter words
+ *       Gaussian entry (i, 4g+r):  (lo32(i), hi32(i), g, 1)
+ *       CountSketch row i:         (lo32(i), hi32(i), 0, 2)
+ *       SVRG step t of epoch e:    (lo32(t), hi32(t), e, 3)
+ *     so results are reproducible bit for bit for a given seed.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RS_ABI_VERSION 1
+
+/* status codes */
+enum {
+  RS_OK = 0,
+  RS_EINVAL = 1,          /* bad shape, stride, alignment, parameter */
+  RS_ENOMEM = 2,          /* scratch allocation failed */
+  RS_ECUDA = 3,           /* CUDA runtime error (message has the CUDA error string) */
+  RS_ENONFINITE = 4,      /* NaN or Inf met in the data or an iterate */
+  RS_ETIMEOUT = 5,        /* a bounded device-side wait gave up */
+  RS_EDIVERGED = 6,       /* SVRG iterate grew without bound (step size too large) */
+  RS_ENOTCONVERGED = 7,   /* tolerance not met within the epoch budget (w_out still written) */
+  RS_EUNSUPPORTED = 8     /* valid request this build does not implement */
+};
+
+typedef enum { RS_F64 = 0, RS_F32 = 1, RS_BF16 = 2, RS_FP8E4M3 = 3 } rs_dtype;
+
+typedef struct rs_ctx rs_ctx;
+
+/* Dense row-major matrix in device memory. */
+typedef struct {
+  const void* data;        /* n rows of ld elements of type dtype */
+  const float* row_scale;  /* RS_FP8E4M3 only: n per-row scales (value = code * scale); else NULL */
+  int64_t n, d, ld;        /* rows, columns, row stride (elements) */
+  int32_t dtype;           /* rs_dtype */
+  int32_t reserved;
+} rs_matrix;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device ``device`` issuing work on ``cuda_stream``
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the handle. */
+int rs_create(rs_ctx** ctx, int device, void* cuda_stream);
+/* Free the context and its scratch memory (synchronises its stream). */
+int rs_destroy(rs_ctx* ctx);
+/* Change the stream later calls are ordered on. */
+int rs_set_stream(rs_ctx* ctx, void* cuda_stream);
+/* Message of the last non-zero status returned on this host thread ("" if none). */
+const char* rs_last_error(void);
+/* RS_ABI_VERSION of the loaded library. */
+int rs_abi_version(void);
+/* Number of kernel launches this context has issued since creation. */
+int64_t rs_launch_count(const rs_ctx* ctx);
+
+/* ------------------------------------------------------- random streams */
+
+/* Raw Philox4x32-10 words: out[4*i + w] = word w of counter (lo32(i), hi32(i), c2, c3)
+ * with key ``seed``, i = 0..count-1.  out: 4*count uint32. */
+int rs_philox_words(rs_ctx* ctx, uint64_t seed, uint32_t c2, uint32_t c3, int64_t count,
+                    uint32_t* out);
+
+/* Gaussian test matrix of Alg. 2: out[r*ld + j] = Pi(row0 + r, j), N(0,1), for
+ * r < rows, j < cols.  Entry (i, 4g+r) is Box-Muller on the words of counter
+ * (i, g, tag 1): words (0,1) -> r = 0,1 and (2,3) -> r = 2,3, each word mapped to
+ * the uniform (2*(w>>9)+1) 2^-24.  dtype RS_F64 evaluates log/sqrt/sincospi in
+ * double, RS_F32 in float (within a few float ulps of the double values). */
+int rs_gaussian(rs_ctx* ctx, uint64_t seed, int64_t row0, int64_t rows, int64_t cols,
+                int32_t dtype, void* out, int64_t ld);
+
+/* CountSketch S X (s x d, T, row stride ld_sx): row h is the sum of sigma(i) x_i over
+ * the rows i with h(i) = h, added in increasing i (deterministic).
+ * h(i) = floor(w0 * s / 2^32), sigma(i) = -1 iff bit 31 of w1, words of counter
+ * (i, 0, tag 2).  bucket_out (int32, n) and sign_out (T, n) may be NULL. */
+int rs_countsketch(rs_ctx* ctx, const rs_matrix* X, uint64_t seed, int64_t s, void* SX,
+                   int64_t ld_sx, int32_t* bucket_out, void* sign_out);
+
+/* ------------------------------------------------------------- sketch (Alg. 2) */
+
+enum { RS_SKETCH_GAUSSIAN = 0, RS_SKETCH_COUNTSKETCH = 1 };
+
+typedef struct {
+  int32_t kind;        /* RS_SKETCH_GAUSSIAN: Pi ~ N(0,1)^{n x k};
+                          RS_SKETCH_COUNTSKETCH: Pi = S^T G', S an s x n CountSketch, G' ~ N(0,1)^{s x k} */
+  int32_t k;           /* rank, 1 <= k <= min(d, 256) */
+  int64_t s;           /* CountSketch rows (kind 1); 0 = min(n, 64 k) */
+  int32_t q_blocks;    /* Krylov blocks q of Alg. 2 (>= 1; 1 = single-pass range sketch) */
+  int32_t reserved;
+  uint64_t seed;
+} rs_sketch_params;
+
+/* First Krylov block of Alg. 2 without its n^{-1/2}: Y = X^T Pi (d x k, T, row-major). */
+int rs_range_sketch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* Y);
+
+/* Orthonormalise the k columns of Y (d x k, T) (Alg. 2, "orthonormalize"): Cholesky-QR
+ * applied twice, Gram matrices accumulated and factored in double.  Q (d x k, T) spans Y
+ * with Q^T Y upper triangular with positive diagonal.  RS_EINVAL if Y is rank deficient
+ * to working precision. */
+int rs_orthonormalize(rs_ctx* ctx, const void* Y, int64_t d, int64_t k, int32_t dtype, void* Q);
+
+/* Symmetric eigen-decomposition G = W diag(evals) W^T of a k x k matrix (double, row-major)
+ * by cyclic Jacobi on one thread block.  evals descending (double, k); W (double, k x k,
+ * column j = eigenvector j).  prec RS_F64 iterates in double, RS_F32 in float. */
+int rs_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W);
+
+/* Rayleigh-Ritz (Alg. 2, last two steps) for Q (d x k, T, orthonormal columns):
+ * G = (X Q)^T (X Q) / n (accumulated in double), G = W diag(sigma2) W^T,
+ * V = Q W (d x k, T), sigma2 (double, k) descending: the Ritz pairs of C = X^T X / n. */
+int rs_ritz(rs_ctx* ctx, const rs_matrix* X, const void* Q, int64_t k, void* V, double* sigma2);
+
+/* Alg. 2 composed: range sketch, q-1 products with C, orthonormalisation, Rayleigh-Ritz.
+ * V (d x k, T): approximate leading eigenvectors of C; sigma2 (double, k) descending. */
+int rs_sketch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* V, double* sigma2);
+
+/* --------------------------------------------------- preconditioner (Eq. (11)) */
+
+/* Apply the sketched preconditioner of Eq. (11) without its scalar c = (sigma2_k + lam)^{-1/2}:
+ *   M = I - V (I - D') V^T,   D'_j = sqrt((sigma2_k + lam) / (sigma2_j + lam)),
+ * and write the N = n + d components of Sec. 5.1 as the rows of Z (Xt):
+ *   rows 0..n-1:   z_i = M x_i            (x~_i of Alg. 3),
+ *   rows n..n+d-1: z_{n+j} = M e_j        (b_j of Alg. 3; M is symmetric).
+ * Xt->data is written (cast away const); Xt->n must be n + d, Xt->d = d, Xt->dtype equal
+ * to X->dtype (RS_F64 or RS_F32) or RS_BF16 when X is RS_BF16.
+ * beta (T, n + d): smoothness beta_i = gamma_i ||z_i||^2 with gamma_i = (n+d)/n for data
+ * rows and lam (n+d) for regulariser rows (Alg. 3).  beta_hat (host, nullable): mean beta. */
+int rs_precondition(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k,
+                    double lambda, rs_matrix* Xt, void* beta, double* beta_hat);
+
+/* w = M w~ (d, T): map an iterate of the preconditioned problem back (Eq. (4)). */
+int rs_map_output(rs_ctx* ctx, const void* V, const double* sigma2, int64_t d, int64_t k,
+                  double lambda, int32_t dtype, const void* w_tilde, void* w);
+
+/* ------------------------------------------------------ sampling (Alg. 1) */
+
+/* Integer sampling weights W_i = max(1, floor(2^24 beta_i / max_j beta_j)) (uint32, N),
+ * computed with one double division per entry, so equal beta gives equal W on any
+ * machine.  RS_ENONFINITE if a beta is NaN/Inf or negative. */
+int rs_sampling_weights(rs_ctx* ctx, const void* beta, int32_t dtype, int64_t N, uint32_t* W);
+
+/* Inclusive prefix sums cum[i] = W_0 + ... + W_i (uint64, N); q_i = W_i / cum[N-1]. */
+int rs_sampling_table(rs_ctx* ctx, const uint32_t* W, int64_t N, uint64_t* cum);
+
+enum { RS_SAMPLE_IMPORTANCE = 0, RS_SAMPLE_UNIFORM = 1 };
+
+/* Index stream of Alg. 1 for steps t = t0..t0+m-1 of epoch ``epoch``: with u the 64-bit
+ * word w1 2^32 + w0 of counter (t, epoch, tag 3) and T = cum[N-1],
+ *   IMPORTANCE: r = floor(u T / 2^64), idx = smallest i with cum[i] > r,
+ *   UNIFORM:    idx = floor(w0 N / 2^32)   (W and cum may be NULL),
+ * and inv_nq[t] = 1 / (N q_idx) (T dtype) with q_i = W_i / T (1/(N q) = 1 for UNIFORM).
+ * idx: uint32 (m), inv_nq: dtype (m). */
+int rs_index_stream(rs_ctx* ctx, const uint32_t* W, const uint64_t* cum, int64_t N, uint64_t seed,
+                    int64_t epoch, int64_t t0, int64_t m, int32_t sampling, int32_t dtype,
+                    uint32_t* idx, void* inv_nq);
+
+/* --------------------------------------------------------- SVRG (Alg. 1) */
+
+/* Full gradient of the preconditioned objective (Alg. 1, v_bar = grad F(w_bar)) over the
+ * N = n + d rows z_i of Z (layout of rs_precondition):
+ *   mu = (1/N) sum_i gamma_i (z_i^T w - y_i) z_i,  y_i = 0 for i >= n,
+ * which equals X~^T (X~ w - y)/n + lam M^T M w.  One streaming pass over Z; deterministic. */
+int rs_full_gradient(rs_ctx* ctx, const rs_matrix* Z, const void* y, int64_t n, double lambda,
+                     const void* w, void* mu);
+
+/* One outer iteration of Alg. 1 for a given index stream (idx, inv_nq from rs_index_stream):
+ *   w_0 = w_bar;  w_t = w_{t-1} - eta ((grad f_i(w_{t-1}) - grad f_i(w_bar)) inv_nq[t] + mu);
+ *   w_next = (1/m) sum_{t=1..m} w_t  (average != 0)  or  w_m  (average == 0),
+ * with grad f_i(w) - grad f_i(w_bar) = gamma_i (z_i^T (w - w_bar)) z_i.  The m sequential
+ * steps are evaluated in blocks of 64 with the block's Gram matrix, which gives the same
+ * iterates as the step-by-step recursion up to rounding.  w_next must not alias w_bar. */
+int rs_svrg_epoch(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lambda, const uint32_t* idx,
+                  const void* inv_nq, int64_t m, double eta, const void* w_bar, const void* mu,
+                  int32_t average, void* w_next);
+
+typedef struct {
+  double lambda;
+  double eta;          /* <= 0: Thm 2 value 0.1 / beta_hat; eta_mult > 0 overrides */
+  double eta_mult;     /* > 0: eta = eta_mult / beta_hat */
+  int64_t m;           /* inner steps per epoch; <= 0: Thm 2 value ceil(beta_hat / lam) */
+  int32_t epochs;      /* outer iterations S */
+  int32_t epoch0;      /* first epoch number (resume at an epoch boundary) */
+  int32_t sampling;    /* RS_SAMPLE_IMPORTANCE (q_i ~ beta_i) or RS_SAMPLE_UNIFORM */
+  int32_t average;     /* 1: epoch output is the average of w_1..w_m (Alg. 1); 0: w_m */
+  uint64_t seed;
+} rs_svrg_params;
+
+typedef struct {
+  int32_t capacity;      /* number of epochs the buffers below hold */
+  int32_t epochs_run;    /* written */
+  void* snapshots;       /* device, nullable: capacity x d (T), w_bar_s in ORIGINAL coordinates (M w~) */
+  double* mu_norm2;      /* host, nullable: ||mu||^2 at the start of each epoch */
+  float* epoch_ms;       /* host, nullable: cumulative device time at the end of each epoch */
+} rs_history;
+
+/* Alg. 1 on the components Z (rs_precondition layout, N = n + d rows) for p->epochs epochs,
+ * starting from w0 (preconditioned coordinates, nullable = 0).  beta (T, N; nullable =
+ * recomputed from Z) sets the sampling weights.  V/sigma2/k give M for the output map:
+ * w_out = M w~_S (original coordinates, Alg. 3 read as w = P^{-1/2} w~).  eta_used / m_used
+ * (host, nullable) receive the resolved step size and epoch length.  Synchronises.
+ * RS_ENONFINITE / RS_EDIVERGED if an iterate becomes non-finite. */
+int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const void* y, const void* beta, const void* V,
+                  const double* sigma2, int64_t k, const rs_svrg_params* p, const void* w0,
+                  void* w_out, rs_history* hist, double* eta_used, int64_t* m_used);
+
+/* Alg. 3 end to end: sketch (Alg. 2), preconditioner and transformed components (Eq. (11),
+ * Sec. 5.1), SVRG (Alg. 1), w_out = M w~ (Eq. (4)).  X->data, y and w_out may be HOST
+ * pointers (detected): the data is then copied to scratch memory and the result back inside
+ * the call.  Scratch holds (n + d) x d elements for the components.  Synchronises. */
+int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp,
+             const rs_svrg_params* p, void* w_out, rs_history* hist);
+
+/* ----------------------------------------------------- accuracy (Eq. (1)) */
+
+/* out[0] = L(w) of Eq. (1); out[1] = 1/2 e^T (C + lam I) e = (1/2n)||X e||^2 + (lam/2)||e||^2
+ * with e = w - w_ref, which is L(w) - L(w_ref) when w_ref minimises L (out[1] = 0 if w_ref
+ * is NULL).  Accumulated in double.  out: host, 2 doubles.  Synchronises. */
+int rs_objective(rs_ctx* ctx, const rs_matrix* X, const void* y, double lambda, const void* w,
+                 const void* w_ref, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H */

@@ -42,12 +42,19 @@ def epoch(Z, yz, gamma, w_bar, idx, q, eta, average=True, v_bar=None):
     (or w_m when ``average`` is False, the last-iterate option).
     """
     N = Z.shape[0]
+    inv_nq = 1.0 / (N * np.asarray(q, np.float64)[np.asarray(idx)])
+    return epoch_scaled(Z, yz, gamma, w_bar, idx, inv_nq, eta, average, v_bar)
+
+
+def epoch_scaled(Z, yz, gamma, w_bar, idx, inv_nq, eta, average=True, v_bar=None):
+    """Alg. 1's inner loop with the factor 1/(N q_{i_t}) of each step given explicitly
+    (``inv_nq[t]``), so that any index stream and weights can be replayed."""
     if v_bar is None:
         v_bar = full_gradient_fast(Z, yz, gamma, w_bar)
     w = np.array(w_bar, np.float64)
     acc = np.zeros_like(w)
-    for i in idx:
-        v = (grad_component(Z, yz, gamma, i, w) - grad_component(Z, yz, gamma, i, w_bar)) / (N * q[i]) + v_bar
+    for t, i in enumerate(idx):
+        v = (grad_component(Z, yz, gamma, i, w) - grad_component(Z, yz, gamma, i, w_bar)) * inv_nq[t] + v_bar
         w = w - eta * v
         acc += w
     return acc / len(idx) if average else w

@@ -1,0 +1,371 @@
+"""ctypes binding of ``librs.so`` (the C ABI in include/rs.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.  Tensors
+must be CUDA tensors (PyTorch supplies device memory and streams); unsigned index
+data travels in int32 / int64 tensors holding the uint32 / uint64 bit patterns.
+There is no CPU fallback: without the built library every call raises.
+"""
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librs.so")
+
+RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENONFINITE, RS_ETIMEOUT, RS_EDIVERGED, RS_ENOTCONVERGED, RS_EUNSUPPORTED = range(9)
+RS_F64, RS_F32, RS_BF16, RS_FP8E4M3 = 0, 1, 2, 3
+RS_SKETCH_GAUSSIAN, RS_SKETCH_COUNTSKETCH = 0, 1
+RS_SAMPLE_IMPORTANCE, RS_SAMPLE_UNIFORM = 0, 1
+
+_DT = {torch.float64: RS_F64, torch.float32: RS_F32, torch.bfloat16: RS_BF16}
+_TORCH = {RS_F64: torch.float64, RS_F32: torch.float32, RS_BF16: torch.bfloat16}
+
+
+class RsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rs status {code}: {msg}")
+        self.code = code
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("row_scale", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("d", ctypes.c_int64), ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SketchParams(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("s", ctypes.c_int64),
+                ("q_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class SvrgParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("eta", ctypes.c_double), ("eta_mult", ctypes.c_double),
+                ("m", ctypes.c_int64), ("epochs", ctypes.c_int32), ("epoch0", ctypes.c_int32),
+                ("sampling", ctypes.c_int32), ("average", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class History(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int32), ("epochs_run", ctypes.c_int32), ("snapshots", ctypes.c_void_p),
+                ("mu_norm2", ctypes.POINTER(ctypes.c_double)), ("epoch_ms", ctypes.POINTER(ctypes.c_float))]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "rs_create": [ctypes.POINTER(_P), ctypes.c_int, _P],
+    "rs_destroy": [_P],
+    "rs_set_stream": [_P, _P],
+    "rs_last_error": [],
+    "rs_abi_version": [],
+    "rs_launch_count": [_P],
+    "rs_philox_words": [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, _P],
+    "rs_gaussian": [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P,
+                    ctypes.c_int64],
+    "rs_countsketch": [_P, ctypes.POINTER(Matrix), ctypes.c_uint64, ctypes.c_int64, _P, ctypes.c_int64, _P, _P],
+    "rs_range_sketch": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(SketchParams), _P],
+    "rs_orthonormalize": [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P],
+    "rs_sym_eig": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P],
+    "rs_ritz": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_int64, _P, _P],
+    "rs_sketch": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(SketchParams), _P, _P],
+    "rs_precondition": [_P, ctypes.POINTER(Matrix), _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(Matrix),
+                        _P, ctypes.POINTER(ctypes.c_double)],
+    "rs_map_output": [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, _P, _P],
+    "rs_sampling_weights": [_P, _P, ctypes.c_int32, ctypes.c_int64, _P],
+    "rs_sampling_table": [_P, _P, ctypes.c_int64, _P],
+    "rs_index_stream": [_P, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                        ctypes.c_int32, ctypes.c_int32, _P, _P],
+    "rs_full_gradient": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_int64, ctypes.c_double, _P, _P],
+    "rs_svrg_epoch": [_P, ctypes.POINTER(Matrix), ctypes.c_int64, ctypes.c_double, _P, _P, ctypes.c_int64,
+                      ctypes.c_double, _P, _P, ctypes.c_int32, _P],
+    "rs_svrg_solve": [_P, ctypes.POINTER(Matrix), _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SvrgParams), _P, _P,
+                      ctypes.POINTER(History), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+    "rs_solve": [_P, ctypes.POINTER(Matrix), _P, ctypes.POINTER(SketchParams), ctypes.POINTER(SvrgParams), _P,
+                 ctypes.POINTER(History)],
+    "rs_objective": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_double)],
+}
+_RESTYPES = {"rs_last_error": ctypes.c_char_p, "rs_launch_count": ctypes.c_int64}
+
+
+def lib():
+    """Load librs.so (built in-tree by ``paper_1602_02350_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run `python -m paper_1602_02350_gb300.build` "
+                               "(the library has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _RESTYPES.get(name, ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _check(rc):
+    if rc != RS_OK:
+        raise RsError(rc, lib().rs_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and (not isinstance(t, torch.Tensor) or not t.is_cuda):
+            raise TypeError("expected a CUDA tensor")
+
+
+def matrix(t, row_scale=None):
+    """rs_matrix descriptor of a row-major 2-D CUDA tensor (row stride = t.stride(0))."""
+    _need_cuda(t)
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("matrix: need a 2-D tensor with unit column stride")
+    return Matrix(t.data_ptr(), None if row_scale is None else row_scale.data_ptr(), t.shape[0], t.shape[1],
+                  t.stride(0), _DT[t.dtype], 0)
+
+
+class Context:
+    """An rs_ctx bound to a CUDA device and stream (default: the current torch stream)."""
+
+    def __init__(self, device=0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("rs: no CUDA device (the library has no CPU fallback)")
+        self.device = torch.device("cuda", device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = s
+        h = ctypes.c_void_p()
+        _check(lib().rs_create(ctypes.byref(h), device, ctypes.c_void_p(s.cuda_stream)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rs_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(lib().rs_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)))
+
+    @property
+    def launches(self):
+        return lib().rs_launch_count(self.h)
+
+    def _empty(self, *shape, dtype):
+        return torch.empty(*shape, dtype=dtype, device=self.device)
+
+
+def _ctdt(t):
+    return RS_F64 if t.dtype == torch.float64 else RS_F32
+
+
+def _compute_dtype(X):
+    return torch.float64 if X.dtype == torch.float64 else torch.float32
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def rs_philox_words(ctx, seed, c2, c3, count):
+    out = ctx._empty(count * 4, dtype=torch.int32)
+    _check(lib().rs_philox_words(ctx.h, seed, c2, c3, count, _ptr(out)))
+    return out
+
+
+def rs_gaussian(ctx, seed, rows, cols, dtype=torch.float32, row0=0):
+    out = ctx._empty(rows, cols, dtype=dtype)
+    _check(lib().rs_gaussian(ctx.h, seed, row0, rows, cols, _DT[dtype], _ptr(out), cols))
+    return out
+
+
+def rs_countsketch(ctx, X, seed, s, with_hash=False):
+    ct = _compute_dtype(X)
+    SX = ctx._empty(s, X.shape[1], dtype=ct)
+    bucket = ctx._empty(X.shape[0], dtype=torch.int32) if with_hash else None
+    sign = ctx._empty(X.shape[0], dtype=ct) if with_hash else None
+    M = matrix(X)
+    _check(lib().rs_countsketch(ctx.h, ctypes.byref(M), seed, s, _ptr(SX), X.shape[1], _ptr(bucket), _ptr(sign)))
+    return (SX, bucket, sign) if with_hash else SX
+
+
+def _sketch_params(k, seed, kind, s, q):
+    kind_i = RS_SKETCH_COUNTSKETCH if kind in ("countsketch", RS_SKETCH_COUNTSKETCH) else RS_SKETCH_GAUSSIAN
+    return SketchParams(kind_i, k, s, q, 0, seed)
+
+
+def rs_range_sketch(ctx, X, k, seed, kind="gaussian", s=0):
+    Y = ctx._empty(X.shape[1], k, dtype=_compute_dtype(X))
+    M = matrix(X)
+    p = _sketch_params(k, seed, kind, s, 1)
+    _check(lib().rs_range_sketch(ctx.h, ctypes.byref(M), ctypes.byref(p), _ptr(Y)))
+    return Y
+
+
+def rs_orthonormalize(ctx, Y):
+    _need_cuda(Y)
+    Y = Y.contiguous()
+    Q = torch.empty_like(Y)
+    _check(lib().rs_orthonormalize(ctx.h, _ptr(Y), Y.shape[0], Y.shape[1], _ctdt(Y), _ptr(Q)))
+    return Q
+
+
+def rs_sym_eig(ctx, G, prec=RS_F64):
+    _need_cuda(G)
+    G = G.to(torch.float64).contiguous()
+    k = G.shape[0]
+    ev = ctx._empty(k, dtype=torch.float64)
+    W = ctx._empty(k, k, dtype=torch.float64)
+    _check(lib().rs_sym_eig(ctx.h, _ptr(G), k, prec, _ptr(ev), _ptr(W)))
+    return ev, W
+
+
+def rs_ritz(ctx, X, Q):
+    k = Q.shape[1]
+    V = ctx._empty(X.shape[1], k, dtype=_compute_dtype(X))
+    s2 = ctx._empty(k, dtype=torch.float64)
+    M = matrix(X)
+    _check(lib().rs_ritz(ctx.h, ctypes.byref(M), _ptr(Q.contiguous()), k, _ptr(V), _ptr(s2)))
+    return V, s2
+
+
+def rs_sketch(ctx, X, k, seed, kind="gaussian", s=0, q=1):
+    V = ctx._empty(X.shape[1], k, dtype=_compute_dtype(X))
+    s2 = ctx._empty(k, dtype=torch.float64)
+    M = matrix(X)
+    p = _sketch_params(k, seed, kind, s, q)
+    _check(lib().rs_sketch(ctx.h, ctypes.byref(M), ctypes.byref(p), _ptr(V), _ptr(s2)))
+    return V, s2
+
+
+def _padded_ld(d, dtype):
+    es = torch.empty((), dtype=dtype).element_size()
+    return ((d * es + 15) // 16 * 16) // es
+
+
+def rs_precondition(ctx, X, V, sigma2, lam, want_beta_hat=True):
+    n, d = X.shape
+    ld = _padded_ld(d, X.dtype)
+    Zs = ctx._empty(n + d, ld, dtype=X.dtype)
+    Z = Zs[:, :d]
+    beta = ctx._empty(n + d, dtype=_compute_dtype(X))
+    MX, MZ = matrix(X), matrix(Z)
+    bh = ctypes.c_double(0.0)
+    _check(lib().rs_precondition(ctx.h, ctypes.byref(MX), _ptr(V.contiguous()), _ptr(sigma2), V.shape[1], lam,
+                                 ctypes.byref(MZ), _ptr(beta), ctypes.byref(bh) if want_beta_hat else None))
+    return Z, beta, bh.value
+
+
+def rs_map_output(ctx, V, sigma2, lam, w_tilde):
+    w = torch.empty_like(w_tilde)
+    _check(lib().rs_map_output(ctx.h, _ptr(V.contiguous()), _ptr(sigma2), V.shape[0], V.shape[1], lam,
+                               _ctdt(w_tilde), _ptr(w_tilde), _ptr(w)))
+    return w
+
+
+def rs_sampling_weights(ctx, beta):
+    W = ctx._empty(beta.shape[0], dtype=torch.int32)
+    _check(lib().rs_sampling_weights(ctx.h, _ptr(beta), _ctdt(beta), beta.shape[0], _ptr(W)))
+    return W
+
+
+def rs_sampling_table(ctx, W):
+    cum = ctx._empty(W.shape[0], dtype=torch.int64)
+    _check(lib().rs_sampling_table(ctx.h, _ptr(W), W.shape[0], _ptr(cum)))
+    return cum
+
+
+def rs_index_stream(ctx, W, cum, N, seed, epoch, m, t0=0, sampling=RS_SAMPLE_IMPORTANCE, dtype=torch.float32):
+    idx = ctx._empty(m, dtype=torch.int32)
+    inq = ctx._empty(m, dtype=dtype)
+    _check(lib().rs_index_stream(ctx.h, _ptr(W), _ptr(cum), N, seed, epoch, t0, m, sampling, _DT[dtype], _ptr(idx),
+                                 _ptr(inq)))
+    return idx, inq
+
+
+def rs_full_gradient(ctx, Z, y, n, lam, w):
+    mu = ctx._empty(Z.shape[1], dtype=w.dtype)
+    M = matrix(Z)
+    _check(lib().rs_full_gradient(ctx.h, ctypes.byref(M), _ptr(y), n, lam, _ptr(w), _ptr(mu)))
+    return mu
+
+
+def rs_svrg_epoch(ctx, Z, n, lam, idx, inv_nq, eta, w_bar, mu, average=True):
+    out = torch.empty_like(w_bar)
+    M = matrix(Z)
+    _check(lib().rs_svrg_epoch(ctx.h, ctypes.byref(M), n, lam, _ptr(idx), _ptr(inv_nq), idx.shape[0], eta,
+                               _ptr(w_bar), _ptr(mu), 1 if average else 0, _ptr(out)))
+    return out
+
+
+def _svrg_params(lam, epochs, seed, eta=0.0, eta_mult=0.0, m=0, epoch0=0, sampling=RS_SAMPLE_IMPORTANCE, average=True):
+    return SvrgParams(lam, eta, eta_mult, m, epochs, epoch0, sampling, 1 if average else 0, seed)
+
+
+def _history(ctx, epochs, d, dtype, snapshots):
+    mu2 = (ctypes.c_double * max(1, epochs))()
+    ems = (ctypes.c_float * max(1, epochs))()
+    snaps = ctx._empty(max(1, epochs), d, dtype=dtype) if snapshots else None
+    h = History(epochs, 0, None if snaps is None else snaps.data_ptr(),
+                ctypes.cast(mu2, ctypes.POINTER(ctypes.c_double)), ctypes.cast(ems, ctypes.POINTER(ctypes.c_float)))
+    return h, mu2, ems, snaps
+
+
+def rs_svrg_solve(ctx, Z, y, V, sigma2, lam, epochs, seed, beta=None, w0=None, eta=0.0, eta_mult=0.0, m=0,
+                  epoch0=0, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False):
+    d = Z.shape[1]
+    w = ctx._empty(d, dtype=V.dtype)
+    p = _svrg_params(lam, epochs, seed, eta, eta_mult, m, epoch0, sampling, average)
+    h, mu2, ems, snaps = _history(ctx, epochs, d, V.dtype, snapshots)
+    eu, mu_ = ctypes.c_double(0), ctypes.c_int64(0)
+    M = matrix(Z)
+    _check(lib().rs_svrg_solve(ctx.h, ctypes.byref(M), _ptr(y), _ptr(beta), _ptr(V.contiguous()), _ptr(sigma2),
+                               V.shape[1], ctypes.byref(p), _ptr(w0), _ptr(w), ctypes.byref(h), ctypes.byref(eu),
+                               ctypes.byref(mu_)))
+    info = {"eta": eu.value, "m": mu_.value, "mu_norm2": list(mu2)[:epochs], "epoch_ms": list(ems)[:epochs],
+            "snapshots": snaps[:epochs] if snaps is not None else None}
+    return w, info
+
+
+def rs_solve(ctx, X, y, k, lam, epochs, sketch_seed, svrg_seed, kind="gaussian", s=0, q=1, eta=0.0, eta_mult=0.0,
+             m=0, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False, w_out=None):
+    """Alg. 3 end to end.  X / y may be CUDA tensors or (pinned) CPU tensors; w_out likewise."""
+    d = X.shape[1]
+    ct = torch.float64 if X.dtype == torch.float64 else torch.float32
+    if w_out is None:
+        w_out = ctx._empty(d, dtype=ct) if X.is_cuda else torch.empty(d, dtype=ct)
+    M = Matrix(X.data_ptr(), None, X.shape[0], d, X.stride(0), _DT[X.dtype], 0)
+    sp = _sketch_params(k, sketch_seed, kind, s, q)
+    p = _svrg_params(lam, epochs, svrg_seed, eta, eta_mult, m, 0, sampling, average)
+    h, mu2, ems, snaps = _history(ctx, epochs, d, ct, snapshots)
+    _check(lib().rs_solve(ctx.h, ctypes.byref(M), _ptr(y), ctypes.byref(sp), ctypes.byref(p), _ptr(w_out),
+                          ctypes.byref(h)))
+    info = {"mu_norm2": list(mu2)[:epochs], "epoch_ms": list(ems)[:epochs],
+            "snapshots": snaps[:epochs] if snaps is not None else None}
+    return w_out, info
+
+
+def rs_objective(ctx, X, y, lam, w, w_ref=None):
+    out = (ctypes.c_double * 2)()
+    M = matrix(X)
+    _check(lib().rs_objective(ctx.h, ctypes.byref(M), _ptr(y), lam, _ptr(w), _ptr(w_ref),
+                              ctypes.cast(out, ctypes.POINTER(ctypes.c_double))))
+    return out[0], out[1]

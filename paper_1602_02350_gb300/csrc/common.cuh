@@ -1,0 +1,176 @@
+// Internal definitions shared by the library's translation units (never by the oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/rs.h"
+
+// ------------------------------------------------------------------ context
+
+struct ScratchSlot {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+enum ScratchId {
+  SCR_OMEGA = 0, SCR_SX, SCR_Y, SCR_Q, SCR_GRAM, SCR_B, SCR_PART, SCR_PART2,
+  SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
+  SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
+  SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_COUNT
+};
+
+struct rs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int64_t launches = 0;
+  ScratchSlot slots[SCR_COUNT];
+  int* d_status = nullptr;     // device status word (bit flags, see STATUS_*)
+};
+
+enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
+
+// thread-local error message
+void rs_set_error(const char* fmt, ...);
+int rs_fail(int code, const char* fmt, ...);
+void* rs_scratch(rs_ctx* ctx, int slot, size_t bytes);   // nullptr on failure (error set)
+
+#define RS_CUDA_TRY(expr)                                                              \
+  do {                                                                                 \
+    cudaError_t _e = (expr);                                                           \
+    if (_e != cudaSuccess)                                                             \
+      return rs_fail(RS_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+  } while (0)
+
+#define RS_TRY(expr)                \
+  do {                              \
+    int _s = (expr);                \
+    if (_s != RS_OK) return _s;     \
+  } while (0)
+
+#define RS_LAUNCH_CHECK(ctx)                                                           \
+  do {                                                                                 \
+    (ctx)->launches++;                                                                 \
+    cudaError_t _e = cudaGetLastError();                                               \
+    if (_e != cudaSuccess)                                                             \
+      return rs_fail(RS_ECUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(_e), __FILE__, __LINE__); \
+  } while (0)
+
+#define RS_CHECK_ARG(cond, ...)                          \
+  do {                                                   \
+    if (!(cond)) return rs_fail(RS_EINVAL, __VA_ARGS__); \
+  } while (0)
+
+// Ensure the ctx's device is current for this host thread.
+int rs_enter(rs_ctx* ctx);
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline size_t dtype_size(int dt) {
+  switch (dt) {
+    case RS_F64: return 8;
+    case RS_F32: return 4;
+    case RS_BF16: return 2;
+    case RS_FP8E4M3: return 1;
+  }
+  return 0;
+}
+
+int check_matrix(const rs_matrix* X, const char* name);
+
+inline int grid_cap(const rs_ctx* ctx, int per_sm) { return ctx->num_sms * per_sm; }
+
+// ---------------------------------------------------------- Philox4x32-10
+
+struct U32x4 {
+  uint32_t x, y, z, w;
+};
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ U32x4 philox4x32_10(U32x4 c, uint64_t seed) {
+  uint32_t k0 = static_cast<uint32_t>(seed);
+  uint32_t k1 = static_cast<uint32_t>(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = U32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+enum { TAG_GAUSS = 1, TAG_COUNTSKETCH = 2, TAG_SAMPLE = 3 };
+
+// uniform (2*(w>>9)+1) 2^-24 on (0,1): exact in float
+__device__ __forceinline__ float u24f(uint32_t w) { return static_cast<float>(2u * (w >> 9) + 1u) * 0x1p-24f; }
+__device__ __forceinline__ double u24d(uint32_t w) { return static_cast<double>(2u * (w >> 9) + 1u) * 0x1p-24; }
+
+__device__ __forceinline__ void box_muller(float ua, float ub, float& z0, float& z1) {
+  const float rho = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  z0 = rho * c;
+  z1 = rho * s;
+}
+__device__ __forceinline__ void box_muller(double ua, double ub, double& z0, double& z1) {
+  const double rho = sqrt(-2.0 * log(ua));
+  double s, c;
+  sincospi(2.0 * ub, &s, &c);
+  z0 = rho * c;
+  z1 = rho * s;
+}
+
+// ----------------------------------------------------------- small helpers
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return static_cast<double>(v); }
+__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return static_cast<double>(__bfloat162float(v)); }
+
+// element conversion without a round trip through double
+template <typename T, typename S> __device__ __forceinline__ T cvt(S v) { return static_cast<T>(v); }
+template <> __device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 v) {
+  return static_cast<double>(__bfloat162float(v));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T> struct Vec;        // 16-byte vector of T
+template <> struct Vec<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int N = 2; };
+
+__device__ __forceinline__ void vec_to_arr(const float4& v, float* a) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
+__device__ __forceinline__ void vec_to_arr(const double2& v, double* a) { a[0] = v.x; a[1] = v.y; }
+
+// Internal launch helpers implemented in dense.cu, used by several entry points.
+template <typename T>
+int launch_gemm(rs_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t sAm,
+                int64_t sAk, const T* B, int64_t sBk, int64_t sBn, double beta, const T* C0, int64_t ldc0,
+                T* C, int64_t ldc, const T* col_scale);
+
+// Gram / transposed product with split-K over the long dimension and double accumulation:
+// G (Ma x Nb, double, row-major) = alpha * sum_r A[r][i] B[r][j], A: rows x Ma (lda), B: rows x Nb (ldb).
+template <typename TA>
+int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, int64_t lda, const TA* B,
+                int64_t ldb, double alpha, double* G);
+
+int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W);
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }

@@ -1,0 +1,849 @@
+// Dense linear algebra of the sketch (Alg. 2) and the preconditioner (Eq. (11)):
+// CUDA-core GEMM and split-K Gram kernels, Cholesky-QR, cyclic Jacobi, Rayleigh-Ritz,
+// the data transform Z = [X M; M], smoothness constants, the output map w = M w~ and
+// the double-precision objective of Eq. (1).
+#include "common.cuh"
+
+int countsketch_dispatch(rs_ctx* ctx, const rs_matrix* X, uint64_t seed, int64_t s, void* SX, int64_t ld_sx,
+                         int32_t* bucket_out, void* sign_out);
+int gaussian_dispatch(rs_ctx* ctx, uint64_t seed, int64_t row0, int64_t rows, int64_t cols, int32_t dtype, void* out,
+                      int64_t ld);
+
+namespace {
+
+// ------------------------------------------------------------------ GEMM (CUDA cores)
+// C[m][n] = alpha * col_scale[n] * sum_k A(m,k) B(k,n) + beta * C0[m][n]
+// A(m,k) = A[m*sAm + k*sAk], B(k,n) = B[k*sBk + n*sBn].  64x64 tile, 16-deep k steps, 4x4 per thread.
+template <typename T, bool A_KCONTIG, bool B_NCONTIG>
+__global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A,
+                                                   int64_t sAm, int64_t sAk, const T* __restrict__ B, int64_t sBk,
+                                                   int64_t sBn, T beta, const T* C0, int64_t ldc0, T* C, int64_t ldc,
+                                                   const T* __restrict__ col_scale) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid * 4 + q;
+      int mm, kk;
+      if (A_KCONTIG) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? A[gm * sAm + gk * sAk] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid * 4 + q;
+      int kk, nn;
+      if (B_NCONTIG) { kk = e / BN; nn = e % BN; } else { nn = e / BK; kk = e % BK; }
+      const int64_t gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gk < K && gn < N) ? B[gk * sBk + gn * sBn] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty * 4 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx * 4 + j;
+      if (gn >= N) continue;
+      T v = alpha * acc[i][j];
+      if (col_scale) v *= col_scale[gn];
+      if (C0) v = fma(beta, C0[gm * ldc0 + gn], v);
+      C[gm * ldc + gn] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ split-K Gram
+// part[chunk][i][j] = sum over rows r of the chunk of A[r][i] B[r][j]  (TACC accumulation)
+template <typename TA, typename TACC>
+__global__ void __launch_bounds__(256) gram_kernel(int64_t rows, int64_t Ma, int64_t Nb, const TA* __restrict__ A,
+                                                   int64_t lda, const TA* __restrict__ B, int64_t ldb,
+                                                   int64_t rows_per_chunk, double* part) {
+  constexpr int BT = 64, BK = 16;
+  __shared__ TACC As[BK][BT + 4];
+  __shared__ TACC Bs[BK][BT + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t i0 = (int64_t)blockIdx.y * BT, j0 = (int64_t)blockIdx.x * BT;
+  const int64_t chunk = blockIdx.z;
+  const int64_t r0 = chunk * rows_per_chunk, r1 = min(rows, r0 + rows_per_chunk);
+  TACC acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = TACC(0);
+  for (int64_t rr = r0; rr < r1; rr += BK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid * 4 + q;
+      const int kk = e / BT, ii = e % BT;
+      const int64_t r = rr + kk;
+      As[kk][ii] = (r < r1 && i0 + ii < Ma) ? cvt<TACC>(A[r * lda + i0 + ii]) : TACC(0);
+      Bs[kk][ii] = (r < r1 && j0 + ii < Nb) ? cvt<TACC>(B[r * ldb + j0 + ii]) : TACC(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TACC a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* out = part + chunk * Ma * Nb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gi = i0 + ty * 4 + i;
+    if (gi >= Ma) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gj = j0 + tx * 4 + j;
+      if (gj < Nb) out[gi * Nb + gj] = (double)acc[i][j];
+    }
+  }
+}
+
+__global__ void reduce_chunks_kernel(const double* part, int64_t nchunks, int64_t count, double alpha, double* G) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t c = 0; c < nchunks; ++c) s += part[c * count + e];
+    G[e] = alpha * s;
+  }
+}
+
+template <typename T>
+__global__ void convert_from_double_kernel(const double* in, int64_t count, T* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)in[e];
+}
+
+// ------------------------------------------------------------------ Cholesky-QR
+// In-place lower Cholesky factor of the k x k double matrix G (G = L L^T), one block.
+__global__ void chol_kernel(double* G, int k, int* status) {
+  __shared__ double djj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    if (warp == 0) {
+      double s = 0.0;
+      for (int p = lane; p < j; p += 32) s += G[j * k + p] * G[j * k + p];
+      s = warp_sum(s);
+      if (lane == 0) {
+        double v = G[j * k + j] - s;
+        if (!(v > 0.0) || !isfinite(v)) {
+          atomicOr(status, 4);
+          v = 1.0;
+        }
+        djj = sqrt(v);
+        G[j * k + j] = djj;
+      }
+    }
+    __syncthreads();
+    for (int i = j + 1 + warp; i < k; i += nw) {
+      double s = 0.0;
+      for (int p = lane; p < j; p += 32) s += G[i * k + p] * G[j * k + p];
+      s = warp_sum(s);
+      if (lane == 0) G[i * k + j] = (G[i * k + j] - s) / djj;
+    }
+    __syncthreads();
+  }
+}
+
+// Q[r] = Y[r] L^{-T} for every row r (solve q L^T = y by forward substitution); warp per row
+template <typename T>
+__global__ void trsm_rows_kernel(const T* Y, int64_t d, int k, const double* L, T* Q) {
+  extern __shared__ double qsh[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* q = qsh + (size_t)warp * k;
+  for (int64_t r = (int64_t)blockIdx.x * nw + warp; r < d; r += (int64_t)gridDim.x * nw) {
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int p = lane; p < j; p += 32) s += q[p] * L[j * k + p];
+      s = warp_sum(s);
+      if (lane == 0) q[j] = ((double)Y[r * k + j] - s) / L[j * k + j];
+      __syncwarp();
+    }
+    for (int j = lane; j < k; j += 32) Q[r * k + j] = (T)q[j];
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi eigensolver
+// Cyclic Jacobi with round-robin pairing: each round rotates k/2 disjoint (p,q) planes at once.
+// A and W point to shared memory when they fit, else to global scratch (same code).
+template <typename TW>
+__global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, int use_smem, double tol, int max_sweeps,
+                              double* evals, double* Wout) {
+  extern __shared__ unsigned char jsh[];
+  const int K = (k + 1) & ~1;   // even number of players; index k is a dummy when k is odd
+  TW* A = use_smem ? reinterpret_cast<TW*>(jsh) : Ag;
+  TW* W = use_smem ? A + (size_t)k * k : Wg;
+  __shared__ int pp[128], qq[128];
+  __shared__ TW cc[128], ss[128];
+  __shared__ double red[32];
+  __shared__ int done;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < k * k; e += nt) {
+    A[e] = (TW)G[e];
+    W[e] = (e / k == e % k) ? TW(1) : TW(0);
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < K - 1; ++r) {
+      for (int i = tid; i < K / 2; i += nt) {
+        auto pos = [&](int j) { return j == 0 ? 0 : ((j - 1 + r) % (K - 1)) + 1; };
+        int p = pos(i), q = pos(K - 1 - i);
+        if (p > q) { int t = p; p = q; q = t; }
+        TW c = TW(1), s = TW(0);
+        if (q < k) {
+          const TW apq = A[p * k + q];
+          if (apq != TW(0)) {
+            const TW app = A[p * k + p], aqq = A[q * k + q];
+            const TW theta = (aqq - app) / (TW(2) * apq);
+            const TW t = (theta >= TW(0) ? TW(1) : TW(-1)) / (fabs(theta) + sqrt(theta * theta + TW(1)));
+            c = TW(1) / sqrt(t * t + TW(1));
+            s = t * c;
+          }
+        }
+        pp[i] = p; qq[i] = q; cc[i] = c; ss[i] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < (K / 2) * k; e += nt) {
+        const int i = e / k, j = e % k;
+        const int p = pp[i], q = qq[i];
+        if (q >= k) continue;
+        const TW c = cc[i], s = ss[i];
+        const TW ap = A[p * k + j], aq = A[q * k + j];
+        A[p * k + j] = c * ap - s * aq;
+        A[q * k + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, W <- W J
+      for (int e = tid; e < (K / 2) * k; e += nt) {
+        const int i = e / k, j = e % k;
+        const int p = pp[i], q = qq[i];
+        if (q >= k) continue;
+        const TW c = cc[i], s = ss[i];
+        const TW ap = A[j * k + p], aq = A[j * k + q];
+        A[j * k + p] = c * ap - s * aq;
+        A[j * k + q] = s * ap + c * aq;
+        const TW wp = W[j * k + p], wq = W[j * k + q];
+        W[j * k + p] = c * wp - s * wq;
+        W[j * k + q] = s * wp + c * wq;
+      }
+      __syncthreads();
+    }
+    // convergence: off-diagonal mass relative to the diagonal
+    double off = 0.0, dia = 0.0;
+    for (int e = tid; e < k * k; e += nt) {
+      const double v = (double)A[e];
+      if (e / k == e % k) dia += v * v;
+      else off += v * v;
+    }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if ((tid & 31) == 0) { red[tid >> 5] = off; }
+    __syncthreads();
+    if (tid == 0) {
+      double o = 0.0;
+      for (int w = 0; w < nt / 32; ++w) o += red[w];
+      red[31] = o;
+    }
+    __syncthreads();
+    const double offsum = red[31];
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = dia;
+    __syncthreads();
+    if (tid == 0) {
+      double dd = 0.0;
+      for (int w = 0; w < nt / 32; ++w) dd += red[w];
+      done = !(offsum > tol * tol * dd);
+    }
+    __syncthreads();
+    if (done) break;
+    __syncthreads();
+  }
+  // sort descending (stable in index) and write out
+  for (int i = tid; i < k; i += nt) {
+    const TW ev = A[i * k + i];
+    int rank = 0;
+    for (int j = 0; j < k; ++j) {
+      const TW ej = A[j * k + j];
+      rank += (ej > ev) || (ej == ev && j < i);
+    }
+    evals[rank] = (double)ev;
+    for (int r = 0; r < k; ++r) Wout[r * k + rank] = (double)W[r * k + i];
+  }
+}
+
+// ------------------------------------------------------------------ preconditioner pieces
+template <typename T>
+__global__ void adiag_kernel(const double* sigma2, int k, double lam, T* a) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) a[j] = (T)(1.0 - sqrt((sigma2[k - 1] + lam) / (sigma2[j] + lam)));
+}
+
+template <typename T>
+__global__ void scale_cols_kernel(const T* V, int64_t d, int k, const T* a, T* Va) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d * k; e += (int64_t)gridDim.x * blockDim.x)
+    Va[e] = V[e] * a[e % k];
+}
+
+template <typename T>
+__global__ void identity_rows_kernel(T* Z, int64_t d, int64_t ld) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d * d; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / d, c = e % d;
+    Z[r * ld + c] = (r == c) ? T(1) : T(0);
+  }
+}
+
+// beta_i = gamma_i ||z_i||^2; warp per row; per-block partial sums of beta for beta_hat
+template <typename T>
+__global__ void row_beta_kernel(const T* Z, int64_t N, int64_t n, int64_t d, int64_t ld, double lam, T* beta,
+                                double* part) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double acc_blk = 0.0;
+  const double gd = (double)N / (double)n, gr = lam * (double)N;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
+    T s = T(0);
+    for (int64_t c = lane; c < d; c += 32) {
+      const T v = Z[i * ld + c];
+      s = fma(v, v, s);
+    }
+    s = warp_sum(s);
+    const double b = (i < n ? gd : gr) * (double)s;
+    if (lane == 0) {
+      beta[i] = (T)b;
+      acc_blk += b;
+    }
+  }
+  if (lane == 0) sh[warp] = acc_blk;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_parts_kernel(const double* part, int np, double scale, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int p = 0; p < np; ++p) s += part[p];
+    *out = s * scale;
+  }
+}
+
+// w[c] = wt[c] - sum_j V[c][j] a_j t_j with t = V^T wt (double)
+template <typename T>
+__global__ void map_output_kernel(const T* V, int64_t d, int k, const T* a, const double* t, const T* wt, T* w) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += (double)V[c * k + j] * (double)a[j] * t[j];
+    w[c] = (T)((double)wt[c] - s);
+  }
+}
+
+// ------------------------------------------------------------------ objective (double)
+template <typename TS, typename T>
+__global__ void objective_kernel(const TS* X, int64_t n, int64_t d, int64_t ld, const T* y, const T* w, const T* wr,
+                                 double* part) {
+  __shared__ double sh[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double r2 = 0.0, e2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw) {
+    double sw = 0.0, se = 0.0;
+    for (int64_t c = lane; c < d; c += 32) {
+      const double x = cvt<double>(X[i * ld + c]);
+      const double wc = (double)w[c];
+      sw = fma(x, wc, sw);
+      if (wr) se = fma(x, wc - (double)wr[c], se);
+    }
+    sw = warp_sum(sw);
+    se = warp_sum(se);
+    const double r = sw - (double)y[i];
+    r2 = fma(r, r, r2);
+    e2 = fma(se, se, e2);
+  }
+  if (lane == 0) { sh[0][warp] = r2; sh[1][warp] = e2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) { a += sh[0][w2]; b += sh[1][w2]; }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+template <typename T>
+__global__ void objective_finish_kernel(const double* part, int np, int64_t n, int64_t d, double lam, const T* w,
+                                        const T* wr, double* out) {
+  __shared__ double sh[2][32];
+  double ww = 0.0, ee = 0.0;
+  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
+    const double wc = (double)w[c];
+    ww = fma(wc, wc, ww);
+    if (wr) {
+      const double e = wc - (double)wr[c];
+      ee = fma(e, e, ee);
+    }
+  }
+  ww = warp_sum(ww);
+  ee = warp_sum(ee);
+  if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = ww; sh[1][threadIdx.x >> 5] = ee; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, r2 = 0.0, e2 = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { a += sh[0][w2]; b += sh[1][w2]; }
+    for (int p = 0; p < np; ++p) { r2 += part[2 * p]; e2 += part[2 * p + 1]; }
+    out[0] = 0.5 * r2 / (double)n + 0.5 * lam * a;
+    out[1] = wr ? 0.5 * e2 / (double)n + 0.5 * lam * b : 0.0;
+  }
+}
+
+int blocks_for(rs_ctx* ctx, int64_t work, int threads = 256) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)ctx->num_sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+// ====================================================================== launchers
+
+template <typename T>
+int launch_gemm(rs_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t sAm, int64_t sAk,
+                const T* B, int64_t sBk, int64_t sBn, double beta, const T* C0, int64_t ldc0, T* C, int64_t ldc,
+                const T* col_scale) {
+  if (M <= 0 || N <= 0) return RS_OK;
+  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+  if (grid.y > 65535) return rs_fail(RS_EINVAL, "gemm: M = %lld too large", (long long)M);
+  const bool ak = (sAk == 1), bn = (sBn == 1);
+  if (ak && bn)
+    gemm_kernel<T, true, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+                                                              C0, ldc0, C, ldc, col_scale);
+  else if (ak)
+    gemm_kernel<T, true, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+                                                               C0, ldc0, C, ldc, col_scale);
+  else if (bn)
+    gemm_kernel<T, false, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+                                                               C0, ldc0, C, ldc, col_scale);
+  else
+    gemm_kernel<T, false, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn,
+                                                                (T)beta, C0, ldc0, C, ldc, col_scale);
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+template int launch_gemm<float>(rs_ctx*, int64_t, int64_t, int64_t, double, const float*, int64_t, int64_t,
+                                const float*, int64_t, int64_t, double, const float*, int64_t, float*, int64_t,
+                                const float*);
+template int launch_gemm<double>(rs_ctx*, int64_t, int64_t, int64_t, double, const double*, int64_t, int64_t,
+                                 const double*, int64_t, int64_t, double, const double*, int64_t, double*, int64_t,
+                                 const double*);
+
+template <typename TA>
+int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, int64_t lda, const TA* B, int64_t ldb,
+                double alpha, double* G) {
+  using TACC = typename std::conditional<sizeof(TA) == 8, double, float>::type;
+  const int64_t tiles = ((Ma + 63) / 64) * ((Nb + 63) / 64);
+  // enough row chunks to fill the GPU; at most 512 rows per chunk in float
+  int64_t target = std::max<int64_t>(1, (int64_t)ctx->num_sms * 4 / tiles);
+  int64_t rpc = std::max<int64_t>(64, (rows + target - 1) / target);
+  if (sizeof(TACC) == 4) rpc = std::min<int64_t>(rpc, 512);
+  rpc = (rpc + 15) / 16 * 16;
+  const int64_t nchunks = (rows + rpc - 1) / rpc;
+  double* part = static_cast<double*>(rs_scratch(ctx, SCR_PART, nchunks * Ma * Nb * sizeof(double)));
+  if (!part) return RS_ENOMEM;
+  if (nchunks > 65535) return rs_fail(RS_EINVAL, "gram: too many row chunks");
+  dim3 grid((unsigned)((Nb + 63) / 64), (unsigned)((Ma + 63) / 64), (unsigned)nchunks);
+  gram_kernel<TA, TACC><<<grid, 256, 0, ctx->stream>>>(rows, Ma, Nb, A, lda, B, ldb, rpc, part);
+  RS_LAUNCH_CHECK(ctx);
+  reduce_chunks_kernel<<<blocks_for(ctx, Ma * Nb), 256, 0, ctx->stream>>>(part, nchunks, Ma * Nb, alpha, G);
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+template int launch_gram<float>(rs_ctx*, int64_t, int64_t, int64_t, const float*, int64_t, const float*, int64_t,
+                                double, double*);
+template int launch_gram<double>(rs_ctx*, int64_t, int64_t, int64_t, const double*, int64_t, const double*, int64_t,
+                                 double, double*);
+
+template <typename T>
+static int to_T(rs_ctx* ctx, const double* in, int64_t count, T* out) {
+  convert_from_double_kernel<T><<<blocks_for(ctx, count), 256, 0, ctx->stream>>>(in, count, out);
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W) {
+  if (k < 1 || k > 256) return rs_fail(RS_EINVAL, "sym_eig: k = %lld outside [1, 256]", (long long)k);
+  const size_t es = prec == RS_F64 ? 8 : 4;
+  const size_t bytes = 2 * (size_t)k * k * es;
+  const bool smem = bytes <= 200 * 1024;
+  void* g = nullptr;
+  if (!smem) {
+    g = rs_scratch(ctx, SCR_EIG, bytes);
+    if (!g) return RS_ENOMEM;
+  }
+  const int threads = 1024;
+  const size_t shm = smem ? bytes : 0;
+  if (prec == RS_F64) {
+    RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    double* Ag = static_cast<double*>(g);
+    jacobi_kernel<double><<<1, threads, shm, ctx->stream>>>(G, (int)k, Ag, Ag ? Ag + k * k : nullptr, smem ? 1 : 0,
+                                                            1e-15, 40, evals, W);
+  } else {
+    RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    float* Ag = static_cast<float*>(g);
+    jacobi_kernel<float><<<1, threads, shm, ctx->stream>>>(G, (int)k, Ag, Ag ? Ag + k * k : nullptr, smem ? 1 : 0,
+                                                           1e-7, 40, evals, W);
+  }
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+// ---------------------------------------------------------------------- Alg. 2 pieces
+
+template <typename T>
+static int orthonormalize_t(rs_ctx* ctx, const T* Y, int64_t d, int64_t k, T* Q) {
+  double* G = static_cast<double*>(rs_scratch(ctx, SCR_GRAM, k * k * sizeof(double)));
+  T* tmp = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, d * k * sizeof(T)));
+  if (!G || !tmp) return RS_ENOMEM;
+  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  const int warps = 8;
+  const size_t shm = warps * k * sizeof(double);
+  const T* src = Y;
+  for (int pass = 0; pass < 2; ++pass) {
+    T* dst = pass == 0 ? tmp : Q;
+    RS_TRY(launch_gram<T>(ctx, d, k, k, src, k, src, k, 1.0, G));
+    chol_kernel<<<1, 1024, 0, ctx->stream>>>(G, (int)k, ctx->d_status);
+    RS_LAUNCH_CHECK(ctx);
+    const int blocks = (int)std::min<int64_t>((d + warps - 1) / warps, (int64_t)ctx->num_sms * 4);
+    trsm_rows_kernel<T><<<blocks, 32 * warps, shm, ctx->stream>>>(src, d, (int)k, G, dst);
+    RS_LAUNCH_CHECK(ctx);
+    src = dst;
+  }
+  return RS_OK;
+}
+
+static int read_status(rs_ctx* ctx, int* st) {
+  RS_CUDA_TRY(cudaMemcpyAsync(st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return RS_OK;
+}
+
+template <typename T>
+static int range_sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, T* Y) {
+  const int64_t n = X->n, d = X->d, k = p->k;
+  const int32_t dt = sizeof(T) == 8 ? RS_F64 : RS_F32;
+  double* Gd = static_cast<double*>(rs_scratch(ctx, SCR_GRAM, d * k * sizeof(double)));
+  if (!Gd) return RS_ENOMEM;
+  if (p->kind == RS_SKETCH_GAUSSIAN) {
+    T* Om = static_cast<T*>(rs_scratch(ctx, SCR_OMEGA, n * k * sizeof(T)));
+    if (!Om) return RS_ENOMEM;
+    RS_TRY(gaussian_dispatch(ctx, p->seed, 0, n, k, dt, Om, k));
+    RS_TRY(launch_gram<T>(ctx, n, d, k, static_cast<const T*>(X->data), X->ld, Om, k, 1.0, Gd));
+  } else {
+    const int64_t s = p->s > 0 ? p->s : std::min<int64_t>(n, 64 * k);
+    T* SX = static_cast<T*>(rs_scratch(ctx, SCR_SX, s * d * sizeof(T)));
+    T* Gp = static_cast<T*>(rs_scratch(ctx, SCR_OMEGA, s * k * sizeof(T)));
+    if (!SX || !Gp) return RS_ENOMEM;
+    RS_TRY(countsketch_dispatch(ctx, X, p->seed, s, SX, d, nullptr, nullptr));
+    RS_TRY(gaussian_dispatch(ctx, p->seed, 0, s, k, dt, Gp, k));
+    RS_TRY(launch_gram<T>(ctx, s, d, k, SX, d, Gp, k, 1.0, Gd));
+  }
+  return to_T<T>(ctx, Gd, d * k, Y);
+}
+
+template <typename T>
+static int ritz_t(rs_ctx* ctx, const rs_matrix* X, const T* Q, int64_t kq, int64_t k, T* V, double* sigma2) {
+  const int64_t n = X->n, d = X->d;
+  T* B = static_cast<T*>(rs_scratch(ctx, SCR_B, n * kq * sizeof(T)));
+  double* G = static_cast<double*>(rs_scratch(ctx, SCR_GRAM, kq * kq * sizeof(double)));
+  double* ev = static_cast<double*>(rs_scratch(ctx, SCR_S2, kq * sizeof(double)));
+  double* Wd = static_cast<double*>(rs_scratch(ctx, SCR_W, kq * kq * sizeof(double)));
+  T* Wt = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, kq * kq * sizeof(T)));
+  if (!B || !G || !ev || !Wd || !Wt) return RS_ENOMEM;
+  // B = X Q (n x kq), G = B^T B / n
+  RS_TRY(launch_gemm<T>(ctx, n, kq, d, 1.0, static_cast<const T*>(X->data), X->ld, 1, Q, kq, 1, 0.0, nullptr, 0, B,
+                        kq, nullptr));
+  RS_TRY(launch_gram<T>(ctx, n, kq, kq, B, kq, B, kq, 1.0 / (double)n, G));
+  RS_TRY(run_sym_eig(ctx, G, kq, sizeof(T) == 8 ? RS_F64 : RS_F32, ev, Wd));
+  RS_TRY(to_T<T>(ctx, Wd, kq * kq, Wt));
+  // V = Q W[:, :k]
+  RS_TRY(launch_gemm<T>(ctx, d, k, kq, 1.0, Q, kq, 1, Wt, kq, 1, 0.0, nullptr, 0, V, k, nullptr));
+  RS_CUDA_TRY(cudaMemcpyAsync(sigma2, ev, k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  return RS_OK;
+}
+
+template <typename T>
+static int sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, T* V, double* sigma2) {
+  const int64_t n = X->n, d = X->d, k = p->k;
+  const int64_t q = std::max(1, p->q_blocks);
+  const int64_t kq = k * q;
+  if (kq > std::min<int64_t>(d, 256)) return rs_fail(RS_EINVAL, "rs_sketch: k * q_blocks = %lld exceeds min(d, 256)", (long long)kq);
+  T* K = static_cast<T*>(rs_scratch(ctx, SCR_Y, d * kq * sizeof(T)));
+  T* Qm = static_cast<T*>(rs_scratch(ctx, SCR_Q, d * kq * sizeof(T)));
+  if (!K || !Qm) return RS_ENOMEM;
+  RS_TRY(range_sketch_t<T>(ctx, X, p, Qm));   // Y0 (d x k) into Qm, then spread into K's columns
+  // K[:, 0:k] = Y0; K[:, jk:(j+1)k] = C K[:, (j-1)k:jk] = X^T (X Y_{j-1}) / n
+  RS_CUDA_TRY(cudaMemcpy2DAsync(K, kq * sizeof(T), Qm, k * sizeof(T), k * sizeof(T), d, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+  if (q > 1) {
+    T* B = static_cast<T*>(rs_scratch(ctx, SCR_B, n * k * sizeof(T)));
+    double* Gd = static_cast<double*>(rs_scratch(ctx, SCR_GRAM, d * k * sizeof(double)));
+    T* Yt = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, d * k * sizeof(T)));
+    if (!B || !Gd || !Yt) return RS_ENOMEM;
+    for (int64_t j = 1; j < q; ++j) {
+      RS_TRY(launch_gemm<T>(ctx, n, k, d, 1.0, static_cast<const T*>(X->data), X->ld, 1, K + (j - 1) * k, kq, 1, 0.0,
+                            nullptr, 0, B, k, nullptr));
+      RS_TRY(launch_gram<T>(ctx, n, d, k, static_cast<const T*>(X->data), X->ld, B, k, 1.0 / (double)n, Gd));
+      RS_TRY(to_T<T>(ctx, Gd, d * k, Yt));
+      RS_CUDA_TRY(cudaMemcpy2DAsync(K + j * k, kq * sizeof(T), Yt, k * sizeof(T), k * sizeof(T), d,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+  }
+  RS_TRY(orthonormalize_t<T>(ctx, K, d, kq, Qm));
+  RS_TRY(ritz_t<T>(ctx, X, Qm, kq, k, V, sigma2));
+  int st = 0;
+  RS_TRY(read_status(ctx, &st));
+  if (st & 4) return rs_fail(RS_EINVAL, "rs_sketch: the sketch is rank deficient to working precision");
+  return RS_OK;
+}
+
+// ---------------------------------------------------------------------- preconditioner
+
+template <typename T>
+static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const double* sigma2, int64_t k, double lam,
+                          rs_matrix* Xt, T* beta, double* beta_hat) {
+  const int64_t n = X->n, d = X->d, N = n + d;
+  T* Z = static_cast<T*>(const_cast<void*>(Xt->data));
+  const int64_t ldz = Xt->ld;
+  T* a = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, k * sizeof(T)));
+  T* P = static_cast<T*>(rs_scratch(ctx, SCR_P, n * k * sizeof(T)));
+  T* Va = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, d * k * sizeof(T)));
+  if (!a || !P || !Va) return RS_ENOMEM;
+  adiag_kernel<T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(sigma2, (int)k, lam, a);
+  RS_LAUNCH_CHECK(ctx);
+  const T* Xd = static_cast<const T*>(X->data);
+  // P = X V diag(a);  Z[0:n] = X - P V^T
+  RS_TRY(launch_gemm<T>(ctx, n, k, d, 1.0, Xd, X->ld, 1, V, k, 1, 0.0, nullptr, 0, P, k, a));
+  RS_TRY(launch_gemm<T>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
+  // Z[n:n+d] = I - V diag(a) V^T   (the rows b_j = M e_j)
+  scale_cols_kernel<T><<<blocks_for(ctx, d * k), 256, 0, ctx->stream>>>(V, d, (int)k, a, Va);
+  RS_LAUNCH_CHECK(ctx);
+  T* Zb = Z + n * ldz;
+  identity_rows_kernel<T><<<blocks_for(ctx, d * d), 256, 0, ctx->stream>>>(Zb, d, ldz);
+  RS_LAUNCH_CHECK(ctx);
+  RS_TRY(launch_gemm<T>(ctx, d, d, k, -1.0, Va, k, 1, V, 1, k, 1.0, Zb, ldz, Zb, ldz, nullptr));
+  // smoothness constants
+  const int blocks = blocks_for(ctx, N * 32);
+  double* part = static_cast<double*>(rs_scratch(ctx, SCR_MISC, (blocks + 1) * sizeof(double)));
+  if (!part) return RS_ENOMEM;
+  row_beta_kernel<T><<<blocks, 256, 0, ctx->stream>>>(Z, N, n, d, ldz, lam, beta, part);
+  RS_LAUNCH_CHECK(ctx);
+  if (beta_hat) {
+    sum_parts_kernel<<<1, 32, 0, ctx->stream>>>(part, blocks, 1.0 / (double)N, part + blocks);
+    RS_LAUNCH_CHECK(ctx);
+    RS_CUDA_TRY(cudaMemcpyAsync(beta_hat, part + blocks, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  return RS_OK;
+}
+
+template <typename T>
+static int map_output_t(rs_ctx* ctx, const T* V, const double* sigma2, int64_t d, int64_t k, double lam, const T* wt,
+                        T* w) {
+  T* a = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, k * sizeof(T)));
+  double* tv = static_cast<double*>(rs_scratch(ctx, SCR_RED, k * sizeof(double)));
+  if (!a || !tv) return RS_ENOMEM;
+  adiag_kernel<T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(sigma2, (int)k, lam, a);
+  RS_LAUNCH_CHECK(ctx);
+  RS_TRY(launch_gram<T>(ctx, d, k, 1, V, k, wt, 1, 1.0, tv));
+  map_output_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(V, d, (int)k, a, tv, wt, w);
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+int map_output_dispatch(rs_ctx* ctx, const void* V, const double* sigma2, int64_t d, int64_t k, double lam,
+                        int32_t dtype, const void* wt, void* w) {
+  if (dtype == RS_F64)
+    return map_output_t<double>(ctx, static_cast<const double*>(V), sigma2, d, k, lam,
+                                static_cast<const double*>(wt), static_cast<double*>(w));
+  return map_output_t<float>(ctx, static_cast<const float*>(V), sigma2, d, k, lam, static_cast<const float*>(wt),
+                             static_cast<float*>(w));
+}
+
+int sketch_dispatch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* V, double* sigma2) {
+  if (X->dtype == RS_F64) return sketch_t<double>(ctx, X, p, static_cast<double*>(V), sigma2);
+  if (X->dtype == RS_F32) return sketch_t<float>(ctx, X, p, static_cast<float*>(V), sigma2);
+  return rs_fail(RS_EUNSUPPORTED, "rs_sketch: dtype %d not supported by this build", X->dtype);
+}
+
+int precondition_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k, double lam,
+                          rs_matrix* Xt, void* beta, double* beta_hat) {
+  if (X->dtype == RS_F64)
+    return precondition_t<double>(ctx, X, static_cast<const double*>(V), sigma2, k, lam, Xt,
+                                  static_cast<double*>(beta), beta_hat);
+  if (X->dtype == RS_F32)
+    return precondition_t<float>(ctx, X, static_cast<const float*>(V), sigma2, k, lam, Xt, static_cast<float*>(beta),
+                                 beta_hat);
+  return rs_fail(RS_EUNSUPPORTED, "rs_precondition: dtype %d not supported by this build", X->dtype);
+}
+
+int objective_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* y, double lam, const void* w, const void* wr,
+                       double* out) {
+  const int64_t n = X->n, d = X->d;
+  const int blocks = blocks_for(ctx, n * 32);
+  double* part = static_cast<double*>(rs_scratch(ctx, SCR_MISC, (2 * blocks + 2) * sizeof(double)));
+  if (!part) return RS_ENOMEM;
+  double* res = part + 2 * blocks;
+  if (X->dtype == RS_F64) {
+    objective_kernel<double, double><<<blocks, 256, 0, ctx->stream>>>(
+        static_cast<const double*>(X->data), n, d, X->ld, static_cast<const double*>(y),
+        static_cast<const double*>(w), static_cast<const double*>(wr), part);
+    RS_LAUNCH_CHECK(ctx);
+    objective_finish_kernel<double><<<1, 256, 0, ctx->stream>>>(part, blocks, n, d, lam, static_cast<const double*>(w),
+                                                                static_cast<const double*>(wr), res);
+  } else if (X->dtype == RS_F32) {
+    objective_kernel<float, float><<<blocks, 256, 0, ctx->stream>>>(
+        static_cast<const float*>(X->data), n, d, X->ld, static_cast<const float*>(y), static_cast<const float*>(w),
+        static_cast<const float*>(wr), part);
+    RS_LAUNCH_CHECK(ctx);
+    objective_finish_kernel<float><<<1, 256, 0, ctx->stream>>>(part, blocks, n, d, lam, static_cast<const float*>(w),
+                                                               static_cast<const float*>(wr), res);
+  } else if (X->dtype == RS_BF16) {
+    objective_kernel<__nv_bfloat16, float><<<blocks, 256, 0, ctx->stream>>>(
+        static_cast<const __nv_bfloat16*>(X->data), n, d, X->ld, static_cast<const float*>(y),
+        static_cast<const float*>(w), static_cast<const float*>(wr), part);
+    RS_LAUNCH_CHECK(ctx);
+    objective_finish_kernel<float><<<1, 256, 0, ctx->stream>>>(part, blocks, n, d, lam, static_cast<const float*>(w),
+                                                               static_cast<const float*>(wr), res);
+  } else {
+    return rs_fail(RS_EUNSUPPORTED, "rs_objective: dtype %d", X->dtype);
+  }
+  RS_LAUNCH_CHECK(ctx);
+  RS_CUDA_TRY(cudaMemcpyAsync(out, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return RS_OK;
+}
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int rs_range_sketch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* Y) {
+  RS_TRY(rs_enter(ctx));
+  RS_TRY(check_matrix(X, "rs_range_sketch X"));
+  RS_CHECK_ARG(p && Y, "rs_range_sketch: null argument");
+  RS_CHECK_ARG(p->k >= 1 && p->k <= X->d && p->k <= 256, "rs_range_sketch: k must be in [1, min(d, 256)]");
+  RS_CHECK_ARG(p->kind == RS_SKETCH_GAUSSIAN || p->kind == RS_SKETCH_COUNTSKETCH, "rs_range_sketch: bad kind");
+  if (X->dtype == RS_F64) return range_sketch_t<double>(ctx, X, p, static_cast<double*>(Y));
+  if (X->dtype == RS_F32) return range_sketch_t<float>(ctx, X, p, static_cast<float*>(Y));
+  return rs_fail(RS_EUNSUPPORTED, "rs_range_sketch: dtype %d", X->dtype);
+}
+
+int rs_orthonormalize(rs_ctx* ctx, const void* Y, int64_t d, int64_t k, int32_t dtype, void* Q) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(Y && Q && d >= 1 && k >= 1 && k <= d && k <= 256, "rs_orthonormalize: bad arguments");
+  int rc;
+  if (dtype == RS_F64) rc = orthonormalize_t<double>(ctx, static_cast<const double*>(Y), d, k, static_cast<double*>(Q));
+  else if (dtype == RS_F32) rc = orthonormalize_t<float>(ctx, static_cast<const float*>(Y), d, k, static_cast<float*>(Q));
+  else return rs_fail(RS_EUNSUPPORTED, "rs_orthonormalize: dtype %d", dtype);
+  if (rc != RS_OK) return rc;
+  int st = 0;
+  RS_TRY(read_status(ctx, &st));
+  if (st & 4) return rs_fail(RS_EINVAL, "rs_orthonormalize: Y is rank deficient to working precision");
+  return RS_OK;
+}
+
+int rs_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(G && evals && W, "rs_sym_eig: null argument");
+  RS_CHECK_ARG(prec == RS_F64 || prec == RS_F32, "rs_sym_eig: prec must be RS_F64 or RS_F32");
+  return run_sym_eig(ctx, G, k, prec, evals, W);
+}
+
+int rs_ritz(rs_ctx* ctx, const rs_matrix* X, const void* Q, int64_t k, void* V, double* sigma2) {
+  RS_TRY(rs_enter(ctx));
+  RS_TRY(check_matrix(X, "rs_ritz X"));
+  RS_CHECK_ARG(Q && V && sigma2 && k >= 1 && k <= X->d && k <= 256, "rs_ritz: bad arguments");
+  if (X->dtype == RS_F64)
+    return ritz_t<double>(ctx, X, static_cast<const double*>(Q), k, k, static_cast<double*>(V), sigma2);
+  if (X->dtype == RS_F32)
+    return ritz_t<float>(ctx, X, static_cast<const float*>(Q), k, k, static_cast<float*>(V), sigma2);
+  return rs_fail(RS_EUNSUPPORTED, "rs_ritz: dtype %d", X->dtype);
+}
+
+int rs_sketch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* V, double* sigma2) {
+  RS_TRY(rs_enter(ctx));
+  RS_TRY(check_matrix(X, "rs_sketch X"));
+  RS_CHECK_ARG(p && V && sigma2, "rs_sketch: null argument");
+  RS_CHECK_ARG(p->k >= 1 && p->k <= X->d && p->k <= 256, "rs_sketch: k must be in [1, min(d, 256)]");
+  RS_CHECK_ARG(p->kind == RS_SKETCH_GAUSSIAN || p->kind == RS_SKETCH_COUNTSKETCH, "rs_sketch: bad kind");
+  return sketch_dispatch(ctx, X, p, V, sigma2);
+}
+
+int rs_precondition(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k, double lambda,
+                    rs_matrix* Xt, void* beta, double* beta_hat) {
+  RS_TRY(rs_enter(ctx));
+  RS_TRY(check_matrix(X, "rs_precondition X"));
+  RS_TRY(check_matrix(Xt, "rs_precondition Xt"));
+  RS_CHECK_ARG(V && sigma2 && beta, "rs_precondition: null argument");
+  RS_CHECK_ARG(k >= 1 && k <= X->d, "rs_precondition: k must be in [1, d]");
+  RS_CHECK_ARG(lambda > 0.0, "rs_precondition: lambda must be positive");
+  RS_CHECK_ARG(Xt->n == X->n + X->d && Xt->d == X->d, "rs_precondition: Xt must be (n + d) x d");
+  RS_CHECK_ARG(Xt->dtype == X->dtype, "rs_precondition: Xt dtype must equal X dtype");
+  return precondition_dispatch(ctx, X, V, sigma2, k, lambda, Xt, beta, beta_hat);
+}
+
+int rs_map_output(rs_ctx* ctx, const void* V, const double* sigma2, int64_t d, int64_t k, double lambda, int32_t dtype,
+                  const void* w_tilde, void* w) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(V && sigma2 && w_tilde && w && d >= 1 && k >= 1 && k <= d, "rs_map_output: bad arguments");
+  RS_CHECK_ARG(dtype == RS_F64 || dtype == RS_F32, "rs_map_output: dtype must be RS_F64 or RS_F32");
+  return map_output_dispatch(ctx, V, sigma2, d, k, lambda, dtype, w_tilde, w);
+}
+
+int rs_objective(rs_ctx* ctx, const rs_matrix* X, const void* y, double lambda, const void* w, const void* w_ref,
+                 double* out) {
+  RS_TRY(rs_enter(ctx));
+  RS_TRY(check_matrix(X, "rs_objective X"));
+  RS_CHECK_ARG(y && w && out, "rs_objective: null argument");
+  return objective_dispatch(ctx, X, y, lambda, w, w_ref, out);
+}
+
+}  // extern "C"

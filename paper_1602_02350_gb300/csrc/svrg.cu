@@ -1,0 +1,766 @@
+// SVRG on the preconditioned components (Alg. 1 with the n+d decomposition of Sec. 5.1):
+// the full-gradient streaming pass, the blocked inner loop (a parallel per-block
+// preparation plus a sequential thread-block-cluster chain), the epoch driver and
+// Alg. 3 end to end.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+int scan_u32_to_u64(rs_ctx* ctx, const uint32_t* in, uint64_t* out, int64_t N);
+int sampling_weights_dispatch(rs_ctx* ctx, const void* beta, int32_t dtype, int64_t N, uint32_t* W);
+int index_stream_dispatch(rs_ctx* ctx, const uint32_t* W, const uint64_t* cum, int64_t N, uint64_t seed,
+                          int64_t epoch, int64_t t0, int64_t m, int32_t sampling, int32_t dtype, uint32_t* idx,
+                          void* inv_nq);
+int map_output_dispatch(rs_ctx* ctx, const void* V, const double* sigma2, int64_t d, int64_t k, double lam,
+                        int32_t dtype, const void* wt, void* w);
+int sketch_dispatch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* V, double* sigma2);
+int precondition_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k, double lam,
+                          rs_matrix* Xt, void* beta, double* beta_hat);
+
+namespace {
+
+constexpr int kBlk = 64;   // inner steps per block of the blocked recursion
+
+int blocks_for(rs_ctx* ctx, int64_t work, int threads = 256) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)ctx->num_sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// ------------------------------------------------------------------ full gradient
+// mu = (1/N) sum_i gamma_i (z_i^T w - y_i) z_i: a warp streams one row at a time (VPL 16-byte
+// vectors per lane), reduces the dot product with shuffles and accumulates r_i z_i in registers;
+// per-block partial vectors are summed in a fixed order by fullgrad_reduce_kernel.
+template <typename T, int VPL>
+__global__ void __launch_bounds__(256) fullgrad_kernel(const T* __restrict__ Z, int64_t N, int64_t n, int64_t d,
+                                                       int64_t ld, const T* __restrict__ y, T lam,
+                                                       const T* __restrict__ w, T* __restrict__ part) {
+  using V = typename Vec<T>::type;
+  constexpr int E = Vec<T>::N;
+  extern __shared__ unsigned char fg_sh[];
+  T* sh = reinterpret_cast<T*>(fg_sh);   // [warps][d]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T wr[VPL][E], acc[VPL][E];
+#pragma unroll
+  for (int q = 0; q < VPL; ++q)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int64_t c = (int64_t)(lane + 32 * q) * E + e;
+      wr[q][e] = c < d ? w[c] : T(0);
+      acc[q][e] = T(0);
+    }
+  const T inv_n = T(1) / (T)n;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
+    const T* row = Z + i * ld;
+    T z[VPL][E];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) {
+      const int64_t c0 = (int64_t)(lane + 32 * q) * E;
+      if (c0 < d) {
+        V v = *reinterpret_cast<const V*>(row + c0);
+        vec_to_arr(v, z[q]);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (c0 + e >= d) z[q][e] = T(0);
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) z[q][e] = T(0);
+      }
+    }
+    T dot = T(0);
+#pragma unroll
+    for (int q = 0; q < VPL; ++q)
+#pragma unroll
+      for (int e = 0; e < E; ++e) dot = fma(z[q][e], wr[q][e], dot);
+    dot = warp_sum(dot);
+    const T r = i < n ? (dot - y[i]) * inv_n : lam * dot;
+#pragma unroll
+    for (int q = 0; q < VPL; ++q)
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[q][e] = fma(r, z[q][e], acc[q][e]);
+  }
+#pragma unroll
+  for (int q = 0; q < VPL; ++q)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int64_t c = (int64_t)(lane + 32 * q) * E + e;
+      if (c < d) sh[warp * d + c] = acc[q][e];
+    }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
+    T s = T(0);
+    for (int w2 = 0; w2 < nw; ++w2) s += sh[w2 * d + c];
+    part[(int64_t)blockIdx.x * d + c] = s;
+  }
+}
+
+template <typename T>
+__global__ void fullgrad_reduce_kernel(const T* part, int np, int64_t d, T* mu, double* norm2_out) {
+  __shared__ double sh[32];
+  double nrm = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < np; ++p) s += (double)part[(int64_t)p * d + c];
+    mu[c] = (T)s;
+    nrm += s * s;
+  }
+  if (norm2_out) {
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2];
+      norm2_out[blockIdx.x] = t;   // launched with one block when norms are wanted
+    }
+  }
+}
+
+// Fallback for rows wider than the register path: r_i = gamma_i (z_i^T w - y_i)/N, then mu = Z^T r.
+template <typename T>
+__global__ void residual_kernel(const T* Z, int64_t N, int64_t n, int64_t d, int64_t ld, const T* y, T lam, const T* w,
+                                T* r) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
+    T s = T(0);
+    for (int64_t c = lane; c < d; c += 32) s = fma(Z[i * ld + c], w[c], s);
+    s = warp_sum(s);
+    if (lane == 0) r[i] = i < n ? (s - y[i]) / (T)n : lam * s;
+  }
+}
+
+template <typename T>
+__global__ void convert_kernel(const double* in, int64_t count, T* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)in[e];
+}
+
+// ------------------------------------------------------------------ blocked inner loop
+//
+// Inside one block of B consecutive steps t0+1..t0+B the recursion of Alg. 1 is, with
+// delta = w - w_bar, z_j the sampled row of step j and kappa_j = gamma_{i_j} / (N q_{i_j}):
+//   a_j   = kappa_j z_j^T delta_{before j}
+//   delta_{after j} = delta_{before j} - eta a_j z_j - eta mu
+// so that a = R (p - eta (j h)) with p_j = z_j^T delta_{t0}, h_j = z_j^T mu and
+// R = (I + eta K L)^{-1} K, L the strictly lower part of the block's Gram matrix.
+// R and c = -eta R (j h) depend only on the sampled rows and mu, so every block's (R, c)
+// is formed in parallel before the sequential chain runs.
+
+// One thread block per block of steps: Gram of the B sampled rows and mu, then R and c.
+template <typename T>
+__global__ void __launch_bounds__(256) epoch_prep_kernel(const T* __restrict__ Z, int64_t ld, int64_t d, int64_t n,
+                                                         int64_t N, double lam, const uint32_t* __restrict__ idx,
+                                                         const T* __restrict__ inv_nq, int64_t m, double eta,
+                                                         const T* __restrict__ mu, T* __restrict__ Rt,
+                                                         T* __restrict__ cvec) {
+  constexpr int B = kBlk, RP = B + 4;   // rows 0..B-1 sampled rows, row B = mu, rows B+1.. zero
+  constexpr int CH = 32;                // columns per staged chunk
+  extern __shared__ unsigned char pr_sh[];
+  T* tile = reinterpret_cast<T*>(pr_sh);          // [RP][CH + 1]
+  T* G = tile + RP * (CH + 1);                    // [RP][RP]
+  T* R = G + RP * RP;                             // [B][B], R[j][c]
+  __shared__ T kap[B];
+  __shared__ int64_t rowid[B];
+  const int64_t b = blockIdx.x;
+  const int64_t t0 = b * B;
+  const int Bb = (int)min64(B, m - t0);
+  const int tid = threadIdx.x;
+  const T Nn = (T)((double)N / (double)n), lN = (T)(lam * (double)N);
+  for (int j = tid; j < B; j += blockDim.x) {
+    if (j < Bb) {
+      const uint32_t i = min(idx[t0 + j], (uint32_t)(N - 1));   // indices are < N by contract; never read outside Z
+      rowid[j] = i;
+      kap[j] = (i < (uint64_t)n ? Nn : lN) * inv_nq[t0 + j];
+    } else {
+      rowid[j] = -1;
+      kap[j] = T(0);
+    }
+  }
+  // lower-triangular 4x4 tiles of the RP x RP Gram matrix: 17*18/2 = 153 tiles
+  int TI = -1, TJ = -1;
+  {
+    int t = tid, I = 0;
+    while (I < RP / 4 && t > I) { t -= I + 1; ++I; }
+    if (I < RP / 4) { TI = I; TJ = t; }
+  }
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < d; c0 += CH) {
+    for (int e = tid; e < RP * CH; e += blockDim.x) {
+      const int r = e / CH, c = e % CH;
+      const int64_t col = c0 + c;
+      T v = T(0);
+      if (col < d) {
+        if (r < B) {
+          if (r < Bb) v = Z[rowid[r] * ld + col];
+        } else if (r == B) {
+          v = mu[col];
+        }
+      }
+      tile[r * (CH + 1) + c] = v;
+    }
+    __syncthreads();
+    if (TI >= 0) {
+#pragma unroll 4
+      for (int c = 0; c < CH; ++c) {
+        T a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = tile[(TI * 4 + i) * (CH + 1) + c];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = tile[(TJ * 4 + j) * (CH + 1) + c];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (TI >= 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gi = TI * 4 + i, gj = TJ * 4 + j;
+        G[gi * RP + gj] = acc[i][j];
+        G[gj * RP + gi] = acc[i][j];
+      }
+  }
+  __syncthreads();
+  // column c of R = (I + eta K L)^{-1} K by forward substitution (independent per column)
+  const T et = (T)eta;
+  if (tid < B) {
+    const int c = tid;
+    for (int j = 0; j < B; ++j) R[j * B + c] = T(0);
+    if (c < Bb) {
+      R[c * B + c] = kap[c];
+      for (int j = c + 1; j < Bb; ++j) {
+        T s = T(0);
+        for (int l = c; l < j; ++l) s = fma(G[j * RP + l], R[l * B + c], s);
+        R[j * B + c] = -et * kap[j] * s;
+      }
+    }
+  }
+  __syncthreads();
+  // c_j = -eta sum_{l <= j} R[j][l] l h_l,  h_l = mu^T z_l = G[B][l]
+  T* Rout = Rt + b * (int64_t)B * B;
+  if (tid < B) {
+    const int j = tid;
+    T s = T(0);
+    for (int l = 0; l <= j && l < Bb; ++l) s = fma(R[j * B + l], (T)l * G[B * RP + l], s);
+    cvec[b * B + j] = j < Bb ? -et * s : T(0);
+  }
+  for (int e = tid; e < B * B; e += blockDim.x) {
+    const int l = e / B, j = e % B;
+    Rout[e] = R[j * B + l];   // transposed: Rt[l][j] = R[j][l]
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Sequential chain over the blocks of one epoch, run by one thread-block cluster of CS blocks.
+// Block r of the cluster owns columns [r cw, (r+1) cw) of delta; per block of steps the partial
+// dot products p_j are exchanged through distributed shared memory (fixed summation order, so
+// every block computes bit-identical a_j).
+template <typename T, int STAGES>
+__global__ void __launch_bounds__(128) epoch_chain_kernel(const T* __restrict__ Z, int64_t N, int64_t ld, int64_t d, int cw,
+                                                          const uint32_t* __restrict__ idx, int64_t m,
+                                                          const T* __restrict__ Rt, const T* __restrict__ cvec,
+                                                          double eta, const T* __restrict__ mu,
+                                                          const T* __restrict__ wbar, int average, T* __restrict__ wnext) {
+  constexpr int B = kBlk;
+  constexpr int E = 16 / sizeof(T);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char ch_sh[];
+  T* Zs = reinterpret_cast<T*>(ch_sh);                    // [STAGES][B][cw]
+  T* Rs = Zs + (size_t)STAGES * B * cw;                   // [STAGES][B][B]
+  T* Cs = Rs + (size_t)STAGES * B * B;                    // [STAGES][B]
+  T* dl = Cs + (size_t)STAGES * B;                        // delta slice [cw]
+  T* mus = dl + cw;                                       // mu slice [cw]
+  double* Ssum = reinterpret_cast<double*>(mus + cw);     // running sum of delta [cw] (8-byte aligned: cw % 4 == 0)
+  T* xbuf = reinterpret_cast<T*>(Ssum + cw);              // [2][B] exchanged partial dots
+  T* pv = xbuf + 2 * B;                                   // [B]
+  T* av = pv + B;                                         // [B]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c0 = (int64_t)rank * cw;
+  const int cwid = (int)max64(0, min64(cw, d - c0));
+  const int cvec_n = (cwid + E - 1) / E;                  // 16-byte chunks per row slice
+  const int64_t nblk = (m + B - 1) / B;
+  const T et = (T)eta;
+
+  for (int c = tid; c < cw; c += blockDim.x) {
+    dl[c] = T(0);
+    Ssum[c] = 0.0;
+    mus[c] = c < cwid ? mu[c0 + c] : T(0);
+  }
+
+  auto load_block = [&](int64_t blk) {
+    const int slot = (int)(blk % STAGES);
+    const int64_t t0 = blk * B;
+    const int Bb = (int)min64(B, m - t0);
+    T* zdst = Zs + (size_t)slot * B * cw;
+    for (int e = tid; e < Bb * cvec_n; e += blockDim.x) {
+      const int j = e / cvec_n, q = e % cvec_n;
+      const int64_t row = min64((int64_t)idx[t0 + j], N - 1);
+      cp_async16(zdst + (size_t)j * cw + q * E, Z + row * ld + c0 + q * E);
+    }
+    const T* rsrc = Rt + blk * (int64_t)B * B;
+    T* rdst = Rs + (size_t)slot * B * B;
+    for (int e = tid; e < B * B / E; e += blockDim.x) cp_async16(rdst + e * E, rsrc + e * E);
+    for (int e = tid; e < B / E; e += blockDim.x) cp_async16(Cs + (size_t)slot * B + e * E, cvec + blk * B + e * E);
+  };
+
+#pragma unroll
+  for (int s = 0; s < STAGES - 1; ++s) {
+    if (s < nblk) load_block(s);
+    cp_async_commit();
+  }
+  cluster.sync();   // every block of the cluster is running before any remote access
+
+  for (int64_t blk = 0; blk < nblk; ++blk) {
+    cp_async_wait<STAGES - 2>();
+    __syncthreads();
+    if (blk + STAGES - 1 < nblk) load_block(blk + STAGES - 1);
+    cp_async_commit();
+    const int slot = (int)(blk % STAGES);
+    const int Bb = (int)min64(B, m - blk * B);
+    const T* zs = Zs + (size_t)slot * B * cw;
+    // partial p_j over this block's columns
+    T* xb = xbuf + (blk & 1) * B;
+    for (int j = warp; j < Bb; j += 4) {
+      T s = T(0);
+      for (int c = lane; c < cwid; c += 32) s = fma(zs[(size_t)j * cw + c], dl[c], s);
+      s = warp_sum(s);
+      if (lane == 0) xb[j] = s;
+    }
+    cluster.sync();
+    if (tid < Bb) {
+      T s = T(0);
+      for (int r = 0; r < CS; ++r) {
+        const T* rx = cluster.map_shared_rank(xb, r);
+        s += rx[tid];
+      }
+      pv[tid] = s;
+    }
+    __syncthreads();
+    if (tid < Bb) {
+      const T* rs = Rs + (size_t)slot * B * B;
+      T s0 = Cs[(size_t)slot * B + tid], s1 = T(0);
+      int l = 0;
+      for (; l + 1 <= tid; l += 2) {
+        s0 = fma(rs[l * B + tid], pv[l], s0);
+        s1 = fma(rs[(l + 1) * B + tid], pv[l + 1], s1);
+      }
+      if (l <= tid) s0 = fma(rs[l * B + tid], pv[l], s0);
+      av[tid] = s0 + s1;
+    }
+    __syncthreads();
+    const T bbT = (T)Bb;
+    const T tri = (T)(0.5 * (double)Bb * (double)(Bb + 1));
+    for (int c = tid; c < cwid; c += blockDim.x) {
+      T upd = T(0), wsum = T(0);
+      for (int j = 0; j < Bb; ++j) {
+        const T az = av[j] * zs[(size_t)j * cw + c];
+        upd += az;
+        wsum = fma((T)(Bb - j), az, wsum);
+      }
+      const T dold = dl[c];
+      Ssum[c] += (double)(bbT * dold - et * (mus[c] * tri + wsum));
+      dl[c] = dold - et * (bbT * mus[c] + upd);
+    }
+  }
+  cp_async_wait<0>();
+  cluster.sync();   // no block leaves while another may still read its exchange buffer
+  for (int c = tid; c < cwid; c += blockDim.x) {
+    const double v = average ? Ssum[c] / (double)m : (double)dl[c];
+    wnext[c0 + c] = (T)((double)wbar[c0 + c] + v);
+  }
+}
+
+template <typename T>
+__global__ void finite_check_kernel(const T* w, int64_t d, double limit, int* status) {
+  bool bad = false, big = false;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)w[c];
+    if (!isfinite(v)) bad = true;
+    else if (fabs(v) > limit) big = true;
+  }
+  if (bad) atomicOr(status, 1);
+  if (big) atomicOr(status, 8);
+}
+
+template <typename T>
+__global__ void row_beta_only_kernel(const T* Z, int64_t N, int64_t n, int64_t d, int64_t ld, double lam, T* beta) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double gd = (double)N / (double)n, gr = lam * (double)N;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
+    T s = T(0);
+    for (int64_t c = lane; c < d; c += 32) s = fma(Z[i * ld + c], Z[i * ld + c], s);
+    s = warp_sum(s);
+    if (lane == 0) beta[i] = (T)((i < n ? gd : gr) * (double)s);
+  }
+}
+
+template <typename T>
+__global__ void mean_kernel(const T* v, int64_t N, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += (double)v[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2];
+    *out = t / (double)N;
+  }
+}
+
+}  // namespace
+
+// ====================================================================== launchers
+
+template <typename T>
+static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t n, double lam, const T* w, T* mu,
+                           double* norm2_dev) {
+  const int64_t N = Z->n, d = Z->d;
+  const T* Zd = static_cast<const T*>(Z->data);
+  constexpr int E = Vec<T>::N;
+  const int64_t vecs = (d + E - 1) / E;
+  const int vpl = (int)((vecs + 31) / 32);
+  const int threads = 256;
+  if (vpl <= 8) {
+    const int blocks = ctx->num_sms * 2;
+    T* part = static_cast<T*>(rs_scratch(ctx, SCR_PART2, (size_t)blocks * d * sizeof(T)));
+    if (!part) return RS_ENOMEM;
+    const size_t shm = (size_t)(threads / 32) * d * sizeof(T);
+#define RS_FG(VV)                                                                                              \
+  do {                                                                                                         \
+    RS_CUDA_TRY(cudaFuncSetAttribute(fullgrad_kernel<T, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                     (int)shm));                                                               \
+    fullgrad_kernel<T, VV><<<blocks, threads, shm, ctx->stream>>>(Zd, N, n, d, Z->ld, y, (T)lam, w, part);     \
+  } while (0)
+    if (vpl <= 1) RS_FG(1);
+    else if (vpl <= 2) RS_FG(2);
+    else if (vpl <= 4) RS_FG(4);
+    else RS_FG(8);
+#undef RS_FG
+    RS_LAUNCH_CHECK(ctx);
+    const int rb = norm2_dev ? 1 : blocks_for(ctx, d);
+    fullgrad_reduce_kernel<T><<<rb, 256, 0, ctx->stream>>>(part, blocks, d, mu, norm2_dev);
+    RS_LAUNCH_CHECK(ctx);
+    return RS_OK;
+  }
+  // wide rows: two passes
+  T* r = static_cast<T*>(rs_scratch(ctx, SCR_PART2, N * sizeof(T)));
+  double* md = static_cast<double*>(rs_scratch(ctx, SCR_TMPV, d * sizeof(double)));
+  if (!r || !md) return RS_ENOMEM;
+  residual_kernel<T><<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(Zd, N, n, d, Z->ld, y, (T)lam, w, r);
+  RS_LAUNCH_CHECK(ctx);
+  RS_TRY(launch_gram<T>(ctx, N, d, 1, Zd, Z->ld, r, 1, 1.0, md));
+  convert_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(md, d, mu);
+  RS_LAUNCH_CHECK(ctx);
+  if (norm2_dev) RS_CUDA_TRY(cudaMemsetAsync(norm2_dev, 0, sizeof(double), ctx->stream));
+  return RS_OK;
+}
+
+struct ChainPlan {
+  int cs = 8, cw = 0, stages = 3;
+  size_t shm = 0;
+};
+
+template <typename T>
+static ChainPlan plan_chain(int64_t d) {
+  constexpr int E = 16 / sizeof(T);
+  ChainPlan best;
+  const int candidates[] = {8, 16, 4, 2, 1};
+  for (int cs : candidates) {
+    int cw = (int)((d + cs - 1) / cs);
+    cw = (cw + E - 1) / E * E;
+    if ((int64_t)cw * (cs - 1) >= d && cs > 1) continue;   // an idle block would own no columns
+    for (int st = 3; st >= 2; --st) {
+      const size_t shm = (size_t)st * kBlk * cw * sizeof(T) + (size_t)st * kBlk * kBlk * sizeof(T) +
+                         (size_t)st * kBlk * sizeof(T) + 2 * (size_t)cw * sizeof(T) + 16 + (size_t)cw * sizeof(double) +
+                         4 * (size_t)kBlk * sizeof(T) + 64;
+      if (shm <= 200 * 1024) {
+        best.cs = cs;
+        best.cw = cw;
+        best.stages = st;
+        best.shm = shm;
+        return best;
+      }
+    }
+  }
+  best.cw = 0;
+  return best;
+}
+
+template <typename T>
+static int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
+                        int64_t m, double eta, const T* wbar, const T* mu, int average, T* wnext) {
+  const int64_t N = Z->n, d = Z->d;
+  const T* Zd = static_cast<const T*>(Z->data);
+  const int64_t nblk = (m + kBlk - 1) / kBlk;
+  T* Rt = static_cast<T*>(rs_scratch(ctx, SCR_R, (size_t)nblk * kBlk * kBlk * sizeof(T)));
+  T* cv = static_cast<T*>(rs_scratch(ctx, SCR_C, (size_t)nblk * kBlk * sizeof(T)));
+  if (!Rt || !cv) return RS_ENOMEM;
+  constexpr int RP = kBlk + 4, CH = 32;
+  const size_t pshm = (size_t)(RP * (CH + 1) + RP * RP + kBlk * kBlk) * sizeof(T);
+  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+  epoch_prep_kernel<T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, Z->ld, d, n, N, lam, idx, inv_nq, m, eta, mu,
+                                                                   Rt, cv);
+  RS_LAUNCH_CHECK(ctx);
+  ChainPlan pl = plan_chain<T>(d);
+  if (pl.cw == 0) return rs_fail(RS_EUNSUPPORTED, "rs_svrg_epoch: d = %lld too wide for the on-chip chain", (long long)d);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.cs, 1, 1);
+  cfg.blockDim = dim3(128, 1, 1);
+  cfg.dynamicSmemBytes = pl.shm;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (pl.stages == 3) {
+    auto kern = epoch_chain_kernel<T, 3>;
+    RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
+    if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, Zd, N, Z->ld, d, pl.cw, idx, m, (const T*)Rt, (const T*)cv, eta, mu, wbar,
+                                   average, wnext));
+  } else {
+    auto kern = epoch_chain_kernel<T, 2>;
+    RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
+    if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, Zd, N, Z->ld, d, pl.cw, idx, m, (const T*)Rt, (const T*)cv, eta, mu, wbar,
+                                   average, wnext));
+  }
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+static int check_components(const rs_matrix* Z, int64_t n) {
+  RS_TRY(check_matrix(Z, "Z"));
+  RS_CHECK_ARG(Z->dtype == RS_F64 || Z->dtype == RS_F32, "components: dtype must be RS_F64 or RS_F32 in this build");
+  RS_CHECK_ARG(n >= 1 && n < Z->n && Z->n - n == Z->d, "components: Z must have n + d rows");
+  return RS_OK;
+}
+
+template <typename T>
+static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, const T* beta_in, const T* V,
+                        const double* sigma2, int64_t k, const rs_svrg_params* p, const T* w0, T* w_out,
+                        rs_history* hist, double* eta_used, int64_t* m_used) {
+  const int64_t N = Z->n, d = Z->d, n = N - d;
+  const int32_t dt = sizeof(T) == 8 ? RS_F64 : RS_F32;
+  const double lam = p->lambda;
+  T* beta = const_cast<T*>(beta_in);
+  if (!beta) {
+    beta = static_cast<T*>(rs_scratch(ctx, SCR_BETA, N * sizeof(T)));
+    if (!beta) return RS_ENOMEM;
+    row_beta_only_kernel<T><<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(static_cast<const T*>(Z->data), N, n, d,
+                                                                               Z->ld, lam, beta);
+    RS_LAUNCH_CHECK(ctx);
+  }
+  uint32_t* W = static_cast<uint32_t*>(rs_scratch(ctx, SCR_W, N * sizeof(uint32_t)));
+  uint64_t* cum = static_cast<uint64_t*>(rs_scratch(ctx, SCR_CUM, N * sizeof(uint64_t)));
+  double* scal = static_cast<double*>(rs_scratch(ctx, SCR_S2, (size_t)(4 + std::max(1, p->epochs)) * sizeof(double)));
+  if (!W || !cum || !scal) return RS_ENOMEM;
+  RS_TRY(sampling_weights_dispatch(ctx, beta, dt, N, W));   // synchronises, checks finiteness
+  RS_TRY(scan_u32_to_u64(ctx, W, cum, N));
+  mean_kernel<T><<<1, 1024, 0, ctx->stream>>>(beta, N, scal);
+  RS_LAUNCH_CHECK(ctx);
+  double bh = 0.0;
+  RS_CUDA_TRY(cudaMemcpyAsync(&bh, scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (!(bh > 0.0) || !std::isfinite(bh)) return rs_fail(RS_ENONFINITE, "rs_svrg_solve: mean smoothness is %g", bh);
+  double eta = p->eta;
+  if (p->eta_mult > 0.0) eta = p->eta_mult / bh;
+  else if (!(eta > 0.0)) eta = 0.1 / bh;
+  int64_t m = p->m > 0 ? p->m : (int64_t)std::ceil(bh / lam);
+  if (m < 1) m = 1;
+  if (eta_used) *eta_used = eta;
+  if (m_used) *m_used = m;
+  T* wa = static_cast<T*>(rs_scratch(ctx, SCR_WBAR, d * sizeof(T)));
+  T* wb = static_cast<T*>(rs_scratch(ctx, SCR_WNEXT, d * sizeof(T)));
+  T* mu = static_cast<T*>(rs_scratch(ctx, SCR_MU, d * sizeof(T)));
+  uint32_t* idx = static_cast<uint32_t*>(rs_scratch(ctx, SCR_IDX, m * sizeof(uint32_t)));
+  T* inq = static_cast<T*>(rs_scratch(ctx, SCR_INVNQ, m * sizeof(T)));
+  if (!wa || !wb || !mu || !idx || !inq) return RS_ENOMEM;
+  if (w0) RS_CUDA_TRY(cudaMemcpyAsync(wa, w0, d * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+  else RS_CUDA_TRY(cudaMemsetAsync(wa, 0, d * sizeof(T), ctx->stream));
+  const int S = p->epochs;
+  std::vector<cudaEvent_t> ev;
+  if (hist && hist->epoch_ms) {
+    ev.resize(S + 1);
+    for (auto& e : ev) RS_CUDA_TRY(cudaEventCreate(&e));
+    RS_CUDA_TRY(cudaEventRecord(ev[0], ctx->stream));
+  }
+  double* norms = scal + 4;
+  for (int s = 0; s < S; ++s) {
+    const bool want_norm = hist && hist->mu_norm2;
+    RS_TRY(full_gradient_t<T>(ctx, Z, y, n, lam, wa, mu, want_norm ? norms + s : nullptr));
+    RS_TRY(index_stream_dispatch(ctx, W, cum, N, p->seed, (int64_t)p->epoch0 + s, 0, m, p->sampling, dt, idx, inq));
+    RS_TRY(svrg_epoch_t<T>(ctx, Z, n, lam, idx, inq, m, eta, wa, mu, p->average, wb));
+    std::swap(wa, wb);
+    if (hist && hist->snapshots && s < hist->capacity)
+      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, static_cast<T*>(hist->snapshots) + (int64_t)s * d));
+    if (!ev.empty()) RS_CUDA_TRY(cudaEventRecord(ev[s + 1], ctx->stream));
+  }
+  RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, w_out));
+  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  finite_check_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(w_out, d, 1e30, ctx->d_status);
+  RS_LAUNCH_CHECK(ctx);
+  int st = 0;
+  RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (hist) {
+    hist->epochs_run = S;
+    if (hist->mu_norm2 && S > 0)
+      RS_CUDA_TRY(cudaMemcpy(hist->mu_norm2, norms, std::min(S, hist->capacity) * sizeof(double),
+                             cudaMemcpyDeviceToHost));
+    if (!ev.empty()) {
+      for (int s = 0; s < S && s < hist->capacity; ++s) RS_CUDA_TRY(cudaEventElapsedTime(&hist->epoch_ms[s], ev[0], ev[s + 1]));
+      for (auto& e : ev) cudaEventDestroy(e);
+    }
+  }
+  if (st & 1) return rs_fail(RS_ENONFINITE, "rs_svrg_solve: the iterate became non-finite (step size too large?)");
+  if (st & 8) return rs_fail(RS_EDIVERGED, "rs_svrg_solve: the iterate diverged (step size too large?)");
+  return RS_OK;
+}
+
+static bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+template <typename T>
+static int solve_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, const rs_sketch_params* sp,
+                   const rs_svrg_params* p, void* w_out, rs_history* hist) {
+  const int64_t n = Xin->n, d = Xin->d, k = sp->k, N = n + d;
+  rs_matrix X = *Xin;
+  const size_t es = sizeof(T);
+  if (is_host_ptr(Xin->data)) {
+    void* xd = rs_scratch(ctx, SCR_XDEV, (size_t)n * Xin->ld * es);
+    if (!xd) return RS_ENOMEM;
+    RS_CUDA_TRY(cudaMemcpyAsync(xd, Xin->data, (size_t)n * Xin->ld * es, cudaMemcpyHostToDevice, ctx->stream));
+    X.data = xd;
+  }
+  const T* y = static_cast<const T*>(yin);
+  if (is_host_ptr(yin)) {
+    T* yd = static_cast<T*>(rs_scratch(ctx, SCR_YDEV, n * es));
+    if (!yd) return RS_ENOMEM;
+    RS_CUDA_TRY(cudaMemcpyAsync(yd, yin, n * es, cudaMemcpyHostToDevice, ctx->stream));
+    y = yd;
+  }
+  const bool host_out = is_host_ptr(w_out);
+  T* wdev = static_cast<T*>(host_out ? rs_scratch(ctx, SCR_WOUT, d * es) : w_out);
+  T* V = static_cast<T*>(rs_scratch(ctx, SCR_V, d * k * es));
+  double* sg = static_cast<double*>(rs_scratch(ctx, SCR_SIGMA, k * sizeof(double)));
+  const int64_t ldz = (d * (int64_t)es + 15) / 16 * 16 / (int64_t)es;
+  T* Zbuf = static_cast<T*>(rs_scratch(ctx, SCR_Z, (size_t)N * ldz * es));
+  T* beta = static_cast<T*>(rs_scratch(ctx, SCR_BETA, N * es));
+  if (!wdev || !V || !sg || !Zbuf || !beta) return RS_ENOMEM;
+  RS_TRY(sketch_dispatch(ctx, &X, sp, V, sg));
+  rs_matrix Zm = {Zbuf, nullptr, N, d, ldz, X.dtype, 0};
+  RS_TRY(precondition_dispatch(ctx, &X, V, sg, k, p->lambda, &Zm, beta, nullptr));
+  RS_TRY(svrg_solve_t<T>(ctx, &Zm, y, beta, V, sg, k, p, nullptr, wdev, hist, nullptr, nullptr));
+  if (host_out) {
+    RS_CUDA_TRY(cudaMemcpyAsync(w_out, wdev, d * es, cudaMemcpyDeviceToHost, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  return RS_OK;
+}
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int rs_full_gradient(rs_ctx* ctx, const rs_matrix* Z, const void* y, int64_t n, double lambda, const void* w,
+                     void* mu) {
+  RS_TRY(rs_enter(ctx));
+  RS_TRY(check_components(Z, n));
+  RS_CHECK_ARG(y && w && mu, "rs_full_gradient: null argument");
+  RS_CHECK_ARG(lambda > 0.0, "rs_full_gradient: lambda must be positive");
+  if (Z->dtype == RS_F64)
+    return full_gradient_t<double>(ctx, Z, static_cast<const double*>(y), n, lambda, static_cast<const double*>(w),
+                                   static_cast<double*>(mu), nullptr);
+  return full_gradient_t<float>(ctx, Z, static_cast<const float*>(y), n, lambda, static_cast<const float*>(w),
+                                static_cast<float*>(mu), nullptr);
+}
+
+int rs_svrg_epoch(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lambda, const uint32_t* idx, const void* inv_nq,
+                  int64_t m, double eta, const void* w_bar, const void* mu, int32_t average, void* w_next) {
+  RS_TRY(rs_enter(ctx));
+  RS_TRY(check_components(Z, n));
+  RS_CHECK_ARG(idx && inv_nq && w_bar && mu && w_next, "rs_svrg_epoch: null argument");
+  RS_CHECK_ARG(m >= 1 && m < (1LL << 31), "rs_svrg_epoch: m out of range");
+  RS_CHECK_ARG(w_next != w_bar, "rs_svrg_epoch: w_next must not alias w_bar");
+  if (Z->dtype == RS_F64)
+    return svrg_epoch_t<double>(ctx, Z, n, lambda, idx, static_cast<const double*>(inv_nq), m, eta,
+                                static_cast<const double*>(w_bar), static_cast<const double*>(mu), average,
+                                static_cast<double*>(w_next));
+  return svrg_epoch_t<float>(ctx, Z, n, lambda, idx, static_cast<const float*>(inv_nq), m, eta,
+                             static_cast<const float*>(w_bar), static_cast<const float*>(mu), average,
+                             static_cast<float*>(w_next));
+}
+
+int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const void* y, const void* beta, const void* V,
+                  const double* sigma2, int64_t k, const rs_svrg_params* p, const void* w0, void* w_out,
+                  rs_history* hist, double* eta_used, int64_t* m_used) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(Z && p, "rs_svrg_solve: null argument");
+  const int64_t n = Z->n - Z->d;
+  RS_TRY(check_components(Z, n));
+  RS_CHECK_ARG(y && V && sigma2 && w_out, "rs_svrg_solve: null argument");
+  RS_CHECK_ARG(k >= 1 && k <= Z->d, "rs_svrg_solve: k must be in [1, d]");
+  RS_CHECK_ARG(p->lambda > 0.0, "rs_svrg_solve: lambda must be positive");
+  RS_CHECK_ARG(p->epochs >= 0 && p->epoch0 >= 0, "rs_svrg_solve: bad epoch counts");
+  RS_CHECK_ARG(p->sampling == RS_SAMPLE_IMPORTANCE || p->sampling == RS_SAMPLE_UNIFORM, "rs_svrg_solve: bad sampling");
+  if (Z->dtype == RS_F64)
+    return svrg_solve_t<double>(ctx, Z, static_cast<const double*>(y), static_cast<const double*>(beta),
+                                static_cast<const double*>(V), sigma2, k, p, static_cast<const double*>(w0),
+                                static_cast<double*>(w_out), hist, eta_used, m_used);
+  return svrg_solve_t<float>(ctx, Z, static_cast<const float*>(y), static_cast<const float*>(beta),
+                             static_cast<const float*>(V), sigma2, k, p, static_cast<const float*>(w0),
+                             static_cast<float*>(w_out), hist, eta_used, m_used);
+}
+
+int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp, const rs_svrg_params* p,
+             void* w_out, rs_history* hist) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(X && X->data && y && sp && p && w_out, "rs_solve: null argument");
+  RS_CHECK_ARG(X->n >= 1 && X->d >= 1 && X->ld >= X->d, "rs_solve: bad shape");
+  RS_CHECK_ARG(X->dtype == RS_F64 || X->dtype == RS_F32, "rs_solve: dtype must be RS_F64 or RS_F32 in this build");
+  RS_CHECK_ARG((X->ld * (int64_t)dtype_size(X->dtype)) % 16 == 0, "rs_solve: row stride must be a multiple of 16 bytes");
+  RS_CHECK_ARG(sp->k >= 1 && sp->k <= X->d && sp->k <= 256, "rs_solve: k must be in [1, min(d, 256)]");
+  RS_CHECK_ARG(p->lambda > 0.0 && p->epochs >= 0, "rs_solve: bad SVRG parameters");
+  if (X->dtype == RS_F64) return solve_t<double>(ctx, X, y, sp, p, w_out, hist);
+  return solve_t<float>(ctx, X, y, sp, p, w_out, hist);
+}
+
+}  // extern "C"

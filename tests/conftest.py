@@ -13,3 +13,18 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
+
+
+import pytest  # noqa: E402
+
+
+@pytest.fixture(scope="session")
+def rsctx():
+    """One library context on cuda:0 for the GPU tests (fails loudly without the built library)."""
+    import torch
+    from paper_1602_02350_gb300 import Context, lib
+    lib()
+    ctx = Context(0)
+    yield ctx
+    torch.cuda.synchronize()
+    ctx.close()

@@ -1,0 +1,48 @@
+"""GPU parity of the preconditioner (Eq. (11), Sec. 5.1): transformed rows, regulariser rows,
+smoothness constants and the output map, against the oracle on generator inputs."""
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1602_02350_gb300 as rs
+from oracle import precond
+from paper_1602_02350_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
+@pytest.mark.parametrize("n,d,k", [(1, 4, 1), (257, 33, 5), (4096, 256, 16), (65536, 1024, 64)])
+def test_precondition_matches_oracle(rsctx, dtype, tol, n, d, k):
+    if dtype == torch.float64 and n * d > 4096 * 256:
+        pytest.skip("double GEMM at this size is covered by the float run")
+    X = torch.from_numpy(synth.random_matrix(n, d, n + d, scale=1.0 / np.sqrt(d))).to(dtype)
+    V = synth.random_orthonormal(d, k, d)
+    s2 = synth.random_sigma2(k, k)
+    lam = 1e-4
+    Vt = torch.from_numpy(V).to(dtype).cuda()
+    Z, beta, bh = rs.rs_precondition(rsctx, X.cuda(), Vt, torch.from_numpy(s2).cuda(), lam)
+    Z = Z.cpu().double().numpy()
+    Xd = X.double().numpy()
+    Vd = Vt.cpu().double().numpy()
+    M = precond.m_matrix(Vd, s2, lam)
+    Xt, B = precond.transform(Xd, M)
+    Zr, yz, g = precond.components(Xt, B, np.zeros(n), lam)
+    scale = np.abs(Xd).max() * (1 + np.sqrt(k))
+    np.testing.assert_allclose(Z[:n], Xt, rtol=0, atol=tol * scale)
+    np.testing.assert_allclose(Z[n:], B, rtol=0, atol=tol * (1 + np.sqrt(k)))
+    beta_ref = precond.smoothness(Zr, g)
+    np.testing.assert_allclose(beta.cpu().double().numpy(), beta_ref, rtol=tol * 20 * np.sqrt(d))
+    assert bh == pytest.approx(precond.beta_hat(beta_ref), rel=tol * 20 * np.sqrt(d))
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
+def test_map_output_matches_oracle(rsctx, dtype, tol):
+    d, k = 300, 20
+    V = torch.from_numpy(synth.random_orthonormal(d, k, 4)).to(dtype)
+    s2 = synth.random_sigma2(k, 2)
+    wt = torch.from_numpy(synth.random_vector(d, 3)).to(dtype)
+    w = rs.rs_map_output(rsctx, V.cuda(), torch.from_numpy(s2).cuda(), 1e-3, wt.cuda()).cpu().double().numpy()
+    ref = precond.m_matrix(V.double().numpy(), s2, 1e-3) @ wt.double().numpy()
+    np.testing.assert_allclose(w, ref, rtol=0, atol=tol * 10 * np.abs(ref).max())

@@ -1,0 +1,86 @@
+"""GPU parity of the sketch (Alg. 2): range sketch, Cholesky-QR, Jacobi eigensolver, Rayleigh-Ritz
+and the composed rs_sketch, against the oracle on the same seeded inputs."""
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1602_02350_gb300 as rs
+from oracle import ridge, sketch as osk
+from paper_1602_02350_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _data(n, d, alpha, seed, dtype):
+    X, y, _ = synth.problem(n, d, np.arange(1, d + 1) ** -alpha, 0.1, seed)
+    return X.to(dtype), y.to(dtype)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 3e-5)])
+@pytest.mark.parametrize("kind,n,d,k,s", [("gaussian", 300, 70, 5, 0), ("gaussian", 4096, 256, 16, 0),
+                                          ("countsketch", 3000, 130, 12, 256)])
+def test_range_sketch_matches_oracle(rsctx, dtype, tol, kind, n, d, k, s):
+    X, _ = _data(n, d, 1.5, 11, dtype)
+    Y = rs.rs_range_sketch(rsctx, X.cuda(), k, 2000, kind=kind, s=s).cpu().double().numpy()
+    ref = osk.range_sketch(X.double().numpy(), k, 2000, kind=kind, s=s)
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=tol * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
+@pytest.mark.parametrize("d,k", [(10, 1), (70, 9), (1024, 64), (300, 200)])
+def test_orthonormalize_matches_oracle(rsctx, dtype, tol, d, k):
+    Y = synth.random_matrix(d, k, d + k) @ np.diag(np.logspace(0, -2, k))
+    Q = rs.rs_orthonormalize(rsctx, torch.from_numpy(Y).to(dtype).cuda()).cpu().double().numpy()
+    Qr = osk.orthonormalize(Y.astype(np.float32).astype(np.float64) if dtype == torch.float32 else Y)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=tol * 10)
+    np.testing.assert_allclose(Q, Qr, atol=tol * 100)
+
+
+def test_orthonormalize_rejects_rank_deficient(rsctx):
+    Y = np.ones((20, 3))
+    with pytest.raises(rs.RsError):
+        rs.rs_orthonormalize(rsctx, torch.from_numpy(Y).cuda())
+
+
+@pytest.mark.parametrize("prec,tol", [(rs.RS_F64, 1e-12), (rs.RS_F32, 2e-5)])
+@pytest.mark.parametrize("k", [1, 2, 7, 16, 64, 97, 128, 256])
+def test_sym_eig_matches_library_eigh(rsctx, prec, tol, k):
+    G = synth.random_symmetric(k, k, spread=4.0)
+    ev, W = rs.rs_sym_eig(rsctx, torch.from_numpy(G).cuda(), prec)
+    ev, W = ev.cpu().numpy(), W.cpu().numpy()
+    ev_ref, W_ref = osk.sym_eig_desc(G)
+    np.testing.assert_allclose(ev, ev_ref, rtol=0, atol=tol * ev_ref[0])
+    # invariant checks: W orthonormal and G W = W diag(ev)
+    np.testing.assert_allclose(W.T @ W, np.eye(k), atol=tol * 10)
+    np.testing.assert_allclose(G @ W, W * ev, atol=tol * 10 * ev_ref[0])
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-10), (torch.float32, 1e-4)])
+def test_ritz_matches_oracle(rsctx, dtype, tol):
+    X, _ = _data(2000, 100, 1.2, 3, dtype)
+    Q = osk.orthonormalize(synth.random_matrix(100, 10, 1))
+    V, s2 = rs.rs_ritz(rsctx, X.cuda(), torch.from_numpy(Q).to(dtype).cuda())
+    V, s2 = V.cpu().double().numpy(), s2.cpu().numpy()
+    Vr, s2r = osk.ritz(X.double().numpy(), Q, 10)
+    np.testing.assert_allclose(s2, s2r, rtol=tol)
+    np.testing.assert_allclose(V @ np.diag(s2) @ V.T, Vr @ np.diag(s2r) @ Vr.T, atol=tol * s2r[0])
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 2e-3)])
+@pytest.mark.parametrize("kind,n,d,k,s,q", [("gaussian", 4096, 256, 16, 0, 1), ("countsketch", 8192, 512, 32, 2048, 1),
+                                            ("gaussian", 2048, 128, 8, 0, 3)])
+def test_sketch_end_to_end_matches_oracle(rsctx, dtype, tol, kind, n, d, k, s, q):
+    X, _ = _data(n, d, 1.5, 21, dtype)
+    V, s2 = rs.rs_sketch(rsctx, X.cuda(), k, 2000, kind=kind, s=s, q=q)
+    V, s2 = V.cpu().double().numpy(), s2.cpu().numpy()
+    Vr, s2r = osk.block_lanczos(X.double().numpy(), k, 2000, q=q, kind=kind, s=s)
+    np.testing.assert_allclose(s2, s2r, rtol=tol)
+    # Ritz values never exceed the true eigenvalues (interlacing)
+    lam = np.sort(np.linalg.eigvalsh(ridge.correlation(X.double().numpy())))[::-1]
+    assert np.all(s2 <= lam[:k] * (1 + 10 * tol))
+    # compare the preconditioner M (sign- and rotation-invariant), not V
+    from oracle import precond
+    M = precond.m_matrix(V, s2, 1e-4)
+    Mr = precond.m_matrix(Vr, s2r, 1e-4)
+    assert np.abs(M - Mr).max() < tol * 10
