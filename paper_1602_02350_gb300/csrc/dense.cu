@@ -149,76 +149,91 @@ __global__ void convert_from_double_kernel(const double* in, int64_t count, T* o
 }
 
 // ------------------------------------------------------------------ Cholesky-QR
-// In-place lower Cholesky factor of the k x k double matrix G (G = L L^T), one block.
-__global__ void chol_kernel(double* G, int k, int* status) {
-  __shared__ double djj;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = 0; j < k; ++j) {
-    if (warp == 0) {
-      double s = 0.0;
-      for (int p = lane; p < j; p += 32) s += G[j * k + p] * G[j * k + p];
-      s = warp_sum(s);
-      if (lane == 0) {
-        double v = G[j * k + j] - s;
-        if (!(v > 0.0) || !isfinite(v)) {
-          atomicOr(status, 4);
-          v = 1.0;
-        }
-        djj = sqrt(v);
-        G[j * k + j] = djj;
-      }
-    }
-    __syncthreads();
-    for (int i = j + 1 + warp; i < k; i += nw) {
-      double s = 0.0;
-      for (int p = lane; p < j; p += 32) s += G[i * k + p] * G[j * k + p];
-      s = warp_sum(s);
-      if (lane == 0) G[i * k + j] = (G[i * k + j] - s) / djj;
-    }
-    __syncthreads();
-  }
-}
-
-// Q[r] = Y[r] L^{-T} for every row r (solve q L^T = y by forward substitution); warp per row
+// Lower Cholesky factor L of the k x k double matrix G (G = L L^T, right-looking, one block) and
+// its inverse L^{-1} (column c by forward substitution, one thread per column), written as T.
+// L and the inverse live in shared memory when they fit (buf = nullptr), else in buf (2 k^2 doubles).
 template <typename T>
-__global__ void trsm_rows_kernel(const T* Y, int64_t d, int k, const double* L, T* Q) {
-  extern __shared__ double qsh[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* q = qsh + (size_t)warp * k;
-  for (int64_t r = (int64_t)blockIdx.x * nw + warp; r < d; r += (int64_t)gridDim.x * nw) {
-    for (int j = 0; j < k; ++j) {
-      double s = 0.0;
-      for (int p = lane; p < j; p += 32) s += q[p] * L[j * k + p];
-      s = warp_sum(s);
-      if (lane == 0) q[j] = ((double)Y[r * k + j] - s) / L[j * k + j];
-      __syncwarp();
-    }
-    for (int j = lane; j < k; j += 32) Q[r * k + j] = (T)q[j];
-    __syncwarp();
+__global__ void chol_inv_kernel(const double* G, int k, double* buf, T* Linv_out, int* status) {
+  extern __shared__ double ci_sh[];
+  double* L = buf ? buf : ci_sh;
+  double* Xi = L + (size_t)k * k;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < k * k; e += nt) {
+    L[e] = G[e];
+    Xi[e] = 0.0;
   }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      double v = L[j * k + j];
+      if (!(v > 0.0) || !isfinite(v)) {
+        atomicOr(status, 4);
+        v = 1.0;
+      }
+      L[j * k + j] = sqrt(v);
+    }
+    __syncthreads();
+    const double djj = L[j * k + j];
+    for (int i = j + 1 + tid; i < k; i += nt) L[i * k + j] /= djj;
+    __syncthreads();
+    const int w = k - j - 1;
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = j + 1 + e / w, l = j + 1 + e % w;
+      if (l <= i) L[i * k + l] -= L[i * k + j] * L[l * k + j];
+    }
+    __syncthreads();
+  }
+  for (int c = tid; c < k; c += nt) {
+    Xi[c * k + c] = 1.0 / L[c * k + c];
+    for (int i = c + 1; i < k; ++i) {
+      double s = 0.0;
+      for (int p = c; p < i; ++p) s = fma(L[i * k + p], Xi[p * k + c], s);
+      Xi[i * k + c] = -s / L[i * k + i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < k * k; e += nt) Linv_out[e] = (T)Xi[e];
 }
 
 // ------------------------------------------------------------------ Jacobi eigensolver
 // Cyclic Jacobi with round-robin pairing: each round rotates k/2 disjoint (p,q) planes at once.
-// A and W point to shared memory when they fit, else to global scratch (same code).
-template <typename TW>
-__global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, int use_smem, double tol, int max_sweeps,
+// A plane is rotated only if |a_pq| exceeds both tol sqrt|a_pp a_qq| and an absolute floor of a
+// few rounding units of ||G||_F; a sweep without rotations ends the iteration.  A and W are in
+// shared memory (SMEM) or in global scratch for large k.
+template <typename TW, bool SMEM>
+__global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol, double floor_ulps, int max_sweeps,
                               double* evals, double* Wout) {
   extern __shared__ unsigned char jsh[];
   const int K = (k + 1) & ~1;   // even number of players; index k is a dummy when k is odd
-  TW* A = use_smem ? reinterpret_cast<TW*>(jsh) : Ag;
-  TW* W = use_smem ? A + (size_t)k * k : Wg;
+  TW* A = SMEM ? reinterpret_cast<TW*>(jsh) : Ag;
+  TW* W = SMEM ? reinterpret_cast<TW*>(jsh) + (size_t)k * k : Wg;
   __shared__ int pp[128], qq[128];
   __shared__ TW cc[128], ss[128];
   __shared__ double red[32];
-  __shared__ int done;
+  __shared__ int rotations;
   const int tid = threadIdx.x, nt = blockDim.x;
+  double fro = 0.0;
   for (int e = tid; e < k * k; e += nt) {
     A[e] = (TW)G[e];
     W[e] = (e / k == e % k) ? TW(1) : TW(0);
+    fro = fma(G[e], G[e], fro);
+  }
+  fro = warp_sum(fro);
+  if ((tid & 31) == 0) red[tid >> 5] = fro;
+  __syncthreads();
+  if (tid == 0) {
+    double f = 0.0;
+    for (int w = 0; w < nt / 32; ++w) f += red[w];
+    red[0] = sqrt(f);
   }
   __syncthreads();
+  const TW abs_floor = (TW)(floor_ulps * red[0] * (sizeof(TW) == 8 ? 0x1p-53 : 0x1p-24));
+  const TW rel = (TW)tol;
+  const int jt = tid % k, it0 = tid / k, istep = nt / k;   // nt >= 4 k by launch configuration
+  const bool active = tid < istep * k;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rotations = 0;
+    __syncthreads();
     for (int r = 0; r < K - 1; ++r) {
       for (int i = tid; i < K / 2; i += nt) {
         auto pos = [&](int j) { return j == 0 ? 0 : ((j - 1 + r) % (K - 1)) + 1; };
@@ -227,34 +242,38 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, int use_sm
         TW c = TW(1), s = TW(0);
         if (q < k) {
           const TW apq = A[p * k + q];
-          if (apq != TW(0)) {
-            const TW app = A[p * k + p], aqq = A[q * k + q];
+          const TW app = A[p * k + p], aqq = A[q * k + q];
+          const TW thr = fmax(rel * sqrt(fabs(app * aqq)), abs_floor);
+          if (fabs(apq) > thr) {
             const TW theta = (aqq - app) / (TW(2) * apq);
             const TW t = (theta >= TW(0) ? TW(1) : TW(-1)) / (fabs(theta) + sqrt(theta * theta + TW(1)));
             c = TW(1) / sqrt(t * t + TW(1));
             s = t * c;
+            atomicAdd(&rotations, 1);
           }
         }
         pp[i] = p; qq[i] = q; cc[i] = c; ss[i] = s;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int e = tid; e < (K / 2) * k; e += nt) {
-        const int i = e / k, j = e % k;
-        const int p = pp[i], q = qq[i];
-        if (q >= k) continue;
-        const TW c = cc[i], s = ss[i];
-        const TW ap = A[p * k + j], aq = A[q * k + j];
-        A[p * k + j] = c * ap - s * aq;
-        A[q * k + j] = s * ap + c * aq;
-      }
+      // rows: A <- J^T A   (thread owns column j = jt of pairs it0, it0 + istep, ...)
+      if (active)
+        for (int i = it0; i < K / 2; i += istep) {
+          const int p = pp[i], q = qq[i];
+          const TW c = cc[i], s = ss[i];
+          if (q >= k || s == TW(0)) continue;
+          const int j = jt;
+          const TW ap = A[p * k + j], aq = A[q * k + j];
+          A[p * k + j] = c * ap - s * aq;
+          A[q * k + j] = s * ap + c * aq;
+        }
       __syncthreads();
-      // columns: A <- A J, W <- W J
-      for (int e = tid; e < (K / 2) * k; e += nt) {
-        const int i = e / k, j = e % k;
+      // columns: A <- A J, W <- W J   (thread owns row j = jt)
+      if (active)
+        for (int i = it0; i < K / 2; i += istep) {
+        const int j = jt;
         const int p = pp[i], q = qq[i];
-        if (q >= k) continue;
         const TW c = cc[i], s = ss[i];
+        if (q >= k || s == TW(0)) continue;
         const TW ap = A[j * k + p], aq = A[j * k + q];
         A[j * k + p] = c * ap - s * aq;
         A[j * k + q] = s * ap + c * aq;
@@ -264,35 +283,9 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, int use_sm
       }
       __syncthreads();
     }
-    // convergence: off-diagonal mass relative to the diagonal
-    double off = 0.0, dia = 0.0;
-    for (int e = tid; e < k * k; e += nt) {
-      const double v = (double)A[e];
-      if (e / k == e % k) dia += v * v;
-      else off += v * v;
-    }
-    off = warp_sum(off);
-    dia = warp_sum(dia);
-    if ((tid & 31) == 0) { red[tid >> 5] = off; }
-    __syncthreads();
-    if (tid == 0) {
-      double o = 0.0;
-      for (int w = 0; w < nt / 32; ++w) o += red[w];
-      red[31] = o;
-    }
-    __syncthreads();
-    const double offsum = red[31];
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = dia;
-    __syncthreads();
-    if (tid == 0) {
-      double dd = 0.0;
-      for (int w = 0; w < nt / 32; ++w) dd += red[w];
-      done = !(offsum > tol * tol * dd);
-    }
+    const int done = rotations == 0;   // read after the round's final barrier
     __syncthreads();
     if (done) break;
-    __syncthreads();
   }
   // sort descending (stable in index) and write out
   for (int i = tid; i < k; i += nt) {
@@ -304,6 +297,41 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, int use_sm
     }
     evals[rank] = (double)ev;
     for (int r = 0; r < k; ++r) Wout[r * k + rank] = (double)W[r * k + i];
+  }
+}
+
+// Rayleigh quotients lambda_j = w_j^T G w_j / w_j^T w_j in double (one block per vector): turns
+// float Jacobi eigenvectors (orthonormal to ~1e-6) into eigenvalues accurate to ~1e-12.
+__global__ void rayleigh_kernel(const double* G, int k, const double* W, double* lam) {
+  __shared__ double sh[2][32];
+  const int j = blockIdx.x;
+  double num = 0.0, den = 0.0;
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    double gw = 0.0;
+    for (int c = 0; c < k; ++c) gw = fma(G[r * k + c], W[c * k + j], gw);
+    const double wr = W[r * k + j];
+    num = fma(wr, gw, num);
+    den = fma(wr, wr, den);
+  }
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = num; sh[1][threadIdx.x >> 5] = den; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { a += sh[0][w2]; b += sh[1][w2]; }
+    lam[j] = a / b;
+  }
+}
+
+// sort (lam, columns of W) descending by lam, stable in the column index
+__global__ void sort_eig_kernel(const double* lam, const double* W, int k, double* evals, double* Wout) {
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double ev = lam[i];
+    int rank = 0;
+    for (int j = 0; j < k; ++j) rank += (lam[j] > ev) || (lam[j] == ev && j < i);
+    evals[rank] = ev;
+    for (int r = 0; r < k; ++r) Wout[r * k + rank] = W[r * k + i];
   }
 }
 
@@ -518,18 +546,39 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
     g = rs_scratch(ctx, SCR_EIG, bytes);
     if (!g) return RS_ENOMEM;
   }
-  const int threads = 1024;
+  const int threads = k <= 16 ? 256 : 1024;   // at least 4 k threads (one column per thread per pair group)
   const size_t shm = smem ? bytes : 0;
   if (prec == RS_F64) {
-    RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     double* Ag = static_cast<double*>(g);
-    jacobi_kernel<double><<<1, threads, shm, ctx->stream>>>(G, (int)k, Ag, Ag ? Ag + k * k : nullptr, smem ? 1 : 0,
-                                                            1e-15, 40, evals, W);
+    if (smem) {
+      RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)shm));
+      jacobi_kernel<double, true><<<1, threads, shm, ctx->stream>>>(G, (int)k, nullptr, nullptr, 1e-15, 8.0, 30,
+                                                                    evals, W);
+    } else {
+      jacobi_kernel<double, false><<<1, threads, 0, ctx->stream>>>(G, (int)k, Ag, Ag + k * k, 1e-15, 8.0, 30, evals,
+                                                                   W);
+    }
   } else {
-    RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    // float iterations, then double Rayleigh quotients of the float eigenvectors and a re-sort
+    double* tmp = static_cast<double*>(rs_scratch(ctx, SCR_RED, (size_t)(k * k + 2 * k) * sizeof(double)));
+    if (!tmp) return RS_ENOMEM;
+    double* Wt = tmp;
+    double* lam0 = tmp + k * k;
+    double* lam1 = lam0 + k;
     float* Ag = static_cast<float*>(g);
-    jacobi_kernel<float><<<1, threads, shm, ctx->stream>>>(G, (int)k, Ag, Ag ? Ag + k * k : nullptr, smem ? 1 : 0,
-                                                           1e-7, 40, evals, W);
+    if (smem) {
+      RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)shm));
+      jacobi_kernel<float, true><<<1, threads, shm, ctx->stream>>>(G, (int)k, nullptr, nullptr, 1e-6, 8.0, 30, lam0,
+                                                                   Wt);
+    } else {
+      jacobi_kernel<float, false><<<1, threads, 0, ctx->stream>>>(G, (int)k, Ag, Ag + k * k, 1e-6, 8.0, 30, lam0, Wt);
+    }
+    RS_LAUNCH_CHECK(ctx);
+    rayleigh_kernel<<<(unsigned)k, 128, 0, ctx->stream>>>(G, (int)k, Wt, lam1);
+    RS_LAUNCH_CHECK(ctx);
+    sort_eig_kernel<<<1, 256, 0, ctx->stream>>>(lam1, Wt, (int)k, evals, W);
   }
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
@@ -541,19 +590,25 @@ template <typename T>
 static int orthonormalize_t(rs_ctx* ctx, const T* Y, int64_t d, int64_t k, T* Q) {
   double* G = static_cast<double*>(rs_scratch(ctx, SCR_GRAM, k * k * sizeof(double)));
   T* tmp = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, d * k * sizeof(T)));
-  if (!G || !tmp) return RS_ENOMEM;
-  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-  const int warps = 8;
-  const size_t shm = warps * k * sizeof(double);
+  T* Linv = static_cast<T*>(rs_scratch(ctx, SCR_LINV, k * k * sizeof(T)));
+  if (!G || !tmp || !Linv) return RS_ENOMEM;
+  const size_t bytes = 2 * (size_t)k * k * sizeof(double);
+  const bool smem = bytes <= 160 * 1024;
+  double* buf = nullptr;
+  if (!smem) {
+    buf = static_cast<double*>(rs_scratch(ctx, SCR_EIG, bytes));
+    if (!buf) return RS_ENOMEM;
+  }
+  const size_t shm = smem ? bytes : 0;
+  RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   const T* src = Y;
   for (int pass = 0; pass < 2; ++pass) {
     T* dst = pass == 0 ? tmp : Q;
     RS_TRY(launch_gram<T>(ctx, d, k, k, src, k, src, k, 1.0, G));
-    chol_kernel<<<1, 1024, 0, ctx->stream>>>(G, (int)k, ctx->d_status);
+    chol_inv_kernel<T><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Linv, ctx->d_status);
     RS_LAUNCH_CHECK(ctx);
-    const int blocks = (int)std::min<int64_t>((d + warps - 1) / warps, (int64_t)ctx->num_sms * 4);
-    trsm_rows_kernel<T><<<blocks, 32 * warps, shm, ctx->stream>>>(src, d, (int)k, G, dst);
-    RS_LAUNCH_CHECK(ctx);
+    // Q = Y L^{-T}: B(p, j) = Linv[j][p]
+    RS_TRY(launch_gemm<T>(ctx, d, k, k, 1.0, src, k, 1, Linv, 1, k, 0.0, nullptr, 0, dst, k, nullptr));
     src = dst;
   }
   return RS_OK;
@@ -615,28 +670,43 @@ static int sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
   const int64_t q = std::max(1, p->q_blocks);
   const int64_t kq = k * q;
   if (kq > std::min<int64_t>(d, 256)) return rs_fail(RS_EINVAL, "rs_sketch: k * q_blocks = %lld exceeds min(d, 256)", (long long)kq);
-  T* K = static_cast<T*>(rs_scratch(ctx, SCR_Y, d * kq * sizeof(T)));
-  T* Qm = static_cast<T*>(rs_scratch(ctx, SCR_Q, d * kq * sizeof(T)));
-  if (!K || !Qm) return RS_ENOMEM;
-  RS_TRY(range_sketch_t<T>(ctx, X, p, Qm));   // Y0 (d x k) into Qm, then spread into K's columns
-  // K[:, 0:k] = Y0; K[:, jk:(j+1)k] = C K[:, (j-1)k:jk] = X^T (X Y_{j-1}) / n
-  RS_CUDA_TRY(cudaMemcpy2DAsync(K, kq * sizeof(T), Qm, k * sizeof(T), k * sizeof(T), d, cudaMemcpyDeviceToDevice,
-                                ctx->stream));
+  // The Krylov space K = [A Pi, C A Pi, ..., C^{q-1} A Pi] of Alg. 2 (C = A A^T) is built block by
+  // block: Q_0 = orth(A Pi); Y_j = C Q_{j-1} with the earlier blocks projected out (twice), Q_j =
+  // orth(Y_j).  [Q_0 .. Q_{q-1}] is then an orthonormal basis of K without forming the badly scaled
+  // powers C^j A Pi explicitly.
+  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  T* Yk = static_cast<T*>(rs_scratch(ctx, SCR_Y, d * k * sizeof(T)));
+  T* Qall = static_cast<T*>(rs_scratch(ctx, SCR_Q, 2 * d * kq * sizeof(T)));
+  if (!Yk || !Qall) return RS_ENOMEM;
+  T* Qb = Qall;              // q blocks, each d x k contiguous
+  T* Qm = Qall + d * kq;     // d x kq row-major basis
+  RS_TRY(range_sketch_t<T>(ctx, X, p, Yk));
+  RS_TRY(orthonormalize_t<T>(ctx, Yk, d, k, Qb));
   if (q > 1) {
     T* B = static_cast<T*>(rs_scratch(ctx, SCR_B, n * k * sizeof(T)));
     double* Gd = static_cast<double*>(rs_scratch(ctx, SCR_GRAM, d * k * sizeof(double)));
-    T* Yt = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, d * k * sizeof(T)));
-    if (!B || !Gd || !Yt) return RS_ENOMEM;
+    double* Pd = static_cast<double*>(rs_scratch(ctx, SCR_MISC, k * k * sizeof(double)));
+    T* Pt = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, k * k * sizeof(T)));
+    if (!B || !Gd || !Pd || !Pt) return RS_ENOMEM;
     for (int64_t j = 1; j < q; ++j) {
-      RS_TRY(launch_gemm<T>(ctx, n, k, d, 1.0, static_cast<const T*>(X->data), X->ld, 1, K + (j - 1) * k, kq, 1, 0.0,
-                            nullptr, 0, B, k, nullptr));
+      const T* Qprev = Qb + (j - 1) * d * k;
+      RS_TRY(launch_gemm<T>(ctx, n, k, d, 1.0, static_cast<const T*>(X->data), X->ld, 1, Qprev, k, 1, 0.0, nullptr,
+                            0, B, k, nullptr));
       RS_TRY(launch_gram<T>(ctx, n, d, k, static_cast<const T*>(X->data), X->ld, B, k, 1.0 / (double)n, Gd));
-      RS_TRY(to_T<T>(ctx, Gd, d * k, Yt));
-      RS_CUDA_TRY(cudaMemcpy2DAsync(K + j * k, kq * sizeof(T), Yt, k * sizeof(T), k * sizeof(T), d,
-                                    cudaMemcpyDeviceToDevice, ctx->stream));
+      RS_TRY(to_T<T>(ctx, Gd, d * k, Yk));
+      for (int pass = 0; pass < 2; ++pass)
+        for (int64_t i = 0; i < j; ++i) {
+          const T* Qi = Qb + i * d * k;
+          RS_TRY(launch_gram<T>(ctx, d, k, k, Qi, k, Yk, k, 1.0, Pd));   // Q_i^T Y_j
+          RS_TRY(to_T<T>(ctx, Pd, k * k, Pt));
+          RS_TRY(launch_gemm<T>(ctx, d, k, k, -1.0, Qi, k, 1, Pt, k, 1, 1.0, Yk, k, Yk, k, nullptr));
+        }
+      RS_TRY(orthonormalize_t<T>(ctx, Yk, d, k, Qb + j * d * k));
     }
   }
-  RS_TRY(orthonormalize_t<T>(ctx, K, d, kq, Qm));
+  for (int64_t j = 0; j < q; ++j)
+    RS_CUDA_TRY(cudaMemcpy2DAsync(Qm + j * k, kq * sizeof(T), Qb + j * d * k, k * sizeof(T), k * sizeof(T), d,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
   RS_TRY(ritz_t<T>(ctx, X, Qm, kq, k, V, sigma2));
   int st = 0;
   RS_TRY(read_status(ctx, &st));
@@ -779,6 +849,7 @@ int rs_range_sketch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
 int rs_orthonormalize(rs_ctx* ctx, const void* Y, int64_t d, int64_t k, int32_t dtype, void* Q) {
   RS_TRY(rs_enter(ctx));
   RS_CHECK_ARG(Y && Q && d >= 1 && k >= 1 && k <= d && k <= 256, "rs_orthonormalize: bad arguments");
+  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   int rc;
   if (dtype == RS_F64) rc = orthonormalize_t<double>(ctx, static_cast<const double*>(Y), d, k, static_cast<double*>(Q));
   else if (dtype == RS_F32) rc = orthonormalize_t<float>(ctx, static_cast<const float*>(Y), d, k, static_cast<float*>(Q));

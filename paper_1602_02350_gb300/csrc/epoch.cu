@@ -1,0 +1,559 @@
+// The inner loop of Alg. 1 (m sequential variance-reduced steps of one epoch) on the GPU.
+//
+// Inside one block of B consecutive steps the recursion is, with delta = w - w_bar, z_j the
+// component row sampled at step j of the block and kappa_j = gamma_{i_j} / (N q_{i_j}):
+//   a_j              = kappa_j z_j^T delta_{before j}
+//   delta_{after j}  = delta_{before j} - eta a_j z_j - eta mu
+// Writing p_j = z_j^T delta_{t0} (delta at the block start) and h_j = z_j^T mu gives
+//   a = R (p - eta (j h)),   R = (I + eta K L)^{-1} K,
+// with L the strictly lower triangle of the block's Gram matrix Z_b Z_b^T and K = diag(kappa).
+// R and c = -eta R (j h) depend only on the sampled rows and mu, so epoch_prep_kernel forms
+// them for every block at once.  epoch_chain_kernel then runs the blocks in order on one
+// thread-block cluster: per block, p = Z_b delta (one exchange of partial dot products through
+// distributed shared memory), a = R p + c, and the rank-B update of delta and of the running
+// sum of the iterates (for the epoch average).  Every iterate of the step-by-step recursion
+// is represented exactly; only the rounding differs.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int kBlk = 64;     // steps per block
+constexpr int kCsMax = 16;   // largest cluster
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ------------------------------------------------------------------ per-block preparation
+// One thread block per block of steps.  Rows 0..B-1 of the staged tile are the sampled rows
+// (zero beyond the last step), row B is mu, rows B+1..B+3 are zero.
+template <typename T>
+__global__ void __launch_bounds__(256) epoch_prep_kernel(const T* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                                         int64_t n, double lam, const uint32_t* __restrict__ idx,
+                                                         const T* __restrict__ inv_nq, int64_t m, double eta,
+                                                         const T* __restrict__ mu, T* __restrict__ Rt,
+                                                         T* __restrict__ cvec) {
+  constexpr int B = kBlk, RP = B + 4;
+  constexpr int E = 16 / sizeof(T);
+  constexpr int CH = 64;              // columns per staged chunk
+  constexpr int TS = CH + E;          // tile row stride (16-byte multiple, skews banks)
+  extern __shared__ __align__(16) unsigned char pr_sh[];
+  T* tile = reinterpret_cast<T*>(pr_sh);        // [2][RP][TS]
+  T* G = tile + 2 * RP * TS;                    // [RP][RP + 1]
+  T* R = G + RP * (RP + 1);                     // [B][B + 1]   R[j][c]
+  T* acc = R + B * (B + 1);                     // [B][B + 1]
+  __shared__ T kap[B];
+  __shared__ int64_t rowid[B];
+  const int tid = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  const int64_t t0 = b * B;
+  const int Bb = (int)min64(B, m - t0);
+  const T Nn = (T)((double)N / (double)n), lN = (T)(lam * (double)N);
+  if (tid < B) {
+    if (tid < Bb) {
+      const uint32_t i = min(idx[t0 + tid], (uint32_t)(N - 1));   // indices are < N by contract
+      rowid[tid] = i;
+      kap[tid] = (i < (uint64_t)n ? Nn : lN) * inv_nq[t0 + tid];
+    } else {
+      rowid[tid] = -1;
+      kap[tid] = T(0);
+    }
+  }
+  __syncthreads();
+  const int nch = (int)((d + CH - 1) / CH);
+  auto stage = [&](int ch, int buf) {
+    T* dst = tile + buf * RP * TS;
+    const int64_t cbase = (int64_t)ch * CH;
+    for (int e = tid; e < RP * (CH / E); e += blockDim.x) {
+      const int r = e / (CH / E), q = e % (CH / E);
+      const int64_t col = cbase + q * E;
+      const T* src = Z;
+      int bytes = 0;
+      if (col < d) {
+        const int valid = (int)min64(E, d - col) * (int)sizeof(T);
+        if (r < B && r < Bb) { src = Z + rowid[r] * ld + col; bytes = valid; }
+        else if (r == B) { src = mu + col; bytes = (reinterpret_cast<uintptr_t>(mu + col) & 15) ? 0 : valid; }
+      }
+      cp_async16(dst + r * TS + q * E, src, bytes);
+    }
+    cp_async_commit();
+  };
+  // mu may not be 16-byte aligned at every chunk: stage it with plain loads when it is not
+  const bool mu_aligned = (reinterpret_cast<uintptr_t>(mu) & 15) == 0;
+  // lower-triangular 4x4 tiles of the RP x RP Gram matrix (17*18/2 = 153 tiles)
+  int TI = -1, TJ = -1;
+  {
+    int t = tid, I = 0;
+    while (I < RP / 4 && t > I) { t -= I + 1; ++I; }
+    if (I < RP / 4) { TI = I; TJ = t; }
+  }
+  T a4[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a4[i][j] = T(0);
+  stage(0, 0);
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) stage(ch + 1, (ch + 1) & 1);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    T* tl = tile + (ch & 1) * RP * TS;
+    if (!mu_aligned) {
+      for (int c = tid; c < CH; c += blockDim.x) {
+        const int64_t col = (int64_t)ch * CH + c;
+        tl[B * TS + c] = col < d ? mu[col] : T(0);
+      }
+      __syncthreads();
+    }
+    if (TI >= 0) {
+      using V = typename Vec<T>::type;
+#pragma unroll 4
+      for (int c = 0; c < CH; c += E) {
+        T x[4][E], y[4][E];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vec_to_arr(*reinterpret_cast<const V*>(tl + (TI * 4 + i) * TS + c), x[i]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) vec_to_arr(*reinterpret_cast<const V*>(tl + (TJ * 4 + j) * TS + c), y[j]);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a4[i][j] = fma(x[i][e], y[j][e], a4[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (TI >= 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gi = TI * 4 + i, gj = TJ * 4 + j;
+        G[gi * (RP + 1) + gj] = a4[i][j];
+        G[gj * (RP + 1) + gi] = a4[i][j];
+      }
+  }
+  for (int e = tid; e < B * (B + 1); e += blockDim.x) {
+    R[e] = T(0);
+    acc[e] = T(0);
+  }
+  __syncthreads();
+  // R = (I + eta K L)^{-1} K row by row: row l is final once rows < l have been folded into acc
+  const T et = (T)eta;
+  const int cc = tid & (B - 1), jg = tid >> 6;      // column and row group of this thread
+  for (int l = 0; l < Bb; ++l) {
+    if (tid <= l) R[l * (B + 1) + tid] = (tid == l) ? kap[l] : -et * kap[l] * acc[l * (B + 1) + tid];
+    __syncthreads();
+    if (cc <= l) {
+      const T rl = R[l * (B + 1) + cc];
+      for (int j = l + 1 + jg; j < Bb; j += 4) acc[j * (B + 1) + cc] = fma(G[j * (RP + 1) + l], rl, acc[j * (B + 1) + cc]);
+    }
+    __syncthreads();
+  }
+  // c_j = -eta sum_{l <= j} R[j][l] l h_l with h_l = mu^T z_l = G[B][l]
+  if (tid < B) {
+    const int j = tid;
+    T s = T(0);
+    for (int l = 0; l <= j && l < Bb; ++l) s = fma(R[j * (B + 1) + l], (T)l * G[B * (RP + 1) + l], s);
+    cvec[b * B + j] = j < Bb ? -et * s : T(0);
+  }
+  T* Rout = Rt + b * (int64_t)B * B;
+  for (int e = tid; e < B * B; e += blockDim.x) {
+    const int l = e / B, j = e % B;
+    Rout[e] = R[j * (B + 1) + l];   // transposed: Rt[l][j] = R[j][l]
+  }
+}
+
+// ------------------------------------------------------------------ sequential chain
+// One cluster of CS blocks; block r owns columns [r CW, (r+1) CW) of delta (CW = 32 QN).
+// Per block of steps each block pushes its partial dot products straight from registers into
+// every block's receive buffer with st.async, which signals the receiver's local mbarrier; the
+// receivers sum the CS partials in rank order, so every block derives bit-identical a_j.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arm(uint64_t* bar, uint32_t tx_bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(tx_bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 16-byte remote store into another block's shared memory that completes tx bytes on its mbarrier
+__device__ __forceinline__ void st_async16(uint32_t raddr, uint32_t rbar, const uint32_t* v) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];\n" ::"r"(raddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(rbar)
+               : "memory");
+}
+
+constexpr long long kWaitCycles = 4000000000LL;   // about two seconds: a wait this long is a fault
+
+template <typename T, int STAGES, int QN>
+__global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                                          const uint32_t* __restrict__ idx, int64_t m,
+                                                          const T* __restrict__ Rt, const T* __restrict__ cvec,
+                                                          double eta, const T* __restrict__ mu,
+                                                          const T* __restrict__ wbar, int average,
+                                                          T* __restrict__ wnext, int* status) {
+  constexpr int B = kBlk;
+  constexpr int E = 16 / sizeof(T);
+  constexpr int CW = 32 * QN;               // columns owned by this block
+  constexpr int NCH = CW / E;               // 16-byte chunks per row slice
+  constexpr int NT = 256;
+  constexpr int TPC = NT / CW > 0 ? NT / CW : 1;   // lanes per column in the update (same warp)
+  constexpr int JPT = B / TPC;                      // steps per lane in the update
+  constexpr int CPW = 32 / TPC;                     // columns per warp in the update
+  constexpr int W16 = 8 * (int)sizeof(T) / 16;      // 16-byte pieces of one warp's 8 partials
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char ch_sh[];
+  // row stride of the staged slices: CW + CPW puts the TPC lanes that share a column (which
+  // read rows j, j+1, .., j+TPC-1 in the update) on distinct shared-memory banks
+  constexpr int ZS = CW + (TPC > 1 ? CPW : 0);
+  T* Zs = reinterpret_cast<T*>(ch_sh);                     // [STAGES][B][ZS]
+  T* Rs = Zs + (size_t)STAGES * B * ZS;                    // [STAGES][B][B]  (Rt layout: [l][j])
+  T* Cs = Rs + (size_t)STAGES * B * B;                     // [STAGES][B]
+  T* recv = Cs + (size_t)STAGES * B;                       // [2][kCsMax][B] partial dots from each rank
+  double* Ssum = reinterpret_cast<double*>(recv + 2 * kCsMax * B);   // [CW]
+  T* dl = reinterpret_cast<T*>(Ssum + CW);                 // [CW]
+  T* mus = dl + CW;                                        // [CW]
+  T* pv = mus + CW;                                        // [B]
+  T* av = pv + B;                                          // [B]
+  T* part4 = av + B;                                       // [4][B] partial sums of R p
+  uint32_t* srow = reinterpret_cast<uint32_t*>(part4 + 4 * B);   // [STAGES][B]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + STAGES * B);   // [2]
+  __shared__ int aborted;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c0 = (int64_t)rank * CW;
+  const int cwid = (int)max64(0, min64(CW, d - c0));
+  const int64_t nblk = (m + B - 1) / B;
+  const T et = (T)eta;
+  const uint32_t tx_per_block = (uint32_t)(CS * B * sizeof(T));
+
+  for (int c = tid; c < CW; c += NT) {
+    dl[c] = T(0);
+    Ssum[c] = 0.0;
+    mus[c] = c < cwid ? mu[c0 + c] : T(0);
+  }
+  auto fetch_rows = [&](int64_t blk) -> uint32_t {
+    const int64_t t = blk * B + tid;
+    return (tid < B && t < m) ? (uint32_t)min64((int64_t)idx[t], N - 1) : 0xFFFFFFFFu;
+  };
+  for (int s = 0; s < STAGES; ++s)
+    if (tid < B) srow[s * B + tid] = fetch_rows(s);
+  uint32_t pend_row = fetch_rows(STAGES);
+  if (tid == 0) {
+    aborted = 0;
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    mbar_arm(&mbar[0], tx_per_block);
+    if (nblk > 1) mbar_arm(&mbar[1], tx_per_block);
+  }
+  __syncthreads();
+
+  // rows beyond the last step and columns beyond d are zero-filled (source size 0)
+  auto load_block = [&](int64_t blk) {
+    const int slot = (int)(blk % STAGES);
+    T* zdst = Zs + (size_t)slot * B * ZS;
+    const uint32_t* rows = srow + slot * B;
+#pragma unroll
+    for (int r = 0; r < B / 8; ++r) {
+      const int j = warp + 8 * r;
+      const uint32_t row = rows[j];
+      for (int q = lane; q < NCH; q += 32) {
+        const int col = q * E;
+        int bytes = 0;
+        const T* src = Z;
+        if (row != 0xFFFFFFFFu && col < cwid) {
+          bytes = min(E, cwid - col) * (int)sizeof(T);
+          src = Z + (int64_t)row * ld + c0 + col;
+        }
+        cp_async16(zdst + j * ZS + col, src, bytes);
+      }
+    }
+    const T* rsrc = Rt + blk * (int64_t)B * B;
+    T* rdst = Rs + (size_t)slot * B * B;
+#pragma unroll
+    for (int e = tid; e < B * B / E; e += NT) cp_async16(rdst + e * E, rsrc + e * E, 16);
+    if (tid < B / E) cp_async16(Cs + (size_t)slot * B + tid * E, cvec + blk * B + tid * E, 16);
+  };
+
+#pragma unroll
+  for (int s = 0; s < STAGES - 1; ++s) {
+    if (s < nblk) load_block(s);
+    cp_async_commit();
+  }
+  cluster.sync();   // every block's mbarriers are initialised before any remote store
+
+  // remote addresses this lane pushes to: receiver = lane (lanes >= CS idle)
+  const int dst = lane < CS ? lane : 0;
+  const uint32_t recv_remote = map_rank(smem_u32(recv), dst);
+  const uint32_t bar_remote0 = map_rank(smem_u32(&mbar[0]), dst);
+  const uint32_t bar_remote1 = map_rank(smem_u32(&mbar[1]), dst);
+
+  for (int64_t blk = 0; blk < nblk; ++blk) {
+    // row indices are read one block ahead of when they enter the ring, so the load's latency is
+    // hidden behind a whole block of steps
+    const uint32_t next_row = pend_row;
+    pend_row = fetch_rows(blk + STAGES + 1);
+    cp_async_wait<STAGES - 2>();
+    __syncthreads();
+    if (blk + STAGES - 1 < nblk) load_block(blk + STAGES - 1);
+    cp_async_commit();
+    const int slot = (int)(blk % STAGES);
+    const int par = (int)(blk & 1);
+    const int Bb = (int)min64(B, m - blk * B);
+    const T* zs = Zs + (size_t)slot * B * ZS;
+    // partial p_j over this block's columns for rows 8 warp .. 8 warp + 7, pushed to every rank
+    {
+      T dv[QN];
+#pragma unroll
+      for (int q = 0; q < QN; ++q) dv[q] = dl[lane + 32 * q];
+      T part[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const T* zr = zs + (8 * warp + r) * ZS + lane;
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < QN; ++q) s = fma(zr[32 * q], dv[q], s);
+        part[r] = s;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) part[r] += __shfl_xor_sync(0xffffffffu, part[r], o);
+      if (lane < CS) {
+        uint32_t pw[8 * sizeof(T) / 4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if constexpr (sizeof(T) == 8) {
+            pw[2 * r] = (uint32_t)__double2loint(part[r]);
+            pw[2 * r + 1] = (uint32_t)__double2hiint(part[r]);
+          } else {
+            pw[r] = __float_as_uint(part[r]);
+          }
+        }
+        const uint32_t base = recv_remote + (uint32_t)(((par * kCsMax + rank) * B + 8 * warp) * sizeof(T));
+        const uint32_t rbar = par ? bar_remote1 : bar_remote0;
+#pragma unroll
+        for (int h = 0; h < W16; ++h) st_async16(base + 16 * h, rbar, pw + 4 * h);
+      }
+    }
+    if (tid < B) srow[slot * B + tid] = next_row;    // this slot now holds block blk + STAGES
+    // wait for the CS partial vectors of this block (bounded), then p = sum over ranks
+    if (!aborted) {
+      const long long t0c = clock64();
+      while (!mbar_try_wait(&mbar[par], (uint32_t)((blk >> 1) & 1))) {
+        if (clock64() - t0c > kWaitCycles) {
+          atomicOr(status, STATUS_TIMEOUT);
+          aborted = 1;
+          break;
+        }
+      }
+    }
+    if (tid < B) {
+      const T* rv = recv + (size_t)par * kCsMax * B + tid;
+      T s = T(0);
+      for (int r = 0; r < CS; ++r) s += rv[r * B];   // rank order: identical in every block
+      pv[tid] = s;
+    }
+    __syncthreads();
+    if (tid == 0 && blk + 2 < nblk) mbar_arm(&mbar[par], tx_per_block);   // next use: block blk + 2
+    // a = R p + c: thread (j, h) sums the terms l = h, h+4, ... <= j (R is lower triangular, zero
+    // above the diagonal, so the loop may run to the end of its group); fixed combine order below
+    {
+      const int j = tid & (B - 1), h = tid >> 6;
+      const T* rs = Rs + (size_t)slot * B * B + j;
+      T s0 = T(0), s1 = T(0);
+      const int lend = j + 1;
+      int l = h;
+      for (; l + 4 < lend; l += 8) {
+        s0 = fma(rs[l * B], pv[l], s0);
+        s1 = fma(rs[(l + 4) * B], pv[l + 4], s1);
+      }
+      if (l < lend) s0 = fma(rs[l * B], pv[l], s0);
+      part4[h * B + j] = s0 + s1;
+    }
+    __syncthreads();
+    if (tid < B)
+      av[tid] = Cs[(size_t)slot * B + tid] + ((part4[tid] + part4[B + tid]) + (part4[2 * B + tid] + part4[3 * B + tid]));
+    __syncthreads();
+    // rank-B update: lanes g = 0..TPC-1 of a column take steps j = g, g + TPC, ... and combine by
+    // shuffles (the padded row stride keeps their shared-memory reads on distinct banks)
+    {
+      const int c = warp * CPW + (lane % CPW), g = lane / CPW;
+      T u = T(0), w = T(0);
+      T wt = (T)(Bb - g);                       // weight B_b - j of the running-sum term
+#pragma unroll 8
+      for (int jj = 0; jj < JPT; ++jj) {
+        const int j = g + TPC * jj;
+        const T az = av[j] * zs[j * ZS + c];
+        u += az;
+        w = fma(wt, az, w);
+        wt -= T(TPC);
+      }
+#pragma unroll
+      for (int o = CPW; o < 32; o <<= 1) {
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+      }
+      if (g == 0) {
+        const T bbT = (T)Bb;
+        const T tri = (T)(0.5 * (double)Bb * (double)(Bb + 1));
+        const T dold = dl[c];
+        Ssum[c] += (double)(bbT * dold - et * (mus[c] * tri + w));
+        dl[c] = dold - et * (bbT * mus[c] + u);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  cluster.sync();   // no block leaves while remote stores to it could still be in flight
+  for (int c = tid; c < cwid; c += NT) {
+    const double v = average ? Ssum[c] / (double)m : (double)dl[c];
+    wnext[c0 + c] = (T)((double)wbar[c0 + c] + v);
+  }
+}
+
+struct ChainPlan {
+  int cs = 0, qn = 0, stages = 0;
+  size_t shm = 0;
+};
+
+template <typename T>
+size_t chain_smem(int qn, int stages) {
+  const int CW = 32 * qn;
+  const int TPC = std::max(1, 256 / CW);
+  const int ZS = CW + (TPC > 1 ? 32 / TPC : 0);
+  return (size_t)stages * kBlk * ZS * sizeof(T) + (size_t)stages * kBlk * kBlk * sizeof(T) +
+         (size_t)stages * kBlk * sizeof(T) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + (size_t)CW * sizeof(double) +
+         2 * (size_t)CW * sizeof(T) + 6 * (size_t)kBlk * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
+         2 * sizeof(uint64_t) + 64;
+}
+
+// Cluster size: enough blocks that each owns at most 64 columns, up to 16 blocks (then up to
+// 256 columns each).  RS_CHAIN_CLUSTER overrides the cluster size (1, 2, 4, 8 or 16).
+int choose_cluster(int64_t d) {
+  const char* env = std::getenv("RS_CHAIN_CLUSTER");
+  if (env) return std::atoi(env);
+  int cs = 1;
+  while (cs < kCsMax && (d + cs - 1) / cs > 64) cs *= 2;
+  return cs;
+}
+
+template <typename T>
+ChainPlan plan_chain(int64_t d, int cs) {
+  ChainPlan p;
+  if (cs < 1 || cs > kCsMax || (cs & (cs - 1))) return p;
+  const int64_t per = (d + cs - 1) / cs;
+  int qn = per <= 64 ? 2 : (per <= 128 ? 4 : (per <= 256 ? 8 : 0));
+  if (!qn) return p;
+  for (int st = 4; st >= 2; --st) {
+    const size_t shm = chain_smem<T>(qn, st);
+    if (shm <= 200 * 1024) {
+      p.cs = cs;
+      p.qn = qn;
+      p.stages = st;
+      p.shm = shm;
+      return p;
+    }
+  }
+  return p;
+}
+
+template <typename T, int ST, int QN>
+int launch_chain(rs_ctx* ctx, const ChainPlan& pl, const T* Z, int64_t N, int64_t ld, int64_t d,
+                 const uint32_t* idx, int64_t m, const T* Rt, const T* cv, double eta, const T* mu, const T* wbar,
+                 int average, T* wnext) {
+  auto kern = epoch_chain_kernel<T, ST, QN>;
+  RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
+  if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.cs, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = pl.shm;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return RS_EUNSUPPORTED;   // this cluster shape cannot be placed on the device: caller tries a smaller one
+  }
+  RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, Z, N, ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext,
+                                 ctx->d_status));
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+}  // namespace
+
+template <typename T>
+int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
+                 int64_t m, double eta, const T* wbar, const T* mu, int average, T* wnext) {
+  const int64_t N = Z->n, d = Z->d;
+  const T* Zd = static_cast<const T*>(Z->data);
+  const int64_t nblk = (m + kBlk - 1) / kBlk;
+  T* Rt = static_cast<T*>(rs_scratch(ctx, SCR_R, (size_t)nblk * kBlk * kBlk * sizeof(T)));
+  T* cv = static_cast<T*>(rs_scratch(ctx, SCR_C, (size_t)nblk * kBlk * sizeof(T)));
+  if (!Rt || !cv) return RS_ENOMEM;
+  constexpr int RP = kBlk + 4, CH = 64, E = 16 / sizeof(T);
+  const size_t pshm = (size_t)(2 * RP * (CH + E) + RP * (RP + 1) + 2 * kBlk * (kBlk + 1)) * sizeof(T);
+  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+  epoch_prep_kernel<T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m, eta, mu,
+                                                                   Rt, cv);
+  RS_LAUNCH_CHECK(ctx);
+  for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
+    const ChainPlan pl = plan_chain<T>(d, cs);
+    if (!pl.cs) continue;
+    int rc = RS_EUNSUPPORTED;
+#define RS_CHAIN(ST, QN)                                                                                          \
+  if (pl.stages == ST && pl.qn == QN)                                                                             \
+    rc = launch_chain<T, ST, QN>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext);
+    RS_CHAIN(4, 2) RS_CHAIN(4, 4) RS_CHAIN(4, 8) RS_CHAIN(3, 2) RS_CHAIN(3, 4) RS_CHAIN(3, 8)
+    RS_CHAIN(2, 2) RS_CHAIN(2, 4) RS_CHAIN(2, 8)
+#undef RS_CHAIN
+    if (rc != RS_EUNSUPPORTED) return rc;
+  }
+  return rs_fail(RS_EUNSUPPORTED, "rs_svrg_epoch: no thread-block cluster layout fits d = %lld", (long long)d);
+}
+
+template int svrg_epoch_t<float>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const float*, int64_t,
+                                 double, const float*, const float*, int, float*);
+template int svrg_epoch_t<double>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const double*, int64_t,
+                                  double, const double*, const double*, int, double*);

@@ -23,7 +23,6 @@ int precondition_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* V, const 
 
 namespace {
 
-constexpr int kBlk = 64;   // inner steps per block of the blocked recursion
 
 int blocks_for(rs_ctx* ctx, int64_t work, int threads = 256) {
   int64_t g = (work + threads - 1) / threads;
@@ -100,25 +99,39 @@ __global__ void __launch_bounds__(256) fullgrad_kernel(const T* __restrict__ Z, 
   }
 }
 
+// mu[c] = sum over the per-block partials, 32 columns per thread block: eight interleaved
+// partial sums per column, then a fixed-order sum of the eight (deterministic).
 template <typename T>
-__global__ void fullgrad_reduce_kernel(const T* part, int np, int64_t d, T* mu, double* norm2_out) {
-  __shared__ double sh[32];
-  double nrm = 0.0;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < np; ++p) s += (double)part[(int64_t)p * d + c];
-    mu[c] = (T)s;
-    nrm += s * s;
+__global__ void __launch_bounds__(256) fullgrad_reduce_kernel(const T* __restrict__ part, int np, int64_t d,
+                                                              T* __restrict__ mu) {
+  __shared__ T sh[8][33];
+  const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+  T s = T(0);
+  if (c < d)
+    for (int p = g; p < np; p += 8) s += part[(int64_t)p * d + c];
+  sh[g][lane] = s;
+  __syncthreads();
+  if (g == 0 && c < d) {
+    T t = T(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += sh[q][lane];
+    mu[c] = t;
   }
-  if (norm2_out) {
-    nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2];
-      norm2_out[blockIdx.x] = t;   // launched with one block when norms are wanted
-    }
+}
+
+template <typename T>
+__global__ void norm2_kernel(const T* v, int64_t d, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) s += (double)v[c] * (double)v[c];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2];
+    *out = t;
   }
 }
 
@@ -139,261 +152,6 @@ template <typename T>
 __global__ void convert_kernel(const double* in, int64_t count, T* out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (T)in[e];
-}
-
-// ------------------------------------------------------------------ blocked inner loop
-//
-// Inside one block of B consecutive steps t0+1..t0+B the recursion of Alg. 1 is, with
-// delta = w - w_bar, z_j the sampled row of step j and kappa_j = gamma_{i_j} / (N q_{i_j}):
-//   a_j   = kappa_j z_j^T delta_{before j}
-//   delta_{after j} = delta_{before j} - eta a_j z_j - eta mu
-// so that a = R (p - eta (j h)) with p_j = z_j^T delta_{t0}, h_j = z_j^T mu and
-// R = (I + eta K L)^{-1} K, L the strictly lower part of the block's Gram matrix.
-// R and c = -eta R (j h) depend only on the sampled rows and mu, so every block's (R, c)
-// is formed in parallel before the sequential chain runs.
-
-// One thread block per block of steps: Gram of the B sampled rows and mu, then R and c.
-template <typename T>
-__global__ void __launch_bounds__(256) epoch_prep_kernel(const T* __restrict__ Z, int64_t ld, int64_t d, int64_t n,
-                                                         int64_t N, double lam, const uint32_t* __restrict__ idx,
-                                                         const T* __restrict__ inv_nq, int64_t m, double eta,
-                                                         const T* __restrict__ mu, T* __restrict__ Rt,
-                                                         T* __restrict__ cvec) {
-  constexpr int B = kBlk, RP = B + 4;   // rows 0..B-1 sampled rows, row B = mu, rows B+1.. zero
-  constexpr int CH = 32;                // columns per staged chunk
-  extern __shared__ unsigned char pr_sh[];
-  T* tile = reinterpret_cast<T*>(pr_sh);          // [RP][CH + 1]
-  T* G = tile + RP * (CH + 1);                    // [RP][RP]
-  T* R = G + RP * RP;                             // [B][B], R[j][c]
-  __shared__ T kap[B];
-  __shared__ int64_t rowid[B];
-  const int64_t b = blockIdx.x;
-  const int64_t t0 = b * B;
-  const int Bb = (int)min64(B, m - t0);
-  const int tid = threadIdx.x;
-  const T Nn = (T)((double)N / (double)n), lN = (T)(lam * (double)N);
-  for (int j = tid; j < B; j += blockDim.x) {
-    if (j < Bb) {
-      const uint32_t i = min(idx[t0 + j], (uint32_t)(N - 1));   // indices are < N by contract; never read outside Z
-      rowid[j] = i;
-      kap[j] = (i < (uint64_t)n ? Nn : lN) * inv_nq[t0 + j];
-    } else {
-      rowid[j] = -1;
-      kap[j] = T(0);
-    }
-  }
-  // lower-triangular 4x4 tiles of the RP x RP Gram matrix: 17*18/2 = 153 tiles
-  int TI = -1, TJ = -1;
-  {
-    int t = tid, I = 0;
-    while (I < RP / 4 && t > I) { t -= I + 1; ++I; }
-    if (I < RP / 4) { TI = I; TJ = t; }
-  }
-  T acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-  __syncthreads();
-  for (int64_t c0 = 0; c0 < d; c0 += CH) {
-    for (int e = tid; e < RP * CH; e += blockDim.x) {
-      const int r = e / CH, c = e % CH;
-      const int64_t col = c0 + c;
-      T v = T(0);
-      if (col < d) {
-        if (r < B) {
-          if (r < Bb) v = Z[rowid[r] * ld + col];
-        } else if (r == B) {
-          v = mu[col];
-        }
-      }
-      tile[r * (CH + 1) + c] = v;
-    }
-    __syncthreads();
-    if (TI >= 0) {
-#pragma unroll 4
-      for (int c = 0; c < CH; ++c) {
-        T a[4], bb[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = tile[(TI * 4 + i) * (CH + 1) + c];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bb[j] = tile[(TJ * 4 + j) * (CH + 1) + c];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
-      }
-    }
-    __syncthreads();
-  }
-  if (TI >= 0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int gi = TI * 4 + i, gj = TJ * 4 + j;
-        G[gi * RP + gj] = acc[i][j];
-        G[gj * RP + gi] = acc[i][j];
-      }
-  }
-  __syncthreads();
-  // column c of R = (I + eta K L)^{-1} K by forward substitution (independent per column)
-  const T et = (T)eta;
-  if (tid < B) {
-    const int c = tid;
-    for (int j = 0; j < B; ++j) R[j * B + c] = T(0);
-    if (c < Bb) {
-      R[c * B + c] = kap[c];
-      for (int j = c + 1; j < Bb; ++j) {
-        T s = T(0);
-        for (int l = c; l < j; ++l) s = fma(G[j * RP + l], R[l * B + c], s);
-        R[j * B + c] = -et * kap[j] * s;
-      }
-    }
-  }
-  __syncthreads();
-  // c_j = -eta sum_{l <= j} R[j][l] l h_l,  h_l = mu^T z_l = G[B][l]
-  T* Rout = Rt + b * (int64_t)B * B;
-  if (tid < B) {
-    const int j = tid;
-    T s = T(0);
-    for (int l = 0; l <= j && l < Bb; ++l) s = fma(R[j * B + l], (T)l * G[B * RP + l], s);
-    cvec[b * B + j] = j < Bb ? -et * s : T(0);
-  }
-  for (int e = tid; e < B * B; e += blockDim.x) {
-    const int l = e / B, j = e % B;
-    Rout[e] = R[j * B + l];   // transposed: Rt[l][j] = R[j][l]
-  }
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// Sequential chain over the blocks of one epoch, run by one thread-block cluster of CS blocks.
-// Block r of the cluster owns columns [r cw, (r+1) cw) of delta; per block of steps the partial
-// dot products p_j are exchanged through distributed shared memory (fixed summation order, so
-// every block computes bit-identical a_j).
-template <typename T, int STAGES>
-__global__ void __launch_bounds__(128) epoch_chain_kernel(const T* __restrict__ Z, int64_t N, int64_t ld, int64_t d, int cw,
-                                                          const uint32_t* __restrict__ idx, int64_t m,
-                                                          const T* __restrict__ Rt, const T* __restrict__ cvec,
-                                                          double eta, const T* __restrict__ mu,
-                                                          const T* __restrict__ wbar, int average, T* __restrict__ wnext) {
-  constexpr int B = kBlk;
-  constexpr int E = 16 / sizeof(T);
-  cg::cluster_group cluster = cg::this_cluster();
-  const int CS = (int)cluster.num_blocks();
-  const int rank = (int)cluster.block_rank();
-  extern __shared__ __align__(16) unsigned char ch_sh[];
-  T* Zs = reinterpret_cast<T*>(ch_sh);                    // [STAGES][B][cw]
-  T* Rs = Zs + (size_t)STAGES * B * cw;                   // [STAGES][B][B]
-  T* Cs = Rs + (size_t)STAGES * B * B;                    // [STAGES][B]
-  T* dl = Cs + (size_t)STAGES * B;                        // delta slice [cw]
-  T* mus = dl + cw;                                       // mu slice [cw]
-  double* Ssum = reinterpret_cast<double*>(mus + cw);     // running sum of delta [cw] (8-byte aligned: cw % 4 == 0)
-  T* xbuf = reinterpret_cast<T*>(Ssum + cw);              // [2][B] exchanged partial dots
-  T* pv = xbuf + 2 * B;                                   // [B]
-  T* av = pv + B;                                         // [B]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t c0 = (int64_t)rank * cw;
-  const int cwid = (int)max64(0, min64(cw, d - c0));
-  const int cvec_n = (cwid + E - 1) / E;                  // 16-byte chunks per row slice
-  const int64_t nblk = (m + B - 1) / B;
-  const T et = (T)eta;
-
-  for (int c = tid; c < cw; c += blockDim.x) {
-    dl[c] = T(0);
-    Ssum[c] = 0.0;
-    mus[c] = c < cwid ? mu[c0 + c] : T(0);
-  }
-
-  auto load_block = [&](int64_t blk) {
-    const int slot = (int)(blk % STAGES);
-    const int64_t t0 = blk * B;
-    const int Bb = (int)min64(B, m - t0);
-    T* zdst = Zs + (size_t)slot * B * cw;
-    for (int e = tid; e < Bb * cvec_n; e += blockDim.x) {
-      const int j = e / cvec_n, q = e % cvec_n;
-      const int64_t row = min64((int64_t)idx[t0 + j], N - 1);
-      cp_async16(zdst + (size_t)j * cw + q * E, Z + row * ld + c0 + q * E);
-    }
-    const T* rsrc = Rt + blk * (int64_t)B * B;
-    T* rdst = Rs + (size_t)slot * B * B;
-    for (int e = tid; e < B * B / E; e += blockDim.x) cp_async16(rdst + e * E, rsrc + e * E);
-    for (int e = tid; e < B / E; e += blockDim.x) cp_async16(Cs + (size_t)slot * B + e * E, cvec + blk * B + e * E);
-  };
-
-#pragma unroll
-  for (int s = 0; s < STAGES - 1; ++s) {
-    if (s < nblk) load_block(s);
-    cp_async_commit();
-  }
-  cluster.sync();   // every block of the cluster is running before any remote access
-
-  for (int64_t blk = 0; blk < nblk; ++blk) {
-    cp_async_wait<STAGES - 2>();
-    __syncthreads();
-    if (blk + STAGES - 1 < nblk) load_block(blk + STAGES - 1);
-    cp_async_commit();
-    const int slot = (int)(blk % STAGES);
-    const int Bb = (int)min64(B, m - blk * B);
-    const T* zs = Zs + (size_t)slot * B * cw;
-    // partial p_j over this block's columns
-    T* xb = xbuf + (blk & 1) * B;
-    for (int j = warp; j < Bb; j += 4) {
-      T s = T(0);
-      for (int c = lane; c < cwid; c += 32) s = fma(zs[(size_t)j * cw + c], dl[c], s);
-      s = warp_sum(s);
-      if (lane == 0) xb[j] = s;
-    }
-    cluster.sync();
-    if (tid < Bb) {
-      T s = T(0);
-      for (int r = 0; r < CS; ++r) {
-        const T* rx = cluster.map_shared_rank(xb, r);
-        s += rx[tid];
-      }
-      pv[tid] = s;
-    }
-    __syncthreads();
-    if (tid < Bb) {
-      const T* rs = Rs + (size_t)slot * B * B;
-      T s0 = Cs[(size_t)slot * B + tid], s1 = T(0);
-      int l = 0;
-      for (; l + 1 <= tid; l += 2) {
-        s0 = fma(rs[l * B + tid], pv[l], s0);
-        s1 = fma(rs[(l + 1) * B + tid], pv[l + 1], s1);
-      }
-      if (l <= tid) s0 = fma(rs[l * B + tid], pv[l], s0);
-      av[tid] = s0 + s1;
-    }
-    __syncthreads();
-    const T bbT = (T)Bb;
-    const T tri = (T)(0.5 * (double)Bb * (double)(Bb + 1));
-    for (int c = tid; c < cwid; c += blockDim.x) {
-      T upd = T(0), wsum = T(0);
-      for (int j = 0; j < Bb; ++j) {
-        const T az = av[j] * zs[(size_t)j * cw + c];
-        upd += az;
-        wsum = fma((T)(Bb - j), az, wsum);
-      }
-      const T dold = dl[c];
-      Ssum[c] += (double)(bbT * dold - et * (mus[c] * tri + wsum));
-      dl[c] = dold - et * (bbT * mus[c] + upd);
-    }
-  }
-  cp_async_wait<0>();
-  cluster.sync();   // no block leaves while another may still read its exchange buffer
-  for (int c = tid; c < cwid; c += blockDim.x) {
-    const double v = average ? Ssum[c] / (double)m : (double)dl[c];
-    wnext[c0 + c] = (T)((double)wbar[c0 + c] + v);
-  }
 }
 
 template <typename T>
@@ -465,9 +223,12 @@ static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t 
     else RS_FG(8);
 #undef RS_FG
     RS_LAUNCH_CHECK(ctx);
-    const int rb = norm2_dev ? 1 : blocks_for(ctx, d);
-    fullgrad_reduce_kernel<T><<<rb, 256, 0, ctx->stream>>>(part, blocks, d, mu, norm2_dev);
+    fullgrad_reduce_kernel<T><<<(unsigned)((d + 31) / 32), 256, 0, ctx->stream>>>(part, blocks, d, mu);
     RS_LAUNCH_CHECK(ctx);
+    if (norm2_dev) {
+      norm2_kernel<T><<<1, 256, 0, ctx->stream>>>(mu, d, norm2_dev);
+      RS_LAUNCH_CHECK(ctx);
+    }
     return RS_OK;
   }
   // wide rows: two passes
@@ -483,82 +244,9 @@ static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t 
   return RS_OK;
 }
 
-struct ChainPlan {
-  int cs = 8, cw = 0, stages = 3;
-  size_t shm = 0;
-};
-
 template <typename T>
-static ChainPlan plan_chain(int64_t d) {
-  constexpr int E = 16 / sizeof(T);
-  ChainPlan best;
-  const int candidates[] = {8, 16, 4, 2, 1};
-  for (int cs : candidates) {
-    int cw = (int)((d + cs - 1) / cs);
-    cw = (cw + E - 1) / E * E;
-    if ((int64_t)cw * (cs - 1) >= d && cs > 1) continue;   // an idle block would own no columns
-    for (int st = 3; st >= 2; --st) {
-      const size_t shm = (size_t)st * kBlk * cw * sizeof(T) + (size_t)st * kBlk * kBlk * sizeof(T) +
-                         (size_t)st * kBlk * sizeof(T) + 2 * (size_t)cw * sizeof(T) + 16 + (size_t)cw * sizeof(double) +
-                         4 * (size_t)kBlk * sizeof(T) + 64;
-      if (shm <= 200 * 1024) {
-        best.cs = cs;
-        best.cw = cw;
-        best.stages = st;
-        best.shm = shm;
-        return best;
-      }
-    }
-  }
-  best.cw = 0;
-  return best;
-}
-
-template <typename T>
-static int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
-                        int64_t m, double eta, const T* wbar, const T* mu, int average, T* wnext) {
-  const int64_t N = Z->n, d = Z->d;
-  const T* Zd = static_cast<const T*>(Z->data);
-  const int64_t nblk = (m + kBlk - 1) / kBlk;
-  T* Rt = static_cast<T*>(rs_scratch(ctx, SCR_R, (size_t)nblk * kBlk * kBlk * sizeof(T)));
-  T* cv = static_cast<T*>(rs_scratch(ctx, SCR_C, (size_t)nblk * kBlk * sizeof(T)));
-  if (!Rt || !cv) return RS_ENOMEM;
-  constexpr int RP = kBlk + 4, CH = 32;
-  const size_t pshm = (size_t)(RP * (CH + 1) + RP * RP + kBlk * kBlk) * sizeof(T);
-  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
-  epoch_prep_kernel<T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, Z->ld, d, n, N, lam, idx, inv_nq, m, eta, mu,
-                                                                   Rt, cv);
-  RS_LAUNCH_CHECK(ctx);
-  ChainPlan pl = plan_chain<T>(d);
-  if (pl.cw == 0) return rs_fail(RS_EUNSUPPORTED, "rs_svrg_epoch: d = %lld too wide for the on-chip chain", (long long)d);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(pl.cs, 1, 1);
-  cfg.blockDim = dim3(128, 1, 1);
-  cfg.dynamicSmemBytes = pl.shm;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = pl.cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (pl.stages == 3) {
-    auto kern = epoch_chain_kernel<T, 3>;
-    RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
-    if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, Zd, N, Z->ld, d, pl.cw, idx, m, (const T*)Rt, (const T*)cv, eta, mu, wbar,
-                                   average, wnext));
-  } else {
-    auto kern = epoch_chain_kernel<T, 2>;
-    RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
-    if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, Zd, N, Z->ld, d, pl.cw, idx, m, (const T*)Rt, (const T*)cv, eta, mu, wbar,
-                                   average, wnext));
-  }
-  RS_LAUNCH_CHECK(ctx);
-  return RS_OK;
-}
+int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
+                 int64_t m, double eta, const T* wbar, const T* mu, int average, T* wnext);   // epoch.cu
 
 static int check_components(const rs_matrix* Z, int64_t n) {
   RS_TRY(check_matrix(Z, "Z"));
@@ -628,7 +316,7 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, const T* be
     if (!ev.empty()) RS_CUDA_TRY(cudaEventRecord(ev[s + 1], ctx->stream));
   }
   RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, w_out));
-  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  // the status word was cleared by rs_sampling_weights above; epochs may have set the timeout bit
   finite_check_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(w_out, d, 1e30, ctx->d_status);
   RS_LAUNCH_CHECK(ctx);
   int st = 0;
@@ -644,6 +332,7 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, const T* be
       for (auto& e : ev) cudaEventDestroy(e);
     }
   }
+  if (st & STATUS_TIMEOUT) return rs_fail(RS_ETIMEOUT, "rs_svrg_solve: a bounded wait of the inner-loop chain gave up");
   if (st & 1) return rs_fail(RS_ENONFINITE, "rs_svrg_solve: the iterate became non-finite (step size too large?)");
   if (st & 8) return rs_fail(RS_EDIVERGED, "rs_svrg_solve: the iterate diverged (step size too large?)");
   return RS_OK;

@@ -8,6 +8,7 @@ import torch
 import paper_1602_02350_gb300 as rs
 from oracle import precond
 from paper_1602_02350_gb300 import synth
+from tests.gpu_helpers import cuda_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +23,7 @@ def test_precondition_matches_oracle(rsctx, dtype, tol, n, d, k):
     s2 = synth.random_sigma2(k, k)
     lam = 1e-4
     Vt = torch.from_numpy(V).to(dtype).cuda()
-    Z, beta, bh = rs.rs_precondition(rsctx, X.cuda(), Vt, torch.from_numpy(s2).cuda(), lam)
+    Z, beta, bh = rs.rs_precondition(rsctx, cuda_rows(X), Vt, torch.from_numpy(s2).cuda(), lam)
     Z = Z.cpu().double().numpy()
     Xd = X.double().numpy()
     Vd = Vt.cpu().double().numpy()

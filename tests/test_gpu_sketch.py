@@ -8,6 +8,7 @@ import torch
 import paper_1602_02350_gb300 as rs
 from oracle import ridge, sketch as osk
 from paper_1602_02350_gb300 import synth
+from tests.gpu_helpers import cuda_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +23,7 @@ def _data(n, d, alpha, seed, dtype):
                                           ("countsketch", 3000, 130, 12, 256)])
 def test_range_sketch_matches_oracle(rsctx, dtype, tol, kind, n, d, k, s):
     X, _ = _data(n, d, 1.5, 11, dtype)
-    Y = rs.rs_range_sketch(rsctx, X.cuda(), k, 2000, kind=kind, s=s).cpu().double().numpy()
+    Y = rs.rs_range_sketch(rsctx, cuda_rows(X), k, 2000, kind=kind, s=s).cpu().double().numpy()
     ref = osk.range_sketch(X.double().numpy(), k, 2000, kind=kind, s=s)
     np.testing.assert_allclose(Y, ref, rtol=0, atol=tol * np.abs(ref).max())
 
@@ -60,7 +61,7 @@ def test_sym_eig_matches_library_eigh(rsctx, prec, tol, k):
 def test_ritz_matches_oracle(rsctx, dtype, tol):
     X, _ = _data(2000, 100, 1.2, 3, dtype)
     Q = osk.orthonormalize(synth.random_matrix(100, 10, 1))
-    V, s2 = rs.rs_ritz(rsctx, X.cuda(), torch.from_numpy(Q).to(dtype).cuda())
+    V, s2 = rs.rs_ritz(rsctx, cuda_rows(X), torch.from_numpy(Q).to(dtype).cuda())
     V, s2 = V.cpu().double().numpy(), s2.cpu().numpy()
     Vr, s2r = osk.ritz(X.double().numpy(), Q, 10)
     np.testing.assert_allclose(s2, s2r, rtol=tol)
@@ -72,7 +73,7 @@ def test_ritz_matches_oracle(rsctx, dtype, tol):
                                             ("gaussian", 2048, 128, 8, 0, 3)])
 def test_sketch_end_to_end_matches_oracle(rsctx, dtype, tol, kind, n, d, k, s, q):
     X, _ = _data(n, d, 1.5, 21, dtype)
-    V, s2 = rs.rs_sketch(rsctx, X.cuda(), k, 2000, kind=kind, s=s, q=q)
+    V, s2 = rs.rs_sketch(rsctx, cuda_rows(X), k, 2000, kind=kind, s=s, q=q)
     V, s2 = V.cpu().double().numpy(), s2.cpu().numpy()
     Vr, s2r = osk.block_lanczos(X.double().numpy(), k, 2000, q=q, kind=kind, s=s)
     np.testing.assert_allclose(s2, s2r, rtol=tol)

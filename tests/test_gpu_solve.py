@@ -57,7 +57,7 @@ def test_fp64_trajectory_parity_same_stream(rsctx, fp64_problem):
     recursion to rounding (the preconditioner comes from the generator, not from either side)."""
     cfg, X, y, Xn, yn, ws = fp64_problem
     V = synth.random_orthonormal(cfg.d, cfg.k, 5)
-    s2 = np.sort(np.linalg.eigvalsh(ridge.correlation(Xn)))[::-1][: cfg.k]
+    s2 = np.sort(np.linalg.eigvalsh(ridge.correlation(Xn)))[::-1][: cfg.k].copy()
     Z, beta, bh = rs.rs_precondition(rsctx, X.cuda(), torch.from_numpy(V).cuda(), torch.from_numpy(s2).cuda(), cfg.lam)
     M = precond.m_matrix(V, s2, cfg.lam)
     Zr, yz, g = precond.components(*precond.transform(Xn, M), yn, cfg.lam)
