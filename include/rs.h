@@ -193,6 +193,25 @@ int rs_index_stream(rs_ctx* ctx, const uint32_t* W, const uint64_t* cum, int64_t
 int rs_full_gradient(rs_ctx* ctx, const rs_matrix* Z, const void* y, int64_t n, double lambda,
                      const void* w, void* mu);
 
+/* Allocation-free rs_full_gradient (the paper has no counterpart; this is a service to callers).
+ * Some callers cannot call cudaMalloc: applications whose device memory is owned end to end by
+ * their own pool or arena (an allocation outside it fails once the pool has reserved the device,
+ * or breaks its accounting) and latency-critical services that must stay off the driver's
+ * allocation path (cudaMalloc/cudaFree can synchronise the device).  This entry point takes no
+ * context and allocates nothing: its per-block partial sums live in a 2 MiB array in the
+ * library's device data, which every GPU that loads the library holds until the process exits.
+ * Same arguments and result as rs_full_gradient (mu is written on ``cuda_stream``, a
+ * cudaStream_t, NULL = legacy default stream, on the caller's current device); the same kernels
+ * run, so results match rs_full_gradient.
+ *   - Limit: d <= 1024 for RS_F32 and d <= 512 for RS_F64 rows; larger d returns RS_EINVAL.
+ *   - The first call on each device resolves the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents; nothing in it needs
+ *     to start at zero (each call overwrites every partial it reads).  Calls that overlap on the
+ *     GPU (different streams, or different host threads without ordering) race on the array. */
+int rs_full_gradient_static(void* cuda_stream, const rs_matrix* Z, const void* y, int64_t n, double lambda,
+                            const void* w, void* mu);
+
 /* One outer iteration of Alg. 1 for a given index stream (idx, inv_nq from rs_index_stream):
  *   w_0 = w_bar;  w_t = w_{t-1} - eta ((grad f_i(w_{t-1}) - grad f_i(w_bar)) inv_nq[t] + mu);
  *   w_next = (1/m) sum_{t=1..m} w_t  (average != 0)  or  w_m  (average == 0),

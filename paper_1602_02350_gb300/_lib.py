@@ -78,6 +78,7 @@ _SIGS = {
     "rs_index_stream": [_P, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                         ctypes.c_int32, ctypes.c_int32, _P, _P],
     "rs_full_gradient": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_int64, ctypes.c_double, _P, _P],
+    "rs_full_gradient_static": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_int64, ctypes.c_double, _P, _P],
     "rs_svrg_epoch": [_P, ctypes.POINTER(Matrix), ctypes.c_int64, ctypes.c_double, _P, _P, ctypes.c_int64,
                       ctypes.c_double, _P, _P, ctypes.c_int32, _P],
     "rs_svrg_solve": [_P, ctypes.POINTER(Matrix), _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SvrgParams), _P, _P,
@@ -305,6 +306,20 @@ def rs_full_gradient(ctx, Z, y, n, lam, w):
     mu = ctx._empty(Z.shape[1], dtype=w.dtype)
     M = matrix(Z)
     _check(lib().rs_full_gradient(ctx.h, ctypes.byref(M), _ptr(y), n, lam, _ptr(w), _ptr(mu)))
+    return mu
+
+
+def rs_full_gradient_static(Z, y, n, lam, w, stream=None, out=None):
+    """Allocation-free full gradient (no context; scratch is a fixed array in the library's device
+    data).  ``out`` may be a preallocated CUDA tensor; the call itself allocates nothing on the
+    device.  ``stream`` defaults to the current torch stream of Z's device."""
+    _need_cuda(Z, y, w)
+    mu = torch.empty(Z.shape[1], dtype=w.dtype, device=Z.device) if out is None else out
+    s = stream if stream is not None else torch.cuda.current_stream(Z.device)
+    M = matrix(Z)
+    with torch.cuda.device(Z.device):
+        _check(lib().rs_full_gradient_static(ctypes.c_void_p(s.cuda_stream), ctypes.byref(M), _ptr(y), n, lam, _ptr(w),
+                                             _ptr(mu)))
     return mu
 
 

@@ -453,3 +453,95 @@ int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_par
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free variant
+//
+// Some callers cannot call cudaMalloc: applications whose device memory is owned end to end by
+// their own pool or arena (an allocation outside it either fails once the pool has reserved the
+// device or breaks the pool's accounting), and latency-critical services that must stay off the
+// driver's allocation path (cudaMalloc and cudaFree can synchronise the device).  For them
+// rs_full_gradient_static runs the same full-gradient pass as rs_full_gradient, with the
+// per-block partial sums in a fixed array in this library's device data instead of context
+// scratch, and without a context.
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(2) << 20;   // 2 MiB, held by every device that loads the library
+static __device__ __align__(256) unsigned char g_fullgrad_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_static_scratch[kMaxDevices];   // device address of g_fullgrad_scratch, per device
+int g_static_sms[kMaxDevices];
+std::mutex g_static_mu;
+
+// Once per device, with that device current: resolve the array's device address (the host-side
+// symbol is only a stand-in and must never be handed to a kernel).
+int static_scratch_setup(int dev, void** scratch, int* sms) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_scratch[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_fullgrad_scratch);
+    if (e != cudaSuccess) return rs_fail(RS_ECUDA, "rs_full_gradient_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    int s = 0;
+    e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return rs_fail(RS_ECUDA, "rs_full_gradient_static: %s", cudaGetErrorString(e));
+    g_static_sms[dev] = s;
+    g_static_scratch[dev] = p;
+  }
+  *scratch = g_static_scratch[dev];
+  *sms = g_static_sms[dev];
+  return RS_OK;
+}
+
+template <typename T>
+int full_gradient_static_t(cudaStream_t stream, const rs_matrix* Z, const T* y, int64_t n, double lam, const T* w,
+                           T* mu, void* scratch, int sms) {
+  const int64_t N = Z->n, d = Z->d;
+  constexpr int E = Vec<T>::N;
+  const int64_t vecs = (d + E - 1) / E;
+  const int vpl = (int)((vecs + 31) / 32);
+  if (vpl > 8)
+    return rs_fail(RS_EINVAL, "rs_full_gradient_static: d = %lld exceeds this entry point's %d-column maximum",
+                   (long long)d, 32 * 8 * E);
+  int64_t blocks = (int64_t)sms * 2;
+  const int64_t fit = (int64_t)(kStaticScratchBytes / ((size_t)d * sizeof(T)));
+  if (blocks > fit) blocks = fit;
+  if (blocks < 1) return rs_fail(RS_EINVAL, "rs_full_gradient_static: d = %lld does not fit the 2 MiB scratch", (long long)d);
+  T* part = static_cast<T*>(scratch);   // every block overwrites its own d partial sums: no clearing needed
+  const int threads = 256;
+  const size_t shm = (size_t)(threads / 32) * d * sizeof(T);   // at most 32 KiB: no attribute change needed
+  const T* Zd = static_cast<const T*>(Z->data);
+  if (vpl <= 1) fullgrad_kernel<T, 1><<<(unsigned)blocks, threads, shm, stream>>>(Zd, N, n, d, Z->ld, y, (T)lam, w, part);
+  else if (vpl <= 2) fullgrad_kernel<T, 2><<<(unsigned)blocks, threads, shm, stream>>>(Zd, N, n, d, Z->ld, y, (T)lam, w, part);
+  else if (vpl <= 4) fullgrad_kernel<T, 4><<<(unsigned)blocks, threads, shm, stream>>>(Zd, N, n, d, Z->ld, y, (T)lam, w, part);
+  else fullgrad_kernel<T, 8><<<(unsigned)blocks, threads, shm, stream>>>(Zd, N, n, d, Z->ld, y, (T)lam, w, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return rs_fail(RS_ECUDA, "rs_full_gradient_static: %s", cudaGetErrorString(e));
+  fullgrad_reduce_kernel<T><<<(unsigned)((d + 31) / 32), 256, 0, stream>>>(part, (int)blocks, d, mu);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return rs_fail(RS_ECUDA, "rs_full_gradient_static: %s", cudaGetErrorString(e));
+  return RS_OK;
+}
+
+}  // namespace
+
+extern "C" int rs_full_gradient_static(void* cuda_stream, const rs_matrix* Z, const void* y, int64_t n, double lambda,
+                                       const void* w, void* mu) {
+  RS_CHECK_ARG(Z && y && w && mu, "rs_full_gradient_static: null argument");
+  RS_TRY(check_components(Z, n));
+  RS_CHECK_ARG(lambda > 0.0, "rs_full_gradient_static: lambda must be positive");
+  int dev = 0;
+  RS_CUDA_TRY(cudaGetDevice(&dev));
+  RS_CHECK_ARG(dev >= 0 && dev < kMaxDevices, "rs_full_gradient_static: device %d out of range", dev);
+  void* scratch = nullptr;
+  int sms = 0;
+  RS_TRY(static_scratch_setup(dev, &scratch, &sms));
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (Z->dtype == RS_F64)
+    return full_gradient_static_t<double>(s, Z, static_cast<const double*>(y), n, lambda, static_cast<const double*>(w),
+                                          static_cast<double*>(mu), scratch, sms);
+  return full_gradient_static_t<float>(s, Z, static_cast<const float*>(y), n, lambda, static_cast<const float*>(w),
+                                       static_cast<float*>(mu), scratch, sms);
+}
