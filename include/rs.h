@@ -232,6 +232,10 @@ typedef struct {
   int32_t sampling;    /* RS_SAMPLE_IMPORTANCE (q_i ~ beta_i) or RS_SAMPLE_UNIFORM */
   int32_t average;     /* 1: epoch output is the average of w_1..w_m (Alg. 1); 0: w_m */
   uint64_t seed;
+  int32_t refine;      /* 1: form each snapshot's full gradient on the stored data X,
+                          mu = M (X^T (X M w~ - y)/n + lam M w~), instead of on Z; the fixed point
+                          is then exact for X as stored even when Z is a rounded (BF16) copy */
+  int32_t reserved;
 } rs_svrg_params;
 
 typedef struct {
@@ -242,18 +246,21 @@ typedef struct {
   float* epoch_ms;       /* host, nullable: cumulative device time at the end of each epoch */
 } rs_history;
 
-/* Alg. 1 on the components Z (rs_precondition layout, N = n + d rows) for p->epochs epochs,
- * starting from w0 (preconditioned coordinates, nullable = 0).  beta (T, N; nullable =
- * recomputed from Z) sets the sampling weights.  V/sigma2/k give M for the output map:
- * w_out = M w~_S (original coordinates, Alg. 3 read as w = P^{-1/2} w~).  eta_used / m_used
- * (host, nullable) receive the resolved step size and epoch length.  Synchronises.
- * RS_ENONFINITE / RS_EDIVERGED if an iterate becomes non-finite. */
-int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const void* y, const void* beta, const void* V,
+/* Alg. 1 on the components Z (rs_precondition layout, N = n + d rows; RS_F64, RS_F32 or RS_BF16
+ * storage) for p->epochs epochs, starting from w0 (preconditioned coordinates, nullable = 0).
+ * X (n x d, same storage as Z) is the stored data, required when p->refine is set, else
+ * nullable.  beta (T, N; nullable = recomputed from Z) sets the sampling weights.  V/sigma2/k
+ * give M for the output map: w_out = M w~_S (original coordinates, Alg. 3 read as
+ * w = P^{-1/2} w~).  eta_used / m_used (host, nullable) receive the resolved step size and
+ * epoch length.  Synchronises.  RS_ENONFINITE / RS_EDIVERGED if an iterate becomes
+ * non-finite, RS_ETIMEOUT if a bounded device wait of the inner loop gave up. */
+int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const void* y, const void* beta, const void* V,
                   const double* sigma2, int64_t k, const rs_svrg_params* p, const void* w0,
                   void* w_out, rs_history* hist, double* eta_used, int64_t* m_used);
 
 /* Alg. 3 end to end: sketch (Alg. 2), preconditioner and transformed components (Eq. (11),
- * Sec. 5.1), SVRG (Alg. 1), w_out = M w~ (Eq. (4)).  X->data, y and w_out may be HOST
+ * Sec. 5.1), SVRG (Alg. 1), w_out = M w~ (Eq. (4)).  X may be RS_F64, RS_F32 or RS_BF16 (the
+ * components are stored in the same type; with RS_BF16 set p->refine).  X->data, y and w_out may be HOST
  * pointers (detected): the data is then copied to scratch memory and the result back inside
  * the call.  Scratch holds (n + d) x d elements for the components.  Synchronises. */
 int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp,

@@ -43,7 +43,8 @@ class SketchParams(ctypes.Structure):
 class SvrgParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("eta", ctypes.c_double), ("eta_mult", ctypes.c_double),
                 ("m", ctypes.c_int64), ("epochs", ctypes.c_int32), ("epoch0", ctypes.c_int32),
-                ("sampling", ctypes.c_int32), ("average", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("sampling", ctypes.c_int32), ("average", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("refine", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class History(ctypes.Structure):
@@ -81,7 +82,8 @@ _SIGS = {
     "rs_full_gradient_static": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_int64, ctypes.c_double, _P, _P],
     "rs_svrg_epoch": [_P, ctypes.POINTER(Matrix), ctypes.c_int64, ctypes.c_double, _P, _P, ctypes.c_int64,
                       ctypes.c_double, _P, _P, ctypes.c_int32, _P],
-    "rs_svrg_solve": [_P, ctypes.POINTER(Matrix), _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SvrgParams), _P, _P,
+    "rs_svrg_solve": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(Matrix), _P, _P, _P, _P, ctypes.c_int64,
+                      ctypes.POINTER(SvrgParams), _P, _P,
                       ctypes.POINTER(History), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
     "rs_solve": [_P, ctypes.POINTER(Matrix), _P, ctypes.POINTER(SketchParams), ctypes.POINTER(SvrgParams), _P,
                  ctypes.POINTER(History)],
@@ -331,8 +333,9 @@ def rs_svrg_epoch(ctx, Z, n, lam, idx, inv_nq, eta, w_bar, mu, average=True):
     return out
 
 
-def _svrg_params(lam, epochs, seed, eta=0.0, eta_mult=0.0, m=0, epoch0=0, sampling=RS_SAMPLE_IMPORTANCE, average=True):
-    return SvrgParams(lam, eta, eta_mult, m, epochs, epoch0, sampling, 1 if average else 0, seed)
+def _svrg_params(lam, epochs, seed, eta=0.0, eta_mult=0.0, m=0, epoch0=0, sampling=RS_SAMPLE_IMPORTANCE, average=True,
+                 refine=False):
+    return SvrgParams(lam, eta, eta_mult, m, epochs, epoch0, sampling, 1 if average else 0, seed, 1 if refine else 0, 0)
 
 
 def _history(ctx, epochs, d, dtype, snapshots):
@@ -345,14 +348,16 @@ def _history(ctx, epochs, d, dtype, snapshots):
 
 
 def rs_svrg_solve(ctx, Z, y, V, sigma2, lam, epochs, seed, beta=None, w0=None, eta=0.0, eta_mult=0.0, m=0,
-                  epoch0=0, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False):
+                  epoch0=0, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False, X=None, refine=False):
     d = Z.shape[1]
     w = ctx._empty(d, dtype=V.dtype)
-    p = _svrg_params(lam, epochs, seed, eta, eta_mult, m, epoch0, sampling, average)
+    p = _svrg_params(lam, epochs, seed, eta, eta_mult, m, epoch0, sampling, average, refine)
+    MX = matrix(X) if X is not None else None
     h, mu2, ems, snaps = _history(ctx, epochs, d, V.dtype, snapshots)
     eu, mu_ = ctypes.c_double(0), ctypes.c_int64(0)
     M = matrix(Z)
-    _check(lib().rs_svrg_solve(ctx.h, ctypes.byref(M), _ptr(y), _ptr(beta), _ptr(V.contiguous()), _ptr(sigma2),
+    _check(lib().rs_svrg_solve(ctx.h, ctypes.byref(M), ctypes.byref(MX) if MX is not None else None, _ptr(y),
+                               _ptr(beta), _ptr(V.contiguous()), _ptr(sigma2),
                                V.shape[1], ctypes.byref(p), _ptr(w0), _ptr(w), ctypes.byref(h), ctypes.byref(eu),
                                ctypes.byref(mu_)))
     info = {"eta": eu.value, "m": mu_.value, "mu_norm2": list(mu2)[:epochs], "epoch_ms": list(ems)[:epochs],
@@ -361,7 +366,7 @@ def rs_svrg_solve(ctx, Z, y, V, sigma2, lam, epochs, seed, beta=None, w0=None, e
 
 
 def rs_solve(ctx, X, y, k, lam, epochs, sketch_seed, svrg_seed, kind="gaussian", s=0, q=1, eta=0.0, eta_mult=0.0,
-             m=0, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False, w_out=None):
+             m=0, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False, w_out=None, refine=None):
     """Alg. 3 end to end.  X / y may be CUDA tensors or (pinned) CPU tensors; w_out likewise."""
     d = X.shape[1]
     ct = torch.float64 if X.dtype == torch.float64 else torch.float32
@@ -369,7 +374,9 @@ def rs_solve(ctx, X, y, k, lam, epochs, sketch_seed, svrg_seed, kind="gaussian",
         w_out = ctx._empty(d, dtype=ct) if X.is_cuda else torch.empty(d, dtype=ct)
     M = Matrix(X.data_ptr(), None, X.shape[0], d, X.stride(0), _DT[X.dtype], 0)
     sp = _sketch_params(k, sketch_seed, kind, s, q)
-    p = _svrg_params(lam, epochs, svrg_seed, eta, eta_mult, m, 0, sampling, average)
+    if refine is None:
+        refine = X.dtype == torch.bfloat16
+    p = _svrg_params(lam, epochs, svrg_seed, eta, eta_mult, m, 0, sampling, average, refine)
     h, mu2, ems, snaps = _history(ctx, epochs, d, ct, snapshots)
     _check(lib().rs_solve(ctx.h, ctypes.byref(M), _ptr(y), ctypes.byref(sp), ctypes.byref(p), _ptr(w_out),
                           ctypes.byref(h)))

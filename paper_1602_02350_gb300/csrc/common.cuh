@@ -49,9 +49,9 @@ void* rs_scratch(rs_ctx* ctx, int slot, size_t bytes);   // nullptr on failure (
       return rs_fail(RS_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
   } while (0)
 
-#define RS_TRY(expr)                \
+#define RS_TRY(...)                 \
   do {                              \
-    int _s = (expr);                \
+    int _s = (__VA_ARGS__);         \
     if (_s != RS_OK) return _s;     \
   } while (0)
 
@@ -159,15 +159,17 @@ __device__ __forceinline__ void vec_to_arr(const float4& v, float* a) { a[0] = v
 __device__ __forceinline__ void vec_to_arr(const double2& v, double* a) { a[0] = v.x; a[1] = v.y; }
 
 // Internal launch helpers implemented in dense.cu, used by several entry points.
-template <typename T>
-int launch_gemm(rs_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t sAm,
-                int64_t sAk, const T* B, int64_t sBk, int64_t sBn, double beta, const T* C0, int64_t ldc0,
-                T* C, int64_t ldc, const T* col_scale);
+template <typename T> struct NoDeduce { using type = T; };   // keeps a parameter out of type deduction
+// A and C (and C0) may be stored in another type than the compute type T (bfloat16 data).
+template <typename T, typename TA = T, typename TC = T>
+int launch_gemm(rs_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t sAm,
+                int64_t sAk, const T* B, int64_t sBk, int64_t sBn, double beta, const typename NoDeduce<TC>::type* C0,
+                int64_t ldc0, TC* C, int64_t ldc, const T* col_scale);
 
 // Gram / transposed product with split-K over the long dimension and double accumulation:
 // G (Ma x Nb, double, row-major) = alpha * sum_r A[r][i] B[r][j], A: rows x Ma (lda), B: rows x Nb (ldb).
-template <typename TA>
-int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, int64_t lda, const TA* B,
+template <typename TA, typename TB = TA>
+int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, int64_t lda, const TB* B,
                 int64_t ldb, double alpha, double* G);
 
 int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W);

@@ -14,10 +14,10 @@ namespace {
 // ------------------------------------------------------------------ GEMM (CUDA cores)
 // C[m][n] = alpha * col_scale[n] * sum_k A(m,k) B(k,n) + beta * C0[m][n]
 // A(m,k) = A[m*sAm + k*sAk], B(k,n) = B[k*sBk + n*sBn].  64x64 tile, 16-deep k steps, 4x4 per thread.
-template <typename T, bool A_KCONTIG, bool B_NCONTIG>
-__global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A,
+template <typename T, typename TA, typename TC, bool A_KCONTIG, bool B_NCONTIG>
+__global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const TA* __restrict__ A,
                                                    int64_t sAm, int64_t sAk, const T* __restrict__ B, int64_t sBk,
-                                                   int64_t sBn, T beta, const T* C0, int64_t ldc0, T* C, int64_t ldc,
+                                                   int64_t sBn, T beta, const TC* C0, int64_t ldc0, TC* C, int64_t ldc,
                                                    const T* __restrict__ col_scale) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ T As[BK][BM + 4];
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t
       int mm, kk;
       if (A_KCONTIG) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
       const int64_t gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? A[gm * sAm + gk * sAk] : T(0);
+      As[kk][mm] = (gm < M && gk < K) ? cvt<T>(A[gm * sAm + gk * sAk]) : T(0);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -72,17 +72,17 @@ __global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t
       if (gn >= N) continue;
       T v = alpha * acc[i][j];
       if (col_scale) v *= col_scale[gn];
-      if (C0) v = fma(beta, C0[gm * ldc0 + gn], v);
-      C[gm * ldc + gn] = v;
+      if (C0) v = fma(beta, cvt<T>(C0[gm * ldc0 + gn]), v);
+      C[gm * ldc + gn] = cvt<TC>(v);
     }
   }
 }
 
 // ------------------------------------------------------------------ split-K Gram
 // part[chunk][i][j] = sum over rows r of the chunk of A[r][i] B[r][j]  (TACC accumulation)
-template <typename TA, typename TACC>
+template <typename TA, typename TB, typename TACC>
 __global__ void __launch_bounds__(256) gram_kernel(int64_t rows, int64_t Ma, int64_t Nb, const TA* __restrict__ A,
-                                                   int64_t lda, const TA* __restrict__ B, int64_t ldb,
+                                                   int64_t lda, const TB* __restrict__ B, int64_t ldb,
                                                    int64_t rows_per_chunk, double* part) {
   constexpr int BT = 64, BK = 16;
   __shared__ TACC As[BK][BT + 4];
@@ -349,16 +349,16 @@ __global__ void scale_cols_kernel(const T* V, int64_t d, int k, const T* a, T* V
 }
 
 template <typename T>
-__global__ void identity_rows_kernel(T* Z, int64_t d, int64_t ld) {
+__global__ void identity_rows_kernel(T* Z, int64_t d, int64_t ld) {   // T: storage type
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d * d; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / d, c = e % d;
-    Z[r * ld + c] = (r == c) ? T(1) : T(0);
+    Z[r * ld + c] = cvt<T>((r == c) ? 1.0f : 0.0f);
   }
 }
 
 // beta_i = gamma_i ||z_i||^2; warp per row; per-block partial sums of beta for beta_hat
-template <typename T>
-__global__ void row_beta_kernel(const T* Z, int64_t N, int64_t n, int64_t d, int64_t ld, double lam, T* beta,
+template <typename S, typename T>
+__global__ void row_beta_kernel(const S* Z, int64_t N, int64_t n, int64_t d, int64_t ld, double lam, T* beta,
                                 double* part) {
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -367,7 +367,7 @@ __global__ void row_beta_kernel(const T* Z, int64_t N, int64_t n, int64_t d, int
   for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
     T s = T(0);
     for (int64_t c = lane; c < d; c += 32) {
-      const T v = Z[i * ld + c];
+      const T v = cvt<T>(Z[i * ld + c]);
       s = fma(v, v, s);
     }
     s = warp_sum(s);
@@ -473,38 +473,41 @@ int blocks_for(rs_ctx* ctx, int64_t work, int threads = 256) {
 
 // ====================================================================== launchers
 
-template <typename T>
-int launch_gemm(rs_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t sAm, int64_t sAk,
-                const T* B, int64_t sBk, int64_t sBn, double beta, const T* C0, int64_t ldc0, T* C, int64_t ldc,
-                const T* col_scale) {
+template <typename T, typename TA, typename TC>
+int launch_gemm(rs_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t sAm, int64_t sAk,
+                const T* B, int64_t sBk, int64_t sBn, double beta, const typename NoDeduce<TC>::type* C0, int64_t ldc0,
+                TC* C, int64_t ldc, const T* col_scale) {
   if (M <= 0 || N <= 0) return RS_OK;
   dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
   if (grid.y > 65535) return rs_fail(RS_EINVAL, "gemm: M = %lld too large", (long long)M);
   const bool ak = (sAk == 1), bn = (sBn == 1);
   if (ak && bn)
-    gemm_kernel<T, true, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+    gemm_kernel<T, TA, TC, true, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
                                                               C0, ldc0, C, ldc, col_scale);
   else if (ak)
-    gemm_kernel<T, true, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+    gemm_kernel<T, TA, TC, true, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
                                                                C0, ldc0, C, ldc, col_scale);
   else if (bn)
-    gemm_kernel<T, false, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+    gemm_kernel<T, TA, TC, false, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
                                                                C0, ldc0, C, ldc, col_scale);
   else
-    gemm_kernel<T, false, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn,
+    gemm_kernel<T, TA, TC, false, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn,
                                                                 (T)beta, C0, ldc0, C, ldc, col_scale);
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
 }
-template int launch_gemm<float>(rs_ctx*, int64_t, int64_t, int64_t, double, const float*, int64_t, int64_t,
-                                const float*, int64_t, int64_t, double, const float*, int64_t, float*, int64_t,
-                                const float*);
-template int launch_gemm<double>(rs_ctx*, int64_t, int64_t, int64_t, double, const double*, int64_t, int64_t,
-                                 const double*, int64_t, int64_t, double, const double*, int64_t, double*, int64_t,
-                                 const double*);
+#define RS_GEMM_INST(T, TA, TC)                                                                                  \
+  template int launch_gemm<T, TA, TC>(rs_ctx*, int64_t, int64_t, int64_t, double, const TA*, int64_t, int64_t,      \
+                                      const T*, int64_t, int64_t, double, const typename NoDeduce<TC>::type*, int64_t, TC*,  \
+                                      int64_t, const T*);
+RS_GEMM_INST(float, float, float)
+RS_GEMM_INST(double, double, double)
+RS_GEMM_INST(float, __nv_bfloat16, float)
+RS_GEMM_INST(float, float, __nv_bfloat16)
+#undef RS_GEMM_INST
 
-template <typename TA>
-int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, int64_t lda, const TA* B, int64_t ldb,
+template <typename TA, typename TB>
+int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, int64_t lda, const TB* B, int64_t ldb,
                 double alpha, double* G) {
   using TACC = typename std::conditional<sizeof(TA) == 8, double, float>::type;
   const int64_t tiles = ((Ma + 63) / 64) * ((Nb + 63) / 64);
@@ -518,16 +521,20 @@ int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, 
   if (!part) return RS_ENOMEM;
   if (nchunks > 65535) return rs_fail(RS_EINVAL, "gram: too many row chunks");
   dim3 grid((unsigned)((Nb + 63) / 64), (unsigned)((Ma + 63) / 64), (unsigned)nchunks);
-  gram_kernel<TA, TACC><<<grid, 256, 0, ctx->stream>>>(rows, Ma, Nb, A, lda, B, ldb, rpc, part);
+  gram_kernel<TA, TB, TACC><<<grid, 256, 0, ctx->stream>>>(rows, Ma, Nb, A, lda, B, ldb, rpc, part);
   RS_LAUNCH_CHECK(ctx);
   reduce_chunks_kernel<<<blocks_for(ctx, Ma * Nb), 256, 0, ctx->stream>>>(part, nchunks, Ma * Nb, alpha, G);
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
 }
-template int launch_gram<float>(rs_ctx*, int64_t, int64_t, int64_t, const float*, int64_t, const float*, int64_t,
-                                double, double*);
-template int launch_gram<double>(rs_ctx*, int64_t, int64_t, int64_t, const double*, int64_t, const double*, int64_t,
-                                 double, double*);
+#define RS_GRAM_INST(TA, TB)                                                                                     \
+  template int launch_gram<TA, TB>(rs_ctx*, int64_t, int64_t, int64_t, const TA*, int64_t, const TB*, int64_t,    \
+                                   double, double*);
+RS_GRAM_INST(float, float)
+RS_GRAM_INST(double, double)
+RS_GRAM_INST(__nv_bfloat16, float)
+RS_GRAM_INST(__nv_bfloat16, __nv_bfloat16)
+#undef RS_GRAM_INST
 
 template <typename T>
 static int to_T(rs_ctx* ctx, const double* in, int64_t count, T* out) {
@@ -620,7 +627,7 @@ static int read_status(rs_ctx* ctx, int* st) {
   return RS_OK;
 }
 
-template <typename T>
+template <typename S, typename T>
 static int range_sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, T* Y) {
   const int64_t n = X->n, d = X->d, k = p->k;
   const int32_t dt = sizeof(T) == 8 ? RS_F64 : RS_F32;
@@ -630,7 +637,7 @@ static int range_sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_param
     T* Om = static_cast<T*>(rs_scratch(ctx, SCR_OMEGA, n * k * sizeof(T)));
     if (!Om) return RS_ENOMEM;
     RS_TRY(gaussian_dispatch(ctx, p->seed, 0, n, k, dt, Om, k));
-    RS_TRY(launch_gram<T>(ctx, n, d, k, static_cast<const T*>(X->data), X->ld, Om, k, 1.0, Gd));
+    RS_TRY(launch_gram<S, T>(ctx, n, d, k, static_cast<const S*>(X->data), X->ld, Om, k, 1.0, Gd));
   } else {
     const int64_t s = p->s > 0 ? p->s : std::min<int64_t>(n, 64 * k);
     T* SX = static_cast<T*>(rs_scratch(ctx, SCR_SX, s * d * sizeof(T)));
@@ -643,7 +650,7 @@ static int range_sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_param
   return to_T<T>(ctx, Gd, d * k, Y);
 }
 
-template <typename T>
+template <typename S, typename T>
 static int ritz_t(rs_ctx* ctx, const rs_matrix* X, const T* Q, int64_t kq, int64_t k, T* V, double* sigma2) {
   const int64_t n = X->n, d = X->d;
   T* B = static_cast<T*>(rs_scratch(ctx, SCR_B, n * kq * sizeof(T)));
@@ -653,7 +660,7 @@ static int ritz_t(rs_ctx* ctx, const rs_matrix* X, const T* Q, int64_t kq, int64
   T* Wt = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, kq * kq * sizeof(T)));
   if (!B || !G || !ev || !Wd || !Wt) return RS_ENOMEM;
   // B = X Q (n x kq), G = B^T B / n
-  RS_TRY(launch_gemm<T>(ctx, n, kq, d, 1.0, static_cast<const T*>(X->data), X->ld, 1, Q, kq, 1, 0.0, nullptr, 0, B,
+  RS_TRY(launch_gemm<T, S, T>(ctx, n, kq, d, 1.0, static_cast<const S*>(X->data), X->ld, 1, Q, kq, 1, 0.0, nullptr, 0, B,
                         kq, nullptr));
   RS_TRY(launch_gram<T>(ctx, n, kq, kq, B, kq, B, kq, 1.0 / (double)n, G));
   RS_TRY(run_sym_eig(ctx, G, kq, sizeof(T) == 8 ? RS_F64 : RS_F32, ev, Wd));
@@ -664,7 +671,7 @@ static int ritz_t(rs_ctx* ctx, const rs_matrix* X, const T* Q, int64_t kq, int64
   return RS_OK;
 }
 
-template <typename T>
+template <typename S, typename T>
 static int sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, T* V, double* sigma2) {
   const int64_t n = X->n, d = X->d, k = p->k;
   const int64_t q = std::max(1, p->q_blocks);
@@ -680,7 +687,7 @@ static int sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
   if (!Yk || !Qall) return RS_ENOMEM;
   T* Qb = Qall;              // q blocks, each d x k contiguous
   T* Qm = Qall + d * kq;     // d x kq row-major basis
-  RS_TRY(range_sketch_t<T>(ctx, X, p, Yk));
+  RS_TRY(range_sketch_t<S, T>(ctx, X, p, Yk));
   RS_TRY(orthonormalize_t<T>(ctx, Yk, d, k, Qb));
   if (q > 1) {
     T* B = static_cast<T*>(rs_scratch(ctx, SCR_B, n * k * sizeof(T)));
@@ -690,9 +697,9 @@ static int sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
     if (!B || !Gd || !Pd || !Pt) return RS_ENOMEM;
     for (int64_t j = 1; j < q; ++j) {
       const T* Qprev = Qb + (j - 1) * d * k;
-      RS_TRY(launch_gemm<T>(ctx, n, k, d, 1.0, static_cast<const T*>(X->data), X->ld, 1, Qprev, k, 1, 0.0, nullptr,
+      RS_TRY(launch_gemm<T, S, T>(ctx, n, k, d, 1.0, static_cast<const S*>(X->data), X->ld, 1, Qprev, k, 1, 0.0, nullptr,
                             0, B, k, nullptr));
-      RS_TRY(launch_gram<T>(ctx, n, d, k, static_cast<const T*>(X->data), X->ld, B, k, 1.0 / (double)n, Gd));
+      RS_TRY(launch_gram<S, T>(ctx, n, d, k, static_cast<const S*>(X->data), X->ld, B, k, 1.0 / (double)n, Gd));
       RS_TRY(to_T<T>(ctx, Gd, d * k, Yk));
       for (int pass = 0; pass < 2; ++pass)
         for (int64_t i = 0; i < j; ++i) {
@@ -707,7 +714,7 @@ static int sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
   for (int64_t j = 0; j < q; ++j)
     RS_CUDA_TRY(cudaMemcpy2DAsync(Qm + j * k, kq * sizeof(T), Qb + j * d * k, k * sizeof(T), k * sizeof(T), d,
                                   cudaMemcpyDeviceToDevice, ctx->stream));
-  RS_TRY(ritz_t<T>(ctx, X, Qm, kq, k, V, sigma2));
+  RS_TRY(ritz_t<S, T>(ctx, X, Qm, kq, k, V, sigma2));
   int st = 0;
   RS_TRY(read_status(ctx, &st));
   if (st & 4) return rs_fail(RS_EINVAL, "rs_sketch: the sketch is rank deficient to working precision");
@@ -716,11 +723,11 @@ static int sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
 
 // ---------------------------------------------------------------------- preconditioner
 
-template <typename T>
+template <typename S, typename T>
 static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const double* sigma2, int64_t k, double lam,
                           rs_matrix* Xt, T* beta, double* beta_hat) {
   const int64_t n = X->n, d = X->d, N = n + d;
-  T* Z = static_cast<T*>(const_cast<void*>(Xt->data));
+  S* Z = static_cast<S*>(const_cast<void*>(Xt->data));
   const int64_t ldz = Xt->ld;
   T* a = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, k * sizeof(T)));
   T* P = static_cast<T*>(rs_scratch(ctx, SCR_P, n * k * sizeof(T)));
@@ -728,22 +735,22 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
   if (!a || !P || !Va) return RS_ENOMEM;
   adiag_kernel<T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(sigma2, (int)k, lam, a);
   RS_LAUNCH_CHECK(ctx);
-  const T* Xd = static_cast<const T*>(X->data);
+  const S* Xd = static_cast<const S*>(X->data);
   // P = X V diag(a);  Z[0:n] = X - P V^T
-  RS_TRY(launch_gemm<T>(ctx, n, k, d, 1.0, Xd, X->ld, 1, V, k, 1, 0.0, nullptr, 0, P, k, a));
-  RS_TRY(launch_gemm<T>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
+  RS_TRY(launch_gemm<T, S, T>(ctx, n, k, d, 1.0, Xd, X->ld, 1, V, k, 1, 0.0, nullptr, 0, P, k, a));
+  RS_TRY(launch_gemm<T, T, S>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
   // Z[n:n+d] = I - V diag(a) V^T   (the rows b_j = M e_j)
   scale_cols_kernel<T><<<blocks_for(ctx, d * k), 256, 0, ctx->stream>>>(V, d, (int)k, a, Va);
   RS_LAUNCH_CHECK(ctx);
-  T* Zb = Z + n * ldz;
-  identity_rows_kernel<T><<<blocks_for(ctx, d * d), 256, 0, ctx->stream>>>(Zb, d, ldz);
+  S* Zb = Z + n * ldz;
+  identity_rows_kernel<S><<<blocks_for(ctx, d * d), 256, 0, ctx->stream>>>(Zb, d, ldz);
   RS_LAUNCH_CHECK(ctx);
-  RS_TRY(launch_gemm<T>(ctx, d, d, k, -1.0, Va, k, 1, V, 1, k, 1.0, Zb, ldz, Zb, ldz, nullptr));
+  RS_TRY(launch_gemm<T, T, S>(ctx, d, d, k, -1.0, Va, k, 1, V, 1, k, 1.0, Zb, ldz, Zb, ldz, nullptr));
   // smoothness constants
   const int blocks = blocks_for(ctx, N * 32);
   double* part = static_cast<double*>(rs_scratch(ctx, SCR_MISC, (blocks + 1) * sizeof(double)));
   if (!part) return RS_ENOMEM;
-  row_beta_kernel<T><<<blocks, 256, 0, ctx->stream>>>(Z, N, n, d, ldz, lam, beta, part);
+  row_beta_kernel<S, T><<<blocks, 256, 0, ctx->stream>>>(Z, N, n, d, ldz, lam, beta, part);
   RS_LAUNCH_CHECK(ctx);
   if (beta_hat) {
     sum_parts_kernel<<<1, 32, 0, ctx->stream>>>(part, blocks, 1.0 / (double)N, part + blocks);
@@ -778,19 +785,23 @@ int map_output_dispatch(rs_ctx* ctx, const void* V, const double* sigma2, int64_
 }
 
 int sketch_dispatch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* V, double* sigma2) {
-  if (X->dtype == RS_F64) return sketch_t<double>(ctx, X, p, static_cast<double*>(V), sigma2);
-  if (X->dtype == RS_F32) return sketch_t<float>(ctx, X, p, static_cast<float*>(V), sigma2);
+  if (X->dtype == RS_F64) return sketch_t<double, double>(ctx, X, p, static_cast<double*>(V), sigma2);
+  if (X->dtype == RS_F32) return sketch_t<float, float>(ctx, X, p, static_cast<float*>(V), sigma2);
+  if (X->dtype == RS_BF16) return sketch_t<__nv_bfloat16, float>(ctx, X, p, static_cast<float*>(V), sigma2);
   return rs_fail(RS_EUNSUPPORTED, "rs_sketch: dtype %d not supported by this build", X->dtype);
 }
 
 int precondition_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k, double lam,
                           rs_matrix* Xt, void* beta, double* beta_hat) {
   if (X->dtype == RS_F64)
-    return precondition_t<double>(ctx, X, static_cast<const double*>(V), sigma2, k, lam, Xt,
+    return precondition_t<double, double>(ctx, X, static_cast<const double*>(V), sigma2, k, lam, Xt,
                                   static_cast<double*>(beta), beta_hat);
   if (X->dtype == RS_F32)
-    return precondition_t<float>(ctx, X, static_cast<const float*>(V), sigma2, k, lam, Xt, static_cast<float*>(beta),
-                                 beta_hat);
+    return precondition_t<float, float>(ctx, X, static_cast<const float*>(V), sigma2, k, lam, Xt,
+                                        static_cast<float*>(beta), beta_hat);
+  if (X->dtype == RS_BF16)
+    return precondition_t<__nv_bfloat16, float>(ctx, X, static_cast<const float*>(V), sigma2, k, lam, Xt,
+                                                static_cast<float*>(beta), beta_hat);
   return rs_fail(RS_EUNSUPPORTED, "rs_precondition: dtype %d not supported by this build", X->dtype);
 }
 
@@ -841,8 +852,9 @@ int rs_range_sketch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
   RS_CHECK_ARG(p && Y, "rs_range_sketch: null argument");
   RS_CHECK_ARG(p->k >= 1 && p->k <= X->d && p->k <= 256, "rs_range_sketch: k must be in [1, min(d, 256)]");
   RS_CHECK_ARG(p->kind == RS_SKETCH_GAUSSIAN || p->kind == RS_SKETCH_COUNTSKETCH, "rs_range_sketch: bad kind");
-  if (X->dtype == RS_F64) return range_sketch_t<double>(ctx, X, p, static_cast<double*>(Y));
-  if (X->dtype == RS_F32) return range_sketch_t<float>(ctx, X, p, static_cast<float*>(Y));
+  if (X->dtype == RS_F64) return range_sketch_t<double, double>(ctx, X, p, static_cast<double*>(Y));
+  if (X->dtype == RS_F32) return range_sketch_t<float, float>(ctx, X, p, static_cast<float*>(Y));
+  if (X->dtype == RS_BF16) return range_sketch_t<__nv_bfloat16, float>(ctx, X, p, static_cast<float*>(Y));
   return rs_fail(RS_EUNSUPPORTED, "rs_range_sketch: dtype %d", X->dtype);
 }
 
@@ -873,9 +885,11 @@ int rs_ritz(rs_ctx* ctx, const rs_matrix* X, const void* Q, int64_t k, void* V, 
   RS_TRY(check_matrix(X, "rs_ritz X"));
   RS_CHECK_ARG(Q && V && sigma2 && k >= 1 && k <= X->d && k <= 256, "rs_ritz: bad arguments");
   if (X->dtype == RS_F64)
-    return ritz_t<double>(ctx, X, static_cast<const double*>(Q), k, k, static_cast<double*>(V), sigma2);
+    return ritz_t<double, double>(ctx, X, static_cast<const double*>(Q), k, k, static_cast<double*>(V), sigma2);
   if (X->dtype == RS_F32)
-    return ritz_t<float>(ctx, X, static_cast<const float*>(Q), k, k, static_cast<float*>(V), sigma2);
+    return ritz_t<float, float>(ctx, X, static_cast<const float*>(Q), k, k, static_cast<float*>(V), sigma2);
+  if (X->dtype == RS_BF16)
+    return ritz_t<__nv_bfloat16, float>(ctx, X, static_cast<const float*>(Q), k, k, static_cast<float*>(V), sigma2);
   return rs_fail(RS_EUNSUPPORTED, "rs_ritz: dtype %d", X->dtype);
 }
 

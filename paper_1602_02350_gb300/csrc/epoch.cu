@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -36,11 +37,23 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// eight bfloat16 (one 16-byte load) widened to float: a bfloat16 is the upper half of a float
+__device__ __forceinline__ void ld_widen8(const __nv_bfloat16* p, float* v) {
+  const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = __uint_as_float(w[k] << 16);
+    v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+  }
+}
+
 // ------------------------------------------------------------------ per-block preparation
 // One thread block per block of steps.  Rows 0..B-1 of the staged tile are the sampled rows
-// (zero beyond the last step), row B is mu, rows B+1..B+3 are zero.
-template <typename T>
-__global__ void __launch_bounds__(256) epoch_prep_kernel(const T* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+// (zero beyond the last step), row B is mu, rows B+1..B+3 are zero.  Z is stored in S and
+// widened to the compute type T while it is staged.
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) epoch_prep_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
                                                          int64_t n, double lam, const uint32_t* __restrict__ idx,
                                                          const T* __restrict__ inv_nq, int64_t m, double eta,
                                                          const T* __restrict__ mu, T* __restrict__ Rt,
@@ -76,14 +89,45 @@ __global__ void __launch_bounds__(256) epoch_prep_kernel(const T* __restrict__ Z
   auto stage = [&](int ch, int buf) {
     T* dst = tile + buf * RP * TS;
     const int64_t cbase = (int64_t)ch * CH;
+    if constexpr (!std::is_same<S, T>::value) {
+      // bfloat16 rows: synchronous 16-byte loads widened to float (the buffer being written was
+      // last read before the previous chunk's closing barrier)
+      constexpr int ES = 16 / sizeof(S);
+      for (int e = tid; e < RP * (CH / ES); e += blockDim.x) {
+        const int r = e / (CH / ES), q = e % (CH / ES);
+        const int64_t col = cbase + q * ES;
+        T v[ES];
+#pragma unroll
+        for (int i = 0; i < ES; ++i) v[i] = T(0);
+        if (r < Bb && col < d) {
+          const S* src = Z + rowid[r] * ld + col;
+          if (col + ES <= d) ld_widen8(src, v);
+          else
+            for (int i = 0; i < (int)(d - col); ++i) v[i] = cvt<T>(src[i]);
+        } else if (r == B) {
+          for (int i = 0; i < ES; ++i)
+            if (col + i < d) v[i] = mu[col + i];
+        }
+        using V = typename Vec<T>::type;
+#pragma unroll
+        for (int i = 0; i < ES; i += E) {
+          V o;
+          if constexpr (sizeof(T) == 4) o = V{v[i], v[i + 1], v[i + 2], v[i + 3]};
+          else o = V{v[i], v[i + 1]};
+          *reinterpret_cast<V*>(dst + r * TS + q * ES + i) = o;
+        }
+      }
+      cp_async_commit();
+      return;
+    }
     for (int e = tid; e < RP * (CH / E); e += blockDim.x) {
       const int r = e / (CH / E), q = e % (CH / E);
       const int64_t col = cbase + q * E;
-      const T* src = Z;
+      const void* src = Z;
       int bytes = 0;
       if (col < d) {
         const int valid = (int)min64(E, d - col) * (int)sizeof(T);
-        if (r < B && r < Bb) { src = Z + rowid[r] * ld + col; bytes = valid; }
+        if (r < B && r < Bb) { src = reinterpret_cast<const T*>(Z) + rowid[r] * ld + col; bytes = valid; }
         else if (r == B) { src = mu + col; bytes = (reinterpret_cast<uintptr_t>(mu + col) & 15) ? 0 : valid; }
       }
       cp_async16(dst + r * TS + q * E, src, bytes);
@@ -217,8 +261,13 @@ __device__ __forceinline__ void st_async16(uint32_t raddr, uint32_t rbar, const 
 
 constexpr long long kWaitCycles = 4000000000LL;   // about two seconds: a wait this long is a fault
 
-template <typename T, int STAGES, int QN>
-__global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+// Row padding of the staged slices when TPC lanes share a column: at least CPW elements and 16 bytes.
+__host__ __device__ constexpr int chain_zpad(int tpc, int cpw, int esize) {
+  return tpc > 1 ? (cpw * esize >= 16 ? cpw : 16 / esize) : 0;
+}
+
+template <typename S, typename T, int STAGES, int QN, int NT>
+__global__ void __launch_bounds__(NT) epoch_chain_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
                                                           const uint32_t* __restrict__ idx, int64_t m,
                                                           const T* __restrict__ Rt, const T* __restrict__ cvec,
                                                           double eta, const T* __restrict__ mu,
@@ -226,22 +275,25 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
                                                           T* __restrict__ wnext, int* status) {
   constexpr int B = kBlk;
   constexpr int E = 16 / sizeof(T);
+  constexpr int ES = 16 / sizeof(S);
   constexpr int CW = 32 * QN;               // columns owned by this block
-  constexpr int NCH = CW / E;               // 16-byte chunks per row slice
-  constexpr int NT = 256;
+  constexpr int NCH = CW / ES;              // 16-byte chunks per row slice
+  constexpr int NW = NT / 32;                 // warps
+  constexpr int RPW = B / NW;                 // rows of the dot product per warp
+  constexpr int H = NT / B;                   // partial sums per row of R p
   constexpr int TPC = NT / CW > 0 ? NT / CW : 1;   // lanes per column in the update (same warp)
   constexpr int JPT = B / TPC;                      // steps per lane in the update
   constexpr int CPW = 32 / TPC;                     // columns per warp in the update
-  constexpr int W16 = 8 * (int)sizeof(T) / 16;      // 16-byte pieces of one warp's 8 partials
+  constexpr int W16 = RPW * (int)sizeof(T) / 16;    // 16-byte pieces of one warp's partials
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) unsigned char ch_sh[];
-  // row stride of the staged slices: CW + CPW puts the TPC lanes that share a column (which
-  // read rows j, j+1, .., j+TPC-1 in the update) on distinct shared-memory banks
-  constexpr int ZS = CW + (TPC > 1 ? CPW : 0);
-  T* Zs = reinterpret_cast<T*>(ch_sh);                     // [STAGES][B][ZS]
-  T* Rs = Zs + (size_t)STAGES * B * ZS;                    // [STAGES][B][B]  (Rt layout: [l][j])
+  // row stride of the staged slices (in S): the padding puts the TPC lanes that share a column
+  // (which read rows j, j+1, .., j+TPC-1 in the update) on distinct shared-memory banks
+  constexpr int ZS = CW + chain_zpad(TPC, CPW, (int)sizeof(S));
+  S* Zs = reinterpret_cast<S*>(ch_sh);                     // [STAGES][B][ZS]
+  T* Rs = reinterpret_cast<T*>(Zs + (size_t)STAGES * B * ZS);   // [STAGES][B][B]  (Rt layout: [l][j])
   T* Cs = Rs + (size_t)STAGES * B * B;                     // [STAGES][B]
   T* recv = Cs + (size_t)STAGES * B;                       // [2][kCsMax][B] partial dots from each rank
   double* Ssum = reinterpret_cast<double*>(recv + 2 * kCsMax * B);   // [CW]
@@ -249,8 +301,8 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
   T* mus = dl + CW;                                        // [CW]
   T* pv = mus + CW;                                        // [B]
   T* av = pv + B;                                          // [B]
-  T* part4 = av + B;                                       // [4][B] partial sums of R p
-  uint32_t* srow = reinterpret_cast<uint32_t*>(part4 + 4 * B);   // [STAGES][B]
+  T* part4 = av + B;                                       // [H][B] partial sums of R p
+  uint32_t* srow = reinterpret_cast<uint32_t*>(part4 + H * B);   // [STAGES][B]
   uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + STAGES * B);   // [2]
   __shared__ int aborted;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -285,18 +337,18 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
   // rows beyond the last step and columns beyond d are zero-filled (source size 0)
   auto load_block = [&](int64_t blk) {
     const int slot = (int)(blk % STAGES);
-    T* zdst = Zs + (size_t)slot * B * ZS;
+    S* zdst = Zs + (size_t)slot * B * ZS;
     const uint32_t* rows = srow + slot * B;
 #pragma unroll
-    for (int r = 0; r < B / 8; ++r) {
-      const int j = warp + 8 * r;
+    for (int r = 0; r < RPW; ++r) {
+      const int j = warp + NW * r;
       const uint32_t row = rows[j];
       for (int q = lane; q < NCH; q += 32) {
-        const int col = q * E;
+        const int col = q * ES;
         int bytes = 0;
-        const T* src = Z;
+        const S* src = Z;
         if (row != 0xFFFFFFFFu && col < cwid) {
-          bytes = min(E, cwid - col) * (int)sizeof(T);
+          bytes = min(ES, cwid - col) * (int)sizeof(S);
           src = Z + (int64_t)row * ld + c0 + col;
         }
         cp_async16(zdst + j * ZS + col, src, bytes);
@@ -334,29 +386,29 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
     const int slot = (int)(blk % STAGES);
     const int par = (int)(blk & 1);
     const int Bb = (int)min64(B, m - blk * B);
-    const T* zs = Zs + (size_t)slot * B * ZS;
+    const S* zs = Zs + (size_t)slot * B * ZS;
     // partial p_j over this block's columns for rows 8 warp .. 8 warp + 7, pushed to every rank
     {
       T dv[QN];
 #pragma unroll
       for (int q = 0; q < QN; ++q) dv[q] = dl[lane + 32 * q];
-      T part[8];
+      T part[RPW];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const T* zr = zs + (8 * warp + r) * ZS + lane;
+      for (int r = 0; r < RPW; ++r) {
+        const S* zr = zs + (RPW * warp + r) * ZS + lane;
         T s = T(0);
 #pragma unroll
-        for (int q = 0; q < QN; ++q) s = fma(zr[32 * q], dv[q], s);
+        for (int q = 0; q < QN; ++q) s = fma(cvt<T>(zr[32 * q]), dv[q], s);
         part[r] = s;
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int r = 0; r < 8; ++r) part[r] += __shfl_xor_sync(0xffffffffu, part[r], o);
+        for (int r = 0; r < RPW; ++r) part[r] += __shfl_xor_sync(0xffffffffu, part[r], o);
       if (lane < CS) {
-        uint32_t pw[8 * sizeof(T) / 4];
+        uint32_t pw[RPW * sizeof(T) / 4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < RPW; ++r) {
           if constexpr (sizeof(T) == 8) {
             pw[2 * r] = (uint32_t)__double2loint(part[r]);
             pw[2 * r + 1] = (uint32_t)__double2hiint(part[r]);
@@ -364,7 +416,7 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
             pw[r] = __float_as_uint(part[r]);
           }
         }
-        const uint32_t base = recv_remote + (uint32_t)(((par * kCsMax + rank) * B + 8 * warp) * sizeof(T));
+        const uint32_t base = recv_remote + (uint32_t)(((par * kCsMax + rank) * B + RPW * warp) * sizeof(T));
         const uint32_t rbar = par ? bar_remote1 : bar_remote0;
 #pragma unroll
         for (int h = 0; h < W16; ++h) st_async16(base + 16 * h, rbar, pw + 4 * h);
@@ -390,7 +442,7 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
     }
     __syncthreads();
     if (tid == 0 && blk + 2 < nblk) mbar_arm(&mbar[par], tx_per_block);   // next use: block blk + 2
-    // a = R p + c: thread (j, h) sums the terms l = h, h+4, ... <= j (R is lower triangular, zero
+    // a = R p + c: thread (j, h) sums the terms l = h, h+H, ... <= j (R is lower triangular, zero
     // above the diagonal, so the loop may run to the end of its group); fixed combine order below
     {
       const int j = tid & (B - 1), h = tid >> 6;
@@ -398,16 +450,21 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
       T s0 = T(0), s1 = T(0);
       const int lend = j + 1;
       int l = h;
-      for (; l + 4 < lend; l += 8) {
+      for (; l + H < lend; l += 2 * H) {
         s0 = fma(rs[l * B], pv[l], s0);
-        s1 = fma(rs[(l + 4) * B], pv[l + 4], s1);
+        s1 = fma(rs[(l + H) * B], pv[l + H], s1);
       }
       if (l < lend) s0 = fma(rs[l * B], pv[l], s0);
       part4[h * B + j] = s0 + s1;
     }
     __syncthreads();
     if (tid < B)
-      av[tid] = Cs[(size_t)slot * B + tid] + ((part4[tid] + part4[B + tid]) + (part4[2 * B + tid] + part4[3 * B + tid]));
+    {
+      T sa = Cs[(size_t)slot * B + tid];
+#pragma unroll
+      for (int hh = 0; hh < H; ++hh) sa += part4[hh * B + tid];   // fixed order
+      av[tid] = sa;
+    }
     __syncthreads();
     // rank-B update: lanes g = 0..TPC-1 of a column take steps j = g, g + TPC, ... and combine by
     // shuffles (the padded row stride keeps their shared-memory reads on distinct banks)
@@ -418,7 +475,7 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
 #pragma unroll 8
       for (int jj = 0; jj < JPT; ++jj) {
         const int j = g + TPC * jj;
-        const T az = av[j] * zs[j * ZS + c];
+        const T az = av[j] * cvt<T>(zs[j * ZS + c]);
         u += az;
         w = fma(wt, az, w);
         wt -= T(TPC);
@@ -446,18 +503,18 @@ __global__ void __launch_bounds__(256) epoch_chain_kernel(const T* __restrict__ 
 }
 
 struct ChainPlan {
-  int cs = 0, qn = 0, stages = 0;
+  int cs = 0, qn = 0, stages = 0, nt = 0;
   size_t shm = 0;
 };
 
-template <typename T>
-size_t chain_smem(int qn, int stages) {
+template <typename S, typename T>
+size_t chain_smem(int qn, int stages, int nt) {
   const int CW = 32 * qn;
-  const int TPC = std::max(1, 256 / CW);
-  const int ZS = CW + (TPC > 1 ? 32 / TPC : 0);
-  return (size_t)stages * kBlk * ZS * sizeof(T) + (size_t)stages * kBlk * kBlk * sizeof(T) +
+  const int TPC = std::max(1, nt / CW);
+  const int ZS = CW + chain_zpad(TPC, 32 / TPC, (int)sizeof(S));
+  return (size_t)stages * kBlk * ZS * sizeof(S) + (size_t)stages * kBlk * kBlk * sizeof(T) +
          (size_t)stages * kBlk * sizeof(T) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + (size_t)CW * sizeof(double) +
-         2 * (size_t)CW * sizeof(T) + 6 * (size_t)kBlk * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
+         2 * (size_t)CW * sizeof(T) + (2 + nt / kBlk) * (size_t)kBlk * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
          2 * sizeof(uint64_t) + 64;
 }
 
@@ -471,16 +528,25 @@ int choose_cluster(int64_t d) {
   return cs;
 }
 
-template <typename T>
+// Threads per block of the chain: 512 by default, RS_CHAIN_THREADS = 256 or 512 overrides.
+int choose_threads() {
+  const char* env = std::getenv("RS_CHAIN_THREADS");
+  const int nt = env ? std::atoi(env) : 512;
+  return (nt == 256 || nt == 512) ? nt : 512;
+}
+
+template <typename S, typename T>
 ChainPlan plan_chain(int64_t d, int cs) {
   ChainPlan p;
+  const int nt = choose_threads();
   if (cs < 1 || cs > kCsMax || (cs & (cs - 1))) return p;
   const int64_t per = (d + cs - 1) / cs;
   int qn = per <= 64 ? 2 : (per <= 128 ? 4 : (per <= 256 ? 8 : 0));
   if (!qn) return p;
   for (int st = 4; st >= 2; --st) {
-    const size_t shm = chain_smem<T>(qn, st);
+    const size_t shm = chain_smem<S, T>(qn, st, nt);
     if (shm <= 200 * 1024) {
+      p.nt = nt;
       p.cs = cs;
       p.qn = qn;
       p.stages = st;
@@ -491,16 +557,16 @@ ChainPlan plan_chain(int64_t d, int cs) {
   return p;
 }
 
-template <typename T, int ST, int QN>
-int launch_chain(rs_ctx* ctx, const ChainPlan& pl, const T* Z, int64_t N, int64_t ld, int64_t d,
+template <typename S, typename T, int ST, int QN, int NT>
+int launch_chain(rs_ctx* ctx, const ChainPlan& pl, const S* Z, int64_t N, int64_t ld, int64_t d,
                  const uint32_t* idx, int64_t m, const T* Rt, const T* cv, double eta, const T* mu, const T* wbar,
                  int average, T* wnext) {
-  auto kern = epoch_chain_kernel<T, ST, QN>;
+  auto kern = epoch_chain_kernel<S, T, ST, QN, NT>;
   RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
   if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(pl.cs, 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
   cfg.dynamicSmemBytes = pl.shm;
   cfg.stream = ctx->stream;
   cudaLaunchAttribute attr[1];
@@ -523,28 +589,30 @@ int launch_chain(rs_ctx* ctx, const ChainPlan& pl, const T* Z, int64_t N, int64_
 
 }  // namespace
 
-template <typename T>
+template <typename S, typename T>
 int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
                  int64_t m, double eta, const T* wbar, const T* mu, int average, T* wnext) {
   const int64_t N = Z->n, d = Z->d;
-  const T* Zd = static_cast<const T*>(Z->data);
+  const S* Zd = static_cast<const S*>(Z->data);
   const int64_t nblk = (m + kBlk - 1) / kBlk;
   T* Rt = static_cast<T*>(rs_scratch(ctx, SCR_R, (size_t)nblk * kBlk * kBlk * sizeof(T)));
   T* cv = static_cast<T*>(rs_scratch(ctx, SCR_C, (size_t)nblk * kBlk * sizeof(T)));
   if (!Rt || !cv) return RS_ENOMEM;
   constexpr int RP = kBlk + 4, CH = 64, E = 16 / sizeof(T);
   const size_t pshm = (size_t)(2 * RP * (CH + E) + RP * (RP + 1) + 2 * kBlk * (kBlk + 1)) * sizeof(T);
-  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
-  epoch_prep_kernel<T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m, eta, mu,
-                                                                   Rt, cv);
+  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+  epoch_prep_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m, eta,
+                                                                      mu, Rt, cv);
   RS_LAUNCH_CHECK(ctx);
   for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
-    const ChainPlan pl = plan_chain<T>(d, cs);
+    const ChainPlan pl = plan_chain<S, T>(d, cs);
     if (!pl.cs) continue;
     int rc = RS_EUNSUPPORTED;
 #define RS_CHAIN(ST, QN)                                                                                          \
-  if (pl.stages == ST && pl.qn == QN)                                                                             \
-    rc = launch_chain<T, ST, QN>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext);
+  if (pl.stages == ST && pl.qn == QN && pl.nt == 256)                                                             \
+    rc = launch_chain<S, T, ST, QN, 256>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext);   \
+  if (pl.stages == ST && pl.qn == QN && pl.nt == 512)                                                             \
+    rc = launch_chain<S, T, ST, QN, 512>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext);
     RS_CHAIN(4, 2) RS_CHAIN(4, 4) RS_CHAIN(4, 8) RS_CHAIN(3, 2) RS_CHAIN(3, 4) RS_CHAIN(3, 8)
     RS_CHAIN(2, 2) RS_CHAIN(2, 4) RS_CHAIN(2, 8)
 #undef RS_CHAIN
@@ -553,7 +621,9 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
   return rs_fail(RS_EUNSUPPORTED, "rs_svrg_epoch: no thread-block cluster layout fits d = %lld", (long long)d);
 }
 
-template int svrg_epoch_t<float>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const float*, int64_t,
-                                 double, const float*, const float*, int, float*);
-template int svrg_epoch_t<double>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const double*, int64_t,
-                                  double, const double*, const double*, int, double*);
+template int svrg_epoch_t<float, float>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const float*,
+                                        int64_t, double, const float*, const float*, int, float*);
+template int svrg_epoch_t<double, double>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const double*,
+                                          int64_t, double, const double*, const double*, int, double*);
+template int svrg_epoch_t<__nv_bfloat16, float>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*,
+                                                const float*, int64_t, double, const float*, const float*, int, float*);

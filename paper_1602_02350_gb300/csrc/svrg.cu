@@ -5,6 +5,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -135,16 +136,56 @@ __global__ void norm2_kernel(const T* v, int64_t d, double* out) {
   }
 }
 
-// Fallback for rows wider than the register path: r_i = gamma_i (z_i^T w - y_i)/N, then mu = Z^T r.
-template <typename T>
-__global__ void residual_kernel(const T* Z, int64_t N, int64_t n, int64_t d, int64_t ld, const T* y, T lam, const T* w,
-                                T* r) {
+// Rows of any width and storage type S (double, float or bfloat16), compute type T: a warp
+// streams one row at a time (16-byte vector loads, eight in flight per lane), reduces the dot
+// product, re-reads the row (an L1 hit) and accumulates r_i z_i into its own shared-memory copy
+// of the gradient; the eight warp copies are summed in a fixed order.
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) fullgrad_wide_kernel(const S* __restrict__ Z, int64_t N, int64_t n, int64_t d,
+                                                            int64_t ld, const T* __restrict__ y, T lam,
+                                                            const T* __restrict__ w, T* __restrict__ part) {
+  constexpr int E = 16 / sizeof(S);
+  extern __shared__ __align__(16) unsigned char fw_sh[];
+  T* ws = reinterpret_cast<T*>(fw_sh);        // [d]
+  T* acc = ws + ((d + 3) & ~int64_t(3));      // [warps][d]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) ws[c] = w[c];
+  for (int64_t c = threadIdx.x; c < (int64_t)nw * d; c += blockDim.x) acc[c] = T(0);
+  __syncthreads();
+  T* my = acc + (int64_t)warp * d;
+  const int64_t nvec = (d + E - 1) / E;
+  const T inv_n = T(1) / (T)n;
   for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
-    T s = T(0);
-    for (int64_t c = lane; c < d; c += 32) s = fma(Z[i * ld + c], w[c], s);
-    s = warp_sum(s);
-    if (lane == 0) r[i] = i < n ? (s - y[i]) / (T)n : lam * s;
+    const S* row = Z + i * ld;
+    T dot = T(0);
+#pragma unroll 8
+    for (int64_t q = lane; q < nvec; q += 32) {
+      S v[E];
+      *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(row + q * E);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t c = q * E + e;
+        if (c < d) dot = fma(cvt<T>(v[e]), ws[c], dot);
+      }
+    }
+    dot = warp_sum(dot);
+    const T r = i < n ? (dot - y[i]) * inv_n : lam * dot;
+#pragma unroll 8
+    for (int64_t q = lane; q < nvec; q += 32) {
+      S v[E];
+      *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(row + q * E);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t c = q * E + e;
+        if (c < d) my[c] = fma(r, cvt<T>(v[e]), my[c]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
+    T t = T(0);
+    for (int w2 = 0; w2 < nw; ++w2) t += acc[(int64_t)w2 * d + c];
+    part[(int64_t)blockIdx.x * d + c] = t;
   }
 }
 
@@ -166,13 +207,16 @@ __global__ void finite_check_kernel(const T* w, int64_t d, double limit, int* st
   if (big) atomicOr(status, 8);
 }
 
-template <typename T>
-__global__ void row_beta_only_kernel(const T* Z, int64_t N, int64_t n, int64_t d, int64_t ld, double lam, T* beta) {
+template <typename S, typename T>
+__global__ void row_beta_only_kernel(const S* Z, int64_t N, int64_t n, int64_t d, int64_t ld, double lam, T* beta) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double gd = (double)N / (double)n, gr = lam * (double)N;
   for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
     T s = T(0);
-    for (int64_t c = lane; c < d; c += 32) s = fma(Z[i * ld + c], Z[i * ld + c], s);
+    for (int64_t c = lane; c < d; c += 32) {
+      const T v = cvt<T>(Z[i * ld + c]);
+      s = fma(v, v, s);
+    }
     s = warp_sum(s);
     if (lane == 0) beta[i] = (T)((i < n ? gd : gr) * (double)s);
   }
@@ -197,16 +241,18 @@ __global__ void mean_kernel(const T* v, int64_t N, double* out) {
 
 // ====================================================================== launchers
 
-template <typename T>
+// mu over the rows of Z (storage S, compute T); the rows i >= n are regulariser rows.  Called
+// with Z = X and n = X->n it gives the data part of the gradient on the stored data.
+template <typename S, typename T>
 static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t n, double lam, const T* w, T* mu,
                            double* norm2_dev) {
   const int64_t N = Z->n, d = Z->d;
-  const T* Zd = static_cast<const T*>(Z->data);
-  constexpr int E = Vec<T>::N;
+  constexpr int E = 16 / sizeof(S);
   const int64_t vecs = (d + E - 1) / E;
   const int vpl = (int)((vecs + 31) / 32);
   const int threads = 256;
-  if (vpl <= 8) {
+  if constexpr (std::is_same<S, T>::value) if (vpl <= 8) {
+    const T* Zd = static_cast<const T*>(Z->data);
     const int blocks = ctx->num_sms * 2;
     T* part = static_cast<T*>(rs_scratch(ctx, SCR_PART2, (size_t)blocks * d * sizeof(T)));
     if (!part) return RS_ENOMEM;
@@ -231,33 +277,50 @@ static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t 
     }
     return RS_OK;
   }
-  // wide rows: two passes
-  T* r = static_cast<T*>(rs_scratch(ctx, SCR_PART2, N * sizeof(T)));
-  double* md = static_cast<double*>(rs_scratch(ctx, SCR_TMPV, d * sizeof(double)));
-  if (!r || !md) return RS_ENOMEM;
-  residual_kernel<T><<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(Zd, N, n, d, Z->ld, y, (T)lam, w, r);
+  // wide rows or bfloat16 storage: shared-memory accumulators
+  const size_t shm = ((size_t)((d + 3) & ~int64_t(3)) + (size_t)(threads / 32) * d) * sizeof(T);
+  if (shm > 220 * 1024) return rs_fail(RS_EUNSUPPORTED, "full gradient: d = %lld too wide for on-chip accumulators", (long long)d);
+  const int blocks = ctx->num_sms * (shm <= 100 * 1024 ? 2 : 1);
+  T* part = static_cast<T*>(rs_scratch(ctx, SCR_PART2, (size_t)blocks * d * sizeof(T)));
+  if (!part) return RS_ENOMEM;
+  RS_CUDA_TRY(cudaFuncSetAttribute(fullgrad_wide_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  fullgrad_wide_kernel<S, T><<<blocks, threads, shm, ctx->stream>>>(static_cast<const S*>(Z->data), N, n, d, Z->ld, y,
+                                                                    (T)lam, w, part);
   RS_LAUNCH_CHECK(ctx);
-  RS_TRY(launch_gram<T>(ctx, N, d, 1, Zd, Z->ld, r, 1, 1.0, md));
-  convert_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(md, d, mu);
+  fullgrad_reduce_kernel<T><<<(unsigned)((d + 31) / 32), 256, 0, ctx->stream>>>(part, blocks, d, mu);
   RS_LAUNCH_CHECK(ctx);
-  if (norm2_dev) RS_CUDA_TRY(cudaMemsetAsync(norm2_dev, 0, sizeof(double), ctx->stream));
+  if (norm2_dev) {
+    norm2_kernel<T><<<1, 256, 0, ctx->stream>>>(mu, d, norm2_dev);
+    RS_LAUNCH_CHECK(ctx);
+  }
   return RS_OK;
 }
 
-template <typename T>
+template <typename S, typename T>
 int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
                  int64_t m, double eta, const T* wbar, const T* mu, int average, T* wnext);   // epoch.cu
 
+// v = g + lam u (the gradient of Eq. (1) at u from its data part g)
+template <typename T>
+__global__ void add_ridge_kernel(const T* g, const T* u, int64_t d, double lam, T* v) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x)
+    v[c] = g[c] + (T)lam * u[c];
+}
+
 static int check_components(const rs_matrix* Z, int64_t n) {
   RS_TRY(check_matrix(Z, "Z"));
-  RS_CHECK_ARG(Z->dtype == RS_F64 || Z->dtype == RS_F32, "components: dtype must be RS_F64 or RS_F32 in this build");
+  RS_CHECK_ARG(Z->dtype == RS_F64 || Z->dtype == RS_F32 || Z->dtype == RS_BF16,
+               "components: dtype must be RS_F64, RS_F32 or RS_BF16");
   RS_CHECK_ARG(n >= 1 && n < Z->n && Z->n - n == Z->d, "components: Z must have n + d rows");
   return RS_OK;
 }
 
-template <typename T>
-static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, const T* beta_in, const T* V,
-                        const double* sigma2, int64_t k, const rs_svrg_params* p, const T* w0, T* w_out,
+// Alg. 1 epochs on the components Z (storage S, compute T).  With p->refine the full gradient
+// is formed on the stored data X instead (mu = M (X^T (X M w - y)/n + lam M w), storage SX), so
+// that the fixed point is exact for the data as stored even when Z is a rounded copy.
+template <typename S, typename T, typename SX>
+static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const T* y, const T* beta_in,
+                        const T* V, const double* sigma2, int64_t k, const rs_svrg_params* p, const T* w0, T* w_out,
                         rs_history* hist, double* eta_used, int64_t* m_used) {
   const int64_t N = Z->n, d = Z->d, n = N - d;
   const int32_t dt = sizeof(T) == 8 ? RS_F64 : RS_F32;
@@ -266,8 +329,8 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, const T* be
   if (!beta) {
     beta = static_cast<T*>(rs_scratch(ctx, SCR_BETA, N * sizeof(T)));
     if (!beta) return RS_ENOMEM;
-    row_beta_only_kernel<T><<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(static_cast<const T*>(Z->data), N, n, d,
-                                                                               Z->ld, lam, beta);
+    row_beta_only_kernel<S, T><<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(static_cast<const S*>(Z->data), N, n,
+                                                                                  d, Z->ld, lam, beta);
     RS_LAUNCH_CHECK(ctx);
   }
   uint32_t* W = static_cast<uint32_t*>(rs_scratch(ctx, SCR_W, N * sizeof(uint32_t)));
@@ -294,22 +357,38 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, const T* be
   T* mu = static_cast<T*>(rs_scratch(ctx, SCR_MU, d * sizeof(T)));
   uint32_t* idx = static_cast<uint32_t*>(rs_scratch(ctx, SCR_IDX, m * sizeof(uint32_t)));
   T* inq = static_cast<T*>(rs_scratch(ctx, SCR_INVNQ, m * sizeof(T)));
-  if (!wa || !wb || !mu || !idx || !inq) return RS_ENOMEM;
+  T* tmp = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, 2 * d * sizeof(T)));
+  if (!wa || !wb || !mu || !idx || !inq || !tmp) return RS_ENOMEM;
+  const bool refine = p->refine && X;
   if (w0) RS_CUDA_TRY(cudaMemcpyAsync(wa, w0, d * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
   else RS_CUDA_TRY(cudaMemsetAsync(wa, 0, d * sizeof(T), ctx->stream));
-  const int S = p->epochs;
+  const int nep = p->epochs;
   std::vector<cudaEvent_t> ev;
   if (hist && hist->epoch_ms) {
-    ev.resize(S + 1);
+    ev.resize(nep + 1);
     for (auto& e : ev) RS_CUDA_TRY(cudaEventCreate(&e));
     RS_CUDA_TRY(cudaEventRecord(ev[0], ctx->stream));
   }
   double* norms = scal + 4;
-  for (int s = 0; s < S; ++s) {
+  for (int s = 0; s < nep; ++s) {
     const bool want_norm = hist && hist->mu_norm2;
-    RS_TRY(full_gradient_t<T>(ctx, Z, y, n, lam, wa, mu, want_norm ? norms + s : nullptr));
+    if (refine) {
+      T* u = tmp;
+      T* g = tmp + d;
+      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, u));                     // u = M w
+      RS_TRY(full_gradient_t<SX, T>(ctx, X, y, X->n, lam, u, g, nullptr));                   // X^T (X u - y) / n
+      add_ridge_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(g, u, d, lam, g);     // + lam u
+      RS_LAUNCH_CHECK(ctx);
+      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, g, mu));                      // mu = M (...)
+      if (want_norm) {
+        norm2_kernel<T><<<1, 256, 0, ctx->stream>>>(mu, d, norms + s);
+        RS_LAUNCH_CHECK(ctx);
+      }
+    } else {
+      RS_TRY(full_gradient_t<S, T>(ctx, Z, y, n, lam, wa, mu, want_norm ? norms + s : nullptr));
+    }
     RS_TRY(index_stream_dispatch(ctx, W, cum, N, p->seed, (int64_t)p->epoch0 + s, 0, m, p->sampling, dt, idx, inq));
-    RS_TRY(svrg_epoch_t<T>(ctx, Z, n, lam, idx, inq, m, eta, wa, mu, p->average, wb));
+    RS_TRY(svrg_epoch_t<S, T>(ctx, Z, n, lam, idx, inq, m, eta, wa, mu, p->average, wb));
     std::swap(wa, wb);
     if (hist && hist->snapshots && s < hist->capacity)
       RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, static_cast<T*>(hist->snapshots) + (int64_t)s * d));
@@ -323,12 +402,12 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, const T* be
   RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   if (hist) {
-    hist->epochs_run = S;
-    if (hist->mu_norm2 && S > 0)
-      RS_CUDA_TRY(cudaMemcpy(hist->mu_norm2, norms, std::min(S, hist->capacity) * sizeof(double),
+    hist->epochs_run = nep;
+    if (hist->mu_norm2 && nep > 0)
+      RS_CUDA_TRY(cudaMemcpy(hist->mu_norm2, norms, std::min(nep, hist->capacity) * sizeof(double),
                              cudaMemcpyDeviceToHost));
     if (!ev.empty()) {
-      for (int s = 0; s < S && s < hist->capacity; ++s) RS_CUDA_TRY(cudaEventElapsedTime(&hist->epoch_ms[s], ev[0], ev[s + 1]));
+      for (int s = 0; s < nep && s < hist->capacity; ++s) RS_CUDA_TRY(cudaEventElapsedTime(&hist->epoch_ms[s], ev[0], ev[s + 1]));
       for (auto& e : ev) cudaEventDestroy(e);
     }
   }
@@ -347,16 +426,16 @@ static bool is_host_ptr(const void* p) {
   return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
-template <typename T>
+template <typename S, typename T>
 static int solve_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, const rs_sketch_params* sp,
                    const rs_svrg_params* p, void* w_out, rs_history* hist) {
   const int64_t n = Xin->n, d = Xin->d, k = sp->k, N = n + d;
   rs_matrix X = *Xin;
-  const size_t es = sizeof(T);
+  const size_t es = sizeof(T), ss = sizeof(S);
   if (is_host_ptr(Xin->data)) {
-    void* xd = rs_scratch(ctx, SCR_XDEV, (size_t)n * Xin->ld * es);
+    void* xd = rs_scratch(ctx, SCR_XDEV, (size_t)n * Xin->ld * ss);
     if (!xd) return RS_ENOMEM;
-    RS_CUDA_TRY(cudaMemcpyAsync(xd, Xin->data, (size_t)n * Xin->ld * es, cudaMemcpyHostToDevice, ctx->stream));
+    RS_CUDA_TRY(cudaMemcpyAsync(xd, Xin->data, (size_t)n * Xin->ld * ss, cudaMemcpyHostToDevice, ctx->stream));
     X.data = xd;
   }
   const T* y = static_cast<const T*>(yin);
@@ -370,14 +449,14 @@ static int solve_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, const rs_
   T* wdev = static_cast<T*>(host_out ? rs_scratch(ctx, SCR_WOUT, d * es) : w_out);
   T* V = static_cast<T*>(rs_scratch(ctx, SCR_V, d * k * es));
   double* sg = static_cast<double*>(rs_scratch(ctx, SCR_SIGMA, k * sizeof(double)));
-  const int64_t ldz = (d * (int64_t)es + 15) / 16 * 16 / (int64_t)es;
-  T* Zbuf = static_cast<T*>(rs_scratch(ctx, SCR_Z, (size_t)N * ldz * es));
+  const int64_t ldz = (d * (int64_t)ss + 15) / 16 * 16 / (int64_t)ss;
+  S* Zbuf = static_cast<S*>(rs_scratch(ctx, SCR_Z, (size_t)N * ldz * ss));
   T* beta = static_cast<T*>(rs_scratch(ctx, SCR_BETA, N * es));
   if (!wdev || !V || !sg || !Zbuf || !beta) return RS_ENOMEM;
   RS_TRY(sketch_dispatch(ctx, &X, sp, V, sg));
   rs_matrix Zm = {Zbuf, nullptr, N, d, ldz, X.dtype, 0};
   RS_TRY(precondition_dispatch(ctx, &X, V, sg, k, p->lambda, &Zm, beta, nullptr));
-  RS_TRY(svrg_solve_t<T>(ctx, &Zm, y, beta, V, sg, k, p, nullptr, wdev, hist, nullptr, nullptr));
+  RS_TRY(svrg_solve_t<S, T, S>(ctx, &Zm, &X, y, beta, V, sg, k, p, nullptr, wdev, hist, nullptr, nullptr));
   if (host_out) {
     RS_CUDA_TRY(cudaMemcpyAsync(w_out, wdev, d * es, cudaMemcpyDeviceToHost, ctx->stream));
     RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -396,10 +475,13 @@ int rs_full_gradient(rs_ctx* ctx, const rs_matrix* Z, const void* y, int64_t n, 
   RS_CHECK_ARG(y && w && mu, "rs_full_gradient: null argument");
   RS_CHECK_ARG(lambda > 0.0, "rs_full_gradient: lambda must be positive");
   if (Z->dtype == RS_F64)
-    return full_gradient_t<double>(ctx, Z, static_cast<const double*>(y), n, lambda, static_cast<const double*>(w),
-                                   static_cast<double*>(mu), nullptr);
-  return full_gradient_t<float>(ctx, Z, static_cast<const float*>(y), n, lambda, static_cast<const float*>(w),
-                                static_cast<float*>(mu), nullptr);
+    return full_gradient_t<double, double>(ctx, Z, static_cast<const double*>(y), n, lambda,
+                                           static_cast<const double*>(w), static_cast<double*>(mu), nullptr);
+  if (Z->dtype == RS_BF16)
+    return full_gradient_t<__nv_bfloat16, float>(ctx, Z, static_cast<const float*>(y), n, lambda,
+                                                 static_cast<const float*>(w), static_cast<float*>(mu), nullptr);
+  return full_gradient_t<float, float>(ctx, Z, static_cast<const float*>(y), n, lambda, static_cast<const float*>(w),
+                                       static_cast<float*>(mu), nullptr);
 }
 
 int rs_svrg_epoch(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lambda, const uint32_t* idx, const void* inv_nq,
@@ -410,15 +492,19 @@ int rs_svrg_epoch(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lambda, con
   RS_CHECK_ARG(m >= 1 && m < (1LL << 31), "rs_svrg_epoch: m out of range");
   RS_CHECK_ARG(w_next != w_bar, "rs_svrg_epoch: w_next must not alias w_bar");
   if (Z->dtype == RS_F64)
-    return svrg_epoch_t<double>(ctx, Z, n, lambda, idx, static_cast<const double*>(inv_nq), m, eta,
-                                static_cast<const double*>(w_bar), static_cast<const double*>(mu), average,
-                                static_cast<double*>(w_next));
-  return svrg_epoch_t<float>(ctx, Z, n, lambda, idx, static_cast<const float*>(inv_nq), m, eta,
-                             static_cast<const float*>(w_bar), static_cast<const float*>(mu), average,
-                             static_cast<float*>(w_next));
+    return svrg_epoch_t<double, double>(ctx, Z, n, lambda, idx, static_cast<const double*>(inv_nq), m, eta,
+                                        static_cast<const double*>(w_bar), static_cast<const double*>(mu), average,
+                                        static_cast<double*>(w_next));
+  if (Z->dtype == RS_BF16)
+    return svrg_epoch_t<__nv_bfloat16, float>(ctx, Z, n, lambda, idx, static_cast<const float*>(inv_nq), m, eta,
+                                              static_cast<const float*>(w_bar), static_cast<const float*>(mu),
+                                              average, static_cast<float*>(w_next));
+  return svrg_epoch_t<float, float>(ctx, Z, n, lambda, idx, static_cast<const float*>(inv_nq), m, eta,
+                                    static_cast<const float*>(w_bar), static_cast<const float*>(mu), average,
+                                    static_cast<float*>(w_next));
 }
 
-int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const void* y, const void* beta, const void* V,
+int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const void* y, const void* beta, const void* V,
                   const double* sigma2, int64_t k, const rs_svrg_params* p, const void* w0, void* w_out,
                   rs_history* hist, double* eta_used, int64_t* m_used) {
   RS_TRY(rs_enter(ctx));
@@ -430,13 +516,24 @@ int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const void* y, const void* be
   RS_CHECK_ARG(p->lambda > 0.0, "rs_svrg_solve: lambda must be positive");
   RS_CHECK_ARG(p->epochs >= 0 && p->epoch0 >= 0, "rs_svrg_solve: bad epoch counts");
   RS_CHECK_ARG(p->sampling == RS_SAMPLE_IMPORTANCE || p->sampling == RS_SAMPLE_UNIFORM, "rs_svrg_solve: bad sampling");
+  if (p->refine) {
+    RS_CHECK_ARG(X != nullptr, "rs_svrg_solve: refinement needs the stored data X");
+    RS_TRY(check_matrix(X, "rs_svrg_solve X"));
+    RS_CHECK_ARG(X->n == n && X->d == Z->d, "rs_svrg_solve: X must be n x d");
+    RS_CHECK_ARG(X->dtype == Z->dtype, "rs_svrg_solve: X and Z must have the same storage type");
+  }
   if (Z->dtype == RS_F64)
-    return svrg_solve_t<double>(ctx, Z, static_cast<const double*>(y), static_cast<const double*>(beta),
-                                static_cast<const double*>(V), sigma2, k, p, static_cast<const double*>(w0),
-                                static_cast<double*>(w_out), hist, eta_used, m_used);
-  return svrg_solve_t<float>(ctx, Z, static_cast<const float*>(y), static_cast<const float*>(beta),
-                             static_cast<const float*>(V), sigma2, k, p, static_cast<const float*>(w0),
-                             static_cast<float*>(w_out), hist, eta_used, m_used);
+    return svrg_solve_t<double, double, double>(ctx, Z, X, static_cast<const double*>(y),
+                                                static_cast<const double*>(beta), static_cast<const double*>(V), sigma2,
+                                                k, p, static_cast<const double*>(w0), static_cast<double*>(w_out), hist,
+                                                eta_used, m_used);
+  if (Z->dtype == RS_BF16)
+    return svrg_solve_t<__nv_bfloat16, float, __nv_bfloat16>(
+        ctx, Z, X, static_cast<const float*>(y), static_cast<const float*>(beta), static_cast<const float*>(V), sigma2,
+        k, p, static_cast<const float*>(w0), static_cast<float*>(w_out), hist, eta_used, m_used);
+  return svrg_solve_t<float, float, float>(ctx, Z, X, static_cast<const float*>(y), static_cast<const float*>(beta),
+                                           static_cast<const float*>(V), sigma2, k, p, static_cast<const float*>(w0),
+                                           static_cast<float*>(w_out), hist, eta_used, m_used);
 }
 
 int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp, const rs_svrg_params* p,
@@ -444,12 +541,14 @@ int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_par
   RS_TRY(rs_enter(ctx));
   RS_CHECK_ARG(X && X->data && y && sp && p && w_out, "rs_solve: null argument");
   RS_CHECK_ARG(X->n >= 1 && X->d >= 1 && X->ld >= X->d, "rs_solve: bad shape");
-  RS_CHECK_ARG(X->dtype == RS_F64 || X->dtype == RS_F32, "rs_solve: dtype must be RS_F64 or RS_F32 in this build");
+  RS_CHECK_ARG(X->dtype == RS_F64 || X->dtype == RS_F32 || X->dtype == RS_BF16,
+               "rs_solve: dtype must be RS_F64, RS_F32 or RS_BF16");
   RS_CHECK_ARG((X->ld * (int64_t)dtype_size(X->dtype)) % 16 == 0, "rs_solve: row stride must be a multiple of 16 bytes");
   RS_CHECK_ARG(sp->k >= 1 && sp->k <= X->d && sp->k <= 256, "rs_solve: k must be in [1, min(d, 256)]");
   RS_CHECK_ARG(p->lambda > 0.0 && p->epochs >= 0, "rs_solve: bad SVRG parameters");
-  if (X->dtype == RS_F64) return solve_t<double>(ctx, X, y, sp, p, w_out, hist);
-  return solve_t<float>(ctx, X, y, sp, p, w_out, hist);
+  if (X->dtype == RS_F64) return solve_t<double, double>(ctx, X, y, sp, p, w_out, hist);
+  if (X->dtype == RS_BF16) return solve_t<__nv_bfloat16, float>(ctx, X, y, sp, p, w_out, hist);
+  return solve_t<float, float>(ctx, X, y, sp, p, w_out, hist);
 }
 
 }  // extern "C"
