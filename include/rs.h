@@ -274,6 +274,69 @@ int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_par
 int rs_objective(rs_ctx* ctx, const rs_matrix* X, const void* y, double lambda, const void* w,
                  const void* w_ref, double* out);
 
+/* tr(C) = ||X||_F^2 / n (Eq. (2)), accumulated in double; the tail sum of the spectrum in the
+ * runtime model of Thm 1 is tr(C) minus the leading sketched eigenvalues.  out: host, 1
+ * double.  Synchronises. */
+int rs_trace_c(rs_ctx* ctx, const rs_matrix* X, double* out);
+
+/* ------------------------------------------------------- parameter proposal
+ *
+ * The paper sets the SVRG parameters from theory (Sec. 3, the SVRG theorem of Xiao and Zhang:
+ * eta = 0.1 / beta^, m = ceil(kappa^_F)) and leaves the sketch rank k to the user (Thm 1 gives
+ * the runtime it trades off).  The library adds a small network that proposes (k, eta, m) from
+ * the sketched spectrum; the theory setting is its fallback.  Nothing below has a counterpart
+ * in the paper except those defaults.
+ *
+ * Network: x (67 inputs) -> ReLU(W1 x + b1) (128) -> ReLU(W2 . + b2) (128) -> W3 . + b3 (3).
+ * Parameters theta: one float vector of RS_MLP_NPARAM entries, W1 (128 x 67), b1, W2
+ * (128 x 128), b2, W3 (3 x 128), b3, each row-major, in that order.
+ * Inputs: log of the 64 leading sketched singular values (sqrt of sigma~_i^2), log lambda,
+ * log n, log d.  Outputs: log2 k, ln eta_mult, log2(m / n), where eta = eta_mult / beta^ and
+ * beta^ is the mean smoothness rs_precondition reports. */
+
+#define RS_MLP_IN 67
+#define RS_MLP_HIDDEN 128
+#define RS_MLP_OUT 3
+#define RS_MLP_NPARAM (RS_MLP_HIDDEN * RS_MLP_IN + RS_MLP_HIDDEN + RS_MLP_HIDDEN * RS_MLP_HIDDEN + RS_MLP_HIDDEN + \
+                       RS_MLP_OUT * RS_MLP_HIDDEN + RS_MLP_OUT)
+
+/* out (float, B x 3) = network(theta, X) for the B rows of X (float, B x 67, row-major). */
+int rs_mlp_forward(rs_ctx* ctx, const float* theta, const float* X, int64_t B, float* out);
+
+typedef struct {
+  float lr, beta1, beta2, eps;   /* Adam (Kingma and Ba, ICLR 2015) */
+  int32_t step;                  /* t >= 1 of this update (bias corrections 1 - beta^t) */
+  int32_t reserved;
+} rs_adam_params;
+
+/* One training step on the batch (X: float B x 67, T: float B x 3 targets, 1 <= B):
+ * loss = (1/B) sum_s ||network(theta, x_s) - t_s||^2, its gradient g by backpropagation
+ * (ReLU derivative 0 at 0), then Adam on theta with moment vectors adam_m, adam_v (float,
+ * RS_MLP_NPARAM each, caller-initialised, zero at t = 1).  grad_out (float, RS_MLP_NPARAM;
+ * nullable) receives g; loss_out (device float; nullable) the loss before the update.
+ * Deterministic: per-block gradient partials are summed in a fixed order. */
+int rs_mlp_train_step(rs_ctx* ctx, float* theta, float* adam_m, float* adam_v, const float* X, const float* T,
+                      int64_t B, const rs_adam_params* p, float* grad_out, float* loss_out);
+
+/* Affine normalisation stored with trained weights: the network sees (x - in_mean) / in_std
+ * and its raw output o gives o * out_std + out_mean. */
+typedef struct {
+  float in_mean[RS_MLP_IN], in_std[RS_MLP_IN], out_mean[RS_MLP_OUT], out_std[RS_MLP_OUT];
+} rs_mlp_norm;
+
+/* Propose (k, eta_mult, m) for a problem with sketched eigenvalues sigma2 (host double, 64,
+ * descending: the first 64 of an Alg. 2 sketch of rank >= 64), regularisation lambda, size n x d
+ * and trace_c = tr(C) = ||X||_F^2 / n.  With theta (device) and norm (host) the network runs
+ * on the GPU; its proposal is k = round(2^o0) (clamped to [1, min(64, d)]), eta_mult = e^o1,
+ * m = round(n 2^o2).  The theory setting is used instead (*used_fallback = 1) when theta is
+ * NULL or an output is non-finite or outside eta_mult in [0.01, 8], m / n in [2^-8, 2^6]:
+ * k minimises n d k + (kappa~(k) + n + d) d with kappa~(k) = (k sigma_k^2 + tr(C)
+ * - sum_{i<=k} sigma_i^2) / lambda (Thm 1), eta_mult = 0.1 and m = ceil(kappa~(k) + d)
+ * (= beta^ / lambda for exact eigenvectors).  Outputs are host pointers.  Synchronises. */
+int rs_propose(rs_ctx* ctx, const float* theta, const rs_mlp_norm* norm, const double* sigma2, double lambda,
+               int64_t n, int64_t d, double trace_c, int32_t* k, double* eta_mult, int64_t* m,
+               int32_t* used_fallback);
+
 #ifdef __cplusplus
 }
 #endif

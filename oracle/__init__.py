@@ -22,6 +22,8 @@ step by step:
                   n+d decomposition of Sec. 5.1, smoothness constants of Alg. 3.
 * ``svrg``      - Alg. 1 (SVRG with importance sampling) on the n+d components.
 * ``pipeline``  - Alg. 3 end to end.
+* ``proposal``  - the theory-set parameters of Sec. 3 / Thm 1 and the parameter-proposal
+                  network (forward, backpropagation, Adam) that the library trains.
 
 Every pinned function is tested in ``tests/test_oracle_*.py`` against facts the
 paper and linear algebra fix (closed forms, identities, brute force on tiny
@@ -29,4 +31,4 @@ inputs, library routines).  Functions without such a pin say
 "parity unpinned" in their docstring.
 """
 
-from . import ridge, streams, sketch, precond, svrg, pipeline  # noqa: F401
+from . import ridge, streams, sketch, precond, svrg, pipeline, proposal  # noqa: F401

@@ -47,6 +47,20 @@ class SvrgParams(ctypes.Structure):
                 ("refine", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class AdamParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("step", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+MLP_IN, MLP_HIDDEN, MLP_OUT = 67, 128, 3
+MLP_NPARAM = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_OUT * MLP_HIDDEN + MLP_OUT
+
+
+class MlpNorm(ctypes.Structure):
+    _fields_ = [("in_mean", ctypes.c_float * MLP_IN), ("in_std", ctypes.c_float * MLP_IN),
+                ("out_mean", ctypes.c_float * MLP_OUT), ("out_std", ctypes.c_float * MLP_OUT)]
+
+
 class History(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int32), ("epochs_run", ctypes.c_int32), ("snapshots", ctypes.c_void_p),
                 ("mu_norm2", ctypes.POINTER(ctypes.c_double)), ("epoch_ms", ctypes.POINTER(ctypes.c_float))]
@@ -88,6 +102,12 @@ _SIGS = {
     "rs_solve": [_P, ctypes.POINTER(Matrix), _P, ctypes.POINTER(SketchParams), ctypes.POINTER(SvrgParams), _P,
                  ctypes.POINTER(History)],
     "rs_objective": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_double)],
+    "rs_trace_c": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(ctypes.c_double)],
+    "rs_mlp_forward": [_P, _P, _P, ctypes.c_int64, _P],
+    "rs_mlp_train_step": [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(AdamParams), _P, _P],
+    "rs_propose": [_P, _P, ctypes.POINTER(MlpNorm), ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int64,
+                   ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
 }
 _RESTYPES = {"rs_last_error": ctypes.c_char_p, "rs_launch_count": ctypes.c_int64}
 
@@ -391,3 +411,61 @@ def rs_objective(ctx, X, y, lam, w, w_ref=None):
     _check(lib().rs_objective(ctx.h, ctypes.byref(M), _ptr(y), lam, _ptr(w), _ptr(w_ref),
                               ctypes.cast(out, ctypes.POINTER(ctypes.c_double))))
     return out[0], out[1]
+
+
+def rs_trace_c(ctx, X):
+    """tr(C) = ||X||_F^2 / n in double."""
+    out = ctypes.c_double(0.0)
+    M = matrix(X)
+    _check(lib().rs_trace_c(ctx.h, ctypes.byref(M), ctypes.byref(out)))
+    return out.value
+
+
+# ----------------------------------------------------------------------------- proposal network
+
+def _f32(ctx, t):
+    _need_cuda(t)
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return t
+
+
+def rs_mlp_forward(ctx, theta, X):
+    """Network outputs (B x 3, float32) for the rows of X (B x 67)."""
+    _f32(ctx, theta), _f32(ctx, X)
+    out = ctx._empty(X.shape[0], MLP_OUT, dtype=torch.float32)
+    _check(lib().rs_mlp_forward(ctx.h, _ptr(theta), _ptr(X), X.shape[0], _ptr(out)))
+    return out
+
+
+def rs_mlp_train_step(ctx, theta, adam_m, adam_v, X, T, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                      want_grad=False, loss_out=None):
+    """One Adam step in place on theta / adam_m / adam_v.  Returns (gradient or None, loss tensor)."""
+    for t in (theta, adam_m, adam_v, X, T):
+        _f32(ctx, t)
+    g = ctx._empty(MLP_NPARAM, dtype=torch.float32) if want_grad else None
+    loss = loss_out if loss_out is not None else ctx._empty(1, dtype=torch.float32)
+    p = AdamParams(lr, beta1, beta2, eps, step, 0)
+    _check(lib().rs_mlp_train_step(ctx.h, _ptr(theta), _ptr(adam_m), _ptr(adam_v), _ptr(X), _ptr(T), X.shape[0],
+                                   ctypes.byref(p), _ptr(g), _ptr(loss)))
+    return g, loss
+
+
+def mlp_norm(in_mean, in_std, out_mean, out_std):
+    nm = MlpNorm()
+    for j in range(MLP_IN):
+        nm.in_mean[j], nm.in_std[j] = float(in_mean[j]), float(in_std[j])
+    for j in range(MLP_OUT):
+        nm.out_mean[j], nm.out_std[j] = float(out_mean[j]), float(out_std[j])
+    return nm
+
+
+def rs_propose(ctx, sigma2, lam, n, d, trace_c, theta=None, norm=None):
+    """(k, eta_mult, m, used_fallback) for sketched eigenvalues sigma2 (64 values, descending)."""
+    s = (ctypes.c_double * 64)(*[float(v) for v in list(sigma2)[:64]])
+    if theta is not None:
+        _f32(ctx, theta)
+    k, em, m, fb = ctypes.c_int32(0), ctypes.c_double(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(lib().rs_propose(ctx.h, _ptr(theta), ctypes.byref(norm) if norm is not None else None, s, lam, n, d,
+                            trace_c, ctypes.byref(k), ctypes.byref(em), ctypes.byref(m), ctypes.byref(fb)))
+    return k.value, em.value, m.value, bool(fb.value)

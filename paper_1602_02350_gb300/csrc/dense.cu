@@ -461,6 +461,35 @@ __global__ void objective_finish_kernel(const double* part, int np, int64_t n, i
   }
 }
 
+// ||X||_F^2 accumulated in double: per-block partials, summed in block order by trace_finish
+template <typename TS>
+__global__ void sumsq_kernel(const TS* X, int64_t n, int64_t d, int64_t ld, double* part) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw)
+    for (int64_t c = lane; c < d; c += 32) {
+      const double x = cvt<double>(X[i * ld + c]);
+      a = fma(x, x, a);
+    }
+  a = warp_sum(a);
+  if (lane == 0) sh[warp] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) t += sh[w2];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void trace_finish_kernel(const double* part, int np, double inv_n, double* out) {
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int p = 0; p < np; ++p) t += part[p];
+    *out = t * inv_n;
+  }
+}
+
 int blocks_for(rs_ctx* ctx, int64_t work, int threads = 256) {
   int64_t g = (work + threads - 1) / threads;
   const int64_t cap = (int64_t)ctx->num_sms * 8;
@@ -842,6 +871,28 @@ int objective_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* y, double la
   return RS_OK;
 }
 
+int trace_dispatch(rs_ctx* ctx, const rs_matrix* X, double* out) {
+  const int64_t n = X->n, d = X->d;
+  const int blocks = blocks_for(ctx, n * 32);
+  double* part = static_cast<double*>(rs_scratch(ctx, SCR_MISC, (blocks + 1) * sizeof(double)));
+  if (!part) return RS_ENOMEM;
+  if (X->dtype == RS_F64)
+    sumsq_kernel<double><<<blocks, 256, 0, ctx->stream>>>(static_cast<const double*>(X->data), n, d, X->ld, part);
+  else if (X->dtype == RS_F32)
+    sumsq_kernel<float><<<blocks, 256, 0, ctx->stream>>>(static_cast<const float*>(X->data), n, d, X->ld, part);
+  else if (X->dtype == RS_BF16)
+    sumsq_kernel<__nv_bfloat16><<<blocks, 256, 0, ctx->stream>>>(static_cast<const __nv_bfloat16*>(X->data), n, d,
+                                                                 X->ld, part);
+  else
+    return rs_fail(RS_EUNSUPPORTED, "rs_trace_c: dtype %d", X->dtype);
+  RS_LAUNCH_CHECK(ctx);
+  trace_finish_kernel<<<1, 32, 0, ctx->stream>>>(part, blocks, 1.0 / (double)n, part + blocks);
+  RS_LAUNCH_CHECK(ctx);
+  RS_CUDA_TRY(cudaMemcpyAsync(out, part + blocks, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return RS_OK;
+}
+
 // ====================================================================== C ABI
 
 extern "C" {
@@ -929,6 +980,13 @@ int rs_objective(rs_ctx* ctx, const rs_matrix* X, const void* y, double lambda, 
   RS_TRY(check_matrix(X, "rs_objective X"));
   RS_CHECK_ARG(y && w && out, "rs_objective: null argument");
   return objective_dispatch(ctx, X, y, lambda, w, w_ref, out);
+}
+
+int rs_trace_c(rs_ctx* ctx, const rs_matrix* X, double* out) {
+  RS_TRY(rs_enter(ctx));
+  RS_TRY(check_matrix(X, "rs_trace_c X"));
+  RS_CHECK_ARG(out, "rs_trace_c: null argument");
+  return trace_dispatch(ctx, X, out);
 }
 
 }  // extern "C"

@@ -162,3 +162,18 @@ def random_indices(N, m, seed):
 def random_positive(m, seed, lo=0.5, hi=2.0):
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, m)
+
+
+# --- proposal network ---------------------------------------------------------------------------
+
+MLP_SHAPES = [(128, 67), (128,), (128, 128), (128,), (3, 128), (3,)]
+
+
+def mlp_init(seed):
+    """Flat float64 parameter vector of the 67 -> 128 -> 128 -> 3 network: weights drawn
+    N(0, 2 / fan_in) (He et al., 2015), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in MLP_SHAPES:
+        parts.append(rng.standard_normal(s).ravel() * np.sqrt(2.0 / s[1]) if len(s) == 2 else np.zeros(s))
+    return np.concatenate(parts)
