@@ -274,6 +274,57 @@ int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_par
 int rs_objective(rs_ctx* ctx, const rs_matrix* X, const void* y, double lambda, const void* w,
                  const void* w_ref, double* out);
 
+/* ------------------------------------------------------- batched solves
+ *
+ * Many ridge problems, each at several lambda (a regularisation path) and/or several SVRG
+ * settings, solved together: one Alg. 2 sketch per problem shared by all its chains, one set of
+ * components Z (Eq. (11), Sec. 5.1) per (problem, lambda), and per epoch one pass over each
+ * problem's stored data for the snapshot gradients of all its chains (refined form:
+ * U = [M_c w~_c], R = X U - y 1^T, G = X^T R / n, mu_c = M_c (G e_c + lam_c M_c w~_c)), one launch
+ * for every chain's index stream, one for every chain's block preparation, and one per distinct
+ * d for the inner loops themselves (one thread-block cluster per chain).  Epochs 2..S are
+ * captured in one CUDA graph and launched once.  The paper solves one problem at a time;
+ * batching is this library's extension. */
+
+typedef struct {
+  rs_matrix X;        /* n x d data, RS_F32 or RS_BF16 (all problems of a call share the dtype) */
+  const float* y;     /* n labels */
+  int32_t k;          /* sketch rank, 1 <= k <= min(d, 256); 0 = max(1, d / 16) */
+  int32_t reserved;
+} rs_problem;
+
+typedef struct {
+  int32_t problem;    /* index into the problem array */
+  int32_t reserved;
+  double lambda;      /* > 0 */
+  double eta_mult;    /* eta = eta_mult / beta^, beta^ the mean smoothness of this chain's
+                         components; <= 0 selects 1 */
+  int64_t m;          /* epoch length; <= 0 selects 2 n */
+  uint64_t seed;      /* SVRG index stream seed (Philox key) */
+  float* w_out;       /* d floats (device): w = M w~_S in original coordinates */
+  float* snapshots;   /* nullable: epochs x d floats (device), w after each epoch */
+} rs_chain;
+
+typedef struct {
+  int32_t epochs;       /* S >= 1 */
+  int32_t sketch_kind;  /* RS_SKETCH_GAUSSIAN or RS_SKETCH_COUNTSKETCH */
+  int32_t q_blocks;     /* Krylov blocks of Alg. 2 (>= 1) */
+  int32_t refine;       /* 1: snapshot gradients on the stored data (required for RS_BF16);
+                           0: one pass over each chain's components Z */
+  int32_t use_graph;    /* 1: capture epochs 2..S in a CUDA graph */
+  int32_t average;      /* epoch output = average of the iterates (Alg. 1) */
+  uint64_t sketch_seed; /* problem p is sketched with seed sketch_seed + p */
+} rs_batch_params;
+
+/* Solve every chain (host array of nchain descriptors; each chain's problem, lambda, step size,
+ * epoch length, seed and outputs).  Chains with the same (problem, lambda) share their
+ * components.  epoch_ms (host, nullable, epochs floats): time from the start of the first epoch
+ * to the end of epoch s.  Synchronises.  RS_ENOMEM if the workspace (components of every
+ * (problem, lambda) pair plus per-chain buffers) does not fit; RS_ENONFINITE / RS_ETIMEOUT as
+ * rs_svrg_solve. */
+int rs_solve_batched(rs_ctx* ctx, const rs_problem* probs, int32_t nprob, const rs_chain* chains, int32_t nchain,
+                     const rs_batch_params* p, float* epoch_ms);
+
 /* tr(C) = ||X||_F^2 / n (Eq. (2)), accumulated in double; the tail sum of the spectrum in the
  * runtime model of Thm 1 is tr(C) minus the leading sketched eigenvalues.  out: host, 1
  * double.  Synchronises. */

@@ -61,6 +61,22 @@ class MlpNorm(ctypes.Structure):
                 ("out_mean", ctypes.c_float * MLP_OUT), ("out_std", ctypes.c_float * MLP_OUT)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("X", Matrix), ("y", ctypes.c_void_p), ("k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Chain(ctypes.Structure):
+    _fields_ = [("problem", ctypes.c_int32), ("reserved", ctypes.c_int32), ("lambda_", ctypes.c_double),
+                ("eta_mult", ctypes.c_double), ("m", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("w_out", ctypes.c_void_p), ("snapshots", ctypes.c_void_p)]
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("sketch_kind", ctypes.c_int32), ("q_blocks", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("average", ctypes.c_int32),
+                ("sketch_seed", ctypes.c_uint64)]
+
+
 class History(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int32), ("epochs_run", ctypes.c_int32), ("snapshots", ctypes.c_void_p),
                 ("mu_norm2", ctypes.POINTER(ctypes.c_double)), ("epoch_ms", ctypes.POINTER(ctypes.c_float))]
@@ -103,6 +119,8 @@ _SIGS = {
                  ctypes.POINTER(History)],
     "rs_objective": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_double)],
     "rs_trace_c": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(ctypes.c_double)],
+    "rs_solve_batched": [_P, ctypes.POINTER(Problem), ctypes.c_int32, ctypes.POINTER(Chain), ctypes.c_int32,
+                         ctypes.POINTER(BatchParams), ctypes.POINTER(ctypes.c_float)],
     "rs_mlp_forward": [_P, _P, _P, ctypes.c_int64, _P],
     "rs_mlp_train_step": [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(AdamParams), _P, _P],
     "rs_propose": [_P, _P, ctypes.POINTER(MlpNorm), ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int64,
@@ -419,6 +437,40 @@ def rs_trace_c(ctx, X):
     M = matrix(X)
     _check(lib().rs_trace_c(ctx.h, ctypes.byref(M), ctypes.byref(out)))
     return out.value
+
+
+def rs_solve_batched(ctx, problems, chains, epochs, sketch_seed=0, kind="gaussian", q=1, refine=None, use_graph=True,
+                     average=True, snapshots=False):
+    """Solve many chains at once.
+
+    problems: list of (X, y, k) with X a CUDA tensor (float32 or bfloat16, row stride padded to 16
+    bytes), y float32 labels and k the sketch rank (0 = d / 16).
+    chains: list of dicts with keys problem, lam, and optionally eta_mult, m, seed.
+    Returns (list of w (float32, d), list of snapshot tensors or None, epoch_ms list)."""
+    np_ = len(problems)
+    P = (Problem * np_)()
+    for i, (X, y, k) in enumerate(problems):
+        _need_cuda(X, y)
+        P[i] = Problem(matrix(X), y.data_ptr(), int(k), 0)
+    nc = len(chains)
+    C = (Chain * nc)()
+    outs, snaps = [], []
+    for i, ch in enumerate(chains):
+        pi = int(ch["problem"])
+        d = problems[pi][0].shape[1] if 0 <= pi < np_ else 1   # an invalid index is rejected by the library
+        w = ctx._empty(d, dtype=torch.float32)
+        sn = ctx._empty(epochs, d, dtype=torch.float32) if snapshots else None
+        outs.append(w)
+        snaps.append(sn)
+        C[i] = Chain(int(ch["problem"]), 0, float(ch["lam"]), float(ch.get("eta_mult", 0.0)), int(ch.get("m", 0)),
+                     int(ch.get("seed", 0)), w.data_ptr(), None if sn is None else sn.data_ptr())
+    if refine is None:
+        refine = problems[0][0].dtype == torch.bfloat16
+    kind_i = RS_SKETCH_COUNTSKETCH if kind in ("countsketch", RS_SKETCH_COUNTSKETCH) else RS_SKETCH_GAUSSIAN
+    bp = BatchParams(epochs, kind_i, q, 1 if refine else 0, 1 if use_graph else 0, 1 if average else 0, sketch_seed)
+    ems = (ctypes.c_float * epochs)()
+    _check(lib().rs_solve_batched(ctx.h, P, np_, C, nc, ctypes.byref(bp), ems))
+    return outs, (snaps if snapshots else None), list(ems)
 
 
 # ----------------------------------------------------------------------------- proposal network

@@ -24,7 +24,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_COUNT
 };
 
 struct rs_ctx {
@@ -174,6 +174,48 @@ int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, 
                 int64_t ldb, double alpha, double* G);
 
 int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W);
+
+// ------------------------------------------------ batched inner loops (many chains per launch)
+
+// One chain of the inner loop of Alg. 1: components Z (storage S, N = n + d rows), the epoch's
+// index stream and 1/(N q) factors, step size, snapshot gradient mu, snapshot wbar, output
+// wnext, and its per-block workspace (Rt: blocks x 64 x 64, cvec: blocks x 64).
+template <typename S, typename T>
+struct ChainJob {
+  const S* Z;
+  int64_t N, ld, d, n, m;
+  const uint32_t* idx;
+  const T* inv_nq;
+  double lam, eta;
+  const T* mu;
+  const T* wbar;
+  T* wnext;
+  T* Rt;
+  T* cvec;
+  int32_t average, reserved;
+};
+
+// Index stream of one chain (float factors): sampling table W / cum over N components.
+struct IdxJob {
+  const uint32_t* W;
+  const uint64_t* cum;
+  int64_t N, m;
+  uint64_t seed;
+  uint32_t* idx;
+  float* inv_nq;
+  int32_t uniform, reserved;
+};
+
+constexpr int kChainBlk = 64;   // steps per block of the blocked inner loop
+
+// All jobs' index streams for one epoch; off (device, nj + 1) holds the prefix sums of m.
+int index_stream_batched(rs_ctx* ctx, const IdxJob* jobs, const int64_t* off, int nj, int64_t total, uint32_t epoch);
+// Per-block preparation for all jobs; blk_off (device, nj + 1): prefix sums of the block counts.
+template <typename S, typename T>
+int epoch_prep_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, const int64_t* blk_off, int nj, int64_t total_blocks);
+// The chains of nj jobs that share d, one thread-block cluster each, in one launch.
+template <typename S, typename T>
+int epoch_chain_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, int nj, int64_t d);
 
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }

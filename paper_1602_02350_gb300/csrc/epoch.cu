@@ -25,7 +25,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kBlk = 64;     // steps per block
+constexpr int kBlk = kChainBlk;   // steps per block
 constexpr int kCsMax = 16;   // largest cluster
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -53,11 +53,10 @@ __device__ __forceinline__ void ld_widen8(const __nv_bfloat16* p, float* v) {
 // (zero beyond the last step), row B is mu, rows B+1..B+3 are zero.  Z is stored in S and
 // widened to the compute type T while it is staged.
 template <typename S, typename T>
-__global__ void __launch_bounds__(256) epoch_prep_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
-                                                         int64_t n, double lam, const uint32_t* __restrict__ idx,
-                                                         const T* __restrict__ inv_nq, int64_t m, double eta,
-                                                         const T* __restrict__ mu, T* __restrict__ Rt,
-                                                         T* __restrict__ cvec) {
+__device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d, int64_t n,
+                                          double lam, const uint32_t* __restrict__ idx, const T* __restrict__ inv_nq,
+                                          int64_t m, double eta, const T* __restrict__ mu, T* __restrict__ Rt,
+                                          T* __restrict__ cvec, int64_t b) {
   constexpr int B = kBlk, RP = B + 4;
   constexpr int E = 16 / sizeof(T);
   constexpr int CH = 64;              // columns per staged chunk
@@ -70,7 +69,6 @@ __global__ void __launch_bounds__(256) epoch_prep_kernel(const S* __restrict__ Z
   __shared__ T kap[B];
   __shared__ int64_t rowid[B];
   const int tid = threadIdx.x;
-  const int64_t b = blockIdx.x;
   const int64_t t0 = b * B;
   const int Bb = (int)min64(B, m - t0);
   const T Nn = (T)((double)N / (double)n), lN = (T)(lam * (double)N);
@@ -222,6 +220,30 @@ __global__ void __launch_bounds__(256) epoch_prep_kernel(const S* __restrict__ Z
   }
 }
 
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) epoch_prep_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                                         int64_t n, double lam, const uint32_t* __restrict__ idx,
+                                                         const T* __restrict__ inv_nq, int64_t m, double eta,
+                                                         const T* __restrict__ mu, T* __restrict__ Rt,
+                                                         T* __restrict__ cvec) {
+  prep_body<S, T>(Z, N, ld, d, n, lam, idx, inv_nq, m, eta, mu, Rt, cvec, blockIdx.x);
+}
+
+// all jobs' blocks in one grid: block g belongs to job j with blk_off[j] <= g < blk_off[j + 1]
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) epoch_prep_batched_kernel(const ChainJob<S, T>* __restrict__ jobs,
+                                                                 const int64_t* __restrict__ blk_off, int nj) {
+  const int64_t g = blockIdx.x;
+  int lo = 0, hi = nj - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (blk_off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  const ChainJob<S, T> J = jobs[lo];
+  prep_body<S, T>(J.Z, J.N, J.ld, J.d, J.n, J.lam, J.idx, J.inv_nq, J.m, J.eta, J.mu, J.Rt, J.cvec, g - blk_off[lo]);
+}
+
 // ------------------------------------------------------------------ sequential chain
 // One cluster of CS blocks; block r owns columns [r CW, (r+1) CW) of delta (CW = 32 QN).
 // Per block of steps each block pushes its partial dot products straight from registers into
@@ -267,12 +289,11 @@ __host__ __device__ constexpr int chain_zpad(int tpc, int cpw, int esize) {
 }
 
 template <typename S, typename T, int STAGES, int QN, int NT>
-__global__ void __launch_bounds__(NT) epoch_chain_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
-                                                          const uint32_t* __restrict__ idx, int64_t m,
-                                                          const T* __restrict__ Rt, const T* __restrict__ cvec,
-                                                          double eta, const T* __restrict__ mu,
-                                                          const T* __restrict__ wbar, int average,
-                                                          T* __restrict__ wnext, int* status) {
+__device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                           const uint32_t* __restrict__ idx, int64_t m, const T* __restrict__ Rt,
+                                           const T* __restrict__ cvec, double eta, const T* __restrict__ mu,
+                                           const T* __restrict__ wbar, int average, T* __restrict__ wnext,
+                                           int* status) {
   constexpr int B = kBlk;
   constexpr int E = 16 / sizeof(T);
   constexpr int ES = 16 / sizeof(S);
@@ -502,6 +523,26 @@ __global__ void __launch_bounds__(NT) epoch_chain_kernel(const S* __restrict__ Z
   }
 }
 
+template <typename S, typename T, int STAGES, int QN, int NT>
+__global__ void __launch_bounds__(NT) epoch_chain_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                                          const uint32_t* __restrict__ idx, int64_t m,
+                                                          const T* __restrict__ Rt, const T* __restrict__ cvec,
+                                                          double eta, const T* __restrict__ mu,
+                                                          const T* __restrict__ wbar, int average,
+                                                          T* __restrict__ wnext, int* status) {
+  chain_body<S, T, STAGES, QN, NT>(Z, N, ld, d, idx, m, Rt, cvec, eta, mu, wbar, average, wnext, status);
+}
+
+// one cluster per job (the cluster's blocks are consecutive in x)
+template <typename S, typename T, int STAGES, int QN, int NT>
+__global__ void __launch_bounds__(NT) epoch_chain_batched_kernel(const ChainJob<S, T>* __restrict__ jobs,
+                                                                  int* status) {
+  const int cs = (int)cg::this_cluster().num_blocks();
+  const ChainJob<S, T> J = jobs[blockIdx.x / cs];
+  chain_body<S, T, STAGES, QN, NT>(J.Z, J.N, J.ld, J.d, J.idx, J.m, J.Rt, J.cvec, J.eta, J.mu, J.wbar, J.average,
+                                   J.wnext, status);
+}
+
 struct ChainPlan {
   int cs = 0, qn = 0, stages = 0, nt = 0;
   size_t shm = 0;
@@ -620,6 +661,88 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
   }
   return rs_fail(RS_EUNSUPPORTED, "rs_svrg_epoch: no thread-block cluster layout fits d = %lld", (long long)d);
 }
+
+// ------------------------------------------------------------------ batched launches
+
+namespace {
+
+// Cluster size of a chain in a batched launch: the fewest blocks (of at most 256 columns each)
+// so that many chains run side by side; RS_BATCH_CLUSTER overrides (1, 2, 4, 8 or 16).
+int choose_batch_cluster(int64_t d) {
+  const char* env = std::getenv("RS_BATCH_CLUSTER");
+  if (env) return std::atoi(env);
+  int cs = 1;
+  while (cs < kCsMax && (d + cs - 1) / cs > 256) cs *= 2;
+  return cs;
+}
+
+template <typename S, typename T, int ST, int QN, int NT>
+int launch_chain_batched(rs_ctx* ctx, const ChainPlan& pl, const ChainJob<S, T>* jobs, int nj) {
+  auto kern = epoch_chain_batched_kernel<S, T, ST, QN, NT>;
+  RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
+  if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(pl.cs * nj), 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = pl.shm;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return RS_EUNSUPPORTED;
+  }
+  RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, jobs, ctx->d_status));
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+}  // namespace
+
+template <typename S, typename T>
+int epoch_prep_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, const int64_t* blk_off, int nj, int64_t total_blocks) {
+  if (nj < 1 || total_blocks < 1) return RS_OK;
+  if (total_blocks > 0x7FFFFFFF) return rs_fail(RS_EINVAL, "batched epoch: too many blocks of steps");
+  constexpr int RP = kBlk + 4, CH = 64, E = 16 / sizeof(T);
+  const size_t pshm = (size_t)(2 * RP * (CH + E) + RP * (RP + 1) + 2 * kBlk * (kBlk + 1)) * sizeof(T);
+  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_batched_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)pshm));
+  epoch_prep_batched_kernel<S, T><<<(unsigned)total_blocks, 256, pshm, ctx->stream>>>(jobs, blk_off, nj);
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+template <typename S, typename T>
+int epoch_chain_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, int nj, int64_t d) {
+  if (nj < 1) return RS_OK;
+  for (int cs = choose_batch_cluster(d); cs >= 1; cs /= 2) {
+    const ChainPlan pl = plan_chain<S, T>(d, cs);
+    if (!pl.cs) continue;
+    int rc = RS_EUNSUPPORTED;
+#define RS_CHAIN(ST, QN)                                                                  \
+  if (pl.stages == ST && pl.qn == QN && pl.nt == 256)                                     \
+    rc = launch_chain_batched<S, T, ST, QN, 256>(ctx, pl, jobs, nj);                      \
+  if (pl.stages == ST && pl.qn == QN && pl.nt == 512)                                     \
+    rc = launch_chain_batched<S, T, ST, QN, 512>(ctx, pl, jobs, nj);
+    RS_CHAIN(4, 2) RS_CHAIN(4, 4) RS_CHAIN(4, 8) RS_CHAIN(3, 2) RS_CHAIN(3, 4) RS_CHAIN(3, 8)
+    RS_CHAIN(2, 2) RS_CHAIN(2, 4) RS_CHAIN(2, 8)
+#undef RS_CHAIN
+    if (rc != RS_EUNSUPPORTED) return rc;
+  }
+  return rs_fail(RS_EUNSUPPORTED, "batched epoch: no thread-block cluster layout fits d = %lld", (long long)d);
+}
+
+template int epoch_prep_batched<float, float>(rs_ctx*, const ChainJob<float, float>*, const int64_t*, int, int64_t);
+template int epoch_prep_batched<__nv_bfloat16, float>(rs_ctx*, const ChainJob<__nv_bfloat16, float>*, const int64_t*,
+                                                      int, int64_t);
+template int epoch_chain_batched<float, float>(rs_ctx*, const ChainJob<float, float>*, int, int64_t);
+template int epoch_chain_batched<__nv_bfloat16, float>(rs_ctx*, const ChainJob<__nv_bfloat16, float>*, int, int64_t);
 
 template int svrg_epoch_t<float, float>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const float*,
                                         int64_t, double, const float*, const float*, int, float*);

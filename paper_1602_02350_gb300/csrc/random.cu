@@ -258,32 +258,58 @@ __global__ void quantize_kernel(const T* beta, int64_t N, const double* part, in
   }
 }
 
+// Step tt of an epoch: component index (Philox counter (tt, epoch, tag 3)) and 1/(N q_i)
+template <typename T>
+__device__ __forceinline__ void draw_index(const uint32_t* W, const uint64_t* cum, int64_t N, uint64_t seed,
+                                           uint32_t epoch, uint64_t tt, int uniform, uint32_t& i, T& c) {
+  U32x4 w = philox4x32_10(U32x4{(uint32_t)tt, (uint32_t)(tt >> 32), epoch, TAG_SAMPLE}, seed);
+  if (uniform) {
+    i = (uint32_t)(((uint64_t)w.x * (uint64_t)N) >> 32);
+    c = T(1);
+  } else {
+    const uint64_t total = cum[N - 1];
+    const uint64_t u = ((uint64_t)w.y << 32) | (uint64_t)w.x;
+    const uint64_t r = __umul64hi(u, total);
+    int64_t lo = 0, hi = N - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (cum[mid] > r) hi = mid;
+      else lo = mid + 1;
+    }
+    i = (uint32_t)lo;
+    c = (T)((double)total / ((double)N * (double)W[lo]));
+  }
+}
+
 template <typename T>
 __global__ void index_stream_kernel(const uint32_t* W, const uint64_t* cum, int64_t N, uint64_t seed, uint32_t epoch,
                                     int64_t t0, int64_t m, int uniform, uint32_t* idx, T* inv_nq) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t tt = (uint64_t)(t0 + t);
-    U32x4 w = philox4x32_10(U32x4{(uint32_t)tt, (uint32_t)(tt >> 32), epoch, TAG_SAMPLE}, seed);
     uint32_t i;
     T c;
-    if (uniform) {
-      i = (uint32_t)(((uint64_t)w.x * (uint64_t)N) >> 32);
-      c = T(1);
-    } else {
-      const uint64_t total = cum[N - 1];
-      const uint64_t u = ((uint64_t)w.y << 32) | (uint64_t)w.x;
-      const uint64_t r = __umul64hi(u, total);
-      int64_t lo = 0, hi = N - 1;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (cum[mid] > r) hi = mid;
-        else lo = mid + 1;
-      }
-      i = (uint32_t)lo;
-      c = (T)((double)total / ((double)N * (double)W[lo]));
-    }
+    draw_index<T>(W, cum, N, seed, epoch, (uint64_t)(t0 + t), uniform, i, c);
     idx[t] = i;
     inv_nq[t] = c;
+  }
+}
+
+// every job's stream: global step t belongs to the job j with off[j] <= t < off[j + 1]
+__global__ void index_stream_batched_kernel(const IdxJob* __restrict__ jobs, const int64_t* __restrict__ off, int nj,
+                                            int64_t total, uint32_t epoch) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nj - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const IdxJob& J = jobs[lo];
+    const int64_t tl = t - off[lo];
+    uint32_t i;
+    float c;
+    draw_index<float>(J.W, J.cum, J.N, J.seed, epoch, (uint64_t)tl, J.uniform, i, c);
+    J.idx[tl] = i;
+    J.inv_nq[tl] = c;
   }
 }
 
@@ -413,6 +439,13 @@ int index_stream_dispatch(rs_ctx* ctx, const uint32_t* W, const uint64_t* cum, i
   else
     index_stream_kernel<float><<<g, kThreads, 0, ctx->stream>>>(W, cum, N, seed, (uint32_t)epoch, t0, m, uni, idx,
                                                                  static_cast<float*>(inv_nq));
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+int index_stream_batched(rs_ctx* ctx, const IdxJob* jobs, const int64_t* off, int nj, int64_t total, uint32_t epoch) {
+  if (nj < 1 || total < 1) return RS_OK;
+  index_stream_batched_kernel<<<grid_for(ctx, total), kThreads, 0, ctx->stream>>>(jobs, off, nj, total, epoch);
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
 }

@@ -55,7 +55,10 @@ def test_train_step_gradient_and_adam_match_oracle(rsctx, B):
     g = g.cpu().double().numpy()
     np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-5 * np.abs(g_ref).max())
     # Adam from the GPU gradient (the update divides by |g|, so it is compared for the same g)
-    th_ref, m_ref, v_ref = proposal.adam_step(theta, np.zeros_like(theta), np.zeros_like(theta), g, 1, lr=1e-3)
+    # the kernel holds the hyper-parameters in float: give the oracle the same values
+    f = lambda v: float(np.float32(v))  # noqa: E731
+    th_ref, m_ref, v_ref = proposal.adam_step(theta, np.zeros_like(theta), np.zeros_like(theta), g, 1, lr=f(1e-3),
+                                              beta1=f(0.9), beta2=f(0.999), eps=f(1e-8))
     # theta is stored in float: the updated value is the FP64 one rounded once (half an ulp)
     np.testing.assert_allclose(th.cpu().double().numpy(), th_ref, rtol=2.0 ** -23, atol=1e-9)
     np.testing.assert_allclose(m.cpu().double().numpy(), m_ref, rtol=1e-6, atol=1e-12)
