@@ -1,9 +1,13 @@
 """Benchmark: time to 1e-6 relative suboptimality of sketched-preconditioned SVRG (Alg. 3) on one GB300.
 
 Workload: n = 65536, d = 1024 FP32 rows with power-law spectrum j^-2 in a random basis,
-y = X w_gen + 0.05 N(0,1), lambda = 1e-5, CountSketch (s = 4096) then Gaussian sketch of rank 64,
-importance-sampled SVRG with m = 2n, eta = 1/beta_hat.  One step = one full solve from the
-device-resident (X, y) to w: sketch, precondition, every epoch needed to reach 1e-6.
+y = X w_gen + 0.05 N(0,1), lambda = 1e-5, CountSketch (s = 4096) then Gaussian sketch.
+One step = one full solve from the device-resident (X, y) to w, every epoch needed to reach 1e-6.
+
+  chosen form (the reported value): rs_solve_proposed -- rank-64 sketch, tr(C), the trained
+    proposal network picks (k, eta, m), BF16 components with snapshot gradients refined on the
+    FP32 data;
+  plain form (alongside): rs_solve -- FP32 components, k = 64, m = 2n, eta = 1/beta_hat.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {rs,reference}]
 
@@ -91,6 +95,27 @@ def max_over_ranks(dist, value):
     return float(t.item())
 
 
+def _load_proposal(rs):
+    """Trained proposal weights (committed with the package), or (None, None) = theory setting."""
+    path = os.path.join(ROOT, "paper_1602_02350_gb300", "proposal_weights.npz")
+    if not os.path.exists(path):
+        return None, None
+    W = np.load(path)
+    theta = torch.from_numpy(W["theta"]).float().cuda()
+    return theta, rs.mlp_norm(W["in_mean"], W["in_std"], W["out_mean"], W["out_std"])
+
+
+def _time_steps(step, steps, stream):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        out = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
 def run_rs(args):
     import paper_1602_02350_gb300 as rs
     from paper_1602_02350_gb300 import synth
@@ -102,10 +127,20 @@ def run_rs(args):
     X, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.float32)
     y = y64.float().contiguous()
     n, d, k, lam = cfg.n, cfg.d, cfg.k, cfg.lam
-    m = 2 * n
-    eta_mult = 1.0
     stream = torch.cuda.current_stream()
     ctx = rs.Context(local, stream)
+    theta, norm = _load_proposal(rs)
+
+    if args.profile:
+        # profiling run: one solve of each form with given epoch counts, nothing else
+        for _ in range(2):
+            rs.rs_solve(ctx, X, y, k, lam, args.plain_epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s,
+                        m=2 * n, eta_mult=1.0)
+            rs.rs_solve_proposed(ctx, X, y, lam, args.chosen_epochs, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
+                                 norm=norm, kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16)
+        torch.cuda.synchronize()
+        ctx.close()
+        return
 
     # reference minimiser for the accuracy target (normal equations in double; measurement only,
     # untimed): the d x d Gram on the device, the d x d solve on the host
@@ -119,20 +154,34 @@ def run_rs(args):
     def rel(w):
         return rs.rs_objective(ctx, X, y, lam, w, w_star)[1] / L_star
 
-    # calibration (untimed): epochs needed to reach the target
-    max_ep = 20
-    _, info = rs.rs_solve(ctx, X, y, k, lam, max_ep, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
-                          eta_mult=eta_mult, snapshots=True)
-    hist = [rel(s) for s in info["snapshots"]]
-    reach = [i for i, r in enumerate(hist) if r <= TARGET]
-    epochs = (reach[0] + 1) if reach else max_ep
+    def first_epoch(snaps, cap):
+        hist = [rel(s) for s in snaps]
+        reach = [i for i, r in enumerate(hist) if r <= TARGET]
+        return ((reach[0] + 1) if reach else cap), hist
 
-    def step():
-        return rs.rs_solve(ctx, X, y, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
-                           eta_mult=eta_mult)[0]
+    # plain form: FP32 components, fixed practice setting m = 2n, eta = 1 / beta^, k = 64
+    m_plain, em_plain = 2 * n, 1.0
+    _, info = rs.rs_solve(ctx, X, y, k, lam, 20, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m_plain,
+                          eta_mult=em_plain, snapshots=True)
+    ep_plain, hist_plain = first_epoch(info["snapshots"], 20)
+
+    def plain_step():
+        return rs.rs_solve(ctx, X, y, k, lam, ep_plain, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s,
+                           m=m_plain, eta_mult=em_plain)[0]
+
+    # chosen form: BF16 components refined on the float data, (k, eta, m) from the proposal network
+    cap = 60
+    _, cinfo = rs.rs_solve_proposed(ctx, X, y, lam, cap, cfg.seed_sketch, cfg.seed_svrg, theta=theta, norm=norm,
+                                    kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16, snapshots=True)
+    ep_chosen, hist_chosen = first_epoch(cinfo["snapshots"], cap)
+
+    def chosen_step():
+        return rs.rs_solve_proposed(ctx, X, y, lam, ep_chosen, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
+                                    norm=norm, kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16)[0]
 
     for _ in range(args.warmup):
-        step()
+        plain_step()
+        chosen_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -140,78 +189,76 @@ def run_rs(args):
     os.makedirs(os.path.dirname(cpath), exist_ok=True)
     sampler, fh = _clock_sampler(cpath)
     time.sleep(0.3)
+    ms_plain, w_plain = _time_steps(plain_step, args.steps, stream)
     l0 = ctx.launches
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        w = step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    launches = ctx.launches - l0
-    ms = e0.elapsed_time(e1) / args.steps
+    ms, w = _time_steps(chosen_step, args.steps, stream)
+    launches = (ctx.launches - l0) // max(1, args.steps)
     if sampler:
         sampler.terminate()
         sampler.wait()
         fh.close()
-    final_rel = rel(w)
+    final_rel, final_rel_plain = rel(w), rel(w_plain)
     ms = max_over_ranks(dist, ms)
+    ms_plain = max_over_ranks(dist, ms_plain)
 
     # end to end through the public call with host buffers (pinned), copies inside the timed region
     Xh = X.cpu().pin_memory()
     yh = y.cpu().pin_memory()
     wh = torch.empty(d, dtype=torch.float32).pin_memory()
-    rs.rs_solve(ctx, Xh, yh, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
-                eta_mult=eta_mult, w_out=wh)
+
+    def e2e_step():
+        return rs.rs_solve_proposed(ctx, Xh, yh, lam, ep_chosen, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
+                                    norm=norm, kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16, w_out=wh)
+
+    e2e_step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        rs.rs_solve(ctx, Xh, yh, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
-                    eta_mult=eta_mult, w_out=wh)
+        e2e_step()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / args.steps)
 
-    # dominant data pass: the full-gradient stream over the n + d component rows (same kernel the
+    # dominant data pass: the full-gradient stream over the n + d component rows (the kernel the
     # solve launches once per epoch), timed alone with events on the library's stream
     V, s2 = rs.rs_sketch(ctx, X, k, cfg.seed_sketch, kind=cfg.kind, s=cfg.s)
     Z, beta, bh = rs.rs_precondition(ctx, X, V, s2, lam)
     wt = torch.zeros(d, dtype=torch.float32, device="cuda")
     for _ in range(3):
         rs.rs_full_gradient(ctx, Z, y, n, lam, wt)
-    reps = 20
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    f0.record(stream)
-    for _ in range(reps):
-        rs.rs_full_gradient(ctx, Z, y, n, lam, wt)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    fg_ms = f0.elapsed_time(f1) / reps
+    fg_ms, _ = _time_steps(lambda: rs.rs_full_gradient(ctx, Z, y, n, lam, wt), 20, stream)
     fg_bytes = (n + d) * d * 4 + n * 4          # algorithmic: every component row and label read once
     peak, peak_kind = _peaks()
     achieved = fg_bytes / (fg_ms * 1e-3) / 1e9
 
-    # per-epoch split of the solve (events recorded by the library between epochs)
-    _, info2 = rs.rs_solve(ctx, X, y, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m,
-                           eta_mult=eta_mult)
-    ems = info2["epoch_ms"]
+    # inner loop of the chosen setting: per-epoch time from the library's epoch events
+    ems = cinfo["epoch_ms"]
     per_epoch = (ems[-1] - ems[0]) / max(1, len(ems) - 1) if len(ems) > 1 else (ems[0] if ems else None)
+    m_ch = cinfo["m"]
 
     out = {
-        "metric": "time-to-1e-6 relative suboptimality", "value": ms / 1e3, "unit": "s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: n=65536 d=1024 fp32, spectrum j^-2, lambda=1e-5, "
-                               "CountSketch s=4096 -> Gaussian k=64, SVRG m=2n eta=1/beta_hat",
-                   "n": n, "d": d, "k": k, "lambda": lam, "m": m, "eta_mult": eta_mult, "epochs": epochs,
-                   "rel_subopt_per_epoch": [float(f"{h:.3e}") for h in hist[:epochs]],
-                   "final_rel_subopt": final_rel, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs exceed L2 (X 268 MB, components 272 MB vs 129 MB L2); no flush"},
-        "roofline": {"kernel": "fullgrad (data pass over the n+d component rows)", "bound": "hbm",
+        "metric": "time-to-1e-6 relative suboptimality (chosen form; plain form alongside)", "value": ms / 1e3,
+        "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: n=65536 d=1024 fp32 data, spectrum j^-2, lambda=1e-5, "
+                               "CountSketch s=4096 -> Gaussian sketch",
+                   "chosen": {"components": "bf16, snapshot gradients refined on the fp32 data",
+                              "proposal": "network" if theta is not None else "theory setting (no weights)",
+                              "k": cinfo["k"], "eta_mult": cinfo["eta_mult"], "m": m_ch,
+                              "fallback": cinfo["fallback"], "epochs": ep_chosen,
+                              "rel_subopt_per_epoch": [float(f"{h:.3e}") for h in hist_chosen[:ep_chosen]],
+                              "final_rel_subopt": final_rel},
+                   "plain": {"components": "fp32", "k": k, "eta_mult": em_plain, "m": m_plain, "epochs": ep_plain,
+                             "seconds": ms_plain / 1e3, "final_rel_subopt": final_rel_plain,
+                             "rel_subopt_per_epoch": [float(f"{h:.3e}") for h in hist_plain[:ep_plain]]},
+                   "speedup_chosen_vs_plain": ms_plain / ms,
+                   "n": n, "d": d, "lambda": lam, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs exceed L2 (X 268 MB, components 272 MB fp32 / 136 MB bf16 vs 129 MB L2); no flush"},
+        "roofline": {"kernel": "fullgrad (data pass over the n+d component rows, fp32)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": None, "ms_per_launch": fg_ms},
-        "inner_loop": {"ms_per_epoch": per_epoch, "ns_per_step": per_epoch * 1e6 / m if per_epoch else None,
-                       "steps_per_s": m / (per_epoch * 1e-3) if per_epoch else None},
+        "inner_loop": {"ms_per_epoch": per_epoch, "m": m_ch,
+                       "ns_per_step": per_epoch * 1e6 / m_ch if per_epoch else None,
+                       "steps_per_s": m_ch / (per_epoch * 1e-3) if per_epoch else None},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * d * 4 + n * 4, "d2h_bytes_per_step": d * 4},
         "gpu_launches": launches,
         "clocks": _clock_summary(cpath),
@@ -292,6 +339,10 @@ def main():
     ap.add_argument("--impl", default="rs", choices=["rs", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle work for the cpu_baseline sample (0 = skip)")
+    ap.add_argument("--profile", action="store_true",
+                    help="run two solves of each form with the given epoch counts and exit (for ncu launch lists)")
+    ap.add_argument("--plain-epochs", type=int, default=4)
+    ap.add_argument("--chosen-epochs", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -152,7 +152,8 @@ int rs_sketch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* 
  *   rows 0..n-1:   z_i = M x_i            (x~_i of Alg. 3),
  *   rows n..n+d-1: z_{n+j} = M e_j        (b_j of Alg. 3; M is symmetric).
  * Xt->data is written (cast away const); Xt->n must be n + d, Xt->d = d, Xt->dtype equal
- * to X->dtype (RS_F64 or RS_F32) or RS_BF16 when X is RS_BF16.
+ * to X->dtype (RS_F64, RS_F32 or RS_BF16), or RS_BF16 for RS_F32 data (each component is
+ * formed in float and rounded once).
  * beta (T, n + d): smoothness beta_i = gamma_i ||z_i||^2 with gamma_i = (n+d)/n for data
  * rows and lam (n+d) for regulariser rows (Alg. 3).  beta_hat (host, nullable): mean beta. */
 int rs_precondition(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k,
@@ -248,7 +249,8 @@ typedef struct {
 
 /* Alg. 1 on the components Z (rs_precondition layout, N = n + d rows; RS_F64, RS_F32 or RS_BF16
  * storage) for p->epochs epochs, starting from w0 (preconditioned coordinates, nullable = 0).
- * X (n x d, same storage as Z) is the stored data, required when p->refine is set, else
+ * X (n x d, stored like Z, or RS_F32 for RS_BF16 components) is the stored data, required
+ * when p->refine is set, else
  * nullable.  beta (T, N; nullable = recomputed from Z) sets the sampling weights.  V/sigma2/k
  * give M for the output map: w_out = M w~_S (original coordinates, Alg. 3 read as
  * w = P^{-1/2} w~).  eta_used / m_used (host, nullable) receive the resolved step size and
@@ -387,6 +389,18 @@ typedef struct {
 int rs_propose(rs_ctx* ctx, const float* theta, const rs_mlp_norm* norm, const double* sigma2, double lambda,
                int64_t n, int64_t d, double trace_c, int32_t* k, double* eta_mult, int64_t* m,
                int32_t* used_fallback);
+
+/* Alg. 3 with proposed parameters, end to end: a rank-64 sketch of X (Alg. 2 with sp, whose k is
+ * replaced by 64; d >= 64), tr(C), rs_propose (theta / norm as there; NULL = theory setting),
+ * the components of Eq. (11) / Sec. 5.1 from the leading k Ritz pairs, stored as z_dtype
+ * (X->dtype, or RS_BF16 for RS_F32 data: then the snapshot gradients are refined on X), and
+ * p->epochs epochs of Alg. 1 with eta = eta_mult / beta^ and the proposed m (p->eta, p->eta_mult
+ * and p->m are ignored).  X, y and w_out may be host pointers as in rs_solve.  k, eta_mult, m,
+ * used_fallback (host, nullable) receive the parameters used.  Synchronises. */
+int rs_solve_proposed(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp,
+                      const rs_svrg_params* p, const float* theta, const rs_mlp_norm* norm, int32_t z_dtype,
+                      void* w_out, rs_history* hist, int32_t* k, double* eta_mult, int64_t* m,
+                      int32_t* used_fallback);
 
 #ifdef __cplusplus
 }

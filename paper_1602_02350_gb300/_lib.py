@@ -122,6 +122,10 @@ _SIGS = {
     "rs_solve_batched": [_P, ctypes.POINTER(Problem), ctypes.c_int32, ctypes.POINTER(Chain), ctypes.c_int32,
                          ctypes.POINTER(BatchParams), ctypes.POINTER(ctypes.c_float)],
     "rs_mlp_forward": [_P, _P, _P, ctypes.c_int64, _P],
+    "rs_solve_proposed": [_P, ctypes.POINTER(Matrix), _P, ctypes.POINTER(SketchParams), ctypes.POINTER(SvrgParams),
+                          _P, ctypes.POINTER(MlpNorm), ctypes.c_int32, _P, ctypes.POINTER(History),
+                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
     "rs_mlp_train_step": [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(AdamParams), _P, _P],
     "rs_propose": [_P, _P, ctypes.POINTER(MlpNorm), ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int64,
                    ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
@@ -302,10 +306,12 @@ def _padded_ld(d, dtype):
     return ((d * es + 15) // 16 * 16) // es
 
 
-def rs_precondition(ctx, X, V, sigma2, lam, want_beta_hat=True):
+def rs_precondition(ctx, X, V, sigma2, lam, want_beta_hat=True, z_dtype=None):
+    """Components Z ((n + d) x d, stored like X or in z_dtype = torch.bfloat16 for float32 X)."""
     n, d = X.shape
-    ld = _padded_ld(d, X.dtype)
-    Zs = ctx._empty(n + d, ld, dtype=X.dtype)
+    zt = X.dtype if z_dtype is None else z_dtype
+    ld = _padded_ld(d, zt)
+    Zs = ctx._empty(n + d, ld, dtype=zt)
     Z = Zs[:, :d]
     beta = ctx._empty(n + d, dtype=_compute_dtype(X))
     MX, MZ = matrix(X), matrix(Z)
@@ -521,3 +527,29 @@ def rs_propose(ctx, sigma2, lam, n, d, trace_c, theta=None, norm=None):
     _check(lib().rs_propose(ctx.h, _ptr(theta), ctypes.byref(norm) if norm is not None else None, s, lam, n, d,
                             trace_c, ctypes.byref(k), ctypes.byref(em), ctypes.byref(m), ctypes.byref(fb)))
     return k.value, em.value, m.value, bool(fb.value)
+
+
+def rs_solve_proposed(ctx, X, y, lam, epochs, sketch_seed, svrg_seed, theta=None, norm=None, kind="gaussian", s=0,
+                      q=1, z_dtype=None, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False, w_out=None):
+    """Alg. 3 with proposed (k, eta, m).  X / y / w_out may be CUDA or (pinned) CPU tensors.
+    Returns (w, info) with info holding k, eta_mult, m, fallback and the epoch history."""
+    d = X.shape[1]
+    ct = torch.float64 if X.dtype == torch.float64 else torch.float32
+    if w_out is None:
+        w_out = ctx._empty(d, dtype=ct) if X.is_cuda else torch.empty(d, dtype=ct)
+    M = Matrix(X.data_ptr(), None, X.shape[0], d, X.stride(0), _DT[X.dtype], 0)
+    sp = _sketch_params(64, sketch_seed, kind, s, q)
+    zt = _DT[z_dtype] if z_dtype is not None else _DT[X.dtype]
+    p = _svrg_params(lam, epochs, svrg_seed, 0.0, 0.0, 0, 0, sampling, average, refine=zt != _DT[X.dtype] or
+                     X.dtype == torch.bfloat16)
+    h, mu2, ems, snaps = _history(ctx, epochs, d, ct, snapshots)
+    if theta is not None:
+        _need_cuda(theta)
+    k, em, m, fb = ctypes.c_int32(0), ctypes.c_double(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(lib().rs_solve_proposed(ctx.h, ctypes.byref(M), _ptr(y), ctypes.byref(sp), ctypes.byref(p), _ptr(theta),
+                                   ctypes.byref(norm) if norm is not None else None, zt, _ptr(w_out), ctypes.byref(h),
+                                   ctypes.byref(k), ctypes.byref(em), ctypes.byref(m), ctypes.byref(fb)))
+    info = {"k": k.value, "eta_mult": em.value, "m": m.value, "fallback": bool(fb.value),
+            "mu_norm2": list(mu2)[:epochs], "epoch_ms": list(ems)[:epochs],
+            "snapshots": snaps[:epochs] if snaps is not None else None}
+    return w_out, info

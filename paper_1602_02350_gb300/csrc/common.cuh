@@ -24,7 +24,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_COUNT
 };
 
 struct rs_ctx {
@@ -161,10 +161,10 @@ __device__ __forceinline__ void vec_to_arr(const double2& v, double* a) { a[0] =
 
 // Internal launch helpers implemented in dense.cu, used by several entry points.
 template <typename T> struct NoDeduce { using type = T; };   // keeps a parameter out of type deduction
-// A and C (and C0) may be stored in another type than the compute type T (bfloat16 data).
-template <typename T, typename TA = T, typename TC = T>
+// A, C and C0 may be stored in other types than the compute type T (bfloat16 data).
+template <typename T, typename TA = T, typename TC = T, typename TC0 = TC>
 int launch_gemm(rs_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t sAm,
-                int64_t sAk, const T* B, int64_t sBk, int64_t sBn, double beta, const typename NoDeduce<TC>::type* C0,
+                int64_t sAk, const T* B, int64_t sBk, int64_t sBn, double beta, const typename NoDeduce<TC0>::type* C0,
                 int64_t ldc0, TC* C, int64_t ldc, const T* col_scale);
 
 // Gram / transposed product with split-K over the long dimension and double accumulation:

@@ -14,10 +14,10 @@ namespace {
 // ------------------------------------------------------------------ GEMM (CUDA cores)
 // C[m][n] = alpha * col_scale[n] * sum_k A(m,k) B(k,n) + beta * C0[m][n]
 // A(m,k) = A[m*sAm + k*sAk], B(k,n) = B[k*sBk + n*sBn].  64x64 tile, 16-deep k steps, 4x4 per thread.
-template <typename T, typename TA, typename TC, bool A_KCONTIG, bool B_NCONTIG>
+template <typename T, typename TA, typename TC, typename TC0, bool A_KCONTIG, bool B_NCONTIG>
 __global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const TA* __restrict__ A,
                                                    int64_t sAm, int64_t sAk, const T* __restrict__ B, int64_t sBk,
-                                                   int64_t sBn, T beta, const TC* C0, int64_t ldc0, TC* C, int64_t ldc,
+                                                   int64_t sBn, T beta, const TC0* C0, int64_t ldc0, TC* C, int64_t ldc,
                                                    const T* __restrict__ col_scale) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ T As[BK][BM + 4];
@@ -502,37 +502,38 @@ int blocks_for(rs_ctx* ctx, int64_t work, int threads = 256) {
 
 // ====================================================================== launchers
 
-template <typename T, typename TA, typename TC>
+template <typename T, typename TA, typename TC, typename TC0>
 int launch_gemm(rs_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t sAm, int64_t sAk,
-                const T* B, int64_t sBk, int64_t sBn, double beta, const typename NoDeduce<TC>::type* C0, int64_t ldc0,
+                const T* B, int64_t sBk, int64_t sBn, double beta, const typename NoDeduce<TC0>::type* C0, int64_t ldc0,
                 TC* C, int64_t ldc, const T* col_scale) {
   if (M <= 0 || N <= 0) return RS_OK;
   dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
   if (grid.y > 65535) return rs_fail(RS_EINVAL, "gemm: M = %lld too large", (long long)M);
   const bool ak = (sAk == 1), bn = (sBn == 1);
   if (ak && bn)
-    gemm_kernel<T, TA, TC, true, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+    gemm_kernel<T, TA, TC, TC0, true, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
                                                               C0, ldc0, C, ldc, col_scale);
   else if (ak)
-    gemm_kernel<T, TA, TC, true, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+    gemm_kernel<T, TA, TC, TC0, true, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
                                                                C0, ldc0, C, ldc, col_scale);
   else if (bn)
-    gemm_kernel<T, TA, TC, false, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
+    gemm_kernel<T, TA, TC, TC0, false, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn, (T)beta,
                                                                C0, ldc0, C, ldc, col_scale);
   else
-    gemm_kernel<T, TA, TC, false, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn,
+    gemm_kernel<T, TA, TC, TC0, false, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, (T)alpha, A, sAm, sAk, B, sBk, sBn,
                                                                 (T)beta, C0, ldc0, C, ldc, col_scale);
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
 }
-#define RS_GEMM_INST(T, TA, TC)                                                                                  \
-  template int launch_gemm<T, TA, TC>(rs_ctx*, int64_t, int64_t, int64_t, double, const TA*, int64_t, int64_t,      \
-                                      const T*, int64_t, int64_t, double, const typename NoDeduce<TC>::type*, int64_t, TC*,  \
-                                      int64_t, const T*);
-RS_GEMM_INST(float, float, float)
-RS_GEMM_INST(double, double, double)
-RS_GEMM_INST(float, __nv_bfloat16, float)
-RS_GEMM_INST(float, float, __nv_bfloat16)
+#define RS_GEMM_INST(T, TA, TC, TC0)                                                                               \
+  template int launch_gemm<T, TA, TC, TC0>(rs_ctx*, int64_t, int64_t, int64_t, double, const TA*, int64_t, int64_t,   \
+                                           const T*, int64_t, int64_t, double, const typename NoDeduce<TC0>::type*,    \
+                                           int64_t, TC*, int64_t, const T*);
+RS_GEMM_INST(float, float, float, float)
+RS_GEMM_INST(double, double, double, double)
+RS_GEMM_INST(float, __nv_bfloat16, float, float)
+RS_GEMM_INST(float, float, __nv_bfloat16, __nv_bfloat16)
+RS_GEMM_INST(float, float, __nv_bfloat16, float)
 #undef RS_GEMM_INST
 
 template <typename TA, typename TB>
@@ -752,11 +753,12 @@ static int sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
 
 // ---------------------------------------------------------------------- preconditioner
 
-template <typename S, typename T>
+// X stored in S, components Z stored in SZ (S, or bfloat16 for float data), compute type T
+template <typename S, typename T, typename SZ = S>
 static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const double* sigma2, int64_t k, double lam,
                           rs_matrix* Xt, T* beta, double* beta_hat) {
   const int64_t n = X->n, d = X->d, N = n + d;
-  S* Z = static_cast<S*>(const_cast<void*>(Xt->data));
+  SZ* Z = static_cast<SZ*>(const_cast<void*>(Xt->data));
   const int64_t ldz = Xt->ld;
   T* a = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, k * sizeof(T)));
   T* P = static_cast<T*>(rs_scratch(ctx, SCR_P, n * k * sizeof(T)));
@@ -767,19 +769,19 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
   const S* Xd = static_cast<const S*>(X->data);
   // P = X V diag(a);  Z[0:n] = X - P V^T
   RS_TRY(launch_gemm<T, S, T>(ctx, n, k, d, 1.0, Xd, X->ld, 1, V, k, 1, 0.0, nullptr, 0, P, k, a));
-  RS_TRY(launch_gemm<T, T, S>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
+  RS_TRY(launch_gemm<T, T, SZ, S>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
   // Z[n:n+d] = I - V diag(a) V^T   (the rows b_j = M e_j)
   scale_cols_kernel<T><<<blocks_for(ctx, d * k), 256, 0, ctx->stream>>>(V, d, (int)k, a, Va);
   RS_LAUNCH_CHECK(ctx);
-  S* Zb = Z + n * ldz;
-  identity_rows_kernel<S><<<blocks_for(ctx, d * d), 256, 0, ctx->stream>>>(Zb, d, ldz);
+  SZ* Zb = Z + n * ldz;
+  identity_rows_kernel<SZ><<<blocks_for(ctx, d * d), 256, 0, ctx->stream>>>(Zb, d, ldz);
   RS_LAUNCH_CHECK(ctx);
-  RS_TRY(launch_gemm<T, T, S>(ctx, d, d, k, -1.0, Va, k, 1, V, 1, k, 1.0, Zb, ldz, Zb, ldz, nullptr));
+  RS_TRY(launch_gemm<T, T, SZ>(ctx, d, d, k, -1.0, Va, k, 1, V, 1, k, 1.0, Zb, ldz, Zb, ldz, nullptr));
   // smoothness constants
   const int blocks = blocks_for(ctx, N * 32);
   double* part = static_cast<double*>(rs_scratch(ctx, SCR_MISC, (blocks + 1) * sizeof(double)));
   if (!part) return RS_ENOMEM;
-  row_beta_kernel<S, T><<<blocks, 256, 0, ctx->stream>>>(Z, N, n, d, ldz, lam, beta, part);
+  row_beta_kernel<SZ, T><<<blocks, 256, 0, ctx->stream>>>(Z, N, n, d, ldz, lam, beta, part);
   RS_LAUNCH_CHECK(ctx);
   if (beta_hat) {
     sum_parts_kernel<<<1, 32, 0, ctx->stream>>>(part, blocks, 1.0 / (double)N, part + blocks);
@@ -825,6 +827,9 @@ int precondition_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* V, const 
   if (X->dtype == RS_F64)
     return precondition_t<double, double>(ctx, X, static_cast<const double*>(V), sigma2, k, lam, Xt,
                                   static_cast<double*>(beta), beta_hat);
+  if (X->dtype == RS_F32 && Xt->dtype == RS_BF16)
+    return precondition_t<float, float, __nv_bfloat16>(ctx, X, static_cast<const float*>(V), sigma2, k, lam, Xt,
+                                                       static_cast<float*>(beta), beta_hat);
   if (X->dtype == RS_F32)
     return precondition_t<float, float>(ctx, X, static_cast<const float*>(V), sigma2, k, lam, Xt,
                                         static_cast<float*>(beta), beta_hat);
@@ -962,7 +967,8 @@ int rs_precondition(rs_ctx* ctx, const rs_matrix* X, const void* V, const double
   RS_CHECK_ARG(k >= 1 && k <= X->d, "rs_precondition: k must be in [1, d]");
   RS_CHECK_ARG(lambda > 0.0, "rs_precondition: lambda must be positive");
   RS_CHECK_ARG(Xt->n == X->n + X->d && Xt->d == X->d, "rs_precondition: Xt must be (n + d) x d");
-  RS_CHECK_ARG(Xt->dtype == X->dtype, "rs_precondition: Xt dtype must equal X dtype");
+  RS_CHECK_ARG(Xt->dtype == X->dtype || (X->dtype == RS_F32 && Xt->dtype == RS_BF16),
+               "rs_precondition: Xt dtype must equal X dtype (or be RS_BF16 for RS_F32 data)");
   return precondition_dispatch(ctx, X, V, sigma2, k, lambda, Xt, beta, beta_hat);
 }
 

@@ -464,6 +464,75 @@ static int solve_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, const rs_
   return RS_OK;
 }
 
+int trace_dispatch(rs_ctx* ctx, const rs_matrix* X, double* out);   // dense.cu
+extern "C" int rs_propose(rs_ctx* ctx, const float* theta, const rs_mlp_norm* norm, const double* sigma2,
+                          double lambda, int64_t n, int64_t d, double trace_c, int32_t* k, double* eta_mult,
+                          int64_t* m, int32_t* used_fallback);
+
+// Alg. 3 with proposed parameters: rank-64 sketch, tr(C), rs_propose, components from the leading
+// k Ritz pairs (stored in ZS), SVRG with eta = eta_mult / beta^ and the proposed m.
+template <typename S, typename T, typename ZS>
+static int solve_proposed_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, const rs_sketch_params* sp,
+                            const rs_svrg_params* p, const float* theta, const rs_mlp_norm* norm, void* w_out,
+                            rs_history* hist, int32_t* k_out, double* eta_out, int64_t* m_out, int32_t* fb_out) {
+  const int64_t n = Xin->n, d = Xin->d, N = n + d, K = 64;
+  rs_matrix X = *Xin;
+  const size_t es = sizeof(T), ss = sizeof(S), zs = sizeof(ZS);
+  if (is_host_ptr(Xin->data)) {
+    void* xd = rs_scratch(ctx, SCR_XDEV, (size_t)n * Xin->ld * ss);
+    if (!xd) return RS_ENOMEM;
+    RS_CUDA_TRY(cudaMemcpyAsync(xd, Xin->data, (size_t)n * Xin->ld * ss, cudaMemcpyHostToDevice, ctx->stream));
+    X.data = xd;
+  }
+  const T* y = static_cast<const T*>(yin);
+  if (is_host_ptr(yin)) {
+    T* yd = static_cast<T*>(rs_scratch(ctx, SCR_YDEV, n * es));
+    if (!yd) return RS_ENOMEM;
+    RS_CUDA_TRY(cudaMemcpyAsync(yd, yin, n * es, cudaMemcpyHostToDevice, ctx->stream));
+    y = yd;
+  }
+  const bool host_out = is_host_ptr(w_out);
+  T* wdev = static_cast<T*>(host_out ? rs_scratch(ctx, SCR_WOUT, d * es) : w_out);
+  T* V = static_cast<T*>(rs_scratch(ctx, SCR_V, d * K * es));
+  double* sg = static_cast<double*>(rs_scratch(ctx, SCR_SIGMA, K * sizeof(double)));
+  if (!wdev || !V || !sg) return RS_ENOMEM;
+  rs_sketch_params s64 = *sp;
+  s64.k = (int32_t)K;
+  RS_TRY(sketch_dispatch(ctx, &X, &s64, V, sg));
+  double trc = 0.0, s2h[64];
+  RS_TRY(trace_dispatch(ctx, &X, &trc));   // synchronises
+  RS_CUDA_TRY(cudaMemcpy(s2h, sg, sizeof(s2h), cudaMemcpyDeviceToHost));
+  int32_t k = 0, fb = 0;
+  double em = 0.0;
+  int64_t m = 0;
+  RS_TRY(rs_propose(ctx, theta, norm, s2h, p->lambda, n, d, trc, &k, &em, &m, &fb));
+  T* Vk = static_cast<T*>(rs_scratch(ctx, SCR_VK, d * k * es));
+  const int64_t ldz = (d * (int64_t)zs + 15) / 16 * 16 / (int64_t)zs;
+  ZS* Zbuf = static_cast<ZS*>(rs_scratch(ctx, SCR_Z, (size_t)N * ldz * zs));
+  T* beta = static_cast<T*>(rs_scratch(ctx, SCR_BETA, N * es));
+  if (!Vk || !Zbuf || !beta) return RS_ENOMEM;
+  // leading k columns of the rank-64 Ritz basis (row-major d x 64 -> d x k)
+  RS_CUDA_TRY(cudaMemcpy2DAsync(Vk, k * es, V, K * es, k * es, d, cudaMemcpyDeviceToDevice, ctx->stream));
+  const int32_t zdt = std::is_same<ZS, __nv_bfloat16>::value ? RS_BF16 : X.dtype;
+  rs_matrix Zm = {Zbuf, nullptr, N, d, ldz, zdt, 0};
+  RS_TRY(precondition_dispatch(ctx, &X, Vk, sg, k, p->lambda, &Zm, beta, nullptr));
+  rs_svrg_params q = *p;
+  q.eta = 0.0;
+  q.eta_mult = em;
+  q.m = m;
+  if (!std::is_same<ZS, S>::value) q.refine = 1;
+  RS_TRY(svrg_solve_t<ZS, T, S>(ctx, &Zm, &X, y, beta, Vk, sg, k, &q, nullptr, wdev, hist, nullptr, nullptr));
+  if (host_out) {
+    RS_CUDA_TRY(cudaMemcpyAsync(w_out, wdev, d * es, cudaMemcpyDeviceToHost, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  if (k_out) *k_out = k;
+  if (eta_out) *eta_out = em;
+  if (m_out) *m_out = m;
+  if (fb_out) *fb_out = fb;
+  return RS_OK;
+}
+
 // ====================================================================== C ABI
 
 extern "C" {
@@ -520,13 +589,18 @@ int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const voi
     RS_CHECK_ARG(X != nullptr, "rs_svrg_solve: refinement needs the stored data X");
     RS_TRY(check_matrix(X, "rs_svrg_solve X"));
     RS_CHECK_ARG(X->n == n && X->d == Z->d, "rs_svrg_solve: X must be n x d");
-    RS_CHECK_ARG(X->dtype == Z->dtype, "rs_svrg_solve: X and Z must have the same storage type");
+    RS_CHECK_ARG(X->dtype == Z->dtype || (Z->dtype == RS_BF16 && X->dtype == RS_F32),
+                 "rs_svrg_solve: X must be stored like Z (or in RS_F32 for RS_BF16 components)");
   }
   if (Z->dtype == RS_F64)
     return svrg_solve_t<double, double, double>(ctx, Z, X, static_cast<const double*>(y),
                                                 static_cast<const double*>(beta), static_cast<const double*>(V), sigma2,
                                                 k, p, static_cast<const double*>(w0), static_cast<double*>(w_out), hist,
                                                 eta_used, m_used);
+  if (Z->dtype == RS_BF16 && p->refine && X->dtype == RS_F32)
+    return svrg_solve_t<__nv_bfloat16, float, float>(
+        ctx, Z, X, static_cast<const float*>(y), static_cast<const float*>(beta), static_cast<const float*>(V), sigma2,
+        k, p, static_cast<const float*>(w0), static_cast<float*>(w_out), hist, eta_used, m_used);
   if (Z->dtype == RS_BF16)
     return svrg_solve_t<__nv_bfloat16, float, __nv_bfloat16>(
         ctx, Z, X, static_cast<const float*>(y), static_cast<const float*>(beta), static_cast<const float*>(V), sigma2,
@@ -549,6 +623,33 @@ int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_par
   if (X->dtype == RS_F64) return solve_t<double, double>(ctx, X, y, sp, p, w_out, hist);
   if (X->dtype == RS_BF16) return solve_t<__nv_bfloat16, float>(ctx, X, y, sp, p, w_out, hist);
   return solve_t<float, float>(ctx, X, y, sp, p, w_out, hist);
+}
+
+int rs_solve_proposed(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp,
+                      const rs_svrg_params* p, const float* theta, const rs_mlp_norm* norm, int32_t z_dtype,
+                      void* w_out, rs_history* hist, int32_t* k, double* eta_mult, int64_t* m, int32_t* used_fallback) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(X && X->data && y && sp && p && w_out, "rs_solve_proposed: null argument");
+  RS_CHECK_ARG(X->n >= 1 && X->d >= 64 && X->ld >= X->d, "rs_solve_proposed: need d >= 64 (rank-64 sketch)");
+  RS_CHECK_ARG((X->ld * (int64_t)dtype_size(X->dtype)) % 16 == 0,
+               "rs_solve_proposed: row stride must be a multiple of 16 bytes");
+  RS_CHECK_ARG(p->lambda > 0.0 && p->epochs >= 0, "rs_solve_proposed: bad SVRG parameters");
+  RS_CHECK_ARG(z_dtype == X->dtype || (z_dtype == RS_BF16 && X->dtype == RS_F32),
+               "rs_solve_proposed: components must be stored like X or in RS_BF16 for RS_F32 data");
+  if (X->dtype == RS_F64)
+    return solve_proposed_t<double, double, double>(ctx, X, y, sp, p, theta, norm, w_out, hist, k, eta_mult, m,
+                                                    used_fallback);
+  if (X->dtype == RS_BF16) {
+    RS_CHECK_ARG(p->refine, "rs_solve_proposed: RS_BF16 data needs refine = 1");
+    return solve_proposed_t<__nv_bfloat16, float, __nv_bfloat16>(ctx, X, y, sp, p, theta, norm, w_out, hist, k,
+                                                                  eta_mult, m, used_fallback);
+  }
+  RS_CHECK_ARG(X->dtype == RS_F32, "rs_solve_proposed: dtype must be RS_F64, RS_F32 or RS_BF16");
+  if (z_dtype == RS_BF16)
+    return solve_proposed_t<float, float, __nv_bfloat16>(ctx, X, y, sp, p, theta, norm, w_out, hist, k, eta_mult, m,
+                                                         used_fallback);
+  return solve_proposed_t<float, float, float>(ctx, X, y, sp, p, theta, norm, w_out, hist, k, eta_mult, m,
+                                               used_fallback);
 }
 
 }  // extern "C"

@@ -126,3 +126,38 @@ def test_bf16_svrg_solve_requires_data_for_refinement(rsctx, bf16_problem):
         rs.rs_svrg_solve(rsctx, Z, yf.cuda(), V, s2, lam, 1, 5, beta=beta, refine=True)   # X missing
     w, _ = rs.rs_svrg_solve(rsctx, Z, yf.cuda(), V, s2, lam, 2, 5, beta=beta, refine=True, X=Xc, m=n)
     assert torch.isfinite(w).all()
+
+
+@pytest.mark.parametrize("n,d,k", [(257, 40, 5), (65536, 1024, 64)])
+def test_bf16_components_from_float_data(rsctx, n, d, k):
+    """Float data, bfloat16 components: each z_i is formed in float and rounded once."""
+    X = torch.from_numpy(synth.random_matrix(n, d, n + 2 * d, scale=1.0 / np.sqrt(d))).float()
+    V = torch.from_numpy(synth.random_orthonormal(d, k, d + 1)).float()
+    s2 = synth.random_sigma2(k, k + 1)
+    lam = 1e-4
+    Z, beta, bh = rs.rs_precondition(rsctx, cuda_rows(X), V.cuda(), torch.from_numpy(s2).cuda(), lam,
+                                     z_dtype=torch.bfloat16)
+    assert Z.dtype == torch.bfloat16
+    Zg = Z.cpu().double().numpy()
+    M = precond.m_matrix(V.double().numpy(), s2, lam)
+    Xt, B = precond.transform(X.double().numpy(), M)
+    scale = np.abs(X.double().numpy()).max() * (1 + np.sqrt(k))
+    assert np.all(np.abs(Zg[:n] - Xt) <= BF16_UNIT * np.abs(Xt) + 4e-6 * scale)
+    assert np.all(np.abs(Zg[n:] - B) <= BF16_UNIT * np.abs(B) + 4e-6 * (1 + np.sqrt(k)))
+
+
+def test_bf16_components_with_float_refinement_reach_float_accuracy(rsctx):
+    """BF16 components and the refined gradient on the float data: the iterate converges to the
+    minimiser of Eq. (1) for the float data itself."""
+    n, d, k, lam = 8192, 256, 16, 1e-4
+    X, y, _ = synth.problem(n, d, np.arange(1, d + 1, dtype=np.float64) ** -1.5, 0.1, 78)
+    Xf, yf = X.float(), y.float()
+    Xd, yn = Xf.double().numpy(), yf.double().numpy()
+    ws = ridge.closed_form(Xd, yn, lam)
+    Xc = cuda_rows(Xf)
+    V, s2 = rs.rs_sketch(rsctx, Xc, k, 3)
+    Z, beta, _ = rs.rs_precondition(rsctx, Xc, V, s2, lam, z_dtype=torch.bfloat16)
+    w, info = rs.rs_svrg_solve(rsctx, Z, yf.cuda(), V, s2, lam, 14, 5, beta=beta, m=2 * n, eta_mult=1.0, X=Xc,
+                               refine=True, snapshots=True)
+    rel = [ridge.rel_suboptimality(Xd, yn, lam, s.double().cpu().numpy(), ws) for s in info["snapshots"]]
+    assert rel[-1] <= 1e-8, rel

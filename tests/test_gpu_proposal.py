@@ -161,3 +161,40 @@ def test_trace_c_matches_oracle(rsctx, dtype):
     X = torch.from_numpy(synth.random_matrix(3001, 70, 4)).to(dtype)
     tr = rs.rs_trace_c(rsctx, cuda_rows(X))
     assert tr == pytest.approx(np.trace(ridge.correlation(X.double().numpy())), rel=1e-12)
+
+
+@pytest.mark.parametrize("z_dtype", [None, torch.bfloat16])
+def test_solve_proposed_equals_its_steps(rsctx, z_dtype):
+    """rs_solve_proposed = rank-64 sketch, tr(C), rs_propose, leading-k components, SVRG, bit for bit;
+    host buffers give the same result as device buffers."""
+    from tests.gpu_helpers import cuda_rows
+    n, d, lam = 6000, 128, 1e-4
+    X, y, _ = synth.problem(n, d, np.arange(1, d + 1, dtype=np.float64) ** -1.6, 0.1, 31)
+    Xc, yc = cuda_rows(X.float()), y.float().cuda()
+    im, isd, om, osd = _norm()
+    nm = rs.mlp_norm(im, isd, om, osd)
+    theta = _f32(_proposal_theta([0.3, 0.2, -0.5])).cuda()
+    w, info = rs.rs_solve_proposed(rsctx, Xc, yc, lam, 3, 11, 12, theta=theta, norm=nm, z_dtype=z_dtype)
+    V, s2 = rs.rs_sketch(rsctx, Xc, 64, 11)
+    k, em, m, fb = rs.rs_propose(rsctx, s2.cpu().numpy(), lam, n, d, rs.rs_trace_c(rsctx, Xc), theta=theta, norm=nm)
+    assert (k, m, fb) == (info["k"], info["m"], info["fallback"]) and em == info["eta_mult"]
+    Vk, s2k = V[:, :k].contiguous(), s2[:k].contiguous()
+    Z, beta, _ = rs.rs_precondition(rsctx, Xc, Vk, s2k, lam, z_dtype=z_dtype)
+    w2, _ = rs.rs_svrg_solve(rsctx, Z, yc, Vk, s2k, lam, 3, 12, beta=beta, m=m, eta_mult=em,
+                             X=Xc if z_dtype is not None else None, refine=z_dtype is not None)
+    assert torch.equal(w, w2)
+    Xh = Xc.cpu().pin_memory()
+    wh, _ = rs.rs_solve_proposed(rsctx, Xh, yc.cpu().pin_memory(), lam, 3, 11, 12, theta=theta, norm=nm,
+                                 z_dtype=z_dtype, w_out=torch.empty(d).pin_memory())
+    assert torch.equal(wh, w.cpu())
+
+
+def test_solve_proposed_without_weights_uses_the_theory_setting(rsctx):
+    from tests.gpu_helpers import cuda_rows
+    n, d, lam = 4000, 96, 1e-3
+    X, y, _ = synth.problem(n, d, np.arange(1, d + 1, dtype=np.float64) ** -1.3, 0.1, 32)
+    Xc = cuda_rows(X.float())
+    _, info = rs.rs_solve_proposed(rsctx, Xc, y.float().cuda(), lam, 1, 3, 4)
+    V, s2 = rs.rs_sketch(rsctx, Xc, 64, 3)
+    th = proposal.theory_defaults(s2.cpu().numpy(), rs.rs_trace_c(rsctx, Xc), lam, n, d)
+    assert info["fallback"] and (info["k"], info["eta_mult"], info["m"]) == th
