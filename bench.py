@@ -272,6 +272,103 @@ def run_rs(args):
     ctx.close()
 
 
+class _Reference:
+    """w* of Eq. (1) from the normal equations accumulated in double on the device in row chunks
+    (measurement only, untimed), and relative suboptimality of iterates through e^T H e / 2."""
+
+    def __init__(self, X, y, lam):
+        n, d = X.shape
+        G = torch.zeros(d, d, dtype=torch.float64, device=X.device)
+        b = torch.zeros(d, dtype=torch.float64, device=X.device)
+        for r0 in range(0, n, 16384):
+            Xb = X[r0:r0 + 16384].double()
+            G += Xb.T @ Xb
+            b += Xb.T @ y[r0:r0 + 16384].double()
+            del Xb
+        self.H = G / n + lam * torch.eye(d, dtype=torch.float64, device=X.device)
+        self.w = torch.from_numpy(np.linalg.solve(self.H.cpu().numpy(), (b / n).cpu().numpy())).to(X.device)
+        r = torch.zeros((), dtype=torch.float64, device=X.device)
+        for r0 in range(0, n, 16384):
+            e = X[r0:r0 + 16384].double() @ self.w - y[r0:r0 + 16384].double()
+            r += e @ e
+        self.L = float(0.5 * r / n + 0.5 * lam * (self.w @ self.w))
+
+    def rel(self, W):
+        E = W.double().reshape(-1, self.w.shape[0]) - self.w
+        return (0.5 * ((E @ self.H) * E).sum(1) / self.L).cpu().numpy()
+
+
+def run_precision(args):
+    """Precision workload (one GPU): n = 2^20, d = 4096, spectrum j^-1.2 with the leading 20
+    directions x100, lambda = 1e-6, k = 256.  Time to 1e-6 for BF16 components with snapshot
+    gradients refined on the BF16 data, against the same solve on FP32 data, and the BF16 solve
+    with the proposal network's (k <= 64, eta, m)."""
+    import paper_1602_02350_gb300 as rs
+    from paper_1602_02350_gb300 import synth
+    name = "bf16_n1048576_d4096"
+    cfg = synth.CONFIGS[name]
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = rs.Context(local, stream)
+    Xb, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.bfloat16)
+    y = y64.float().contiguous()
+    del y64
+    n, d, k, lam = cfg.n, cfg.d, cfg.k, cfg.lam
+    ref = _Reference(Xb, y, lam)
+    theta, norm = _load_proposal(rs)
+    cap = args.precision_epochs
+
+    def first(snaps):
+        rel = ref.rel(snaps)
+        hit = [i for i, r in enumerate(rel) if r <= TARGET]
+        return (hit[0] + 1 if hit else cap), [float(f"{r:.3e}") for r in rel]
+
+    forms = {}
+
+    def timed(fn):
+        fn()
+        ms, _ = _time_steps(fn, 1, stream)
+        return ms
+
+    # BF16 data, k = 256, practice setting m = 2n, eta = 1/beta^, refined snapshot gradients
+    _, info = rs.rs_solve(ctx, Xb, y, k, lam, cap, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0,
+                          snapshots=True, refine=True)
+    e, hist = first(info["snapshots"])
+    del info
+    ms = timed(lambda: rs.rs_solve(ctx, Xb, y, k, lam, e, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0,
+                                   refine=True))
+    forms["bf16_refined_k256"] = {"seconds": ms / 1e3, "epochs": e, "rel_subopt_per_epoch": hist[:e]}
+    # BF16 data, proposal network
+    _, info = rs.rs_solve_proposed(ctx, Xb, y, lam, cap, cfg.seed_sketch, cfg.seed_svrg, theta=theta, norm=norm,
+                                   snapshots=True)
+    e, hist = first(info["snapshots"])
+    ms = timed(lambda: rs.rs_solve_proposed(ctx, Xb, y, lam, e, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
+                                            norm=norm))
+    forms["bf16_refined_proposal"] = {"seconds": ms / 1e3, "epochs": e, "k": info["k"], "eta_mult": info["eta_mult"],
+                                      "m": info["m"], "fallback": info["fallback"], "rel_subopt_per_epoch": hist[:e]}
+    del info
+    # FP32 data, same setting as the first form
+    Xf = Xb.float()
+    del Xb
+    torch.cuda.empty_cache()
+    _, info = rs.rs_solve(ctx, Xf, y, k, lam, cap, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0,
+                          snapshots=True)
+    e, hist = first(info["snapshots"])
+    del info
+    ms = timed(lambda: rs.rs_solve(ctx, Xf, y, k, lam, e, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0))
+    forms["fp32_k256"] = {"seconds": ms / 1e3, "epochs": e, "rel_subopt_per_epoch": hist[:e]}
+    best = min(forms, key=lambda f: forms[f]["seconds"])
+    out = {"metric": "time-to-1e-6 relative suboptimality (precision workload)", "value": forms[best]["seconds"],
+           "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False, "dtype": "bf16+f32",
+           "data": "synthetic",
+           "config": {"workload": f"{name}: n=2^20 d=4096, spectrum j^-1.2 (x100 for j<=20), lambda=1e-6, "
+                                  "Gaussian sketch", "best_form": best, "forms": forms,
+                      "l2": "inputs exceed L2 (X 8.6 GB bf16); no flush"}}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def cpu_baseline_sample(budget_s=20.0, epochs=None):
     """Time the FP64 oracle on host cores on a bounded sample of the workload and extrapolate
     to one solve: (sketch + precondition) once, plus epochs x (full gradient + m steps)."""
@@ -342,10 +439,15 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run two solves of each form with the given epoch counts and exit (for ncu launch lists)")
     ap.add_argument("--plain-epochs", type=int, default=4)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bf16_n1048576_d4096"],
+                    help="bf16_n1048576_d4096: the precision workload (its own JSON line)")
+    ap.add_argument("--precision-epochs", type=int, default=30)
     ap.add_argument("--chosen-epochs", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "bf16_n1048576_d4096":
+        run_precision(args)
     else:
         run_rs(args)
 

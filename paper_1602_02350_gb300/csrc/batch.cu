@@ -125,7 +125,7 @@ struct ChainWs {
   int pair, r;       // r: column of this chain in its problem's U / G
   int64_t m, nblk;
   double eta;
-  float *wa, *wb, *mu, *u, *inq, *Rt, *cv;
+  float *wa, *wb, *mu, *u, *inq, *Rt, *cv, *Kt, *hn;
   uint32_t* idx;
 };
 
@@ -205,6 +205,8 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
       cw[c].inq = cv.take<float>(cw[c].m);
       cw[c].Rt = cv.take<float>(cw[c].nblk * kChainBlk * kChainBlk);
       cw[c].cv = cv.take<float>(cw[c].nblk * kChainBlk);
+      cw[c].Kt = cv.take<float>(cw[c].nblk * kChainBlk * kChainBlk);   // look-ahead cross Gram matrices
+      cw[c].hn = cv.take<float>(cw[c].nblk * kChainBlk);
     }
     jobs_dev = cv.take<ChainJob<S, float>>(2 * (size_t)nc);
     idx_dev = cv.take<IdxJob>(nc);
@@ -274,6 +276,8 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
       J.wnext = par ? cw[c].wa : cw[c].wb;
       J.Rt = cw[c].Rt;
       J.cvec = cw[c].cv;
+      J.Kt = cw[c].Kt;
+      J.hn = cw[c].hn;
       J.average = bp->average;
       J.reserved = 0;
       MapJob u{};

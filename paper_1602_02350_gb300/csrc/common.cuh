@@ -24,7 +24,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_COUNT
 };
 
 struct rs_ctx {
@@ -159,6 +159,49 @@ template <> struct Vec<double> { using type = double2; static constexpr int N = 
 __device__ __forceinline__ void vec_to_arr(const float4& v, float* a) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
 __device__ __forceinline__ void vec_to_arr(const double2& v, double* a) { a[0] = v.x; a[1] = v.y; }
 
+// ------------------------------------------ mbarrier and bulk-copy primitives (CTA scope)
+
+__device__ __forceinline__ uint32_t cta_smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init_cta(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(cta_smem_addr(bar)), "r"(count) : "memory");
+}
+// arrive once and add tx_bytes to the transaction count of the current phase
+__device__ __forceinline__ void mbar_expect_tx_cta(uint64_t* bar, uint32_t tx_bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+                   cta_smem_addr(bar)),
+               "r"(tx_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t* bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(cta_smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_parity_cta(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(cta_smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase of the given parity to complete, at most `budget` clock cycles
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  while (!mbar_test_parity_cta(bar, parity))
+    if (clock64() - t0 > budget) return false;
+  return true;
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) that completes
+// its bytes on the mbarrier
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   cta_smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(cta_smem_addr(bar))
+               : "memory");
+}
+
 // Internal launch helpers implemented in dense.cu, used by several entry points.
 template <typename T> struct NoDeduce { using type = T; };   // keeps a parameter out of type deduction
 // A, C and C0 may be stored in other types than the compute type T (bfloat16 data).
@@ -192,6 +235,8 @@ struct ChainJob {
   T* wnext;
   T* Rt;
   T* cvec;
+  T* Kt;        // look-ahead: blocks x 64 x 64 cross Gram matrices (next block's rows . this block's)
+  T* hn;        // look-ahead: blocks x 64, next block's rows . mu
   int32_t average, reserved;
 };
 

@@ -51,23 +51,28 @@ __device__ __forceinline__ void ld_widen8(const __nv_bfloat16* p, float* v) {
 // ------------------------------------------------------------------ per-block preparation
 // One thread block per block of steps.  Rows 0..B-1 of the staged tile are the sampled rows
 // (zero beyond the last step), row B is mu, rows B+1..B+3 are zero.  Z is stored in S and
-// widened to the compute type T while it is staged.
-template <typename S, typename T>
+// widened to the compute type T while it is staged.  With LA (look-ahead) the rows of the next
+// block follow as rows B+4..2B+3, and the block also writes the cross Gram matrix
+// Kt[l][j] = z'_j . z_l (z' the next block's rows) and hn_j = z'_j . mu.
+template <typename S, typename T, bool LA = false>
 __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d, int64_t n,
                                           double lam, const uint32_t* __restrict__ idx, const T* __restrict__ inv_nq,
                                           int64_t m, double eta, const T* __restrict__ mu, T* __restrict__ Rt,
-                                          T* __restrict__ cvec, int64_t b) {
-  constexpr int B = kBlk, RP = B + 4;
+                                          T* __restrict__ cvec, T* __restrict__ Kt, T* __restrict__ hn, int64_t b) {
+  constexpr int B = kBlk, RP0 = B + 4, RP = LA ? RP0 + B : RP0;
   constexpr int E = 16 / sizeof(T);
   constexpr int CH = 64;              // columns per staged chunk
   constexpr int TS = CH + E;          // tile row stride (16-byte multiple, skews banks)
+  constexpr int NLT = (RP0 / 4) * (RP0 / 4 + 1) / 2;   // lower-triangular 4x4 tiles of the block Gram (153)
+  constexpr int NXT = LA ? (B / 4) * (RP0 / 4) : 0;    // cross tiles next-block rows x (rows, mu) (272)
   extern __shared__ __align__(16) unsigned char pr_sh[];
   T* tile = reinterpret_cast<T*>(pr_sh);        // [2][RP][TS]
-  T* G = tile + 2 * RP * TS;                    // [RP][RP + 1]
-  T* R = G + RP * (RP + 1);                     // [B][B + 1]   R[j][c]
+  T* G = tile + 2 * RP * TS;                    // [RP0][RP0 + 1]
+  T* R = G + RP0 * (RP0 + 1);                   // [B][B + 1]   R[j][c]
   T* acc = R + B * (B + 1);                     // [B][B + 1]
+  T* Gx = acc + B * (B + 1);                    // [B][RP0 + 1] (LA only)
   __shared__ T kap[B];
-  __shared__ int64_t rowid[B];
+  __shared__ int64_t rowid[LA ? 2 * B : B];
   const int tid = threadIdx.x;
   const int64_t t0 = b * B;
   const int Bb = (int)min64(B, m - t0);
@@ -81,8 +86,16 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
       rowid[tid] = -1;
       kap[tid] = T(0);
     }
+  } else if (LA && tid < 2 * B) {
+    rowid[tid] = (t0 + tid < m) ? (int64_t)min(idx[t0 + tid], (uint32_t)(N - 1)) : -1;
   }
   __syncthreads();
+  // staged row r: a sampled row of this block, mu, a zero row, or a sampled row of the next block
+  auto row_of = [&](int r) -> int64_t {
+    if (r < B) return r < Bb ? rowid[r] : -1;
+    if (LA && r >= RP0) return rowid[B + r - RP0];
+    return -1;
+  };
   const int nch = (int)((d + CH - 1) / CH);
   auto stage = [&](int ch, int buf) {
     T* dst = tile + buf * RP * TS;
@@ -97,8 +110,9 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
         T v[ES];
 #pragma unroll
         for (int i = 0; i < ES; ++i) v[i] = T(0);
-        if (r < Bb && col < d) {
-          const S* src = Z + rowid[r] * ld + col;
+        const int64_t rid = row_of(r);
+        if (rid >= 0 && col < d) {
+          const S* src = Z + rid * ld + col;
           if (col + ES <= d) ld_widen8(src, v);
           else
             for (int i = 0; i < (int)(d - col); ++i) v[i] = cvt<T>(src[i]);
@@ -125,7 +139,8 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
       int bytes = 0;
       if (col < d) {
         const int valid = (int)min64(E, d - col) * (int)sizeof(T);
-        if (r < B && r < Bb) { src = reinterpret_cast<const T*>(Z) + rowid[r] * ld + col; bytes = valid; }
+        const int64_t rid = row_of(r);
+        if (rid >= 0) { src = reinterpret_cast<const T*>(Z) + rid * ld + col; bytes = valid; }
         else if (r == B) { src = mu + col; bytes = (reinterpret_cast<uintptr_t>(mu + col) & 15) ? 0 : valid; }
       }
       cp_async16(dst + r * TS + q * E, src, bytes);
@@ -134,18 +149,29 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
   };
   // mu may not be 16-byte aligned at every chunk: stage it with plain loads when it is not
   const bool mu_aligned = (reinterpret_cast<uintptr_t>(mu) & 15) == 0;
-  // lower-triangular 4x4 tiles of the RP x RP Gram matrix (17*18/2 = 153 tiles)
-  int TI = -1, TJ = -1;
-  {
-    int t = tid, I = 0;
-    while (I < RP / 4 && t > I) { t -= I + 1; ++I; }
-    if (I < RP / 4) { TI = I; TJ = t; }
-  }
-  T a4[4][4];
+  // 4x4 tiles: thread tid takes tile tid and (look-ahead) tile tid + 256.  Tiles 0..152 are the
+  // lower triangle of the RP0 x RP0 Gram matrix; tiles 153.. pair next-block rows with rows 0..RP0-1
+  auto tile_of = [&](int id, int& I, int& J) {
+    I = -1;
+    J = -1;
+    if (id < NLT) {
+      int t = id, q = 0;
+      while (q < RP0 / 4 && t > q) { t -= q + 1; ++q; }
+      I = q;
+      J = t;
+    } else if (id < NLT + NXT) {
+      I = RP0 / 4 + (id - NLT) / (RP0 / 4);
+      J = (id - NLT) % (RP0 / 4);
+    }
+  };
+  int TI, TJ, TI2 = -1, TJ2 = -1;
+  tile_of(tid, TI, TJ);
+  if (LA) tile_of(tid + 256, TI2, TJ2);
+  T a4[4][4], b4[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a4[i][j] = T(0);
+    for (int j = 0; j < 4; ++j) a4[i][j] = b4[i][j] = T(0);
   stage(0, 0);
   for (int ch = 0; ch < nch; ++ch) {
     if (ch + 1 < nch) stage(ch + 1, (ch + 1) & 1);
@@ -177,18 +203,42 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
             for (int j = 0; j < 4; ++j) a4[i][j] = fma(x[i][e], y[j][e], a4[i][j]);
       }
     }
+    if (LA && TI2 >= 0) {
+      using V = typename Vec<T>::type;
+#pragma unroll 4
+      for (int c = 0; c < CH; c += E) {
+        T x[4][E], y[4][E];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vec_to_arr(*reinterpret_cast<const V*>(tl + (TI2 * 4 + i) * TS + c), x[i]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) vec_to_arr(*reinterpret_cast<const V*>(tl + (TJ2 * 4 + j) * TS + c), y[j]);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b4[i][j] = fma(x[i][e], y[j][e], b4[i][j]);
+      }
+    }
     __syncthreads();
   }
-  if (TI >= 0) {
+  auto store_tile = [&](int I, int J, T (&t4)[4][4]) {
+    if (I < 0) return;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int gi = TI * 4 + i, gj = TJ * 4 + j;
-        G[gi * (RP + 1) + gj] = a4[i][j];
-        G[gj * (RP + 1) + gi] = a4[i][j];
+        const int gi = I * 4 + i, gj = J * 4 + j;
+        if (gi < RP0) {
+          G[gi * (RP0 + 1) + gj] = t4[i][j];
+          G[gj * (RP0 + 1) + gi] = t4[i][j];
+        } else {
+          Gx[(gi - RP0) * (RP0 + 1) + gj] = t4[i][j];
+        }
       }
-  }
+  };
+  store_tile(TI, TJ, a4);
+  if (LA) store_tile(TI2, TJ2, b4);
   for (int e = tid; e < B * (B + 1); e += blockDim.x) {
     R[e] = T(0);
     acc[e] = T(0);
@@ -202,7 +252,7 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
     __syncthreads();
     if (cc <= l) {
       const T rl = R[l * (B + 1) + cc];
-      for (int j = l + 1 + jg; j < Bb; j += 4) acc[j * (B + 1) + cc] = fma(G[j * (RP + 1) + l], rl, acc[j * (B + 1) + cc]);
+      for (int j = l + 1 + jg; j < Bb; j += 4) acc[j * (B + 1) + cc] = fma(G[j * (RP0 + 1) + l], rl, acc[j * (B + 1) + cc]);
     }
     __syncthreads();
   }
@@ -210,7 +260,7 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
   if (tid < B) {
     const int j = tid;
     T s = T(0);
-    for (int l = 0; l <= j && l < Bb; ++l) s = fma(R[j * (B + 1) + l], (T)l * G[B * (RP + 1) + l], s);
+    for (int l = 0; l <= j && l < Bb; ++l) s = fma(R[j * (B + 1) + l], (T)l * G[B * (RP0 + 1) + l], s);
     cvec[b * B + j] = j < Bb ? -et * s : T(0);
   }
   T* Rout = Rt + b * (int64_t)B * B;
@@ -218,6 +268,21 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
     const int l = e / B, j = e % B;
     Rout[e] = R[j * (B + 1) + l];   // transposed: Rt[l][j] = R[j][l]
   }
+  if constexpr (LA) {
+    T* Kout = Kt + b * (int64_t)B * B;
+    for (int e = tid; e < B * B; e += blockDim.x) {
+      const int l = e / B, j = e % B;
+      Kout[e] = Gx[j * (RP0 + 1) + l];   // Kt[l][j] = z'_j . z_l
+    }
+    if (tid < B) hn[b * B + tid] = Gx[tid * (RP0 + 1) + B];
+  }
+}
+
+// dynamic shared memory of prep_body
+template <typename T, bool LA>
+constexpr size_t prep_smem_bytes() {
+  constexpr int B = kBlk, RP0 = B + 4, RP = LA ? RP0 + B : RP0, E = 16 / sizeof(T);
+  return (size_t)(2 * RP * (64 + E) + RP0 * (RP0 + 1) + 2 * B * (B + 1) + (LA ? B * (RP0 + 1) : 0)) * sizeof(T);
 }
 
 template <typename S, typename T>
@@ -226,11 +291,21 @@ __global__ void __launch_bounds__(256) epoch_prep_kernel(const S* __restrict__ Z
                                                          const T* __restrict__ inv_nq, int64_t m, double eta,
                                                          const T* __restrict__ mu, T* __restrict__ Rt,
                                                          T* __restrict__ cvec) {
-  prep_body<S, T>(Z, N, ld, d, n, lam, idx, inv_nq, m, eta, mu, Rt, cvec, blockIdx.x);
+  prep_body<S, T>(Z, N, ld, d, n, lam, idx, inv_nq, m, eta, mu, Rt, cvec, nullptr, nullptr, blockIdx.x);
+}
+
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) epoch_prep_la_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                                            int64_t n, double lam, const uint32_t* __restrict__ idx,
+                                                            const T* __restrict__ inv_nq, int64_t m, double eta,
+                                                            const T* __restrict__ mu, T* __restrict__ Rt,
+                                                            T* __restrict__ cvec, T* __restrict__ Kt,
+                                                            T* __restrict__ hn) {
+  prep_body<S, T, true>(Z, N, ld, d, n, lam, idx, inv_nq, m, eta, mu, Rt, cvec, Kt, hn, blockIdx.x);
 }
 
 // all jobs' blocks in one grid: block g belongs to job j with blk_off[j] <= g < blk_off[j + 1]
-template <typename S, typename T>
+template <typename S, typename T, bool LA>
 __global__ void __launch_bounds__(256) epoch_prep_batched_kernel(const ChainJob<S, T>* __restrict__ jobs,
                                                                  const int64_t* __restrict__ blk_off, int nj) {
   const int64_t g = blockIdx.x;
@@ -241,7 +316,8 @@ __global__ void __launch_bounds__(256) epoch_prep_batched_kernel(const ChainJob<
     else hi = mid - 1;
   }
   const ChainJob<S, T> J = jobs[lo];
-  prep_body<S, T>(J.Z, J.N, J.ld, J.d, J.n, J.lam, J.idx, J.inv_nq, J.m, J.eta, J.mu, J.Rt, J.cvec, g - blk_off[lo]);
+  prep_body<S, T, LA>(J.Z, J.N, J.ld, J.d, J.n, J.lam, J.idx, J.inv_nq, J.m, J.eta, J.mu, J.Rt, J.cvec, J.Kt, J.hn,
+                      g - blk_off[lo]);
 }
 
 // ------------------------------------------------------------------ sequential chain
@@ -543,6 +619,294 @@ __global__ void __launch_bounds__(NT) epoch_chain_batched_kernel(const ChainJob<
                                    J.wnext, status);
 }
 
+// ------------------------------------------------------------------ look-ahead chain
+// The same recursion with the cluster exchange taken off the critical path.  With delta_b the
+// state at the start of block b, q = Z_{b+1} delta_b and K = Z_{b+1} Z_b^T (from the look-ahead
+// preparation),
+//   p_{b+1} = q - eta K a_b - B_b eta (Z_{b+1} mu),
+// so the partial dot products of q are pushed to every rank at the start of block b and travel
+// while the block forms a_b = R_b p_b + c_b and updates delta; p_0 = 0 because delta_0 = 0.
+// Per block: Z rows in a ring of ZST stages (blocks b and b+1 resident, b+2.. in flight), and
+// R_b, K_b, c_b, hn_b in a two-slot ring.
+template <typename S, typename T, int ZST, int QN, int NT>
+__device__ __forceinline__ void chain_la_body(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                              const uint32_t* __restrict__ idx, int64_t m, const T* __restrict__ Rt,
+                                              const T* __restrict__ cvec, const T* __restrict__ Kt,
+                                              const T* __restrict__ hn, double eta, const T* __restrict__ mu,
+                                              const T* __restrict__ wbar, int average, T* __restrict__ wnext,
+                                              int* status) {
+  constexpr int B = kBlk;
+  constexpr int E = 16 / sizeof(T);
+  constexpr int ES = 16 / sizeof(S);
+  constexpr int CW = 32 * QN;
+  constexpr int NCH = CW / ES;
+  constexpr int NW = NT / 32;
+  constexpr int RPW = B / NW;
+  constexpr int H = NT / B;
+  constexpr int TPC = NT / CW > 0 ? NT / CW : 1;
+  constexpr int JPT = B / TPC;
+  constexpr int CPW = 32 / TPC;
+  constexpr int W16 = RPW * (int)sizeof(T) / 16;
+  constexpr int ZS = CW + chain_zpad(TPC, CPW, (int)sizeof(S));
+  constexpr int AUX = 2 * B * B + 2 * B;   // one slot: R (l, j), K (l, j), c, hn
+  static_assert(ZST >= 3, "blocks b and b+1 resident plus one in flight");
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char ch_sh[];
+  S* Zs = reinterpret_cast<S*>(ch_sh);                                 // [ZST][B][ZS]
+  T* aux = reinterpret_cast<T*>(Zs + (size_t)ZST * B * ZS);           // [2][AUX]
+  T* recv = aux + 2 * AUX;                                             // [2][kCsMax][B]
+  double* Ssum = reinterpret_cast<double*>(recv + 2 * kCsMax * B);     // [CW]
+  T* dl = reinterpret_cast<T*>(Ssum + CW);                             // [CW]
+  T* mus = dl + CW;                                                    // [CW]
+  T* pv = mus + CW;                                                    // [B]
+  T* av = pv + B;                                                      // [B]
+  T* part4 = av + B;                                                   // [H][B]
+  uint32_t* srow = reinterpret_cast<uint32_t*>(part4 + H * B);         // [ZST][B]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + ZST * B);        // [2]
+  __shared__ int aborted;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c0 = (int64_t)rank * CW;
+  const int cwid = (int)max64(0, min64(CW, d - c0));
+  const int64_t nblk = (m + B - 1) / B;
+  const T et = (T)eta;
+  const uint32_t tx_per_block = (uint32_t)(CS * B * sizeof(T));
+
+  for (int c = tid; c < CW; c += NT) {
+    dl[c] = T(0);
+    Ssum[c] = 0.0;
+    mus[c] = c < cwid ? mu[c0 + c] : T(0);
+  }
+  if (tid < B) pv[tid] = T(0);
+  auto fetch_rows = [&](int64_t blk) -> uint32_t {
+    const int64_t t = blk * B + tid;
+    return (tid < B && t < m) ? (uint32_t)min64((int64_t)idx[t], N - 1) : 0xFFFFFFFFu;
+  };
+  for (int s = 0; s < ZST; ++s)
+    if (tid < B) srow[s * B + tid] = fetch_rows(s);
+  uint32_t pend_row = fetch_rows(ZST);
+  if (tid == 0) {
+    aborted = 0;
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (nblk > 1) mbar_arm(&mbar[1], tx_per_block);   // exchange for block 1
+    if (nblk > 2) mbar_arm(&mbar[0], tx_per_block);   // exchange for block 2
+  }
+  __syncthreads();
+
+  auto load_z = [&](int64_t blk) {
+    const int slot = (int)(blk % ZST);
+    S* zdst = Zs + (size_t)slot * B * ZS;
+    const uint32_t* rows = srow + slot * B;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int j = warp + NW * r;
+      const uint32_t row = rows[j];
+      for (int q = lane; q < NCH; q += 32) {
+        const int col = q * ES;
+        int bytes = 0;
+        const S* src = Z;
+        if (row != 0xFFFFFFFFu && col < cwid) {
+          bytes = min(ES, cwid - col) * (int)sizeof(S);
+          src = Z + (int64_t)row * ld + c0 + col;
+        }
+        cp_async16(zdst + j * ZS + col, src, bytes);
+      }
+    }
+  };
+  auto load_aux = [&](int64_t blk) {
+    T* dst = aux + (size_t)(blk & 1) * AUX;
+    for (int e = tid; e < AUX / E; e += NT) {
+      const int o = e * E;
+      const T* src;
+      if (o < B * B) src = Rt + blk * (int64_t)B * B + o;
+      else if (o < 2 * B * B) src = Kt + blk * (int64_t)B * B + (o - B * B);
+      else if (o < 2 * B * B + B) src = cvec + blk * B + (o - 2 * B * B);
+      else src = hn + blk * B + (o - 2 * B * B - B);
+      cp_async16(dst + o, src, 16);
+    }
+  };
+
+  for (int s = 0; s < ZST - 1; ++s)
+    if (s < nblk) load_z(s);
+  load_aux(0);
+  cp_async_commit();
+  cluster.sync();   // every block's mbarriers are initialised before any remote store
+
+  const int dst = lane < CS ? lane : 0;
+  const uint32_t recv_remote = map_rank(smem_u32(recv), dst);
+  const uint32_t bar_remote0 = map_rank(smem_u32(&mbar[0]), dst);
+  const uint32_t bar_remote1 = map_rank(smem_u32(&mbar[1]), dst);
+
+  for (int64_t blk = 0; blk < nblk; ++blk) {
+    cp_async_wait<0>();
+    __syncthreads();
+    if (blk + ZST - 1 < nblk) load_z(blk + ZST - 1);
+    if (blk + 1 < nblk) load_aux(blk + 1);
+    cp_async_commit();
+    {
+      const uint32_t nr = pend_row;
+      pend_row = fetch_rows(blk + ZST + 1);
+      if (tid < B) srow[(int)((blk + ZST) % ZST) * B + tid] = nr;   // that slot's block was issued long ago
+    }
+    const int Bb = (int)min64(B, m - blk * B);
+    const bool has_next = blk + 1 < nblk;
+    const T* A = aux + (size_t)(blk & 1) * AUX;
+    const T* Rs = A;
+    const T* Ks = A + B * B;
+    const T* Cs = A + 2 * B * B;
+    const T* Hs = Cs + B;
+    // (A) partial dots of the next block's rows with delta_b, pushed to every rank
+    if (has_next) {
+      const S* zsn = Zs + (size_t)((blk + 1) % ZST) * B * ZS;
+      T dv[QN];
+#pragma unroll
+      for (int q = 0; q < QN; ++q) dv[q] = dl[lane + 32 * q];
+      T part[RPW];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        const S* zr = zsn + (RPW * warp + r) * ZS + lane;
+        T sacc = T(0);
+#pragma unroll
+        for (int q = 0; q < QN; ++q) sacc = fma(cvt<T>(zr[32 * q]), dv[q], sacc);
+        part[r] = sacc;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) part[r] += __shfl_xor_sync(0xffffffffu, part[r], o);
+      if (lane < CS) {
+        uint32_t pw[RPW * sizeof(T) / 4];
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) {
+          if constexpr (sizeof(T) == 8) {
+            pw[2 * r] = (uint32_t)__double2loint(part[r]);
+            pw[2 * r + 1] = (uint32_t)__double2hiint(part[r]);
+          } else {
+            pw[r] = __float_as_uint(part[r]);
+          }
+        }
+        const int par = (int)((blk + 1) & 1);
+        const uint32_t base = recv_remote + (uint32_t)(((par * kCsMax + rank) * B + RPW * warp) * sizeof(T));
+        const uint32_t rbar = par ? bar_remote1 : bar_remote0;
+#pragma unroll
+        for (int h = 0; h < W16; ++h) st_async16(base + 16 * h, rbar, pw + 4 * h);
+      }
+    }
+    // (B) a_b = R_b p_b + c_b: thread (j, h) sums the terms l = h, h + H, ... <= j
+    {
+      const int j = tid & (B - 1), h = tid >> 6;
+      const T* rs = Rs + j;
+      T s0 = T(0), s1 = T(0);
+      const int lend = j + 1;
+      int l = h;
+      for (; l + H < lend; l += 2 * H) {
+        s0 = fma(rs[l * B], pv[l], s0);
+        s1 = fma(rs[(l + H) * B], pv[l + H], s1);
+      }
+      if (l < lend) s0 = fma(rs[l * B], pv[l], s0);
+      part4[h * B + j] = s0 + s1;
+    }
+    __syncthreads();
+    if (tid < B) {
+      T sa = Cs[tid];
+#pragma unroll
+      for (int hh = 0; hh < H; ++hh) sa += part4[hh * B + tid];   // fixed order
+      av[tid] = sa;
+    }
+    __syncthreads();
+    // (C) rank-B update of delta and of the running sum with this block's rows
+    {
+      const S* zs = Zs + (size_t)(blk % ZST) * B * ZS;
+      const int c = warp * CPW + (lane % CPW), g = lane / CPW;
+      T u = T(0), w = T(0);
+      T wt = (T)(Bb - g);
+#pragma unroll 8
+      for (int jj = 0; jj < JPT; ++jj) {
+        const int j = g + TPC * jj;
+        const T az = av[j] * cvt<T>(zs[j * ZS + c]);
+        u += az;
+        w = fma(wt, az, w);
+        wt -= T(TPC);
+      }
+#pragma unroll
+      for (int o = CPW; o < 32; o <<= 1) {
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+      }
+      if (g == 0) {
+        const T bbT = (T)Bb;
+        const T tri = (T)(0.5 * (double)Bb * (double)(Bb + 1));
+        const T dold = dl[c];
+        Ssum[c] += (double)(bbT * dold - et * (mus[c] * tri + w));
+        dl[c] = dold - et * (bbT * mus[c] + u);
+      }
+    }
+    // (E) K a_b: thread (j, h) sums the terms l = h, h + H, ... (K is full)
+    if (has_next) {
+      const int j = tid & (B - 1), h = tid >> 6;
+      const T* ks = Ks + j;
+      T s0 = T(0), s1 = T(0);
+#pragma unroll 4
+      for (int l = h; l < B; l += 2 * H) {
+        s0 = fma(ks[l * B], av[l], s0);
+        s1 = fma(ks[(l + H) * B], av[l + H], s1);
+      }
+      part4[h * B + j] = s0 + s1;
+    }
+    // (D) the next block's partial dots from every rank (bounded wait)
+    if (has_next && !aborted) {
+      const long long t0c = clock64();
+      while (!mbar_try_wait(&mbar[(blk + 1) & 1], (uint32_t)((blk >> 1) & 1))) {
+        if (clock64() - t0c > kWaitCycles) {
+          atomicOr(status, STATUS_TIMEOUT);
+          aborted = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (has_next && tid < B) {
+      const T* rv = recv + (size_t)((blk + 1) & 1) * kCsMax * B + tid;
+      T q = T(0);
+      for (int r = 0; r < CS; ++r) q += rv[r * B];   // rank order: identical in every block
+      T kx = T(0);
+#pragma unroll
+      for (int hh = 0; hh < H; ++hh) kx += part4[hh * B + tid];
+      pv[tid] = q - et * kx - et * (T)Bb * Hs[tid];
+    }
+    if (tid == 0 && blk + 3 < nblk) mbar_arm(&mbar[(blk + 1) & 1], tx_per_block);   // that slot's next use
+  }
+  cp_async_wait<0>();
+  cluster.sync();   // no block leaves while remote stores to it could still be in flight
+  for (int c = tid; c < cwid; c += NT) {
+    const double v = average ? Ssum[c] / (double)m : (double)dl[c];
+    wnext[c0 + c] = (T)((double)wbar[c0 + c] + v);
+  }
+}
+
+template <typename S, typename T, int ZST, int QN, int NT>
+__global__ void __launch_bounds__(NT) epoch_chain_la_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                                             const uint32_t* __restrict__ idx, int64_t m,
+                                                             const T* __restrict__ Rt, const T* __restrict__ cvec,
+                                                             const T* __restrict__ Kt, const T* __restrict__ hn,
+                                                             double eta, const T* __restrict__ mu,
+                                                             const T* __restrict__ wbar, int average,
+                                                             T* __restrict__ wnext, int* status) {
+  chain_la_body<S, T, ZST, QN, NT>(Z, N, ld, d, idx, m, Rt, cvec, Kt, hn, eta, mu, wbar, average, wnext, status);
+}
+
+template <typename S, typename T, int ZST, int QN, int NT>
+__global__ void __launch_bounds__(NT) epoch_chain_la_batched_kernel(const ChainJob<S, T>* __restrict__ jobs,
+                                                                     int* status) {
+  const int cs = (int)cg::this_cluster().num_blocks();
+  const ChainJob<S, T> J = jobs[blockIdx.x / cs];
+  chain_la_body<S, T, ZST, QN, NT>(J.Z, J.N, J.ld, J.d, J.idx, J.m, J.Rt, J.cvec, J.Kt, J.hn, J.eta, J.mu, J.wbar,
+                                   J.average, J.wnext, status);
+}
+
 struct ChainPlan {
   int cs = 0, qn = 0, stages = 0, nt = 0;
   size_t shm = 0;
@@ -628,6 +992,99 @@ int launch_chain(rs_ctx* ctx, const ChainPlan& pl, const S* Z, int64_t N, int64_
   return RS_OK;
 }
 
+// look-ahead chain: shared memory, plan (ZST = 4 or 3 stages within 200 KB, 512 threads)
+template <typename S, typename T>
+size_t chain_la_smem(int qn, int zst, int nt) {
+  const int CW = 32 * qn;
+  const int TPC = std::max(1, nt / CW);
+  const int ZS = CW + chain_zpad(TPC, 32 / TPC, (int)sizeof(S));
+  return (size_t)zst * kBlk * ZS * sizeof(S) + 2 * (size_t)(2 * kBlk * kBlk + 2 * kBlk) * sizeof(T) +
+         2 * (size_t)kCsMax * kBlk * sizeof(T) + (size_t)CW * sizeof(double) + 2 * (size_t)CW * sizeof(T) +
+         (2 + nt / kBlk) * (size_t)kBlk * sizeof(T) + (size_t)zst * kBlk * sizeof(uint32_t) + 2 * sizeof(uint64_t) +
+         64;
+}
+
+template <typename S, typename T>
+ChainPlan plan_chain_la(int64_t d, int cs) {
+  ChainPlan p;
+  const int nt = 512;
+  if (cs < 1 || cs > kCsMax || (cs & (cs - 1))) return p;
+  const int64_t per = (d + cs - 1) / cs;
+  const int qn = per <= 64 ? 2 : (per <= 128 ? 4 : (per <= 256 ? 8 : 0));
+  if (!qn) return p;
+  for (int st = 4; st >= 3; --st) {
+    const size_t shm = chain_la_smem<S, T>(qn, st, nt);
+    if (shm <= 200 * 1024) {
+      p.nt = nt;
+      p.cs = cs;
+      p.qn = qn;
+      p.stages = st;
+      p.shm = shm;
+      return p;
+    }
+  }
+  return p;
+}
+
+// The look-ahead variant runs for float arithmetic unless RS_CHAIN_LOOKAHEAD=0.
+template <typename T>
+bool use_lookahead() {
+  if (sizeof(T) != 4) return false;
+  const char* env = std::getenv("RS_CHAIN_LOOKAHEAD");
+  return !(env && env[0] == '0');
+}
+
+template <typename K>
+int config_cluster_launch(rs_ctx* ctx, K kern, const ChainPlan& pl, int nclusters, cudaLaunchConfig_t& cfg,
+                          cudaLaunchAttribute* attr) {
+  RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
+  if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cfg = {};
+  cfg.gridDim = dim3((unsigned)(pl.cs * nclusters), 1, 1);
+  cfg.blockDim = dim3(pl.nt, 1, 1);
+  cfg.dynamicSmemBytes = pl.shm;
+  cfg.stream = ctx->stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return RS_EUNSUPPORTED;
+  }
+  return RS_OK;
+}
+
+template <typename S, typename T, int ZST, int QN>
+int launch_chain_la(rs_ctx* ctx, const ChainPlan& pl, const S* Z, int64_t N, int64_t ld, int64_t d,
+                    const uint32_t* idx, int64_t m, const T* Rt, const T* cv, const T* Kt, const T* hn, double eta,
+                    const T* mu, const T* wbar, int average, T* wnext) {
+  auto kern = epoch_chain_la_kernel<S, T, ZST, QN, 512>;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  const int rc = config_cluster_launch(ctx, kern, pl, 1, cfg, attr);
+  if (rc != RS_OK) return rc;
+  RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, Z, N, ld, d, idx, m, Rt, cv, Kt, hn, eta, mu, wbar, average, wnext,
+                                 ctx->d_status));
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+template <typename S, typename T, int ZST, int QN>
+int launch_chain_la_batched(rs_ctx* ctx, const ChainPlan& pl, const ChainJob<S, T>* jobs, int nj) {
+  auto kern = epoch_chain_la_batched_kernel<S, T, ZST, QN, 512>;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  const int rc = config_cluster_launch(ctx, kern, pl, nj, cfg, attr);
+  if (rc != RS_OK) return rc;
+  RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, jobs, ctx->d_status));
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
 }  // namespace
 
 template <typename S, typename T>
@@ -639,12 +1096,39 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
   T* Rt = static_cast<T*>(rs_scratch(ctx, SCR_R, (size_t)nblk * kBlk * kBlk * sizeof(T)));
   T* cv = static_cast<T*>(rs_scratch(ctx, SCR_C, (size_t)nblk * kBlk * sizeof(T)));
   if (!Rt || !cv) return RS_ENOMEM;
-  constexpr int RP = kBlk + 4, CH = 64, E = 16 / sizeof(T);
-  const size_t pshm = (size_t)(2 * RP * (CH + E) + RP * (RP + 1) + 2 * kBlk * (kBlk + 1)) * sizeof(T);
-  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
-  epoch_prep_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m, eta,
-                                                                      mu, Rt, cv);
-  RS_LAUNCH_CHECK(ctx);
+  const bool la = use_lookahead<T>();
+  if constexpr (sizeof(T) == 4) {
+    if (la) {
+      T* Kt = static_cast<T*>(rs_scratch(ctx, SCR_KT, (size_t)nblk * kBlk * kBlk * sizeof(T)));
+      T* hn = static_cast<T*>(rs_scratch(ctx, SCR_HN, (size_t)nblk * kBlk * sizeof(T)));
+      if (!Kt || !hn) return RS_ENOMEM;
+      constexpr size_t pshm = prep_smem_bytes<T, true>();
+      RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_la_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)pshm));
+      epoch_prep_la_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m,
+                                                                             eta, mu, Rt, cv, Kt, hn);
+      RS_LAUNCH_CHECK(ctx);
+      for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
+        const ChainPlan pl = plan_chain_la<S, T>(d, cs);
+        if (!pl.cs) continue;
+        int rc = RS_EUNSUPPORTED;
+#define RS_CHAIN_LA(ST, QN)                                                                                          \
+  if (pl.stages == ST && pl.qn == QN)                                                                                \
+    rc = launch_chain_la<S, T, ST, QN>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, Kt, hn, eta, mu, wbar, average, wnext);
+        RS_CHAIN_LA(4, 2) RS_CHAIN_LA(4, 4) RS_CHAIN_LA(4, 8) RS_CHAIN_LA(3, 2) RS_CHAIN_LA(3, 4) RS_CHAIN_LA(3, 8)
+#undef RS_CHAIN_LA
+        if (rc != RS_EUNSUPPORTED) return rc;
+      }
+      // no look-ahead layout fits: the plain chain below uses the same R and c
+    }
+  }
+  if (!la) {
+    constexpr size_t pshm = prep_smem_bytes<T, false>();
+    RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+    epoch_prep_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m, eta,
+                                                                        mu, Rt, cv);
+    RS_LAUNCH_CHECK(ctx);
+  }
   for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
     const ChainPlan pl = plan_chain<S, T>(d, cs);
     if (!pl.cs) continue;
@@ -709,11 +1193,17 @@ template <typename S, typename T>
 int epoch_prep_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, const int64_t* blk_off, int nj, int64_t total_blocks) {
   if (nj < 1 || total_blocks < 1) return RS_OK;
   if (total_blocks > 0x7FFFFFFF) return rs_fail(RS_EINVAL, "batched epoch: too many blocks of steps");
-  constexpr int RP = kBlk + 4, CH = 64, E = 16 / sizeof(T);
-  const size_t pshm = (size_t)(2 * RP * (CH + E) + RP * (RP + 1) + 2 * kBlk * (kBlk + 1)) * sizeof(T);
-  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_batched_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)pshm));
-  epoch_prep_batched_kernel<S, T><<<(unsigned)total_blocks, 256, pshm, ctx->stream>>>(jobs, blk_off, nj);
+  if (use_lookahead<T>()) {
+    constexpr size_t pshm = prep_smem_bytes<T, true>();
+    RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_batched_kernel<S, T, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+    epoch_prep_batched_kernel<S, T, true><<<(unsigned)total_blocks, 256, pshm, ctx->stream>>>(jobs, blk_off, nj);
+  } else {
+    constexpr size_t pshm = prep_smem_bytes<T, false>();
+    RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_batched_kernel<S, T, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+    epoch_prep_batched_kernel<S, T, false><<<(unsigned)total_blocks, 256, pshm, ctx->stream>>>(jobs, blk_off, nj);
+  }
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
 }
@@ -721,6 +1211,20 @@ int epoch_prep_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, const int64_t* b
 template <typename S, typename T>
 int epoch_chain_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, int nj, int64_t d) {
   if (nj < 1) return RS_OK;
+  if (use_lookahead<T>()) {
+    const int64_t maxc = sizeof(S) == 2 ? 256 : 128;
+    int cs = 1;
+    while (cs < kCsMax && (d + cs - 1) / cs > maxc) cs *= 2;
+    const ChainPlan pl = plan_chain_la<S, T>(d, cs);
+    int rc = RS_EUNSUPPORTED;
+    if (pl.cs) {
+#define RS_CHAIN_LA(ST, QN) \
+  if (pl.stages == ST && pl.qn == QN) rc = launch_chain_la_batched<S, T, ST, QN>(ctx, pl, jobs, nj);
+      RS_CHAIN_LA(4, 2) RS_CHAIN_LA(4, 4) RS_CHAIN_LA(4, 8) RS_CHAIN_LA(3, 2) RS_CHAIN_LA(3, 4) RS_CHAIN_LA(3, 8)
+#undef RS_CHAIN_LA
+    }
+    if (rc != RS_EUNSUPPORTED) return rc;
+  }
   for (int cs = choose_batch_cluster(d); cs >= 1; cs /= 2) {
     const ChainPlan pl = plan_chain<S, T>(d, cs);
     if (!pl.cs) continue;

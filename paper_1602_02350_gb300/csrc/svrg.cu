@@ -100,6 +100,140 @@ __global__ void __launch_bounds__(256) fullgrad_kernel(const T* __restrict__ Z, 
   }
 }
 
+// Bulk-copy staged variant of fullgrad_kernel (one CTA per SM): a producer warp streams tiles of
+// eight rows into a ring of shared-memory stages with cp.async.bulk, the copied bytes counted on
+// the stage's mbarrier; eight consumer warps take one row of each tile (vectorised shared-memory
+// reads, shuffle dot product, register accumulation) and release the stage.  Up to
+// kFgStages x 8 rows are in flight per SM whatever the register pressure.  Waits are bounded.
+constexpr int kFgStages = 6, kFgRows = 8;
+constexpr long long kFgWait = 2000000000LL;   // about a second
+
+template <typename T, int VPL>
+__global__ void __launch_bounds__(32 * (kFgRows + 1)) fullgrad_bulk_kernel(const T* __restrict__ Z, int64_t N,
+                                                                          int64_t n, int64_t d, int64_t ld,
+                                                                          const T* __restrict__ y, T lam,
+                                                                          const T* __restrict__ w,
+                                                                          T* __restrict__ part, int* status) {
+  using V = typename Vec<T>::type;
+  constexpr int E = Vec<T>::N;
+  extern __shared__ __align__(128) unsigned char fb_sh[];
+  __shared__ uint64_t full[kFgStages], empty[kFgStages];
+  const int64_t rs = ((d * (int64_t)sizeof(T) + 127) / 128) * 128 / (int64_t)sizeof(T);   // staged row stride
+  T* stage = reinterpret_cast<T*>(fb_sh);   // [kFgStages][kFgRows][rs]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (N + kFgRows - 1) / kFgRows;
+  // bulk copies move whole 16-byte units: the row is read up to the next 16-byte boundary, which
+  // lies inside its row stride (ld * sizeof(T) is a multiple of 16); staged elements >= d are ignored
+  const uint32_t row_bytes = (uint32_t)((d * (int64_t)sizeof(T) + 15) / 16 * 16);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFgStages; ++s) {
+      mbar_init_cta(&full[s], 1);
+      mbar_init_cta(&empty[s], kFgRows);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  T acc[VPL][E];
+#pragma unroll
+  for (int q = 0; q < VPL; ++q)
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[q][e] = T(0);
+  if (warp == kFgRows) {
+    if (lane == 0) {   // producer
+      int64_t it = 0;
+      int64_t last_use[kFgStages];
+      for (int s = 0; s < kFgStages; ++s) last_use[s] = -1;
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int s = (int)(it % kFgStages);
+        const int64_t u = it / kFgStages;
+        if (u >= 1 && !mbar_wait_bounded(&empty[s], (uint32_t)((u - 1) & 1), kFgWait)) {
+          atomicOr(status, STATUS_TIMEOUT);
+          break;
+        }
+        const int64_t r0 = t * kFgRows;
+        const int rows = (int)min64(kFgRows, N - r0);
+        mbar_expect_tx_cta(&full[s], (uint32_t)rows * row_bytes);
+        for (int r = 0; r < rows; ++r)
+          bulk_copy_g2s(stage + ((int64_t)s * kFgRows + r) * rs, Z + (r0 + r) * ld, row_bytes, &full[s]);
+        last_use[s] = u;
+      }
+      // every issued copy has landed before the stages are reused for the reduction below
+      for (int s = 0; s < kFgStages; ++s)
+        if (last_use[s] >= 0 && !mbar_wait_bounded(&full[s], (uint32_t)(last_use[s] & 1), kFgWait))
+          atomicOr(status, STATUS_TIMEOUT);
+    }
+  } else {   // consumers
+    T wr[VPL][E];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q)
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t c = (int64_t)(lane + 32 * q) * E + e;
+        wr[q][e] = c < d ? w[c] : T(0);
+      }
+    const T inv_n = T(1) / (T)n;
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int s = (int)(it % kFgStages);
+      const int64_t u = it / kFgStages;
+      const int64_t i = t * kFgRows + warp;
+      const T yi = (i < n) ? y[i] : T(0);
+      if (!mbar_wait_bounded(&full[s], (uint32_t)(u & 1), kFgWait)) {
+        if (lane == 0) atomicOr(status, STATUS_TIMEOUT);
+        break;
+      }
+      if (i < N) {
+        const T* row = stage + ((int64_t)s * kFgRows + warp) * rs;
+        T z[VPL][E];
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) {
+          const int64_t c0 = (int64_t)(lane + 32 * q) * E;
+          if (c0 < d) {
+            vec_to_arr(*reinterpret_cast<const V*>(row + c0), z[q]);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+              if (c0 + e >= d) z[q][e] = T(0);
+          } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) z[q][e] = T(0);
+          }
+        }
+        T dot = T(0);
+#pragma unroll
+        for (int q = 0; q < VPL; ++q)
+#pragma unroll
+          for (int e = 0; e < E; ++e) dot = fma(z[q][e], wr[q][e], dot);
+        dot = warp_sum(dot);
+        const T r = i < n ? (dot - yi) * inv_n : lam * dot;
+#pragma unroll
+        for (int q = 0; q < VPL; ++q)
+#pragma unroll
+          for (int e = 0; e < E; ++e) acc[q][e] = fma(r, z[q][e], acc[q][e]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&empty[s]);
+    }
+  }
+  __syncthreads();
+  // per-warp sums in the (now idle) stage memory, then a fixed-order sum over the warps
+  T* sh = stage;   // [kFgRows][d]
+  if (warp < kFgRows) {
+#pragma unroll
+    for (int q = 0; q < VPL; ++q)
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t c = (int64_t)(lane + 32 * q) * E + e;
+        if (c < d) sh[warp * d + c] = acc[q][e];
+      }
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
+    T s2 = T(0);
+    for (int w2 = 0; w2 < kFgRows; ++w2) s2 += sh[w2 * d + c];
+    part[(int64_t)blockIdx.x * d + c] = s2;
+  }
+}
+
 // mu[c] = sum over the per-block partials, 32 columns per thread block: eight interleaved
 // partial sums per column, then a fixed-order sum of the eight (deterministic).
 template <typename T>
@@ -253,15 +387,19 @@ static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t 
   const int threads = 256;
   if constexpr (std::is_same<S, T>::value) if (vpl <= 8) {
     const T* Zd = static_cast<const T*>(Z->data);
-    const int blocks = ctx->num_sms * 2;
+    const int blocks = ctx->num_sms;
     T* part = static_cast<T*>(rs_scratch(ctx, SCR_PART2, (size_t)blocks * d * sizeof(T)));
     if (!part) return RS_ENOMEM;
-    const size_t shm = (size_t)(threads / 32) * d * sizeof(T);
+    const int64_t rs_bytes = (d * (int64_t)sizeof(T) + 127) / 128 * 128;
+    const size_t shm = std::max((size_t)kFgStages * kFgRows * rs_bytes, (size_t)kFgRows * d * sizeof(T));
+    (void)threads;
 #define RS_FG(VV)                                                                                              \
   do {                                                                                                         \
-    RS_CUDA_TRY(cudaFuncSetAttribute(fullgrad_kernel<T, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+    RS_CUDA_TRY(cudaFuncSetAttribute(fullgrad_bulk_kernel<T, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      (int)shm));                                                               \
-    fullgrad_kernel<T, VV><<<blocks, threads, shm, ctx->stream>>>(Zd, N, n, d, Z->ld, y, (T)lam, w, part);     \
+    fullgrad_bulk_kernel<T, VV><<<blocks, 32 * (kFgRows + 1), shm, ctx->stream>>>(Zd, N, n, d, Z->ld, y,       \
+                                                                                   (T)lam, w, part,            \
+                                                                                   ctx->d_status);             \
   } while (0)
     if (vpl <= 1) RS_FG(1);
     else if (vpl <= 2) RS_FG(2);

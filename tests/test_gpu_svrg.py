@@ -77,3 +77,25 @@ def test_epoch_rejects_bad_arguments(rsctx):
                                               rs._lib._ptr(w), 1, rs._lib._ptr(w)))
     with pytest.raises(rs.RsError):
         rs.rs_full_gradient(rsctx, Z, y, 25, 1e-3, w)     # n + d != rows
+
+
+@pytest.mark.parametrize("lookahead", ["0", "1"])
+@pytest.mark.parametrize("n,d,m", [(300, 64, 65), (2000, 256, 1000), (8000, 1024, 4160), (3000, 520, 129)])
+def test_epoch_both_chain_variants(rsctx, monkeypatch, lookahead, n, d, m):
+    """The plain chain (exchange on the critical path) and the look-ahead chain (next block's dots
+    exchanged while the current block updates) both follow the oracle's recursion."""
+    monkeypatch.setenv("RS_CHAIN_LOOKAHEAD", lookahead)
+    lam = 1e-3
+    Z, Zd, y, yz, g = _components(n, d, 11 * n + d, torch.float32, lam)
+    N = n + d
+    idx = synth.random_indices(N, m, m + 3 * d)
+    inq_t = torch.from_numpy(synth.random_positive(m, m + 1, 0.5, 1.5)).float()
+    beta = precond.smoothness(Zd, g)
+    eta = 0.3 / beta.mean()
+    wb_t = torch.from_numpy(synth.random_vector(d, 7, scale=0.1)).float()
+    mu_t = torch.from_numpy(synth.random_vector(d, 8, scale=1e-3)).float()
+    got = rs.rs_svrg_epoch(rsctx, Z, n, lam, torch.from_numpy(idx.astype(np.int32)).cuda(), inq_t.cuda(), eta,
+                           wb_t.cuda(), mu_t.cuda(), True).cpu().double().numpy()
+    ref = svrg.epoch_scaled(Zd, yz, g, wb_t.double().numpy(), idx, inq_t.double().numpy(), eta, True,
+                            v_bar=mu_t.double().numpy())
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-4
