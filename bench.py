@@ -138,6 +138,9 @@ def run_rs(args):
                         m=2 * n, eta_mult=1.0)
             rs.rs_solve_proposed(ctx, X, y, lam, args.chosen_epochs, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
                                  norm=norm, kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16)
+        # the same data stored in bfloat16: sketch and components through the tensor-core product
+        Xb = X.to(torch.bfloat16)
+        rs.rs_solve(ctx, Xb, y, k, lam, 1, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0, refine=True)
         torch.cuda.synchronize()
         ctx.close()
         return
@@ -272,19 +275,26 @@ def run_rs(args):
     ctx.close()
 
 
+def _normal_equations(X, y):
+    """X^T X and X^T y accumulated in double on the device in row chunks (measurement only)."""
+    n, d = X.shape
+    G = torch.zeros(d, d, dtype=torch.float64, device=X.device)
+    b = torch.zeros(d, dtype=torch.float64, device=X.device)
+    for r0 in range(0, n, 16384):
+        Xb = X[r0:r0 + 16384].double()
+        G += Xb.T @ Xb
+        b += Xb.T @ y[r0:r0 + 16384].double()
+        del Xb
+    return G, b
+
+
 class _Reference:
     """w* of Eq. (1) from the normal equations accumulated in double on the device in row chunks
     (measurement only, untimed), and relative suboptimality of iterates through e^T H e / 2."""
 
-    def __init__(self, X, y, lam):
+    def __init__(self, X, y, lam, normal=None):
         n, d = X.shape
-        G = torch.zeros(d, d, dtype=torch.float64, device=X.device)
-        b = torch.zeros(d, dtype=torch.float64, device=X.device)
-        for r0 in range(0, n, 16384):
-            Xb = X[r0:r0 + 16384].double()
-            G += Xb.T @ Xb
-            b += Xb.T @ y[r0:r0 + 16384].double()
-            del Xb
+        G, b = normal if normal is not None else _normal_equations(X, y)
         self.H = G / n + lam * torch.eye(d, dtype=torch.float64, device=X.device)
         self.w = torch.from_numpy(np.linalg.solve(self.H.cpu().numpy(), (b / n).cpu().numpy())).to(X.device)
         r = torch.zeros((), dtype=torch.float64, device=X.device)
@@ -369,6 +379,63 @@ def run_precision(args):
     ctx.close()
 
 
+def run_batched(args):
+    """Batching workload (one GPU): 64 BF16 problems (n uniform in [8192, 262144], d in {256, 512,
+    1024, 2048}, spectrum j^-alpha with alpha ~ U[1, 2.5]), each at the 8 lambda 10^(-3-4j/7) with
+    one sketch of rank d/16 per problem, solved in one rs_solve_batched call (epochs 2..S in one
+    CUDA graph), eta = 1.5 / beta^, m = n / 4.  Reports the batch's time, aggregate inner steps/s
+    and how many of the 512 chains reached 1e-6 (against FP64 normal-equation solutions)."""
+    import paper_1602_02350_gb300 as rs
+    from paper_1602_02350_gb300 import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = rs.Context(local, stream)
+    rng = np.random.default_rng(4004)
+    nprob = args.batch_problems
+    lams = [10.0 ** (-3 - 4 * j / 7) for j in range(8)]
+    probs, specs = [], []
+    for p in range(nprob):
+        n = int(rng.integers(8192 // 64, 262144 // 64 + 1)) * 64
+        d = int(rng.choice([256, 512, 1024, 2048]))
+        alpha = float(rng.uniform(1.0, 2.5))
+        X, y, _ = synth.problem(n, d, np.arange(1, d + 1, dtype=np.float64) ** -alpha, 0.05, 5000 + p,
+                                device="cuda", dtype=torch.bfloat16)
+        probs.append((X, y.float().contiguous(), 0))
+        specs.append((n, d, alpha))
+    chains = [dict(problem=p, lam=lam, eta_mult=1.5, m=specs[p][0] // 4, seed=p) for p in range(nprob) for lam in lams]
+    S = args.batch_epochs
+    steps = sum(c["m"] for c in chains) * S
+    rs.rs_solve_batched(ctx, probs, chains[:8], 2, sketch_seed=7)          # warm-up of the code paths
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ws, snaps, ems = rs.rs_solve_batched(ctx, probs, chains, S, sketch_seed=7, snapshots=True)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    reached, first = 0, []
+    for p in range(nprob):
+        X, y, _ = probs[p]
+        ne = _normal_equations(X, y)
+        ref_p = [_Reference(X, y, lam, ne) for lam in lams]
+        for j in range(8):
+            rel = ref_p[j].rel(snaps[p * 8 + j])
+            hit = [i for i, r in enumerate(rel) if r <= TARGET]
+            if hit:
+                reached += 1
+                first.append(hit[0] + 1)
+        del ref_p
+    out = {"metric": "batched solve time (64 problems x 8 lambda, one graph)", "value": secs, "unit": "s",
+           "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False, "dtype": "bf16+f32",
+           "data": "synthetic",
+           "config": {"workload": f"{nprob} bf16 problems x 8 lambda, k=d/16, eta=1.5/beta^, m=n/4, {S} epochs",
+                      "chains": len(chains), "inner_steps": steps, "inner_steps_per_s": steps / secs,
+                      "epoch_ms_cumulative": ems, "chains_reaching_1e-6": reached,
+                      "median_epochs_to_1e-6": float(np.median(first)) if first else None,
+                      "data_bytes": int(sum(X.numel() * 2 for X, _, _ in probs))}}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def cpu_baseline_sample(budget_s=20.0, epochs=None):
     """Time the FP64 oracle on host cores on a bounded sample of the workload and extrapolate
     to one solve: (sketch + precondition) once, plus epochs x (full gradient + m steps)."""
@@ -439,8 +506,11 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run two solves of each form with the given epoch counts and exit (for ncu launch lists)")
     ap.add_argument("--plain-epochs", type=int, default=4)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bf16_n1048576_d4096"],
-                    help="bf16_n1048576_d4096: the precision workload (its own JSON line)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bf16_n1048576_d4096", "batched"],
+                    help="bf16_n1048576_d4096: the precision workload; batched: 64 problems x 8 lambda "
+                         "(each its own JSON line)")
+    ap.add_argument("--batch-problems", type=int, default=64)
+    ap.add_argument("--batch-epochs", type=int, default=20)
     ap.add_argument("--precision-epochs", type=int, default=30)
     ap.add_argument("--chosen-epochs", type=int, default=16)
     args = ap.parse_args()
@@ -448,6 +518,8 @@ def main():
         run_reference(args)
     elif args.workload == "bf16_n1048576_d4096":
         run_precision(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_rs(args)
 

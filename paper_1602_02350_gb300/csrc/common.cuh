@@ -24,7 +24,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_COUNT
 };
 
 struct rs_ctx {
@@ -217,6 +217,12 @@ int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, 
                 int64_t ldb, double alpha, double* G);
 
 int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W);
+
+// tcgen05 product for bfloat16 data (umma.cu): C = X W diag(col_scale), X M x K bfloat16 rows, W K x N
+// float (N <= 256), C float; RS_EUNSUPPORTED when the tensor path cannot run (caller falls back).
+bool umma_enabled();
+int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, const float* col_scale, float* C,
+                 int64_t ldc);
 
 // ------------------------------------------------ batched inner loops (many chains per launch)
 

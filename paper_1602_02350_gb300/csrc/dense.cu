@@ -2,6 +2,8 @@
 // CUDA-core GEMM and split-K Gram kernels, Cholesky-QR, cyclic Jacobi, Rayleigh-Ritz,
 // the data transform Z = [X M; M], smoothness constants, the output map w = M w~ and
 // the double-precision objective of Eq. (1).
+#include <type_traits>
+
 #include "common.cuh"
 
 int countsketch_dispatch(rs_ctx* ctx, const rs_matrix* X, uint64_t seed, int64_t s, void* SX, int64_t ld_sx,
@@ -205,8 +207,11 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
                               double* evals, double* Wout) {
   extern __shared__ unsigned char jsh[];
   const int K = (k + 1) & ~1;   // even number of players; index k is a dummy when k is odd
+  // rows padded to k + 1 elements: the column updates (consecutive threads on consecutive rows)
+  // then fall on distinct shared-memory banks
+  const int LD = k + 1;
   TW* A = SMEM ? reinterpret_cast<TW*>(jsh) : Ag;
-  TW* W = SMEM ? reinterpret_cast<TW*>(jsh) + (size_t)k * k : Wg;
+  TW* W = SMEM ? reinterpret_cast<TW*>(jsh) + (size_t)k * LD : Wg;
   __shared__ int pp[128], qq[128];
   __shared__ TW cc[128], ss[128];
   __shared__ double red[32];
@@ -214,8 +219,9 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
   const int tid = threadIdx.x, nt = blockDim.x;
   double fro = 0.0;
   for (int e = tid; e < k * k; e += nt) {
-    A[e] = (TW)G[e];
-    W[e] = (e / k == e % k) ? TW(1) : TW(0);
+    const int r = e / k, c = e % k;
+    A[r * LD + c] = (TW)G[e];
+    W[r * LD + c] = (r == c) ? TW(1) : TW(0);
     fro = fma(G[e], G[e], fro);
   }
   fro = warp_sum(fro);
@@ -241,8 +247,8 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
         if (p > q) { int t = p; p = q; q = t; }
         TW c = TW(1), s = TW(0);
         if (q < k) {
-          const TW apq = A[p * k + q];
-          const TW app = A[p * k + p], aqq = A[q * k + q];
+          const TW apq = A[p * LD + q];
+          const TW app = A[p * LD + p], aqq = A[q * LD + q];
           const TW thr = fmax(rel * sqrt(fabs(app * aqq)), abs_floor);
           if (fabs(apq) > thr) {
             const TW theta = (aqq - app) / (TW(2) * apq);
@@ -262,9 +268,9 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
           const TW c = cc[i], s = ss[i];
           if (q >= k || s == TW(0)) continue;
           const int j = jt;
-          const TW ap = A[p * k + j], aq = A[q * k + j];
-          A[p * k + j] = c * ap - s * aq;
-          A[q * k + j] = s * ap + c * aq;
+          const TW ap = A[p * LD + j], aq = A[q * LD + j];
+          A[p * LD + j] = c * ap - s * aq;
+          A[q * LD + j] = s * ap + c * aq;
         }
       __syncthreads();
       // columns: A <- A J, W <- W J   (thread owns row j = jt)
@@ -274,12 +280,12 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
         const int p = pp[i], q = qq[i];
         const TW c = cc[i], s = ss[i];
         if (q >= k || s == TW(0)) continue;
-        const TW ap = A[j * k + p], aq = A[j * k + q];
-        A[j * k + p] = c * ap - s * aq;
-        A[j * k + q] = s * ap + c * aq;
-        const TW wp = W[j * k + p], wq = W[j * k + q];
-        W[j * k + p] = c * wp - s * wq;
-        W[j * k + q] = s * wp + c * wq;
+        const TW ap = A[j * LD + p], aq = A[j * LD + q];
+        A[j * LD + p] = c * ap - s * aq;
+        A[j * LD + q] = s * ap + c * aq;
+        const TW wp = W[j * LD + p], wq = W[j * LD + q];
+        W[j * LD + p] = c * wp - s * wq;
+        W[j * LD + q] = s * wp + c * wq;
       }
       __syncthreads();
     }
@@ -289,14 +295,14 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
   }
   // sort descending (stable in index) and write out
   for (int i = tid; i < k; i += nt) {
-    const TW ev = A[i * k + i];
+    const TW ev = A[i * LD + i];
     int rank = 0;
     for (int j = 0; j < k; ++j) {
-      const TW ej = A[j * k + j];
+      const TW ej = A[j * LD + j];
       rank += (ej > ev) || (ej == ev && j < i);
     }
     evals[rank] = (double)ev;
-    for (int r = 0; r < k; ++r) Wout[r * k + rank] = (double)W[r * k + i];
+    for (int r = 0; r < k; ++r) Wout[r * k + rank] = (double)W[r * LD + i];
   }
 }
 
@@ -461,17 +467,28 @@ __global__ void objective_finish_kernel(const double* part, int np, int64_t n, i
   }
 }
 
-// ||X||_F^2 accumulated in double: per-block partials, summed in block order by trace_finish
+// ||X||_F^2: each lane sums its part of a row in float (a few dozen terms), the row and block sums
+// are accumulated in double; per-block partials are summed in block order by trace_finish
 template <typename TS>
 __global__ void sumsq_kernel(const TS* X, int64_t n, int64_t d, int64_t ld, double* part) {
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double a = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw)
-    for (int64_t c = lane; c < d; c += 32) {
-      const double x = cvt<double>(X[i * ld + c]);
-      a = fma(x, x, a);
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw) {
+    if constexpr (sizeof(TS) == 8) {
+      for (int64_t c = lane; c < d; c += 32) {
+        const double x = cvt<double>(X[i * ld + c]);
+        a = fma(x, x, a);
+      }
+    } else {
+      float r = 0.0f;
+      for (int64_t c = lane; c < d; c += 32) {
+        const float x = cvt<float>(X[i * ld + c]);
+        r = fmaf(x, x, r);
+      }
+      a += (double)r;
     }
+  }
   a = warp_sum(a);
   if (lane == 0) sh[warp] = a;
   __syncthreads();
@@ -576,7 +593,7 @@ static int to_T(rs_ctx* ctx, const double* in, int64_t count, T* out) {
 int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W) {
   if (k < 1 || k > 256) return rs_fail(RS_EINVAL, "sym_eig: k = %lld outside [1, 256]", (long long)k);
   const size_t es = prec == RS_F64 ? 8 : 4;
-  const size_t bytes = 2 * (size_t)k * k * es;
+  const size_t bytes = 2 * (size_t)k * (k + 1) * es;   // rows padded to k + 1
   const bool smem = bytes <= 200 * 1024;
   void* g = nullptr;
   if (!smem) {
@@ -593,7 +610,7 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
       jacobi_kernel<double, true><<<1, threads, shm, ctx->stream>>>(G, (int)k, nullptr, nullptr, 1e-15, 8.0, 30,
                                                                     evals, W);
     } else {
-      jacobi_kernel<double, false><<<1, threads, 0, ctx->stream>>>(G, (int)k, Ag, Ag + k * k, 1e-15, 8.0, 30, evals,
+      jacobi_kernel<double, false><<<1, threads, 0, ctx->stream>>>(G, (int)k, Ag, Ag + k * (k + 1), 1e-15, 8.0, 30, evals,
                                                                    W);
     }
   } else {
@@ -610,7 +627,7 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
       jacobi_kernel<float, true><<<1, threads, shm, ctx->stream>>>(G, (int)k, nullptr, nullptr, 1e-6, 8.0, 30, lam0,
                                                                    Wt);
     } else {
-      jacobi_kernel<float, false><<<1, threads, 0, ctx->stream>>>(G, (int)k, Ag, Ag + k * k, 1e-6, 8.0, 30, lam0, Wt);
+      jacobi_kernel<float, false><<<1, threads, 0, ctx->stream>>>(G, (int)k, Ag, Ag + k * (k + 1), 1e-6, 8.0, 30, lam0, Wt);
     }
     RS_LAUNCH_CHECK(ctx);
     rayleigh_kernel<<<(unsigned)k, 128, 0, ctx->stream>>>(G, (int)k, Wt, lam1);
@@ -689,9 +706,15 @@ static int ritz_t(rs_ctx* ctx, const rs_matrix* X, const T* Q, int64_t kq, int64
   double* Wd = static_cast<double*>(rs_scratch(ctx, SCR_W, kq * kq * sizeof(double)));
   T* Wt = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, kq * kq * sizeof(T)));
   if (!B || !G || !ev || !Wd || !Wt) return RS_ENOMEM;
-  // B = X Q (n x kq), G = B^T B / n
-  RS_TRY(launch_gemm<T, S, T>(ctx, n, kq, d, 1.0, static_cast<const S*>(X->data), X->ld, 1, Q, kq, 1, 0.0, nullptr, 0, B,
-                        kq, nullptr));
+  // B = X Q (n x kq), G = B^T B / n   (bfloat16 data: X Q on the tensor cores)
+  int rc_b = RS_EUNSUPPORTED;
+  if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<T, float>::value)
+    if (umma_enabled()) rc_b = umma_gemm_xw(ctx, X, Q, kq, nullptr, B, kq);
+  if (rc_b == RS_EUNSUPPORTED)
+    RS_TRY(launch_gemm<T, S, T>(ctx, n, kq, d, 1.0, static_cast<const S*>(X->data), X->ld, 1, Q, kq, 1, 0.0, nullptr, 0,
+                                B, kq, nullptr));
+  else if (rc_b != RS_OK)
+    return rc_b;
   RS_TRY(launch_gram<T>(ctx, n, kq, kq, B, kq, B, kq, 1.0 / (double)n, G));
   RS_TRY(run_sym_eig(ctx, G, kq, sizeof(T) == 8 ? RS_F64 : RS_F32, ev, Wd));
   RS_TRY(to_T<T>(ctx, Wd, kq * kq, Wt));
@@ -767,8 +790,14 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
   adiag_kernel<T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(sigma2, (int)k, lam, a);
   RS_LAUNCH_CHECK(ctx);
   const S* Xd = static_cast<const S*>(X->data);
-  // P = X V diag(a);  Z[0:n] = X - P V^T
-  RS_TRY(launch_gemm<T, S, T>(ctx, n, k, d, 1.0, Xd, X->ld, 1, V, k, 1, 0.0, nullptr, 0, P, k, a));
+  // P = X V diag(a);  Z[0:n] = X - P V^T   (bfloat16 data: X V on the tensor cores)
+  int rc_p = RS_EUNSUPPORTED;
+  if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<T, float>::value)
+    if (umma_enabled()) rc_p = umma_gemm_xw(ctx, X, V, k, a, P, k);
+  if (rc_p == RS_EUNSUPPORTED)
+    RS_TRY(launch_gemm<T, S, T>(ctx, n, k, d, 1.0, Xd, X->ld, 1, V, k, 1, 0.0, nullptr, 0, P, k, a));
+  else if (rc_p != RS_OK)
+    return rc_p;
   RS_TRY(launch_gemm<T, T, SZ, S>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
   // Z[n:n+d] = I - V diag(a) V^T   (the rows b_j = M e_j)
   scale_cols_kernel<T><<<blocks_for(ctx, d * k), 256, 0, ctx->stream>>>(V, d, (int)k, a, Va);

@@ -1026,12 +1026,14 @@ ChainPlan plan_chain_la(int64_t d, int cs) {
   return p;
 }
 
-// The look-ahead variant runs for float arithmetic unless RS_CHAIN_LOOKAHEAD=0.
+// The look-ahead variant (float arithmetic only) runs when RS_CHAIN_LOOKAHEAD=1.  Measured on
+// GB300 it is slower than the plain chain (the cross Gram matrices double the preparation work and
+// the second matrix-vector product lengthens each block), so it is off by default.
 template <typename T>
 bool use_lookahead() {
   if (sizeof(T) != 4) return false;
   const char* env = std::getenv("RS_CHAIN_LOOKAHEAD");
-  return !(env && env[0] == '0');
+  return env && env[0] == '1';
 }
 
 template <typename K>

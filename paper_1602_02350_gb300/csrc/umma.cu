@@ -1,0 +1,264 @@
+// Tensor-core (tcgen05) product of bfloat16 data with a float matrix: C = X W diag(s), X (M x K,
+// bfloat16, row-major), W (K x N, float), C (M x N, float).  This is the X V contraction of the
+// preconditioner (Eq. (11)) and the X Q product of the Rayleigh-Ritz step (Alg. 2) for bfloat16
+// data.  W is split into three bfloat16 parts, W = W0 + W1 + W2 (W1 = bf16(W - W0), ...), so the
+// three accumulating products reproduce the float W to about 2^-24 relative; X is exact in
+// bfloat16.  Accumulation is FP32 in tensor memory.
+//
+// One CTA per 128 x 128 output tile, 128 threads: warp 0 allocates 128 tensor-memory columns and
+// (lane 0) produces: TMA (cp.async.bulk.tensor, 128-byte swizzle) loads of the 128 x 64 X tile and
+// the three 128 x 64 W-part tiles into a 3-stage ring whose full/empty mbarriers count the copied
+// bytes and the completed MMAs; warp 1 lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16, kind
+// f16 with bfloat16 operands) and commits each stage back to its empty barrier; after the last
+// stage all four warps read their 32 accumulator lanes with tcgen05.ld, scale the columns and
+// store.  Every wait is bounded: on timeout the status word is flagged, no further copies or MMAs
+// are issued, and the CTA still waits (bounded) for what it issued before freeing tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int UM = 128, UN = 128, UK = 64, UST = 3, NSPLIT = 3;
+constexpr uint32_t A_BYTES = UM * UK * 2;               // 16 KB
+constexpr uint32_t B_BYTES = UN * UK * 2;               // 16 KB per W part
+constexpr uint32_t STAGE_BYTES = A_BYTES + NSPLIT * B_BYTES;
+constexpr long long kUmmaWait = 2000000000LL;
+
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  // K-major, 128-byte swizzle: start >> 4, leading offset (unused, 16 B), stride 1024 B between
+  // 8-row groups, descriptor version 1, layout SWIZZLE_128B (2)
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// instruction descriptor: f32 accumulate, bf16 A and B, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          cta_smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(cta_smem_addr(bar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) umma_xw_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                         const __grid_constant__ CUtensorMap tmW, int64_t M, int K,
+                                                         int N, int kp, const float* __restrict__ col_scale,
+                                                         float* __restrict__ C, int64_t ldc, int* status) {
+  extern __shared__ unsigned char um_raw[];
+  // the swizzled tiles need 1024-byte alignment
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(um_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full[UST], empty[UST], done;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * UM;
+  const int n0 = blockIdx.y * UN;
+  const int KB = (K + UK - 1) / UK;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < UST; ++s) {
+      mbar_init_cta(&full[s], 1);
+      mbar_init_cta(&empty[s], 1);
+    }
+    mbar_init_cta(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(cta_smem_addr(&tmem_holder)),
+                 "r"(UN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+
+  if (threadIdx.x == 0) {   // producer
+    int issued_last[UST];
+    for (int s = 0; s < UST; ++s) issued_last[s] = -1;
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % UST, u = kb / UST;
+      if (u >= 1 && !mbar_wait_bounded(&empty[s], (uint32_t)((u - 1) & 1), kUmmaWait)) {
+        atomicOr(status, STATUS_TIMEOUT);
+        abort_flag = 1;
+        break;
+      }
+      if (abort_flag) break;
+      unsigned char* st = base + (size_t)s * STAGE_BYTES;
+      mbar_expect_tx_cta(&full[s], STAGE_BYTES);
+      tma_load_2d(st, &tmX, kb * UK, (int)m0, &full[s]);
+      for (int p = 0; p < NSPLIT; ++p) tma_load_2d(st + A_BYTES + p * B_BYTES, &tmW, kb * UK, p * kp + n0, &full[s]);
+      issued_last[s] = u;
+    }
+    for (int s = 0; s < UST; ++s)   // every issued copy lands before the CTA moves on
+      if (issued_last[s] >= 0 && !mbar_wait_bounded(&full[s], (uint32_t)(issued_last[s] & 1), kUmmaWait))
+        atomicOr(status, STATUS_TIMEOUT);
+  } else if (threadIdx.x == 32) {   // MMA issuer
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % UST, u = kb / UST;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)(u & 1), kUmmaWait)) {
+        atomicOr(status, STATUS_TIMEOUT);
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sa = cta_smem_addr(base + (size_t)s * STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < UK / 16; ++kk) {
+        const uint64_t da = smem_desc_sw128(sa + kk * 32);
+#pragma unroll
+        for (int p = 0; p < NSPLIT; ++p) {
+          const uint64_t db = smem_desc_sw128(sa + A_BYTES + p * B_BYTES + kk * 32);
+          const uint32_t accum = (kb | kk | p) != 0;
+          asm volatile(
+              "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(kIdesc), "r"(accum)
+              : "memory");
+        }
+      }
+      // the stage is free once these MMAs have read it
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       cta_smem_addr(&empty[s]))
+                   : "memory");
+    }
+    // completion of every MMA issued above
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     cta_smem_addr(&done))
+                 : "memory");
+  }
+  __syncwarp();
+  // epilogue: warp w owns accumulator lanes 32w..32w+31 (output rows m0 + 32w + lane)
+  bool ok = mbar_wait_bounded(&done, 0u, kUmmaWait);
+  if (!ok && lane == 0) atomicOr(status, STATUS_TIMEOUT);
+  ok = __all_sync(0xffffffffu, ok && !abort_flag);   // tcgen05.ld is warp-collective
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const int64_t row = m0 + warp * 32 + lane;
+  if (ok) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < UN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < N) C[row * ldc + col] = __uint_as_float(v[j]) * (col_scale ? col_scale[col] : 1.0f);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(UN) : "memory");
+  }
+}
+
+// W (K x N float, row-major) -> parts (NSPLIT x kp x ldp bfloat16): part p row j = column j of
+// W_p, W = W0 + W1 + W2 with W_{p} = bf16(W - W_0 - .. - W_{p-1}); rows j >= N are zero
+__global__ void split_transpose_kernel(const float* __restrict__ W, int K, int N, int kp, int ldp,
+                                       __nv_bfloat16* __restrict__ out) {
+  const int64_t total = (int64_t)kp * ldp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / ldp), c = (int)(e % ldp);
+    float r = (j < N && c < K) ? W[(int64_t)c * N + j] : 0.0f;
+#pragma unroll
+    for (int p = 0; p < NSPLIT; ++p) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(r);
+      out[(int64_t)p * total + e] = h;
+      r -= __bfloat162float(h);
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+int make_map(CUtensorMap* map, const void* ptr, int64_t inner, int64_t rows, int64_t ld_elems, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return rs_fail(RS_EUNSUPPORTED, "tensor-map encoder unavailable");
+  cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)ld_elems * 2};
+  cuuint32_t box[2] = {(cuuint32_t)UK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), gdim, gstride, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return rs_fail(RS_EUNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return RS_OK;
+}
+
+}  // namespace
+
+// The tensor-core path is on unless RS_UMMA=0.
+bool umma_enabled() {
+  const char* env = std::getenv("RS_UMMA");
+  return !(env && env[0] == '0');
+}
+
+// C (M x N, float, ldc) = X (bfloat16 rows, M x K) W (K x N, float) diag(col_scale); N <= 256.
+// RS_EUNSUPPORTED if the tensor-map encoder is unavailable (the caller then uses CUDA cores).
+int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, const float* col_scale, float* C,
+                 int64_t ldc) {
+  const int64_t M = X->n, K = X->d;
+  if (N < 1 || N > 256 || K < 1) return RS_EUNSUPPORTED;
+  if (!encode_fn()) return RS_EUNSUPPORTED;
+  const int kp = (int)((N + UN - 1) / UN * UN);
+  const int ldp = (int)((K + 7) / 8 * 8);        // 16-byte rows
+  __nv_bfloat16* parts =
+      static_cast<__nv_bfloat16*>(rs_scratch(ctx, SCR_UMMA, (size_t)NSPLIT * kp * ldp * sizeof(__nv_bfloat16)));
+  if (!parts) return RS_ENOMEM;
+  split_transpose_kernel<<<(unsigned)std::min<int64_t>(((int64_t)kp * ldp + 255) / 256, ctx->num_sms * 8), 256, 0,
+                           ctx->stream>>>(W, (int)K, (int)N, kp, ldp, parts);
+  RS_LAUNCH_CHECK(ctx);
+  CUtensorMap mx, mw;
+  RS_TRY(make_map(&mx, X->data, K, M, X->ld, UM));
+  RS_TRY(make_map(&mw, parts, K, (int64_t)NSPLIT * kp, ldp, UN));
+  const size_t shm = (size_t)UST * STAGE_BYTES + 1024;
+  RS_CUDA_TRY(cudaFuncSetAttribute(umma_xw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  dim3 grid((unsigned)((M + UM - 1) / UM), (unsigned)(kp / UN));
+  if (grid.x > 0x7FFFFFFF) return rs_fail(RS_EINVAL, "umma gemm: too many row tiles");
+  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  umma_xw_kernel<<<grid, 128, shm, ctx->stream>>>(mx, mw, M, (int)K, (int)N, kp, col_scale, C, ldc, ctx->d_status);
+  RS_LAUNCH_CHECK(ctx);
+  int st = 0;
+  RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (st & STATUS_TIMEOUT) return rs_fail(RS_ETIMEOUT, "tensor-core product: a bounded wait gave up");
+  return RS_OK;
+}

@@ -161,3 +161,21 @@ def test_bf16_components_with_float_refinement_reach_float_accuracy(rsctx):
                                refine=True, snapshots=True)
     rel = [ridge.rel_suboptimality(Xd, yn, lam, s.double().cpu().numpy(), ws) for s in info["snapshots"]]
     assert rel[-1] <= 1e-8, rel
+
+
+@pytest.mark.parametrize("umma", ["1", "0"])
+@pytest.mark.parametrize("n,d,k", [(1, 8, 1), (300, 72, 5), (4097, 256, 16), (20000, 1024, 130)])
+def test_bf16_x_times_v_both_paths(rsctx, monkeypatch, umma, n, d, k):
+    """X V for bfloat16 data on the tensor cores (tcgen05, V split into three bfloat16 parts) and
+    on CUDA cores give the oracle's components to the same tolerance."""
+    monkeypatch.setenv("RS_UMMA", umma)
+    X = torch.from_numpy(synth.random_matrix(n, d, 3 * n + d, scale=1.0 / np.sqrt(d))).to(torch.bfloat16)
+    V = torch.from_numpy(synth.random_orthonormal(d, k, d + 5)).float()
+    s2 = synth.random_sigma2(k, k + 3)
+    lam = 1e-4
+    Z, beta, bh = rs.rs_precondition(rsctx, cuda_rows(X), V.cuda(), torch.from_numpy(s2).cuda(), lam)
+    Zg = Z.cpu().double().numpy()
+    M = precond.m_matrix(V.double().numpy(), s2, lam)
+    Xt, B = precond.transform(X.double().numpy(), M)
+    scale = np.abs(X.double().numpy()).max() * (1 + np.sqrt(k))
+    assert np.all(np.abs(Zg[:n] - Xt) <= BF16_UNIT * np.abs(Xt) + 4e-6 * scale)

@@ -160,7 +160,9 @@ def test_trace_c_matches_oracle(rsctx, dtype):
     from tests.gpu_helpers import cuda_rows
     X = torch.from_numpy(synth.random_matrix(3001, 70, 4)).to(dtype)
     tr = rs.rs_trace_c(rsctx, cuda_rows(X))
-    assert tr == pytest.approx(np.trace(ridge.correlation(X.double().numpy())), rel=1e-12)
+    # lanes sum their part of a row in float (float data) before the double accumulation
+    tol = 1e-12 if dtype == torch.float64 else 1e-6
+    assert tr == pytest.approx(np.trace(ridge.correlation(X.double().numpy())), rel=tol)
 
 
 @pytest.mark.parametrize("z_dtype", [None, torch.bfloat16])
