@@ -31,6 +31,9 @@ import torch  # noqa: E402
 
 TARGET = 1e-6
 WORKLOAD = "fp32_n65536_d1024"
+# dram__bytes_read.sum + dram__bytes_write.sum that ncu measured for one fullgrad_bulk_kernel launch on
+# this workload (update with the kernel)
+FULLGRAD_TRAFFIC_BYTES = 276.15e6
 
 
 def _peaks():
@@ -256,9 +259,10 @@ def run_rs(args):
                    "speedup_chosen_vs_plain": ms_plain / ms,
                    "n": n, "d": d, "lambda": lam, "parallelism": f"replicas x{ws}",
                    "l2": "inputs exceed L2 (X 268 MB, components 272 MB fp32 / 136 MB bf16 vs 129 MB L2); no flush"},
-        "roofline": {"kernel": "fullgrad (data pass over the n+d component rows, fp32)", "bound": "hbm",
+        "roofline": {"kernel": "fullgrad_bulk_kernel (data pass over the n+d component rows, fp32)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "traffic": None, "ms_per_launch": fg_ms},
+                     "peak_kind": peak_kind, "traffic": FULLGRAD_TRAFFIC_BYTES, "traffic_unit": "B per launch",
+                     "algorithmic_bytes": fg_bytes, "ms_per_launch": fg_ms},
         "inner_loop": {"ms_per_epoch": per_epoch, "m": m_ch,
                        "ns_per_step": per_epoch * 1e6 / m_ch if per_epoch else None,
                        "steps_per_s": m_ch / (per_epoch * 1e-3) if per_epoch else None},
