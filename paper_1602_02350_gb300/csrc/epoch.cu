@@ -393,8 +393,11 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   T* Rs = reinterpret_cast<T*>(Zs + (size_t)STAGES * B * ZS);   // [STAGES][B][B]  (Rt layout: [l][j])
   T* Cs = Rs + (size_t)STAGES * B * B;                     // [STAGES][B]
   T* recv = Cs + (size_t)STAGES * B;                       // [2][kCsMax][B] partial dots from each rank
-  double* Ssum = reinterpret_cast<double*>(recv + 2 * kCsMax * B);   // [CW]
-  T* dl = reinterpret_cast<T*>(Ssum + CW);                 // [CW]
+  // running sum of the iterates (epoch average) as a compensated (Kahan) pair in T: on GB300 a
+  // double add sits on the critical path of every block with a long latency
+  T* Ssum = recv + 2 * kCsMax * B;                         // [CW]
+  T* Scmp = Ssum + CW;                                     // [CW] compensation
+  T* dl = Scmp + CW;                                       // [CW]
   T* mus = dl + CW;                                        // [CW]
   T* pv = mus + CW;                                        // [B]
   T* av = pv + B;                                          // [B]
@@ -411,7 +414,8 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
 
   for (int c = tid; c < CW; c += NT) {
     dl[c] = T(0);
-    Ssum[c] = 0.0;
+    Ssum[c] = T(0);
+    Scmp[c] = T(0);
     mus[c] = c < cwid ? mu[c0 + c] : T(0);
   }
   auto fetch_rows = [&](int64_t blk) -> uint32_t {
@@ -584,9 +588,13 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
       }
       if (g == 0) {
         const T bbT = (T)Bb;
-        const T tri = (T)(0.5 * (double)Bb * (double)(Bb + 1));
+        const T tri = (T)((Bb * (Bb + 1)) / 2);   // exact
         const T dold = dl[c];
-        Ssum[c] += (double)(bbT * dold - et * (mus[c] * tri + w));
+        const T x = bbT * dold - et * (mus[c] * tri + w);
+        const T yk = x - Scmp[c];
+        const T tk = Ssum[c] + yk;
+        Scmp[c] = (tk - Ssum[c]) - yk;
+        Ssum[c] = tk;
         dl[c] = dold - et * (bbT * mus[c] + u);
       }
     }
@@ -594,7 +602,7 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   cp_async_wait<0>();
   cluster.sync();   // no block leaves while remote stores to it could still be in flight
   for (int c = tid; c < cwid; c += NT) {
-    const double v = average ? Ssum[c] / (double)m : (double)dl[c];
+    const double v = average ? ((double)Ssum[c] - (double)Scmp[c]) / (double)m : (double)dl[c];
     wnext[c0 + c] = (T)((double)wbar[c0 + c] + v);
   }
 }
@@ -657,8 +665,9 @@ __device__ __forceinline__ void chain_la_body(const S* __restrict__ Z, int64_t N
   S* Zs = reinterpret_cast<S*>(ch_sh);                                 // [ZST][B][ZS]
   T* aux = reinterpret_cast<T*>(Zs + (size_t)ZST * B * ZS);           // [2][AUX]
   T* recv = aux + 2 * AUX;                                             // [2][kCsMax][B]
-  double* Ssum = reinterpret_cast<double*>(recv + 2 * kCsMax * B);     // [CW]
-  T* dl = reinterpret_cast<T*>(Ssum + CW);                             // [CW]
+  T* Ssum = recv + 2 * kCsMax * B;                                     // [CW] compensated running sum
+  T* Scmp = Ssum + CW;                                                 // [CW]
+  T* dl = Scmp + CW;                                                   // [CW]
   T* mus = dl + CW;                                                    // [CW]
   T* pv = mus + CW;                                                    // [B]
   T* av = pv + B;                                                      // [B]
@@ -675,7 +684,8 @@ __device__ __forceinline__ void chain_la_body(const S* __restrict__ Z, int64_t N
 
   for (int c = tid; c < CW; c += NT) {
     dl[c] = T(0);
-    Ssum[c] = 0.0;
+    Ssum[c] = T(0);
+    Scmp[c] = T(0);
     mus[c] = c < cwid ? mu[c0 + c] : T(0);
   }
   if (tid < B) pv[tid] = T(0);
@@ -838,9 +848,13 @@ __device__ __forceinline__ void chain_la_body(const S* __restrict__ Z, int64_t N
       }
       if (g == 0) {
         const T bbT = (T)Bb;
-        const T tri = (T)(0.5 * (double)Bb * (double)(Bb + 1));
+        const T tri = (T)((Bb * (Bb + 1)) / 2);   // exact
         const T dold = dl[c];
-        Ssum[c] += (double)(bbT * dold - et * (mus[c] * tri + w));
+        const T x = bbT * dold - et * (mus[c] * tri + w);
+        const T yk = x - Scmp[c];
+        const T tk = Ssum[c] + yk;
+        Scmp[c] = (tk - Ssum[c]) - yk;
+        Ssum[c] = tk;
         dl[c] = dold - et * (bbT * mus[c] + u);
       }
     }
@@ -882,7 +896,7 @@ __device__ __forceinline__ void chain_la_body(const S* __restrict__ Z, int64_t N
   cp_async_wait<0>();
   cluster.sync();   // no block leaves while remote stores to it could still be in flight
   for (int c = tid; c < cwid; c += NT) {
-    const double v = average ? Ssum[c] / (double)m : (double)dl[c];
+    const double v = average ? ((double)Ssum[c] - (double)Scmp[c]) / (double)m : (double)dl[c];
     wnext[c0 + c] = (T)((double)wbar[c0 + c] + v);
   }
 }
@@ -918,7 +932,7 @@ size_t chain_smem(int qn, int stages, int nt) {
   const int TPC = std::max(1, nt / CW);
   const int ZS = CW + chain_zpad(TPC, 32 / TPC, (int)sizeof(S));
   return (size_t)stages * kBlk * ZS * sizeof(S) + (size_t)stages * kBlk * kBlk * sizeof(T) +
-         (size_t)stages * kBlk * sizeof(T) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + (size_t)CW * sizeof(double) +
+         (size_t)stages * kBlk * sizeof(T) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + 2 * (size_t)CW * sizeof(T) +
          2 * (size_t)CW * sizeof(T) + (2 + nt / kBlk) * (size_t)kBlk * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
          2 * sizeof(uint64_t) + 64;
 }
@@ -999,7 +1013,7 @@ size_t chain_la_smem(int qn, int zst, int nt) {
   const int TPC = std::max(1, nt / CW);
   const int ZS = CW + chain_zpad(TPC, 32 / TPC, (int)sizeof(S));
   return (size_t)zst * kBlk * ZS * sizeof(S) + 2 * (size_t)(2 * kBlk * kBlk + 2 * kBlk) * sizeof(T) +
-         2 * (size_t)kCsMax * kBlk * sizeof(T) + (size_t)CW * sizeof(double) + 2 * (size_t)CW * sizeof(T) +
+         2 * (size_t)kCsMax * kBlk * sizeof(T) + 2 * (size_t)CW * sizeof(T) + 2 * (size_t)CW * sizeof(T) +
          (2 + nt / kBlk) * (size_t)kBlk * sizeof(T) + (size_t)zst * kBlk * sizeof(uint32_t) + 2 * sizeof(uint64_t) +
          64;
 }
