@@ -362,6 +362,17 @@ def run_precision(args):
     forms["bf16_refined_proposal"] = {"seconds": ms / 1e3, "epochs": e, "k": info["k"], "eta_mult": info["eta_mult"],
                                       "m": info["m"], "fallback": info["fallback"], "rel_subopt_per_epoch": hist[:e]}
     del info
+    # BF16 data, FP8-e4m3 components with per-row scales, snapshot gradients refined on the BF16 data
+    def fp8_solve(epochs, snapshots=False):
+        V, s2 = rs.rs_sketch(ctx, Xb, k, cfg.seed_sketch)
+        Z8, beta8, _ = rs.rs_precondition(ctx, Xb, V, s2, lam, z_dtype=torch.float8_e4m3fn)
+        return rs.rs_svrg_solve(ctx, Z8, y, V, s2, lam, epochs, cfg.seed_svrg, beta=beta8, m=2 * n, eta_mult=1.0,
+                                X=Xb, refine=True, snapshots=snapshots)
+    _, info = fp8_solve(cap, snapshots=True)
+    e, hist = first(info["snapshots"])
+    del info
+    ms = timed(lambda: fp8_solve(e))
+    forms["fp8_refined_k256"] = {"seconds": ms / 1e3, "epochs": e, "rel_subopt_per_epoch": hist[:e]}
     # FP32 data, same setting as the first form
     Xf = Xb.float()
     del Xb

@@ -153,7 +153,9 @@ int rs_sketch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* 
  *   rows n..n+d-1: z_{n+j} = M e_j        (b_j of Alg. 3; M is symmetric).
  * Xt->data is written (cast away const); Xt->n must be n + d, Xt->d = d, Xt->dtype equal
  * to X->dtype (RS_F64, RS_F32 or RS_BF16), or RS_BF16 for RS_F32 data (each component is
- * formed in float and rounded once).
+ * formed in float and rounded once), or RS_FP8E4M3 for RS_F32 / RS_BF16 data: one scale per row,
+ * s_i = max_c |z_ic| / 448, written to Xt->row_scale (float, n + d), codes e4m3(z_ic / s_i) rounded
+ * to nearest; beta is then computed from the stored values.
  * beta (T, n + d): smoothness beta_i = gamma_i ||z_i||^2 with gamma_i = (n+d)/n for data
  * rows and lam (n+d) for regulariser rows (Alg. 3).  beta_hat (host, nullable): mean beta. */
 int rs_precondition(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k,
@@ -247,8 +249,8 @@ typedef struct {
   float* epoch_ms;       /* host, nullable: cumulative device time at the end of each epoch */
 } rs_history;
 
-/* Alg. 1 on the components Z (rs_precondition layout, N = n + d rows; RS_F64, RS_F32 or RS_BF16
- * storage) for p->epochs epochs, starting from w0 (preconditioned coordinates, nullable = 0).
+/* Alg. 1 on the components Z (rs_precondition layout, N = n + d rows; RS_F64, RS_F32, RS_BF16 or
+ * RS_FP8E4M3 storage; FP8 components need p->refine, X and beta) for p->epochs epochs, starting from w0 (preconditioned coordinates, nullable = 0).
  * X (n x d, stored like Z, or RS_F32 for RS_BF16 components) is the stored data, required
  * when p->refine is set, else
  * nullable.  beta (T, N; nullable = recomputed from Z) sets the sampling weights.  V/sigma2/k

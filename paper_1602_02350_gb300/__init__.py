@@ -7,7 +7,7 @@ synthetic-input generator ``synth``.
 """
 
 from ._lib import (  # noqa: F401
-    Context, RsError, declared_symbols, lib, matrix,
+    Context, RsError, declared_symbols, lib, matrix, Fp8Rows,
     RS_F64, RS_F32, RS_BF16, RS_FP8E4M3, RS_SKETCH_GAUSSIAN, RS_SKETCH_COUNTSKETCH,
     RS_SAMPLE_IMPORTANCE, RS_SAMPLE_UNIFORM,
     rs_philox_words, rs_gaussian, rs_countsketch, rs_range_sketch, rs_orthonormalize, rs_sym_eig,

@@ -19,7 +19,7 @@ RS_F64, RS_F32, RS_BF16, RS_FP8E4M3 = 0, 1, 2, 3
 RS_SKETCH_GAUSSIAN, RS_SKETCH_COUNTSKETCH = 0, 1
 RS_SAMPLE_IMPORTANCE, RS_SAMPLE_UNIFORM = 0, 1
 
-_DT = {torch.float64: RS_F64, torch.float32: RS_F32, torch.bfloat16: RS_BF16}
+_DT = {torch.float64: RS_F64, torch.float32: RS_F32, torch.bfloat16: RS_BF16, torch.float8_e4m3fn: RS_FP8E4M3}
 _TORCH = {RS_F64: torch.float64, RS_F32: torch.float32, RS_BF16: torch.bfloat16}
 
 
@@ -169,8 +169,23 @@ def _need_cuda(*ts):
             raise TypeError("expected a CUDA tensor")
 
 
+class Fp8Rows:
+    """FP8-e4m3 rows with one float scale per row (value = code * scale): the component storage
+    rs_precondition writes for z_dtype=torch.float8_e4m3fn."""
+
+    def __init__(self, codes, scale):
+        self.codes, self.scale = codes, scale
+        self.shape = codes.shape
+        self.dtype = codes.dtype
+
+    def dequantize(self):
+        return self.codes.float() * self.scale[:, None]
+
+
 def matrix(t, row_scale=None):
-    """rs_matrix descriptor of a row-major 2-D CUDA tensor (row stride = t.stride(0))."""
+    """rs_matrix descriptor of a row-major 2-D CUDA tensor (row stride = t.stride(0)), or of Fp8Rows."""
+    if isinstance(t, Fp8Rows):
+        return matrix(t.codes, row_scale=t.scale)
     _need_cuda(t)
     if t.dim() != 2 or t.stride(1) != 1:
         raise ValueError("matrix: need a 2-D tensor with unit column stride")
@@ -307,12 +322,15 @@ def _padded_ld(d, dtype):
 
 
 def rs_precondition(ctx, X, V, sigma2, lam, want_beta_hat=True, z_dtype=None):
-    """Components Z ((n + d) x d, stored like X or in z_dtype = torch.bfloat16 for float32 X)."""
+    """Components Z ((n + d) x d, stored like X, or in z_dtype = torch.bfloat16 for float32 X, or
+    z_dtype = torch.float8_e4m3fn: then Z is Fp8Rows (codes and per-row scales))."""
     n, d = X.shape
     zt = X.dtype if z_dtype is None else z_dtype
     ld = _padded_ld(d, zt)
     Zs = ctx._empty(n + d, ld, dtype=zt)
     Z = Zs[:, :d]
+    if zt == torch.float8_e4m3fn:
+        Z = Fp8Rows(Z, ctx._empty(n + d, dtype=torch.float32))
     beta = ctx._empty(n + d, dtype=_compute_dtype(X))
     MX, MZ = matrix(X), matrix(Z)
     bh = ctypes.c_double(0.0)

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include <cstdarg>
@@ -24,7 +25,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_COUNT
 };
 
 struct rs_ctx {
@@ -151,6 +152,14 @@ template <> __device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bf
   return static_cast<double>(__bfloat162float(v));
 }
 template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+// FP8-e4m3 codes (components stored with a per-row scale: value = code * scale)
+template <> __device__ __forceinline__ float cvt<float, __nv_fp8_e4m3>(__nv_fp8_e4m3 v) { return static_cast<float>(v); }
+template <> __device__ __forceinline__ double cvt<double, __nv_fp8_e4m3>(__nv_fp8_e4m3 v) {
+  return static_cast<double>(static_cast<float>(v));
+}
+using fp8_t = __nv_fp8_e4m3;
+template <typename S> struct IsFp8 { static constexpr bool value = false; };
+template <> struct IsFp8<__nv_fp8_e4m3> { static constexpr bool value = true; };
 
 template <typename T> struct Vec;        // 16-byte vector of T
 template <> struct Vec<float> { using type = float4; static constexpr int N = 4; };

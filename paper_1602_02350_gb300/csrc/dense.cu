@@ -507,6 +507,52 @@ __global__ void trace_finish_kernel(const double* part, int np, double inv_n, do
   }
 }
 
+// mean of a float vector in double (one block)
+__global__ void mean_f_kernel(const float* v, int64_t N, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += (double)v[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = t / (double)N;
+  }
+}
+
+// FP8-e4m3 components with per-row scales: s_i = max_c |z_ic| / 448 (1 for a zero row), code_ic =
+// e4m3(z_ic / s_i) (round to nearest, saturating), and beta_i = gamma_i s_i^2 sum_c code_ic^2 from the
+// stored values.  One warp per row of the bfloat16 staging copy.
+__global__ void quantize_fp8_rows_kernel(const __nv_bfloat16* __restrict__ Zb, int64_t N, int64_t n, int64_t d,
+                                         int64_t ldb, double lam, __nv_fp8_e4m3* __restrict__ Zq, int64_t ldq,
+                                         float* __restrict__ scale, float* __restrict__ beta) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double gd = (double)N / (double)n, gr = lam * (double)N;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
+    const __nv_bfloat16* row = Zb + i * ldb;
+    float mx = 0.0f;
+    for (int64_t c = lane; c < d; c += 32) mx = fmaxf(mx, fabsf(__bfloat162float(row[c])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float sc = mx > 0.0f ? mx / 448.0f : 1.0f;
+    const float inv = 1.0f / sc;
+    float ss = 0.0f;
+    for (int64_t c = lane; c < d; c += 32) {
+      const __nv_fp8_e4m3 q(__bfloat162float(row[c]) * inv);
+      Zq[i * ldq + c] = q;
+      const float v = static_cast<float>(q);
+      ss = fmaf(v, v, ss);
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) {
+      scale[i] = sc;
+      beta[i] = (float)((i < n ? gd : gr) * (double)sc * (double)sc * (double)ss);
+    }
+  }
+}
+
 int blocks_for(rs_ctx* ctx, int64_t work, int threads = 256) {
   int64_t g = (work + threads - 1) / threads;
   const int64_t cap = (int64_t)ctx->num_sms * 8;
@@ -853,6 +899,37 @@ int sketch_dispatch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, 
 
 int precondition_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k, double lam,
                           rs_matrix* Xt, void* beta, double* beta_hat) {
+  if (Xt->dtype == RS_FP8E4M3) {
+    // bfloat16 components in scratch, then per-row scaled FP8 codes and beta from the stored values
+    const int64_t n = X->n, d = X->d, N = n + d;
+    const int64_t ldb = (d + 7) / 8 * 8;
+    __nv_bfloat16* Zb = static_cast<__nv_bfloat16*>(rs_scratch(ctx, SCR_Z8, (size_t)N * ldb * sizeof(__nv_bfloat16)));
+    if (!Zb) return RS_ENOMEM;
+    rs_matrix Zm = {Zb, nullptr, N, d, ldb, RS_BF16, 0};
+    int rc;
+    if (X->dtype == RS_F32)
+      rc = precondition_t<float, float, __nv_bfloat16>(ctx, X, static_cast<const float*>(V), sigma2, k, lam, &Zm,
+                                                       static_cast<float*>(beta), nullptr);
+    else if (X->dtype == RS_BF16)
+      rc = precondition_t<__nv_bfloat16, float>(ctx, X, static_cast<const float*>(V), sigma2, k, lam, &Zm,
+                                                static_cast<float*>(beta), nullptr);
+    else
+      return rs_fail(RS_EUNSUPPORTED, "rs_precondition: FP8 components need RS_F32 or RS_BF16 data");
+    if (rc != RS_OK) return rc;
+    quantize_fp8_rows_kernel<<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(
+        Zb, N, n, d, ldb, lam, static_cast<__nv_fp8_e4m3*>(const_cast<void*>(Xt->data)), Xt->ld,
+        const_cast<float*>(Xt->row_scale), static_cast<float*>(beta));
+    RS_LAUNCH_CHECK(ctx);
+    if (beta_hat) {
+      double* part = static_cast<double*>(rs_scratch(ctx, SCR_MISC, 2 * sizeof(double)));
+      if (!part) return RS_ENOMEM;
+      mean_f_kernel<<<1, 1024, 0, ctx->stream>>>(static_cast<const float*>(beta), N, part);
+      RS_LAUNCH_CHECK(ctx);
+      RS_CUDA_TRY(cudaMemcpyAsync(beta_hat, part, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    return RS_OK;
+  }
   if (X->dtype == RS_F64)
     return precondition_t<double, double>(ctx, X, static_cast<const double*>(V), sigma2, k, lam, Xt,
                                   static_cast<double*>(beta), beta_hat);
@@ -996,8 +1073,9 @@ int rs_precondition(rs_ctx* ctx, const rs_matrix* X, const void* V, const double
   RS_CHECK_ARG(k >= 1 && k <= X->d, "rs_precondition: k must be in [1, d]");
   RS_CHECK_ARG(lambda > 0.0, "rs_precondition: lambda must be positive");
   RS_CHECK_ARG(Xt->n == X->n + X->d && Xt->d == X->d, "rs_precondition: Xt must be (n + d) x d");
-  RS_CHECK_ARG(Xt->dtype == X->dtype || (X->dtype == RS_F32 && Xt->dtype == RS_BF16),
-               "rs_precondition: Xt dtype must equal X dtype (or be RS_BF16 for RS_F32 data)");
+  RS_CHECK_ARG(Xt->dtype == X->dtype || (X->dtype == RS_F32 && Xt->dtype == RS_BF16) ||
+                   (Xt->dtype == RS_FP8E4M3 && (X->dtype == RS_F32 || X->dtype == RS_BF16)),
+               "rs_precondition: Xt dtype must equal X dtype (or be RS_BF16 for RS_F32 data, or RS_FP8E4M3)");
   return precondition_dispatch(ctx, X, V, sigma2, k, lambda, Xt, beta, beta_hat);
 }
 

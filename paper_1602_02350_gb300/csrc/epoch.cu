@@ -37,6 +37,14 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// sixteen FP8-e4m3 codes (one 16-byte load) widened to float and scaled
+__device__ __forceinline__ void ld_widen(const __nv_fp8_e4m3* p, float* v, float sc) {
+  const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+  const __nv_fp8_e4m3* q = reinterpret_cast<const __nv_fp8_e4m3*>(&raw);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = static_cast<float>(q[k]) * sc;
+}
+
 // eight bfloat16 (one 16-byte load) widened to float: a bfloat16 is the upper half of a float
 __device__ __forceinline__ void ld_widen8(const __nv_bfloat16* p, float* v) {
   const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
@@ -47,6 +55,7 @@ __device__ __forceinline__ void ld_widen8(const __nv_bfloat16* p, float* v) {
     v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
   }
 }
+__device__ __forceinline__ void ld_widen(const __nv_bfloat16* p, float* v, float) { ld_widen8(p, v); }
 
 // ------------------------------------------------------------------ per-block preparation
 // One thread block per block of steps.  Rows 0..B-1 of the staged tile are the sampled rows
@@ -58,7 +67,8 @@ template <typename S, typename T, bool LA = false>
 __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d, int64_t n,
                                           double lam, const uint32_t* __restrict__ idx, const T* __restrict__ inv_nq,
                                           int64_t m, double eta, const T* __restrict__ mu, T* __restrict__ Rt,
-                                          T* __restrict__ cvec, T* __restrict__ Kt, T* __restrict__ hn, int64_t b) {
+                                          T* __restrict__ cvec, T* __restrict__ Kt, T* __restrict__ hn, int64_t b,
+                                          const float* __restrict__ rsc = nullptr) {
   constexpr int B = kBlk, RP0 = B + 4, RP = LA ? RP0 + B : RP0;
   constexpr int E = 16 / sizeof(T);
   constexpr int CH = 64;              // columns per staged chunk
@@ -113,10 +123,11 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
         const int64_t rid = row_of(r);
         if (rid >= 0 && col < d) {
           const S* src = Z + rid * ld + col;
-          if (col + ES <= d) ld_widen8(src, v);
+          const float sc = IsFp8<S>::value ? rsc[rid] : 1.0f;   // FP8 codes carry a per-row scale
+          if (col + ES <= d) ld_widen(src, v, sc);
           else
-            for (int i = 0; i < (int)(d - col); ++i) v[i] = cvt<T>(src[i]);
-        } else if (r == B) {
+            for (int i = 0; i < (int)(d - col); ++i) v[i] = cvt<T>(src[i]) * sc;
+        } else if (r == B && mu) {
           for (int i = 0; i < ES; ++i)
             if (col + i < d) v[i] = mu[col + i];
         }
@@ -141,14 +152,14 @@ __device__ __forceinline__ void prep_body(const S* __restrict__ Z, int64_t N, in
         const int valid = (int)min64(E, d - col) * (int)sizeof(T);
         const int64_t rid = row_of(r);
         if (rid >= 0) { src = reinterpret_cast<const T*>(Z) + rid * ld + col; bytes = valid; }
-        else if (r == B) { src = mu + col; bytes = (reinterpret_cast<uintptr_t>(mu + col) & 15) ? 0 : valid; }
+        else if (r == B && mu) { src = mu + col; bytes = (reinterpret_cast<uintptr_t>(mu + col) & 15) ? 0 : valid; }
       }
       cp_async16(dst + r * TS + q * E, src, bytes);
     }
     cp_async_commit();
   };
   // mu may not be 16-byte aligned at every chunk: stage it with plain loads when it is not
-  const bool mu_aligned = (reinterpret_cast<uintptr_t>(mu) & 15) == 0;
+  const bool mu_aligned = mu == nullptr || (reinterpret_cast<uintptr_t>(mu) & 15) == 0;
   // 4x4 tiles: thread tid takes tile tid and (look-ahead) tile tid + 256.  Tiles 0..152 are the
   // lower triangle of the RP0 x RP0 Gram matrix; tiles 153.. pair next-block rows with rows 0..RP0-1
   auto tile_of = [&](int id, int& I, int& J) {
@@ -290,8 +301,8 @@ __global__ void __launch_bounds__(256) epoch_prep_kernel(const S* __restrict__ Z
                                                          int64_t n, double lam, const uint32_t* __restrict__ idx,
                                                          const T* __restrict__ inv_nq, int64_t m, double eta,
                                                          const T* __restrict__ mu, T* __restrict__ Rt,
-                                                         T* __restrict__ cvec) {
-  prep_body<S, T>(Z, N, ld, d, n, lam, idx, inv_nq, m, eta, mu, Rt, cvec, nullptr, nullptr, blockIdx.x);
+                                                         T* __restrict__ cvec, const float* __restrict__ rsc) {
+  prep_body<S, T>(Z, N, ld, d, n, lam, idx, inv_nq, m, eta, mu, Rt, cvec, nullptr, nullptr, blockIdx.x, rsc);
 }
 
 template <typename S, typename T>
@@ -369,7 +380,7 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
                                            const uint32_t* __restrict__ idx, int64_t m, const T* __restrict__ Rt,
                                            const T* __restrict__ cvec, double eta, const T* __restrict__ mu,
                                            const T* __restrict__ wbar, int average, T* __restrict__ wnext,
-                                           int* status) {
+                                           int* status, const float* __restrict__ rsc) {
   constexpr int B = kBlk;
   constexpr int E = 16 / sizeof(T);
   constexpr int ES = 16 / sizeof(S);
@@ -403,7 +414,9 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   T* av = pv + B;                                          // [B]
   T* part4 = av + B;                                       // [H][B] partial sums of R p
   uint32_t* srow = reinterpret_cast<uint32_t*>(part4 + H * B);   // [STAGES][B]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + STAGES * B);   // [2]
+  float* sscale = reinterpret_cast<float*>(srow + STAGES * B);   // [STAGES][B] row scales (FP8 codes)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sscale + STAGES * B);   // [2]
+  constexpr bool F8 = IsFp8<S>::value;
   __shared__ int aborted;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c0 = (int64_t)rank * CW;
@@ -423,7 +436,11 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
     return (tid < B && t < m) ? (uint32_t)min64((int64_t)idx[t], N - 1) : 0xFFFFFFFFu;
   };
   for (int s = 0; s < STAGES; ++s)
-    if (tid < B) srow[s * B + tid] = fetch_rows(s);
+    if (tid < B) {
+      const uint32_t row = fetch_rows(s);
+      srow[s * B + tid] = row;
+      if (F8) sscale[s * B + tid] = row != 0xFFFFFFFFu ? rsc[row] : 1.0f;
+    }
   uint32_t pend_row = fetch_rows(STAGES);
   if (tid == 0) {
     aborted = 0;
@@ -480,12 +497,15 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
     // hidden behind a whole block of steps
     const uint32_t next_row = pend_row;
     pend_row = fetch_rows(blk + STAGES + 1);
+    float next_scale = 1.0f;
+    if (F8 && tid < B && next_row != 0xFFFFFFFFu) next_scale = rsc[next_row];
     cp_async_wait<STAGES - 2>();
     __syncthreads();
     if (blk + STAGES - 1 < nblk) load_block(blk + STAGES - 1);
     cp_async_commit();
     const int slot = (int)(blk % STAGES);
     const int par = (int)(blk & 1);
+    const float myscale = (F8 && tid < B) ? sscale[slot * B + tid] : 1.0f;   // row tid of this block
     const int Bb = (int)min64(B, m - blk * B);
     const S* zs = Zs + (size_t)slot * B * ZS;
     // partial p_j over this block's columns for rows 8 warp .. 8 warp + 7, pushed to every rank
@@ -523,7 +543,10 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
         for (int h = 0; h < W16; ++h) st_async16(base + 16 * h, rbar, pw + 4 * h);
       }
     }
-    if (tid < B) srow[slot * B + tid] = next_row;    // this slot now holds block blk + STAGES
+    if (tid < B) {
+      srow[slot * B + tid] = next_row;    // this slot now holds block blk + STAGES
+      if (F8) sscale[slot * B + tid] = next_scale;
+    }
     // wait for the CS partial vectors of this block (bounded), then p = sum over ranks
     if (!aborted) {
       const long long t0c = clock64();
@@ -539,7 +562,7 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
       const T* rv = recv + (size_t)par * kCsMax * B + tid;
       T s = T(0);
       for (int r = 0; r < CS; ++r) s += rv[r * B];   // rank order: identical in every block
-      pv[tid] = s;
+      pv[tid] = F8 ? s * myscale : s;
     }
     __syncthreads();
     if (tid == 0 && blk + 2 < nblk) mbar_arm(&mbar[par], tx_per_block);   // next use: block blk + 2
@@ -564,7 +587,7 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
       T sa = Cs[(size_t)slot * B + tid];
 #pragma unroll
       for (int hh = 0; hh < H; ++hh) sa += part4[hh * B + tid];   // fixed order
-      av[tid] = sa;
+      av[tid] = F8 ? sa * myscale : sa;   // the update multiplies stored codes
     }
     __syncthreads();
     // rank-B update: lanes g = 0..TPC-1 of a column take steps j = g, g + TPC, ... and combine by
@@ -613,8 +636,8 @@ __global__ void __launch_bounds__(NT) epoch_chain_kernel(const S* __restrict__ Z
                                                           const T* __restrict__ Rt, const T* __restrict__ cvec,
                                                           double eta, const T* __restrict__ mu,
                                                           const T* __restrict__ wbar, int average,
-                                                          T* __restrict__ wnext, int* status) {
-  chain_body<S, T, STAGES, QN, NT>(Z, N, ld, d, idx, m, Rt, cvec, eta, mu, wbar, average, wnext, status);
+                                                          T* __restrict__ wnext, int* status, const float* rsc) {
+  chain_body<S, T, STAGES, QN, NT>(Z, N, ld, d, idx, m, Rt, cvec, eta, mu, wbar, average, wnext, status, rsc);
 }
 
 // one cluster per job (the cluster's blocks are consecutive in x)
@@ -624,7 +647,7 @@ __global__ void __launch_bounds__(NT) epoch_chain_batched_kernel(const ChainJob<
   const int cs = (int)cg::this_cluster().num_blocks();
   const ChainJob<S, T> J = jobs[blockIdx.x / cs];
   chain_body<S, T, STAGES, QN, NT>(J.Z, J.N, J.ld, J.d, J.idx, J.m, J.Rt, J.cvec, J.eta, J.mu, J.wbar, J.average,
-                                   J.wnext, status);
+                                   J.wnext, status, nullptr);
 }
 
 // ------------------------------------------------------------------ look-ahead chain
@@ -934,7 +957,7 @@ size_t chain_smem(int qn, int stages, int nt) {
   return (size_t)stages * kBlk * ZS * sizeof(S) + (size_t)stages * kBlk * kBlk * sizeof(T) +
          (size_t)stages * kBlk * sizeof(T) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + 2 * (size_t)CW * sizeof(T) +
          2 * (size_t)CW * sizeof(T) + (2 + nt / kBlk) * (size_t)kBlk * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
-         2 * sizeof(uint64_t) + 64;
+         (size_t)stages * kBlk * sizeof(float) + 2 * sizeof(uint64_t) + 64;
 }
 
 // Cluster size: enough blocks that each owns at most 64 columns, up to 16 blocks (then up to
@@ -979,7 +1002,7 @@ ChainPlan plan_chain(int64_t d, int cs) {
 template <typename S, typename T, int ST, int QN, int NT>
 int launch_chain(rs_ctx* ctx, const ChainPlan& pl, const S* Z, int64_t N, int64_t ld, int64_t d,
                  const uint32_t* idx, int64_t m, const T* Rt, const T* cv, double eta, const T* mu, const T* wbar,
-                 int average, T* wnext) {
+                 int average, T* wnext, const float* rsc) {
   auto kern = epoch_chain_kernel<S, T, ST, QN, NT>;
   RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.shm));
   if (pl.cs > 8) RS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -1001,7 +1024,7 @@ int launch_chain(rs_ctx* ctx, const ChainPlan& pl, const S* Z, int64_t N, int64_
     return RS_EUNSUPPORTED;   // this cluster shape cannot be placed on the device: caller tries a smaller one
   }
   RS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, Z, N, ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext,
-                                 ctx->d_status));
+                                 ctx->d_status, rsc));
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
 }
@@ -1112,8 +1135,8 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
   T* Rt = static_cast<T*>(rs_scratch(ctx, SCR_R, (size_t)nblk * kBlk * kBlk * sizeof(T)));
   T* cv = static_cast<T*>(rs_scratch(ctx, SCR_C, (size_t)nblk * kBlk * sizeof(T)));
   if (!Rt || !cv) return RS_ENOMEM;
-  const bool la = use_lookahead<T>();
-  if constexpr (sizeof(T) == 4) {
+  const bool la = use_lookahead<T>() && !IsFp8<S>::value;
+  if constexpr (sizeof(T) == 4 && !IsFp8<S>::value) {
     if (la) {
       T* Kt = static_cast<T*>(rs_scratch(ctx, SCR_KT, (size_t)nblk * kBlk * kBlk * sizeof(T)));
       T* hn = static_cast<T*>(rs_scratch(ctx, SCR_HN, (size_t)nblk * kBlk * sizeof(T)));
@@ -1142,7 +1165,7 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
     constexpr size_t pshm = prep_smem_bytes<T, false>();
     RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
     epoch_prep_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m, eta,
-                                                                        mu, Rt, cv);
+                                                                        mu, Rt, cv, Z->row_scale);
     RS_LAUNCH_CHECK(ctx);
   }
   for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
@@ -1151,9 +1174,11 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
     int rc = RS_EUNSUPPORTED;
 #define RS_CHAIN(ST, QN)                                                                                          \
   if (pl.stages == ST && pl.qn == QN && pl.nt == 256)                                                             \
-    rc = launch_chain<S, T, ST, QN, 256>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext);   \
+    rc = launch_chain<S, T, ST, QN, 256>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext,   \
+                                         Z->row_scale);                                                           \
   if (pl.stages == ST && pl.qn == QN && pl.nt == 512)                                                             \
-    rc = launch_chain<S, T, ST, QN, 512>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext);
+    rc = launch_chain<S, T, ST, QN, 512>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext, \
+                                         Z->row_scale);
     RS_CHAIN(4, 2) RS_CHAIN(4, 4) RS_CHAIN(4, 8) RS_CHAIN(3, 2) RS_CHAIN(3, 4) RS_CHAIN(3, 8)
     RS_CHAIN(2, 2) RS_CHAIN(2, 4) RS_CHAIN(2, 8)
 #undef RS_CHAIN
@@ -1161,6 +1186,101 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
   }
   return rs_fail(RS_EUNSUPPORTED, "rs_svrg_epoch: no thread-block cluster layout fits d = %lld", (long long)d);
 }
+
+// ------------------------------------------------------------------ split preparation
+// R of every block depends only on the sampled rows and the step size, c also on mu.  The
+// one-problem solver therefore prepares the next epoch's R (epoch_prep_kernel with mu = null,
+// on a second stream, on SMs the inner loop leaves idle) while the current epoch runs, and forms
+// c after the snapshot gradient: h_l = z_l^T mu for the block's rows, c_j = -eta sum_{l<=j} R_jl l h_l.
+namespace {
+
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) epoch_c_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+                                                      const uint32_t* __restrict__ idx, int64_t m, double eta,
+                                                      const T* __restrict__ mu, const T* __restrict__ Rt,
+                                                      T* __restrict__ cvec, const float* __restrict__ rsc) {
+  constexpr int B = kBlk;
+  __shared__ T h[B];
+  const int64_t b = blockIdx.x, t0 = b * B;
+  const int Bb = (int)min64(B, m - t0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = warp; l < B; l += nw) {
+    T s = T(0);
+    int64_t ri = 0;
+    if (l < Bb) {
+      ri = min64((int64_t)idx[t0 + l], N - 1);
+      const S* row = Z + ri * ld;
+      for (int64_t c = lane; c < d; c += 32) s = fma(cvt<T>(row[c]), mu[c], s);
+    }
+    s = warp_sum(s);
+    if (IsFp8<S>::value && l < Bb) s *= (T)rsc[ri];
+    if (lane == 0) h[l] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < B) {
+    const int j = threadIdx.x;
+    const T* R = Rt + b * (int64_t)B * B;   // R[j][l] = Rt[l][j]
+    T s = T(0);
+    for (int l = 0; l <= j && l < Bb; ++l) s = fma(R[l * B + j], (T)l * h[l], s);
+    cvec[b * B + j] = j < Bb ? -(T)eta * s : T(0);
+  }
+}
+
+}  // namespace
+
+// R (and zero c) of every block of an epoch, without mu, on the context's stream.
+template <typename S, typename T>
+int epoch_prep_r_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
+                   int64_t m, double eta, T* Rt, T* cv) {
+  const S* Zd = static_cast<const S*>(Z->data);
+  const int64_t nblk = (m + kBlk - 1) / kBlk;
+  constexpr size_t pshm = prep_smem_bytes<T, false>();
+  RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+  epoch_prep_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, Z->n, Z->ld, Z->d, n, lam, idx, inv_nq, m,
+                                                                      eta, nullptr, Rt, cv, Z->row_scale);
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+// c of every block from mu and the prepared R, then the inner-loop chain.
+template <typename S, typename T>
+int epoch_finish_t(rs_ctx* ctx, const rs_matrix* Z, const uint32_t* idx, int64_t m, double eta, const T* Rt, T* cv,
+                   const T* wbar, const T* mu, int average, T* wnext) {
+  const S* Zd = static_cast<const S*>(Z->data);
+  const int64_t N = Z->n, d = Z->d;
+  const int64_t nblk = (m + kBlk - 1) / kBlk;
+  epoch_c_kernel<S, T><<<(unsigned)nblk, 256, 0, ctx->stream>>>(Zd, N, Z->ld, d, idx, m, eta, mu, Rt, cv,
+                                                                 Z->row_scale);
+  RS_LAUNCH_CHECK(ctx);
+  for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
+    const ChainPlan pl = plan_chain<S, T>(d, cs);
+    if (!pl.cs) continue;
+    int rc = RS_EUNSUPPORTED;
+#define RS_CHAIN(ST, QN)                                                                                          \
+  if (pl.stages == ST && pl.qn == QN && pl.nt == 256)                                                             \
+    rc = launch_chain<S, T, ST, QN, 256>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext,   \
+                                         Z->row_scale);                                                           \
+  if (pl.stages == ST && pl.qn == QN && pl.nt == 512)                                                             \
+    rc = launch_chain<S, T, ST, QN, 512>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, eta, mu, wbar, average, wnext, \
+                                         Z->row_scale);
+    RS_CHAIN(4, 2) RS_CHAIN(4, 4) RS_CHAIN(4, 8) RS_CHAIN(3, 2) RS_CHAIN(3, 4) RS_CHAIN(3, 8)
+    RS_CHAIN(2, 2) RS_CHAIN(2, 4) RS_CHAIN(2, 8)
+#undef RS_CHAIN
+    if (rc != RS_EUNSUPPORTED) return rc;
+  }
+  return rs_fail(RS_EUNSUPPORTED, "svrg epoch: no thread-block cluster layout fits d = %lld", (long long)d);
+}
+
+#define RS_SPLIT_INST(S, T)                                                                                      \
+  template int epoch_prep_r_t<S, T>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const T*, int64_t, \
+                                    double, T*, T*);                                                             \
+  template int epoch_finish_t<S, T>(rs_ctx*, const rs_matrix*, const uint32_t*, int64_t, double, const T*, T*,     \
+                                    const T*, const T*, int, T*);
+RS_SPLIT_INST(float, float)
+RS_SPLIT_INST(double, double)
+RS_SPLIT_INST(__nv_bfloat16, float)
+RS_SPLIT_INST(__nv_fp8_e4m3, float)
+#undef RS_SPLIT_INST
 
 // ------------------------------------------------------------------ batched launches
 
@@ -1269,4 +1389,6 @@ template int svrg_epoch_t<float, float>(rs_ctx*, const rs_matrix*, int64_t, doub
 template int svrg_epoch_t<double, double>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const double*,
                                           int64_t, double, const double*, const double*, int, double*);
 template int svrg_epoch_t<__nv_bfloat16, float>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*,
+                                                const float*, int64_t, double, const float*, const float*, int, float*);
+template int svrg_epoch_t<__nv_fp8_e4m3, float>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*,
                                                 const float*, int64_t, double, const float*, const float*, int, float*);

@@ -437,6 +437,29 @@ static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t 
 template <typename S, typename T>
 int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
                  int64_t m, double eta, const T* wbar, const T* mu, int average, T* wnext);   // epoch.cu
+template <typename S, typename T>
+int epoch_prep_r_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
+                   int64_t m, double eta, T* Rt, T* cv);                                      // epoch.cu
+template <typename S, typename T>
+int epoch_finish_t(rs_ctx* ctx, const rs_matrix* Z, const uint32_t* idx, int64_t m, double eta, const T* Rt, T* cv,
+                   const T* wbar, const T* mu, int average, T* wnext);                        // epoch.cu
+
+// A second stream and its events for the look-ahead preparation of the next epoch; the context's
+// stream is restored on every exit.
+struct SideStream {
+  rs_ctx* ctx = nullptr;
+  cudaStream_t main = nullptr, side = nullptr;
+  cudaEvent_t ready[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr}, start = nullptr;
+  ~SideStream() {
+    if (ctx) ctx->stream = main;
+    for (int q = 0; q < 2; ++q) {
+      if (ready[q]) cudaEventDestroy(ready[q]);
+      if (used[q]) cudaEventDestroy(used[q]);
+    }
+    if (start) cudaEventDestroy(start);
+    if (side) cudaStreamDestroy(side);
+  }
+};
 
 // v = g + lam u (the gradient of Eq. (1) at u from its data part g)
 template <typename T>
@@ -445,10 +468,10 @@ __global__ void add_ridge_kernel(const T* g, const T* u, int64_t d, double lam, 
     v[c] = g[c] + (T)lam * u[c];
 }
 
-static int check_components(const rs_matrix* Z, int64_t n) {
+static int check_components(const rs_matrix* Z, int64_t n, bool allow_fp8 = false) {
   RS_TRY(check_matrix(Z, "Z"));
-  RS_CHECK_ARG(Z->dtype == RS_F64 || Z->dtype == RS_F32 || Z->dtype == RS_BF16,
-               "components: dtype must be RS_F64, RS_F32 or RS_BF16");
+  RS_CHECK_ARG(Z->dtype == RS_F64 || Z->dtype == RS_F32 || Z->dtype == RS_BF16 || (allow_fp8 && Z->dtype == RS_FP8E4M3),
+               "components: dtype must be RS_F64, RS_F32 or RS_BF16 (RS_FP8E4M3 where stated)");
   RS_CHECK_ARG(n >= 1 && n < Z->n && Z->n - n == Z->d, "components: Z must have n + d rows");
   return RS_OK;
 }
@@ -464,12 +487,18 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, con
   const int32_t dt = sizeof(T) == 8 ? RS_F64 : RS_F32;
   const double lam = p->lambda;
   T* beta = const_cast<T*>(beta_in);
+  if constexpr (IsFp8<S>::value) {
+    if (!beta || !(p->refine && X))
+      return rs_fail(RS_EINVAL, "rs_svrg_solve: FP8 components need beta (from rs_precondition) and refine with X");
+  }
   if (!beta) {
     beta = static_cast<T*>(rs_scratch(ctx, SCR_BETA, N * sizeof(T)));
     if (!beta) return RS_ENOMEM;
-    row_beta_only_kernel<S, T><<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(static_cast<const S*>(Z->data), N, n,
-                                                                                  d, Z->ld, lam, beta);
-    RS_LAUNCH_CHECK(ctx);
+    if constexpr (!IsFp8<S>::value) {
+      row_beta_only_kernel<S, T><<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(static_cast<const S*>(Z->data), N,
+                                                                                    n, d, Z->ld, lam, beta);
+      RS_LAUNCH_CHECK(ctx);
+    }
   }
   uint32_t* W = static_cast<uint32_t*>(rs_scratch(ctx, SCR_W, N * sizeof(uint32_t)));
   uint64_t* cum = static_cast<uint64_t*>(rs_scratch(ctx, SCR_CUM, N * sizeof(uint64_t)));
@@ -493,10 +522,40 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, con
   T* wa = static_cast<T*>(rs_scratch(ctx, SCR_WBAR, d * sizeof(T)));
   T* wb = static_cast<T*>(rs_scratch(ctx, SCR_WNEXT, d * sizeof(T)));
   T* mu = static_cast<T*>(rs_scratch(ctx, SCR_MU, d * sizeof(T)));
-  uint32_t* idx = static_cast<uint32_t*>(rs_scratch(ctx, SCR_IDX, m * sizeof(uint32_t)));
-  T* inq = static_cast<T*>(rs_scratch(ctx, SCR_INVNQ, m * sizeof(T)));
+  // two sets of per-epoch data: the next epoch's index stream and R matrices are prepared on a
+  // second stream (on SMs the inner loop leaves idle) while the current epoch runs
+  const int64_t nblk = (m + kChainBlk - 1) / kChainBlk;
+  uint32_t* idx2 = static_cast<uint32_t*>(rs_scratch(ctx, SCR_IDX, 2 * m * sizeof(uint32_t)));
+  T* inq2 = static_cast<T*>(rs_scratch(ctx, SCR_INVNQ, 2 * m * sizeof(T)));
+  T* Rt2 = static_cast<T*>(rs_scratch(ctx, SCR_R, 2 * (size_t)nblk * kChainBlk * kChainBlk * sizeof(T)));
+  T* cv2 = static_cast<T*>(rs_scratch(ctx, SCR_C, 2 * (size_t)nblk * kChainBlk * sizeof(T)));
   T* tmp = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, 2 * d * sizeof(T)));
-  if (!wa || !wb || !mu || !idx || !inq || !tmp) return RS_ENOMEM;
+  if (!wa || !wb || !mu || !idx2 || !inq2 || !Rt2 || !cv2 || !tmp) return RS_ENOMEM;
+  SideStream sd;
+  sd.main = ctx->stream;
+  RS_CUDA_TRY(cudaStreamCreateWithFlags(&sd.side, cudaStreamNonBlocking));
+  sd.ctx = ctx;
+  for (int q = 0; q < 2; ++q) {
+    RS_CUDA_TRY(cudaEventCreateWithFlags(&sd.ready[q], cudaEventDisableTiming));
+    RS_CUDA_TRY(cudaEventCreateWithFlags(&sd.used[q], cudaEventDisableTiming));
+  }
+  RS_CUDA_TRY(cudaEventCreateWithFlags(&sd.start, cudaEventDisableTiming));
+  auto set_idx = [&](int q) { return idx2 + (int64_t)q * m; };
+  auto set_inq = [&](int q) { return inq2 + (int64_t)q * m; };
+  auto set_rt = [&](int q) { return Rt2 + (int64_t)q * nblk * kChainBlk * kChainBlk; };
+  auto set_cv = [&](int q) { return cv2 + (int64_t)q * nblk * kChainBlk; };
+  // index stream and R of epoch s into set s & 1, on the second stream
+  auto prepare = [&](int s) -> int {
+    const int q = s & 1;
+    ctx->stream = sd.side;
+    int rc = index_stream_dispatch(ctx, W, cum, N, p->seed, (int64_t)p->epoch0 + s, 0, m, p->sampling, dt, set_idx(q),
+                                   set_inq(q));
+    if (rc == RS_OK) rc = epoch_prep_r_t<S, T>(ctx, Z, n, lam, set_idx(q), set_inq(q), m, eta, set_rt(q), set_cv(q));
+    ctx->stream = sd.main;
+    if (rc != RS_OK) return rc;
+    RS_CUDA_TRY(cudaEventRecord(sd.ready[q], sd.side));
+    return RS_OK;
+  };
   const bool refine = p->refine && X;
   if (w0) RS_CUDA_TRY(cudaMemcpyAsync(wa, w0, d * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
   else RS_CUDA_TRY(cudaMemsetAsync(wa, 0, d * sizeof(T), ctx->stream));
@@ -508,7 +567,12 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, con
     RS_CUDA_TRY(cudaEventRecord(ev[0], ctx->stream));
   }
   double* norms = scal + 4;
+  // the second stream starts after the sampling table (built on the main stream) is complete
+  RS_CUDA_TRY(cudaEventRecord(sd.start, ctx->stream));
+  RS_CUDA_TRY(cudaStreamWaitEvent(sd.side, sd.start, 0));
+  if (nep > 0) RS_TRY(prepare(0));
   for (int s = 0; s < nep; ++s) {
+    const int q = s & 1;
     const bool want_norm = hist && hist->mu_norm2;
     if (refine) {
       T* u = tmp;
@@ -523,10 +587,17 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, con
         RS_LAUNCH_CHECK(ctx);
       }
     } else {
-      RS_TRY(full_gradient_t<S, T>(ctx, Z, y, n, lam, wa, mu, want_norm ? norms + s : nullptr));
+      if constexpr (!IsFp8<S>::value)
+        RS_TRY(full_gradient_t<S, T>(ctx, Z, y, n, lam, wa, mu, want_norm ? norms + s : nullptr));
     }
-    RS_TRY(index_stream_dispatch(ctx, W, cum, N, p->seed, (int64_t)p->epoch0 + s, 0, m, p->sampling, dt, idx, inq));
-    RS_TRY(svrg_epoch_t<S, T>(ctx, Z, n, lam, idx, inq, m, eta, wa, mu, p->average, wb));
+    RS_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, sd.ready[q], 0));
+    RS_TRY(epoch_finish_t<S, T>(ctx, Z, set_idx(q), m, eta, set_rt(q), set_cv(q), wa, mu, p->average, wb));
+    RS_CUDA_TRY(cudaEventRecord(sd.used[q], ctx->stream));
+    if (s + 1 < nep) {
+      // set q ^ 1 was last read by epoch s - 1
+      if (s >= 1) RS_CUDA_TRY(cudaStreamWaitEvent(sd.side, sd.used[q ^ 1], 0));
+      RS_TRY(prepare(s + 1));
+    }
     std::swap(wa, wb);
     if (hist && hist->snapshots && s < hist->capacity)
       RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, static_cast<T*>(hist->snapshots) + (int64_t)s * d));
@@ -694,10 +765,14 @@ int rs_full_gradient(rs_ctx* ctx, const rs_matrix* Z, const void* y, int64_t n, 
 int rs_svrg_epoch(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lambda, const uint32_t* idx, const void* inv_nq,
                   int64_t m, double eta, const void* w_bar, const void* mu, int32_t average, void* w_next) {
   RS_TRY(rs_enter(ctx));
-  RS_TRY(check_components(Z, n));
+  RS_TRY(check_components(Z, n, true));
   RS_CHECK_ARG(idx && inv_nq && w_bar && mu && w_next, "rs_svrg_epoch: null argument");
   RS_CHECK_ARG(m >= 1 && m < (1LL << 31), "rs_svrg_epoch: m out of range");
   RS_CHECK_ARG(w_next != w_bar, "rs_svrg_epoch: w_next must not alias w_bar");
+  if (Z->dtype == RS_FP8E4M3)
+    return svrg_epoch_t<__nv_fp8_e4m3, float>(ctx, Z, n, lambda, idx, static_cast<const float*>(inv_nq), m, eta,
+                                              static_cast<const float*>(w_bar), static_cast<const float*>(mu), average,
+                                              static_cast<float*>(w_next));
   if (Z->dtype == RS_F64)
     return svrg_epoch_t<double, double>(ctx, Z, n, lambda, idx, static_cast<const double*>(inv_nq), m, eta,
                                         static_cast<const double*>(w_bar), static_cast<const double*>(mu), average,
@@ -717,7 +792,7 @@ int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const voi
   RS_TRY(rs_enter(ctx));
   RS_CHECK_ARG(Z && p, "rs_svrg_solve: null argument");
   const int64_t n = Z->n - Z->d;
-  RS_TRY(check_components(Z, n));
+  RS_TRY(check_components(Z, n, true));
   RS_CHECK_ARG(y && V && sigma2 && w_out, "rs_svrg_solve: null argument");
   RS_CHECK_ARG(k >= 1 && k <= Z->d, "rs_svrg_solve: k must be in [1, d]");
   RS_CHECK_ARG(p->lambda > 0.0, "rs_svrg_solve: lambda must be positive");
@@ -727,8 +802,20 @@ int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const voi
     RS_CHECK_ARG(X != nullptr, "rs_svrg_solve: refinement needs the stored data X");
     RS_TRY(check_matrix(X, "rs_svrg_solve X"));
     RS_CHECK_ARG(X->n == n && X->d == Z->d, "rs_svrg_solve: X must be n x d");
-    RS_CHECK_ARG(X->dtype == Z->dtype || (Z->dtype == RS_BF16 && X->dtype == RS_F32),
-                 "rs_svrg_solve: X must be stored like Z (or in RS_F32 for RS_BF16 components)");
+    RS_CHECK_ARG(X->dtype == Z->dtype || (Z->dtype == RS_BF16 && X->dtype == RS_F32) ||
+                     (Z->dtype == RS_FP8E4M3 && (X->dtype == RS_F32 || X->dtype == RS_BF16)),
+                 "rs_svrg_solve: X must be stored like Z (or in RS_F32 for RS_BF16 components, RS_F32 or RS_BF16 "
+                 "for RS_FP8E4M3 components)");
+  }
+  if (Z->dtype == RS_FP8E4M3) {
+    RS_CHECK_ARG(p->refine && X && beta, "rs_svrg_solve: FP8 components need refine, X and beta");
+    if (X->dtype == RS_F32)
+      return svrg_solve_t<__nv_fp8_e4m3, float, float>(
+          ctx, Z, X, static_cast<const float*>(y), static_cast<const float*>(beta), static_cast<const float*>(V),
+          sigma2, k, p, static_cast<const float*>(w0), static_cast<float*>(w_out), hist, eta_used, m_used);
+    return svrg_solve_t<__nv_fp8_e4m3, float, __nv_bfloat16>(
+        ctx, Z, X, static_cast<const float*>(y), static_cast<const float*>(beta), static_cast<const float*>(V), sigma2,
+        k, p, static_cast<const float*>(w0), static_cast<float*>(w_out), hist, eta_used, m_used);
   }
   if (Z->dtype == RS_F64)
     return svrg_solve_t<double, double, double>(ctx, Z, X, static_cast<const double*>(y),
