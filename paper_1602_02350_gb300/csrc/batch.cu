@@ -81,6 +81,79 @@ __global__ void sub_labels_kernel(float* R, int64_t n, int r, const float* y) {
     R[e] -= y[e / r];
 }
 
+// Skinny products of a problem's stored data with its chains' vectors (R <= RMAX columns), each one
+// streaming pass over X:  Rm = X U - y 1^T (warp per row, R dot products), and G = X^T Rm / n
+// (thread per column over a chunk of rows, R accumulators; chunk partials summed in chunk order).
+template <typename S, int RMAX>
+__global__ void __launch_bounds__(256) skinny_xu_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
+                                                        const float* __restrict__ U, int R, const float* __restrict__ y,
+                                                        float* __restrict__ Rm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw) {
+    float acc[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) acc[r] = 0.0f;
+    const S* row = X + i * ld;
+    for (int64_t c = lane; c < d; c += 32) {
+      const float xv = cvt<float>(row[c]);
+      const float* u = U + c * R;
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r < R) acc[r] = fmaf(xv, u[r], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r)
+      if (r < R) acc[r] = warp_sum(acc[r]);
+    if (lane == 0) {
+      const float yi = y[i];
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r < R) Rm[i * R + r] = acc[r] - yi;
+    }
+  }
+}
+
+template <typename S, int RMAX>
+__global__ void __launch_bounds__(256) skinny_xtr_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
+                                                         const float* __restrict__ Rm, int R, int64_t rows_per_chunk,
+                                                         float* __restrict__ part) {
+  __shared__ float rs[64 * RMAX];
+  const int64_t c = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * rows_per_chunk, i1 = min64(n, i0 + rows_per_chunk);
+  float acc[RMAX];
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) acc[r] = 0.0f;
+  for (int64_t b0 = i0; b0 < i1; b0 += 64) {
+    const int nb = (int)min64(64, i1 - b0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * R; e += blockDim.x) rs[(e / R) * RMAX + e % R] = Rm[(b0 + e / R) * R + e % R];
+    __syncthreads();
+    if (c < d) {
+      for (int ii = 0; ii < nb; ++ii) {
+        const float xv = cvt<float>(X[(b0 + ii) * ld + c]);
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) acc[r] = fmaf(xv, rs[ii * RMAX + r], acc[r]);
+      }
+    }
+  }
+  if (c < d) {
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r)
+      if (r < R) part[((int64_t)blockIdx.x * d + c) * R + r] = acc[r];
+  }
+}
+
+// G[c][r] = (1/n) sum over chunks of the partials, in chunk order, in double
+__global__ void skinny_reduce_kernel(const float* __restrict__ part, int nchunks, int64_t dr, double inv_n,
+                                     double* __restrict__ G) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < dr; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nchunks; ++q) s += (double)part[(int64_t)q * dr + e];
+    G[e] = s * inv_n;
+  }
+}
+
 int blocks_cap(rs_ctx* ctx, int64_t work) {
   int64_t g = (work + 255) / 256;
   g = std::min<int64_t>(g, (int64_t)ctx->num_sms * 8);
@@ -365,12 +438,34 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
         if (pw[p].R == 0) continue;
         const rs_matrix& X = P[p].X;
         const int64_t n = X.n, d = X.d, R = pw[p].R;
-        RS_TRY(launch_gemm<float, S, float>(ctx, n, R, d, 1.0, static_cast<const S*>(X.data), X.ld, 1, pw[p].U, R, 1,
-                                            0.0, nullptr, 0, pw[p].Rm, R, nullptr));
-        sub_labels_kernel<<<blocks_cap(ctx, n * R), 256, 0, ctx->stream>>>(pw[p].Rm, n, (int)R, P[p].y);
-        RS_LAUNCH_CHECK(ctx);
-        RS_TRY(launch_gram<S, float>(ctx, n, d, R, static_cast<const S*>(X.data), X.ld, pw[p].Rm, R, 1.0 / (double)n,
-                                     pw[p].G));
+        const S* Xd = static_cast<const S*>(X.data);
+        if (R <= 32) {
+          // two streaming passes over X with the R columns in registers
+          const int xu_blocks = blocks_cap(ctx, n * 32);
+          if (R <= 8) skinny_xu_kernel<S, 8><<<xu_blocks, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].U, (int)R, P[p].y, pw[p].Rm);
+          else if (R <= 16) skinny_xu_kernel<S, 16><<<xu_blocks, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].U, (int)R, P[p].y, pw[p].Rm);
+          else skinny_xu_kernel<S, 32><<<xu_blocks, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].U, (int)R, P[p].y, pw[p].Rm);
+          RS_LAUNCH_CHECK(ctx);
+          const int cb = (int)((d + 255) / 256);
+          const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 4 / cb, (n + 63) / 64));
+          const int64_t rpc = (n + nch - 1) / nch;
+          float* part = static_cast<float*>(rs_scratch(ctx, SCR_BPART, (size_t)nch * d * R * sizeof(float)));
+          if (!part) return RS_ENOMEM;
+          dim3 g2((unsigned)nch, (unsigned)cb);
+          if (R <= 8) skinny_xtr_kernel<S, 8><<<g2, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part);
+          else if (R <= 16) skinny_xtr_kernel<S, 16><<<g2, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part);
+          else skinny_xtr_kernel<S, 32><<<g2, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part);
+          RS_LAUNCH_CHECK(ctx);
+          skinny_reduce_kernel<<<blocks_cap(ctx, d * R), 256, 0, ctx->stream>>>(part, nch, d * R, 1.0 / (double)n,
+                                                                                pw[p].G);
+          RS_LAUNCH_CHECK(ctx);
+        } else {
+          RS_TRY(launch_gemm<float, S, float>(ctx, n, R, d, 1.0, Xd, X.ld, 1, pw[p].U, R, 1, 0.0, nullptr, 0, pw[p].Rm,
+                                              R, nullptr));
+          sub_labels_kernel<<<blocks_cap(ctx, n * R), 256, 0, ctx->stream>>>(pw[p].Rm, n, (int)R, P[p].y);
+          RS_LAUNCH_CHECK(ctx);
+          RS_TRY(launch_gram<S, float>(ctx, n, d, R, Xd, X.ld, pw[p].Rm, R, 1.0 / (double)n, pw[p].G));
+        }
       }
       bmap_kernel<<<nc, 256, 0, ctx->stream>>>(mumap_dev, 0, ctx->d_status);
       RS_LAUNCH_CHECK(ctx);

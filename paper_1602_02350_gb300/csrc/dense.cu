@@ -157,44 +157,58 @@ __global__ void convert_from_double_kernel(const double* in, int64_t count, T* o
 template <typename T>
 __global__ void chol_inv_kernel(const double* G, int k, double* buf, T* Linv_out, int* status) {
   extern __shared__ double ci_sh[];
+  // rows padded to k + 1: column accesses by consecutive threads spread over the banks
+  const int LD = k + 1;
   double* L = buf ? buf : ci_sh;
-  double* Xi = L + (size_t)k * k;
+  double* Xi = L + (size_t)k * LD;
+  double* dinv = Xi + (size_t)k * LD;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < k * k; e += nt) {
-    L[e] = G[e];
-    Xi[e] = 0.0;
+    const int r = e / k, c = e % k;
+    L[r * LD + c] = G[e];
+    Xi[r * LD + c] = 0.0;
   }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
     if (tid == 0) {
-      double v = L[j * k + j];
+      double v = L[j * LD + j];
       if (!(v > 0.0) || !isfinite(v)) {
         atomicOr(status, 4);
         v = 1.0;
       }
-      L[j * k + j] = sqrt(v);
+      const double r = sqrt(v);
+      L[j * LD + j] = r;
+      dinv[j] = 1.0 / r;
     }
     __syncthreads();
-    const double djj = L[j * k + j];
-    for (int i = j + 1 + tid; i < k; i += nt) L[i * k + j] /= djj;
+    const double rj = dinv[j];
+    for (int i = j + 1 + tid; i < k; i += nt) L[i * LD + j] *= rj;
     __syncthreads();
     const int w = k - j - 1;
     for (int e = tid; e < w * w; e += nt) {
       const int i = j + 1 + e / w, l = j + 1 + e % w;
-      if (l <= i) L[i * k + l] -= L[i * k + j] * L[l * k + j];
+      if (l <= i) L[i * LD + l] -= L[i * LD + j] * L[l * LD + j];
     }
     __syncthreads();
   }
+  // column c of L^{-1} by forward substitution, four interleaved partial sums
   for (int c = tid; c < k; c += nt) {
-    Xi[c * k + c] = 1.0 / L[c * k + c];
+    Xi[c * LD + c] = dinv[c];
     for (int i = c + 1; i < k; ++i) {
-      double s = 0.0;
-      for (int p = c; p < i; ++p) s = fma(L[i * k + p], Xi[p * k + c], s);
-      Xi[i * k + c] = -s / L[i * k + i];
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int p = c;
+      for (; p + 3 < i; p += 4) {
+        s0 = fma(L[i * LD + p], Xi[p * LD + c], s0);
+        s1 = fma(L[i * LD + p + 1], Xi[(p + 1) * LD + c], s1);
+        s2 = fma(L[i * LD + p + 2], Xi[(p + 2) * LD + c], s2);
+        s3 = fma(L[i * LD + p + 3], Xi[(p + 3) * LD + c], s3);
+      }
+      for (; p < i; ++p) s0 = fma(L[i * LD + p], Xi[p * LD + c], s0);
+      Xi[i * LD + c] = -((s0 + s1) + (s2 + s3)) * dinv[i];
     }
   }
   __syncthreads();
-  for (int e = tid; e < k * k; e += nt) Linv_out[e] = (T)Xi[e];
+  for (int e = tid; e < k * k; e += nt) Linv_out[e] = (T)Xi[(e / k) * LD + e % k];
 }
 
 // ------------------------------------------------------------------ Jacobi eigensolver
@@ -507,6 +521,44 @@ __global__ void trace_finish_kernel(const double* part, int np, double inv_n, do
   }
 }
 
+// w = M x = x - V diag(a) V^T x in one block (a_j = 1 - D'_j from sigma2): partial sums of V^T x by
+// (column, row-group), a fixed-order combine, then each thread forms its entries of w.  A is the
+// accumulation type (double for double data).
+template <typename T, typename A>
+__global__ void __launch_bounds__(1024) map_fused_kernel(const T* __restrict__ V, const double* __restrict__ sigma2,
+                                                         int64_t d, int k, double lam, const T* __restrict__ x,
+                                                         T* __restrict__ y) {
+  __shared__ A part[1024];
+  __shared__ A tv[256];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int G = nt / k;                    // row groups (k <= 256 so G >= 4)
+  const int j = tid % k, g = tid / k;
+  if (g < G) {
+    A s = A(0);
+    for (int64_t c = g; c < d; c += G) s += (A)V[c * k + j] * (A)x[c];
+    part[g * k + j] = s;
+  }
+  __syncthreads();
+  if (tid < k) {
+    A t = A(0);
+    for (int q = 0; q < G; ++q) t += part[q * k + tid];   // fixed order
+    const double a = 1.0 - sqrt((sigma2[k - 1] + lam) / (sigma2[tid] + lam));
+    tv[tid] = (A)a * t;
+  }
+  __syncthreads();
+  for (int64_t c = tid; c < d; c += nt) {
+    const T* v = V + c * k;
+    A s0 = A(0), s1 = A(0);
+    int q = 0;
+    for (; q + 1 < k; q += 2) {
+      s0 += (A)v[q] * tv[q];
+      s1 += (A)v[q + 1] * tv[q + 1];
+    }
+    if (q < k) s0 += (A)v[q] * tv[q];
+    y[c] = (T)((A)x[c] - (s0 + s1));
+  }
+}
+
 // mean of a float vector in double (one block)
 __global__ void mean_f_kernel(const float* v, int64_t N, double* out) {
   __shared__ double sh[32];
@@ -692,7 +744,7 @@ static int orthonormalize_t(rs_ctx* ctx, const T* Y, int64_t d, int64_t k, T* Q)
   T* tmp = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, d * k * sizeof(T)));
   T* Linv = static_cast<T*>(rs_scratch(ctx, SCR_LINV, k * k * sizeof(T)));
   if (!G || !tmp || !Linv) return RS_ENOMEM;
-  const size_t bytes = 2 * (size_t)k * k * sizeof(double);
+  const size_t bytes = (2 * (size_t)k * (k + 1) + k) * sizeof(double);   // L, L^{-1} (rows k + 1), 1/diag
   const bool smem = bytes <= 160 * 1024;
   double* buf = nullptr;
   if (!smem) {
@@ -870,6 +922,11 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
 template <typename T>
 static int map_output_t(rs_ctx* ctx, const T* V, const double* sigma2, int64_t d, int64_t k, double lam, const T* wt,
                         T* w) {
+  if (k <= 256) {   // one launch
+    map_fused_kernel<T, T><<<1, 1024, 0, ctx->stream>>>(V, sigma2, d, (int)k, lam, wt, w);
+    RS_LAUNCH_CHECK(ctx);
+    return RS_OK;
+  }
   T* a = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, k * sizeof(T)));
   double* tv = static_cast<double*>(rs_scratch(ctx, SCR_RED, k * sizeof(double)));
   if (!a || !tv) return RS_ENOMEM;

@@ -472,11 +472,6 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
         cp_async16(zdst + j * ZS + col, src, bytes);
       }
     }
-    const T* rsrc = Rt + blk * (int64_t)B * B;
-    T* rdst = Rs + (size_t)slot * B * B;
-#pragma unroll
-    for (int e = tid; e < B * B / E; e += NT) cp_async16(rdst + e * E, rsrc + e * E, 16);
-    if (tid < B / E) cp_async16(Cs + (size_t)slot * B + tid * E, cvec + blk * B + tid * E, 16);
   };
 
 #pragma unroll
@@ -508,6 +503,21 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
     const float myscale = (F8 && tid < B) ? sscale[slot * B + tid] : 1.0f;   // row tid of this block
     const int Bb = (int)min64(B, m - blk * B);
     const S* zs = Zs + (size_t)slot * B * ZS;
+    // this block's R column entries and c_j go straight from L2 into registers: issued here, used
+    // after the exchange, so their latency is hidden behind the dot products
+    constexpr int RPT = B / H;   // R entries per thread
+    T rreg[RPT];
+    T creg = T(0);
+    {
+      const int j = tid & (B - 1), h = tid >> 6;
+      const T* rsrc = Rt + blk * (int64_t)B * B + j;
+#pragma unroll
+      for (int t = 0; t < RPT; ++t) {
+        const int l = h + H * t;
+        rreg[t] = l <= j ? __ldg(rsrc + l * B) : T(0);
+      }
+      if (tid < B) creg = __ldg(cvec + blk * B + tid);
+    }
     // partial p_j over this block's columns for rows 8 warp .. 8 warp + 7, pushed to every rank
     {
       T dv[QN];
@@ -570,21 +580,18 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
     // above the diagonal, so the loop may run to the end of its group); fixed combine order below
     {
       const int j = tid & (B - 1), h = tid >> 6;
-      const T* rs = Rs + (size_t)slot * B * B + j;
       T s0 = T(0), s1 = T(0);
-      const int lend = j + 1;
-      int l = h;
-      for (; l + H < lend; l += 2 * H) {
-        s0 = fma(rs[l * B], pv[l], s0);
-        s1 = fma(rs[(l + H) * B], pv[l + H], s1);
+#pragma unroll
+      for (int t = 0; t < RPT; t += 2) {
+        s0 = fma(rreg[t], pv[h + H * t], s0);
+        if (t + 1 < RPT) s1 = fma(rreg[t + 1], pv[h + H * (t + 1)], s1);
       }
-      if (l < lend) s0 = fma(rs[l * B], pv[l], s0);
       part4[h * B + j] = s0 + s1;
     }
     __syncthreads();
     if (tid < B)
     {
-      T sa = Cs[(size_t)slot * B + tid];
+      T sa = creg;
 #pragma unroll
       for (int hh = 0; hh < H; ++hh) sa += part4[hh * B + tid];   // fixed order
       av[tid] = F8 ? sa * myscale : sa;   // the update multiplies stored codes
