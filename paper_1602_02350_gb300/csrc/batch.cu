@@ -84,10 +84,20 @@ __global__ void sub_labels_kernel(float* R, int64_t n, int r, const float* y) {
 // Skinny products of a problem's stored data with its chains' vectors (R <= RMAX columns), each one
 // streaming pass over X:  Rm = X U - y 1^T (warp per row, R dot products), and G = X^T Rm / n
 // (thread per column over a chunk of rows, R accumulators; chunk partials summed in chunk order).
-template <typename S, int RMAX>
+template <typename S, int RMAX, bool USM>
 __global__ void __launch_bounds__(256) skinny_xu_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
                                                         const float* __restrict__ U, int R, const float* __restrict__ y,
                                                         float* __restrict__ Rm) {
+  // USM: U (d x R) is staged once per block in shared memory, columns padded to RMAX (zeros beyond R)
+  extern __shared__ float us[];   // [d][RMAX]
+  if (USM) {
+    for (int64_t e = threadIdx.x; e < d * RMAX; e += blockDim.x) {
+      const int64_t c = e / RMAX;
+      const int r = (int)(e % RMAX);
+      us[e] = r < R ? U[c * R + r] : 0.0f;
+    }
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw) {
     float acc[RMAX];
@@ -96,14 +106,25 @@ __global__ void __launch_bounds__(256) skinny_xu_kernel(const S* __restrict__ X,
     const S* row = X + i * ld;
     for (int64_t c = lane; c < d; c += 32) {
       const float xv = cvt<float>(row[c]);
-      const float* u = U + c * R;
+      if (USM) {
+        const float4* u4 = reinterpret_cast<const float4*>(us + c * RMAX);
 #pragma unroll
-      for (int r = 0; r < RMAX; ++r)
-        if (r < R) acc[r] = fmaf(xv, u[r], acc[r]);
+        for (int q = 0; q < RMAX / 4; ++q) {
+          const float4 u = u4[q];
+          acc[4 * q] = fmaf(xv, u.x, acc[4 * q]);
+          acc[4 * q + 1] = fmaf(xv, u.y, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(xv, u.z, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(xv, u.w, acc[4 * q + 3]);
+        }
+      } else {
+        const float* u = U + c * R;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) acc[r] = fmaf(xv, u[r], acc[r]);
+      }
     }
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r)
-      if (r < R) acc[r] = warp_sum(acc[r]);
+    for (int r = 0; r < RMAX; ++r) acc[r] = warp_sum(acc[r]);
     if (lane == 0) {
       const float yi = y[i];
 #pragma unroll
@@ -441,10 +462,26 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
         const S* Xd = static_cast<const S*>(X.data);
         if (R <= 32) {
           // two streaming passes over X with the R columns in registers
-          const int xu_blocks = blocks_cap(ctx, n * 32);
-          if (R <= 8) skinny_xu_kernel<S, 8><<<xu_blocks, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].U, (int)R, P[p].y, pw[p].Rm);
-          else if (R <= 16) skinny_xu_kernel<S, 16><<<xu_blocks, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].U, (int)R, P[p].y, pw[p].Rm);
-          else skinny_xu_kernel<S, 32><<<xu_blocks, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].U, (int)R, P[p].y, pw[p].Rm);
+          const int rmax = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
+          const size_t ushm = (size_t)d * rmax * sizeof(float);
+          const bool usm = ushm <= 96 * 1024;
+          const int xu_blocks = usm ? ctx->num_sms * 2 : blocks_cap(ctx, n * 32);
+#define RS_XU(RM)                                                                                                    \
+  do {                                                                                                               \
+    if (usm) {                                                                                                       \
+      RS_CUDA_TRY(cudaFuncSetAttribute(skinny_xu_kernel<S, RM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                       (int)ushm));                                                                  \
+      skinny_xu_kernel<S, RM, true><<<xu_blocks, 256, ushm, ctx->stream>>>(Xd, n, d, X.ld, pw[p].U, (int)R, P[p].y,  \
+                                                                           pw[p].Rm);                                \
+    } else {                                                                                                         \
+      skinny_xu_kernel<S, RM, false><<<xu_blocks, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].U, (int)R, P[p].y,    \
+                                                                         pw[p].Rm);                                  \
+    }                                                                                                                \
+  } while (0)
+          if (rmax == 8) RS_XU(8);
+          else if (rmax == 16) RS_XU(16);
+          else RS_XU(32);
+#undef RS_XU
           RS_LAUNCH_CHECK(ctx);
           const int cb = (int)((d + 255) / 256);
           const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 4 / cb, (n + 63) / 64));

@@ -255,6 +255,14 @@ struct ChainJob {
   int32_t average, reserved;
 };
 
+// Tensor-core (tcgen05) preparation of the blocked inner loop for bfloat16 components (umma.cu):
+// R and c of every block of steps, as the CUDA-core preparation computes them.  jobs == nullptr:
+// the single chain `one` over total_blocks blocks; otherwise CTA g serves the job j with
+// blk_off[j] <= g < blk_off[j + 1] (device arrays, every Z 16-byte aligned with ld % 8 == 0).
+// RS_EUNSUPPORTED when the tensor path is disabled or cannot run.
+int umma_prep(rs_ctx* ctx, const ChainJob<__nv_bfloat16, float>& one, const ChainJob<__nv_bfloat16, float>* jobs,
+              const int64_t* blk_off, int nj, int64_t total_blocks);
+
 // Index stream of one chain (float factors): sampling table W / cum over N components.
 struct IdxJob {
   const uint32_t* W;

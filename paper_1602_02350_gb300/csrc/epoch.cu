@@ -1133,6 +1133,32 @@ int launch_chain_la_batched(rs_ctx* ctx, const ChainPlan& pl, const ChainJob<S, 
 
 }  // namespace
 
+// The tensor-core preparation for bfloat16 components (RS_OK when it ran, RS_EUNSUPPORTED when
+// the CUDA-core kernel has to run instead).
+template <typename S, typename T>
+int try_umma_prep(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
+                  int64_t m, double eta, const T* mu, T* Rt, T* cv) {
+  if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<T, float>::value) {
+    ChainJob<S, T> one{};
+    one.Z = static_cast<const S*>(Z->data);
+    one.N = Z->n;
+    one.ld = Z->ld;
+    one.d = Z->d;
+    one.n = n;
+    one.m = m;
+    one.idx = idx;
+    one.inv_nq = inv_nq;
+    one.lam = lam;
+    one.eta = eta;
+    one.mu = mu;
+    one.Rt = Rt;
+    one.cvec = cv;
+    return umma_prep(ctx, one, nullptr, nullptr, 0, (m + kBlk - 1) / kBlk);
+  } else {
+    return RS_EUNSUPPORTED;
+  }
+}
+
 template <typename S, typename T>
 int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const uint32_t* idx, const T* inv_nq,
                  int64_t m, double eta, const T* wbar, const T* mu, int average, T* wnext) {
@@ -1169,11 +1195,16 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
     }
   }
   if (!la) {
-    constexpr size_t pshm = prep_smem_bytes<T, false>();
-    RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
-    epoch_prep_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m, eta,
-                                                                        mu, Rt, cv, Z->row_scale);
-    RS_LAUNCH_CHECK(ctx);
+    const int urc = try_umma_prep<S, T>(ctx, Z, n, lam, idx, inv_nq, m, eta, mu, Rt, cv);
+    if (urc != RS_OK && urc != RS_EUNSUPPORTED) return urc;
+    if (urc == RS_EUNSUPPORTED) {
+      constexpr size_t pshm = prep_smem_bytes<T, false>();
+      RS_CUDA_TRY(
+          cudaFuncSetAttribute(epoch_prep_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+      epoch_prep_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, N, Z->ld, d, n, lam, idx, inv_nq, m,
+                                                                          eta, mu, Rt, cv, Z->row_scale);
+      RS_LAUNCH_CHECK(ctx);
+    }
   }
   for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
     const ChainPlan pl = plan_chain<S, T>(d, cs);
@@ -1241,6 +1272,8 @@ int epoch_prep_r_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const
                    int64_t m, double eta, T* Rt, T* cv) {
   const S* Zd = static_cast<const S*>(Z->data);
   const int64_t nblk = (m + kBlk - 1) / kBlk;
+  const int urc = try_umma_prep<S, T>(ctx, Z, n, lam, idx, inv_nq, m, eta, (const T*)nullptr, Rt, cv);
+  if (urc != RS_EUNSUPPORTED) return urc;
   constexpr size_t pshm = prep_smem_bytes<T, false>();
   RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
   epoch_prep_kernel<S, T><<<(unsigned)nblk, 256, pshm, ctx->stream>>>(Zd, Z->n, Z->ld, Z->d, n, lam, idx, inv_nq, m,
@@ -1342,6 +1375,10 @@ int epoch_prep_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, const int64_t* b
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
     epoch_prep_batched_kernel<S, T, true><<<(unsigned)total_blocks, 256, pshm, ctx->stream>>>(jobs, blk_off, nj);
   } else {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<T, float>::value) {
+      const int urc = umma_prep(ctx, ChainJob<S, T>{}, jobs, blk_off, nj, total_blocks);
+      if (urc != RS_EUNSUPPORTED) return urc;
+    }
     constexpr size_t pshm = prep_smem_bytes<T, false>();
     RS_CUDA_TRY(cudaFuncSetAttribute(epoch_prep_batched_kernel<S, T, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));

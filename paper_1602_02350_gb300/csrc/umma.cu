@@ -178,6 +178,253 @@ __global__ void __launch_bounds__(128, 1) umma_xw_kernel(const __grid_constant__
   }
 }
 
+// ------------------------------------------------------------------ block preparation
+// R = (I + eta K L)^{-1} K and c = -eta R (j . h) of one block of 64 inner steps (the blocked form
+// of the inner loop of Alg. 1; K = diag(kappa) the importance weights of the sampled rows, L the
+// strictly lower part of their Gram matrix G, h_l = mu^T z_l) for bfloat16 components.  The Gram
+// matrix is a dense contraction over d: the CTA gathers the 64 sampled rows chunk by chunk (64
+// columns, 128 bytes per row) into a 128-row tile in the 128-byte-swizzled K-major layout with
+// 16-byte cp.async copies, rows 64..66 hold mu split into three bfloat16 parts (mu = m0 + m1 + m2
+// to about 2^-24 relative), rows 67..127 are zero, and one thread issues tcgen05.mma (M = 128,
+// N = 64: D = tile x rows 0..63^T, FP32 accumulation in tensor memory).  Products of bfloat16
+// values are exact in FP32, so G matches the CUDA-core Gram matrix up to summation order.  After
+// the last chunk warps 0-1 read G (accumulator lanes 0..63) and warp 2 the mu rows (lanes 64..66)
+// into shared memory; then each of the 64 threads of warps 0-1 forward-substitutes one column of
+// R (r_l = kappa_l (delta_lc - eta sum_{l'<l} G_ll' r_l')) in registers, and warp 2 the vector
+// R (j . h) the same way (right-hand side kappa_l l h_l), with no block-wide barrier inside.
+constexpr int PST = 3;                       // ring stages (64 columns each)
+constexpr uint32_t P_STAGE = 128 * 128;      // 128 rows x 128 bytes
+constexpr int GLD = 68;                      // Gram row stride in floats (16-byte rows)
+constexpr uint32_t kPrepIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(cta_smem_addr(smem)), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+
+// r_l = kap_l (rhs_l - et sum_{l' < l} G[l][l'] r_l') for l = 0..63; rhs = e_c for c >= 0, else v
+__device__ __forceinline__ void block_fwd_subst(const float* __restrict__ G, const float* __restrict__ kap,
+                                                const float* __restrict__ v, int c, float et, float (&r)[64]) {
+#pragma unroll
+  for (int l = 0; l < 64; ++l) {
+    const float* Gl = G + l * GLD;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < l / 4; ++q) {
+      const float4 g = *reinterpret_cast<const float4*>(Gl + 4 * q);
+      s0 = fmaf(g.x, r[4 * q], s0);
+      s1 = fmaf(g.y, r[4 * q + 1], s1);
+      s2 = fmaf(g.z, r[4 * q + 2], s2);
+      s3 = fmaf(g.w, r[4 * q + 3], s3);
+    }
+#pragma unroll
+    for (int e = (l / 4) * 4; e < l; ++e) s0 = fmaf(Gl[e], r[e], s0);
+    const float s = (s0 + s1) + (s2 + s3);
+    const float rhs = c >= 0 ? (l == c ? 1.0f : 0.0f) : v[l];
+    r[l] = kap[l] * fmaf(-et, s, rhs);
+  }
+}
+
+// Grid: one CTA per block of steps.  jobs == nullptr: every CTA belongs to `one`; otherwise CTA g
+// belongs to job j with blk_off[j] <= g < blk_off[j + 1].
+__global__ void __launch_bounds__(128, 4) umma_prep_kernel(const __grid_constant__ ChainJob<__nv_bfloat16, float> one,
+                                                           const ChainJob<__nv_bfloat16, float>* __restrict__ jobs,
+                                                           const int64_t* __restrict__ blk_off, int nj, int* status) {
+  extern __shared__ unsigned char up_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(up_raw) + 1023) & ~uintptr_t(1023));
+  float* G = reinterpret_cast<float*>(base);   // [64][GLD], over the ring once every MMA has completed
+  __shared__ uint64_t empty[PST], done;
+  __shared__ uint32_t tmem_holder;
+  __shared__ float kap[64], vv[64], hpart[3][64];
+  __shared__ int64_t rowid[64];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int64_t b = blockIdx.x;
+  const ChainJob<__nv_bfloat16, float>* Jp = &one;
+  if (jobs) {
+    int lo = 0, hi = nj - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (blk_off[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    Jp = jobs + lo;
+    b -= blk_off[lo];
+  }
+  const __nv_bfloat16* __restrict__ Z = Jp->Z;
+  const int64_t N = Jp->N, ld = Jp->ld, d = Jp->d, n = Jp->n, m = Jp->m;
+  const float* __restrict__ mu = Jp->mu;
+  const float et = (float)Jp->eta;
+  const int64_t t0 = b * 64;
+  const int Bb = (int)min64(64, m - t0);
+  if (tid < 64) {
+    if (tid < Bb) {
+      const uint32_t i = min(Jp->idx[t0 + tid], (uint32_t)(N - 1));   // indices are < N by contract
+      rowid[tid] = i;
+      const float Nn = (float)((double)N / (double)n), lN = (float)(Jp->lam * (double)N);
+      kap[tid] = (i < (uint64_t)n ? Nn : lN) * Jp->inv_nq[t0 + tid];
+    } else {
+      rowid[tid] = -1;
+      kap[tid] = 0.0f;
+    }
+  }
+  if (tid == 0) {
+    for (int s = 0; s < PST; ++s) mbar_init_cta(&empty[s], 1);
+    mbar_init_cta(&done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(cta_smem_addr(&tmem_holder)),
+                 "r"(64)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  // rows 64..127 of every stage start at zero (rows 64..66 take mu's parts per chunk)
+  for (int e = tid; e < PST * 64 * 8; e += 128) {
+    const int s = e / 512, r = 64 + (e % 512) / 8, q = e % 8;
+    *reinterpret_cast<uint4*>(base + s * P_STAGE + r * 128 + q * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+  const int nch = (int)((d + 63) / 64);
+  auto fill = [&](int kc, int s) {
+    unsigned char* st = base + s * P_STAGE;
+    const int64_t c0 = (int64_t)kc * 64;
+    for (int e = tid; e < 64 * 8; e += 128) {
+      const int r = e >> 3, q = e & 7;
+      const int64_t col = c0 + q * 8;
+      const int64_t rid = rowid[r];
+      const void* src = Z;
+      int bytes = 0;
+      if (rid >= 0 && col < d) {
+        src = Z + rid * ld + col;
+        bytes = (int)min64(8, d - col) * 2;
+      }
+      cp_async16_zfill(st + r * 128 + ((q ^ (r & 7)) << 4), src, bytes);
+    }
+    if (mu && tid < 8) {
+      const int q = tid;
+      const int64_t col = c0 + q * 8;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = col + i < d ? mu[col + i] : 0.0f;
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const __nv_bfloat16 lo = __float2bfloat16_rn(v[2 * i]), hi = __float2bfloat16_rn(v[2 * i + 1]);
+          v[2 * i] -= __bfloat162float(lo);
+          v[2 * i + 1] -= __bfloat162float(hi);
+          w[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        const int r = 64 + p;
+        *reinterpret_cast<uint4*>(st + r * 128 + ((q ^ (r & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  for (int kc = 0; kc < PST - 1; ++kc) {
+    if (kc < nch) fill(kc, kc);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  for (int kc = 0; kc < nch; ++kc) {
+    const int kn = kc + PST - 1;
+    if (kn < nch) {
+      const int s = kn % PST;
+      // the stage was last read by the MMAs of chunk kn - PST
+      if (kn >= PST && !mbar_wait_bounded(&empty[s], (uint32_t)(((kn - PST) / PST) & 1), kUmmaWait))
+        atomicOr(status, STATUS_TIMEOUT);
+      fill(kn, s);
+    } else {
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PST - 1) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // generic-proxy writes -> tensor core
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sa = cta_smem_addr(base + (kc % PST) * P_STAGE);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t da = smem_desc_sw128(sa + kk * 32);
+        const uint32_t accum = (kc | kk) != 0;
+        asm volatile(
+            "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(da), "r"(kPrepIdesc), "r"(accum)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       cta_smem_addr(&empty[kc % PST]))
+                   : "memory");
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (tid == 0)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     cta_smem_addr(&done))
+                 : "memory");
+  __syncwarp();
+  bool ok = mbar_wait_bounded(&done, 0u, kUmmaWait);
+  if (!ok && lane == 0) atomicOr(status, STATUS_TIMEOUT);
+  ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld is warp-collective
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  __syncthreads();   // every warp is past its wait before G overwrites the ring
+  if (warp < 3 && ok) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (warp < 2) {
+        float* gr = G + (warp * 32 + lane) * GLD + c0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<float4*>(gr + j) =
+              make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                          __uint_as_float(v[j + 3]));
+      } else if (lane < 3) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) hpart[lane][c0 + j] = __uint_as_float(v[j]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(64) : "memory");
+  }
+  if (tid < 64) vv[tid] = mu ? (float)tid * ((hpart[1][tid] + hpart[2][tid]) + hpart[0][tid]) : 0.0f;
+  __syncthreads();
+  if (warp < 3) {
+    float r[64];
+    block_fwd_subst(G, kap, vv, warp < 2 ? tid : -1, et, r);
+    if (warp < 2) {   // column tid of R is row tid of Rt
+      float* out = Jp->Rt + (b * 64 + tid) * 64;
+#pragma unroll
+      for (int j = 0; j < 64; j += 4) *reinterpret_cast<float4*>(out + j) = make_float4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+    } else if (lane == 0) {
+      float* out = Jp->cvec + b * 64;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) out[j] = (mu && j < Bb) ? -et * r[j] : 0.0f;
+    }
+  }
+}
+
 // W (K x N float, row-major) -> parts (NSPLIT x kp x ldp bfloat16): part p row j = column j of
 // W_p, W = W0 + W1 + W2 with W_{p} = bf16(W - W_0 - .. - W_{p-1}); rows j >= N are zero
 __global__ void split_transpose_kernel(const float* __restrict__ W, int K, int N, int kp, int ldp,
@@ -229,6 +476,23 @@ int make_map(CUtensorMap* map, const void* ptr, int64_t inner, int64_t rows, int
 bool umma_enabled() {
   const char* env = std::getenv("RS_UMMA");
   return !(env && env[0] == '0');
+}
+
+// R and c of every block of steps of the given bfloat16 chains on tensor cores (on unless RS_UMMA=0
+// or RS_UMMA_PREP=0).  RS_EUNSUPPORTED when it cannot run: the caller uses the CUDA-core path.
+int umma_prep(rs_ctx* ctx, const ChainJob<__nv_bfloat16, float>& one, const ChainJob<__nv_bfloat16, float>* jobs,
+              const int64_t* blk_off, int nj, int64_t total_blocks) {
+  if (!umma_enabled()) return RS_EUNSUPPORTED;
+  const char* env = std::getenv("RS_UMMA_PREP");
+  if (env && env[0] == '0') return RS_EUNSUPPORTED;
+  if (total_blocks < 1) return RS_OK;
+  if (total_blocks > 0x7FFFFFFF) return RS_EUNSUPPORTED;
+  if (!jobs && ((reinterpret_cast<uintptr_t>(one.Z) & 15) || (one.ld & 7) || one.n < 1)) return RS_EUNSUPPORTED;
+  const size_t shm = (size_t)PST * P_STAGE + 1024;
+  RS_CUDA_TRY(cudaFuncSetAttribute(umma_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  umma_prep_kernel<<<(unsigned)total_blocks, 128, shm, ctx->stream>>>(one, jobs, blk_off, nj, ctx->d_status);
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
 }
 
 // C (M x N, float, ldc) = X (bfloat16 rows, M x K) W (K x N, float) diag(col_scale); N <= 256.

@@ -60,10 +60,13 @@ def test_full_gradient_bf16_matches_oracle(rsctx, n, d):
     np.testing.assert_allclose(mu, ref, rtol=0, atol=1e-5 * max(scale, np.abs(ref).max()))
 
 
-@pytest.mark.parametrize("n,d,m", [(50, 8, 1), (300, 64, 65), (2000, 256, 1000), (3000, 104, 777),
-                                   (8000, 1024, 4160), (4000, 2048, 640)])
+@pytest.mark.parametrize("n,d,m", [(50, 8, 1), (300, 64, 65), (2000, 256, 1000), (3000, 104, 777), (700, 100, 300),
+                                   (40, 3, 70), (8000, 1024, 4160), (4000, 2048, 640)])
 @pytest.mark.parametrize("average", [True, False])
-def test_epoch_bf16_matches_stepwise_oracle(rsctx, n, d, m, average):
+@pytest.mark.parametrize("tc_prep", ["1", "0"])
+def test_epoch_bf16_matches_stepwise_oracle(rsctx, monkeypatch, n, d, m, average, tc_prep):
+    """Both block preparations: tensor-core Gram matrices (tcgen05) and the CUDA-core kernel."""
+    monkeypatch.setenv("RS_UMMA_PREP", tc_prep)
     lam = 1e-3
     Z, Zd, y, yz, g = _bf16_components(n, d, 7 * n + d, lam)
     N = n + d
