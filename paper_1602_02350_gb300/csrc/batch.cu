@@ -81,87 +81,180 @@ __global__ void sub_labels_kernel(float* R, int64_t n, int r, const float* y) {
     R[e] -= y[e / r];
 }
 
-// Skinny products of a problem's stored data with its chains' vectors (R <= RMAX columns), each one
-// streaming pass over X:  Rm = X U - y 1^T (warp per row, R dot products), and G = X^T Rm / n
-// (thread per column over a chunk of rows, R accumulators; chunk partials summed in chunk order).
+// Skinny products of a problem's stored data with its chains' vectors (R <= RMAX columns; U and
+// Rm carry RMAX columns, the ones beyond R ignored), each one streaming pass over X at full load
+// width (16 bytes per lane):  Rm = X U - y 1^T  and  G = X^T Rm / n.
+// CPL consecutive columns of one row widened to float (vector loads when the row holds them all;
+// rows are 16-byte aligned by the C ABI's contract, c is a multiple of CPL)
+template <int CPL>
+__device__ __forceinline__ void ld_cols(const __nv_bfloat16* p, int64_t c, int64_t d, float* v) {
+  if (c + CPL <= d) {
+    uint32_t w[CPL / 2];
+    if constexpr (CPL == 8) {
+      const uint4 q = *reinterpret_cast<const uint4*>(p + c);
+      w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
+    } else if constexpr (CPL == 4) {
+      const uint2 q = *reinterpret_cast<const uint2*>(p + c);
+      w[0] = q.x; w[1] = q.y;
+    } else {
+      w[0] = *reinterpret_cast<const uint32_t*>(p + c);
+    }
+#pragma unroll
+    for (int k = 0; k < CPL / 2; ++k) {
+      v[2 * k] = __uint_as_float(w[k] << 16);
+      v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) v[e] = c + e < d ? __bfloat162float(p[c + e]) : 0.0f;
+  }
+}
+template <int CPL>
+__device__ __forceinline__ void ld_cols(const float* p, int64_t c, int64_t d, float* v) {
+  if (c + CPL <= d) {
+#pragma unroll
+    for (int k = 0; k < CPL; k += 4) {
+      if constexpr (CPL >= 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p + c + k);
+        v[k] = q.x; v[k + 1] = q.y; v[k + 2] = q.z; v[k + 3] = q.w;
+      } else {
+        const float2 q = *reinterpret_cast<const float2*>(p + c);
+        v[0] = q.x; v[1] = q.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) v[e] = c + e < d ? p[c + e] : 0.0f;
+  }
+}
+
+// Sum of v[k] over the 32 lanes for k = 0..31, scattered: lane L returns the sum for k = L
+// (31 shuffles instead of 32 x 5)
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int o = 16 >> s;
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const float send = upper ? v[k] : v[k + o];
+      const float keep = upper ? v[k + o] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
+// Rm[i][r] = x_i . U[:, r] - y_i (zero for r >= R).  A warp takes RW = 32 / RMAX rows at a time; a
+// lane loads CPL consecutive columns of each.  USM: U is staged in shared memory with 4 floats of
+// padding after every CPL rows, so the quarter-warp's 16-byte reads fall on distinct banks.
 template <typename S, int RMAX, bool USM>
 __global__ void __launch_bounds__(256) skinny_xu_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
                                                         const float* __restrict__ U, int R, const float* __restrict__ y,
                                                         float* __restrict__ Rm) {
-  // USM: U (d x R) is staged once per block in shared memory, columns padded to RMAX (zeros beyond R)
-  extern __shared__ float us[];   // [d][RMAX]
+  constexpr int RW = 32 / RMAX;
+  constexpr int CPL = 16 / (int)sizeof(S);
+  constexpr int USTR = CPL * RMAX + 4;   // floats per CPL rows of U in shared memory
+  extern __shared__ float4 us4[];
+  float* us = reinterpret_cast<float*>(us4);
+  const int64_t ng = (d + CPL - 1) / CPL;
   if (USM) {
-    for (int64_t e = threadIdx.x; e < d * RMAX; e += blockDim.x) {
-      const int64_t c = e / RMAX;
+    for (int64_t e = threadIdx.x; e < ng * CPL * RMAX; e += blockDim.x) {
+      const int64_t cc = e / RMAX;
       const int r = (int)(e % RMAX);
-      us[e] = r < R ? U[c * R + r] : 0.0f;
+      us[(cc / CPL) * USTR + (cc % CPL) * RMAX + r] = cc < d ? U[cc * RMAX + r] : 0.0f;
     }
     __syncthreads();
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw) {
-    float acc[RMAX];
+  for (int64_t i0 = ((int64_t)blockIdx.x * nw + warp) * RW; i0 < n; i0 += (int64_t)gridDim.x * nw * RW) {
+    float acc[32];
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) acc[r] = 0.0f;
-    const S* row = X + i * ld;
-    for (int64_t c = lane; c < d; c += 32) {
-      const float xv = cvt<float>(row[c]);
-      if (USM) {
-        const float4* u4 = reinterpret_cast<const float4*>(us + c * RMAX);
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+    for (int64_t g = lane; g < ng; g += 32) {
+      const int64_t c = g * CPL;
+      float xv[RW][CPL];
+#pragma unroll
+      for (int rr = 0; rr < RW; ++rr) {
+        if (i0 + rr < n) ld_cols<CPL>(X + (i0 + rr) * ld, c, d, xv[rr]);
+        else
+#pragma unroll
+          for (int e = 0; e < CPL; ++e) xv[rr][e] = 0.0f;
+      }
+      const float4* u4 = USM ? reinterpret_cast<const float4*>(us + g * USTR)
+                             : reinterpret_cast<const float4*>(U + c * RMAX);
+#pragma unroll
+      for (int e = 0; e < CPL; ++e) {
+        if (!USM && c + e >= d) break;
 #pragma unroll
         for (int q = 0; q < RMAX / 4; ++q) {
-          const float4 u = u4[q];
-          acc[4 * q] = fmaf(xv, u.x, acc[4 * q]);
-          acc[4 * q + 1] = fmaf(xv, u.y, acc[4 * q + 1]);
-          acc[4 * q + 2] = fmaf(xv, u.z, acc[4 * q + 2]);
-          acc[4 * q + 3] = fmaf(xv, u.w, acc[4 * q + 3]);
-        }
-      } else {
-        const float* u = U + c * R;
+          const float4 u = u4[e * (RMAX / 4) + q];
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-          if (r < R) acc[r] = fmaf(xv, u[r], acc[r]);
+          for (int rr = 0; rr < RW; ++rr) {
+            acc[rr * RMAX + 4 * q] = fmaf(xv[rr][e], u.x, acc[rr * RMAX + 4 * q]);
+            acc[rr * RMAX + 4 * q + 1] = fmaf(xv[rr][e], u.y, acc[rr * RMAX + 4 * q + 1]);
+            acc[rr * RMAX + 4 * q + 2] = fmaf(xv[rr][e], u.z, acc[rr * RMAX + 4 * q + 2]);
+            acc[rr * RMAX + 4 * q + 3] = fmaf(xv[rr][e], u.w, acc[rr * RMAX + 4 * q + 3]);
+          }
+        }
       }
     }
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) acc[r] = warp_sum(acc[r]);
-    if (lane == 0) {
-      const float yi = y[i];
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r)
-        if (r < R) Rm[i * R + r] = acc[r] - yi;
-    }
+    const float v = warp_reduce_scatter32(acc, lane);
+    const int64_t i = i0 + lane / RMAX;
+    const int r = lane % RMAX;
+    if (i < n) Rm[i * RMAX + r] = r < R ? v - y[i] : 0.0f;
   }
 }
 
+// part[chunk][c][r] = sum over the chunk's rows of X[i][c] Rm[i][r] (r < R).  A block covers
+// 32 CPL columns (CPL = 64 / RMAX per lane, 64 accumulators); its 8 warps take interleaved rows,
+// then the warps' sums are added in warp order through shared memory (64 KB).
 template <typename S, int RMAX>
 __global__ void __launch_bounds__(256) skinny_xtr_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
                                                          const float* __restrict__ Rm, int R, int64_t rows_per_chunk,
                                                          float* __restrict__ part) {
-  __shared__ float rs[64 * RMAX];
-  const int64_t c = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  constexpr int CPL = 64 / RMAX;
+  constexpr int CPW = 32 * CPL;
+  extern __shared__ float4 red4[];
+  float* red = reinterpret_cast<float*>(red4);   // [8][CPL * RMAX][32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c = (int64_t)blockIdx.y * CPW + lane * CPL;
   const int64_t i0 = (int64_t)blockIdx.x * rows_per_chunk, i1 = min64(n, i0 + rows_per_chunk);
-  float acc[RMAX];
+  float acc[CPL][RMAX];
 #pragma unroll
-  for (int r = 0; r < RMAX; ++r) acc[r] = 0.0f;
-  for (int64_t b0 = i0; b0 < i1; b0 += 64) {
-    const int nb = (int)min64(64, i1 - b0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * R; e += blockDim.x) rs[(e / R) * RMAX + e % R] = Rm[(b0 + e / R) * R + e % R];
-    __syncthreads();
-    if (c < d) {
-      for (int ii = 0; ii < nb; ++ii) {
-        const float xv = cvt<float>(X[(b0 + ii) * ld + c]);
+  for (int e = 0; e < CPL; ++e)
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-          if (r < R) acc[r] = fmaf(xv, rs[ii * RMAX + r], acc[r]);
+    for (int r = 0; r < RMAX; ++r) acc[e][r] = 0.0f;
+  if (c < d) {
+    for (int64_t i = i0 + warp; i < i1; i += 8) {
+      float xv[CPL];
+      ld_cols<CPL>(X + i * ld, c, d, xv);
+      const float4* rr = reinterpret_cast<const float4*>(Rm + i * RMAX);
+#pragma unroll
+      for (int q = 0; q < RMAX / 4; ++q) {
+        const float4 rq = rr[q];
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+          acc[e][4 * q] = fmaf(xv[e], rq.x, acc[e][4 * q]);
+          acc[e][4 * q + 1] = fmaf(xv[e], rq.y, acc[e][4 * q + 1]);
+          acc[e][4 * q + 2] = fmaf(xv[e], rq.z, acc[e][4 * q + 2]);
+          acc[e][4 * q + 3] = fmaf(xv[e], rq.w, acc[e][4 * q + 3]);
+        }
       }
     }
   }
-  if (c < d) {
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r)
-      if (r < R) part[((int64_t)blockIdx.x * d + c) * R + r] = acc[r];
+  for (int e = 0; e < CPL; ++e)
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) red[((warp * CPL + e) * RMAX + r) * 32 + lane] = acc[e][r];
+  __syncthreads();
+  for (int k = threadIdx.x; k < CPL * RMAX * 32; k += blockDim.x) {
+    float s = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += red[w * CPL * RMAX * 32 + k];
+    const int L = k % 32, er = k / 32, e = er / RMAX, r = er % RMAX;
+    const int64_t col = (int64_t)blockIdx.y * CPW + L * CPL + e;
+    if (col < d && r < R) part[((int64_t)blockIdx.x * d + col) * R + r] = s;
   }
 }
 
@@ -205,6 +298,35 @@ struct Pair {        // one (problem, lambda): components and sampling table
   double bh;
 };
 
+// Side streams (non-blocking) and fork/join events for work that runs side by side; released on
+// scope exit (a stream with work still queued is released once that work completes).
+struct SideStreams {
+  std::vector<cudaStream_t> s;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  int open(int count) {
+    if (count <= 0) return RS_OK;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+      return rs_fail(RS_ECUDA, "side streams: event creation failed");
+    for (int i = 0; i < count; ++i) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        return rs_fail(RS_ECUDA, "side streams: stream creation failed");
+      s.push_back(st);
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+        return rs_fail(RS_ECUDA, "side streams: event creation failed");
+      join.push_back(ev);
+    }
+    return RS_OK;
+  }
+  ~SideStreams() {
+    for (auto e : join) cudaEventDestroy(e);
+    for (auto st : s) cudaStreamDestroy(st);
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
 struct ProbWs {
   float* V;
   double* s2;
@@ -212,6 +334,7 @@ struct ProbWs {
   float* Rm;         // n x R
   double* G;         // d x R
   int R;
+  int Rp;            // column stride of U and Rm: R padded to 8, 16 or 32 (R itself beyond 32)
   int64_t k;
 };
 
@@ -274,10 +397,12 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
     cv.off = 0;
     for (int p = 0; p < np; ++p) {
       const int64_t n = P[p].X.n, d = P[p].X.d, k = pw[p].k, R = std::max(1, pw[p].R);
+      pw[p].Rp = R <= 8 ? 8 : (R <= 16 ? 16 : (R <= 32 ? 32 : (int)R));
+      const int64_t Rp = pw[p].Rp;
       pw[p].V = cv.take<float>(d * k);
       pw[p].s2 = cv.take<double>(k);
-      pw[p].U = refine ? cv.take<float>(d * R) : nullptr;
-      pw[p].Rm = refine ? cv.take<float>(n * R) : nullptr;
+      pw[p].U = refine ? cv.take<float>(d * Rp) : nullptr;
+      pw[p].Rm = refine ? cv.take<float>(n * Rp) : nullptr;
       pw[p].G = refine ? cv.take<double>(d * R) : nullptr;
     }
     for (auto& q : pairs) {
@@ -337,6 +462,8 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
                                                                                  q.a);
     RS_LAUNCH_CHECK(ctx);
   }
+  for (int p = 0; p < np; ++p)
+    if (refine) RS_CUDA_TRY(cudaMemsetAsync(pw[p].U, 0, (size_t)P[p].X.d * pw[p].Rp * sizeof(float), ctx->stream));
   for (int c = 0; c < nc; ++c) {
     cw[c].eta = (C[c].eta_mult > 0.0 ? C[c].eta_mult : 1.0) / pairs[cw[c].pair].bh;
     RS_CUDA_TRY(cudaMemsetAsync(cw[c].wa, 0, P[C[c].problem].X.d * sizeof(float), ctx->stream));
@@ -382,7 +509,7 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
       u.xf = par ? cw[c].wb : cw[c].wa;
       u.xf_scale = 1.0;
       u.y = refine ? W.U + cw[c].r : cw[c].u;
-      u.y_ld = refine ? W.R : 1;
+      u.y_ld = refine ? W.Rp : 1;
       u.y2 = refine ? cw[c].u : nullptr;
       um[par * (size_t)nc + o] = u;
       if (C[c].snapshots) {
@@ -449,6 +576,8 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
     o = e;
   }
   const int64_t total_blocks = blk_off[nc], total_steps = idx_off[nc];
+  SideStreams side;
+  RS_TRY(side.open(std::min<int>((int)groups.size() - 1, 7)));
 
   auto run_epoch = [&](int s) -> int {
     const int par = s & 1;
@@ -462,10 +591,12 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
         const S* Xd = static_cast<const S*>(X.data);
         if (R <= 32) {
           // two streaming passes over X with the R columns in registers
-          const int rmax = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
-          const size_t ushm = (size_t)d * rmax * sizeof(float);
-          const bool usm = ushm <= 96 * 1024;
-          const int xu_blocks = usm ? ctx->num_sms * 2 : blocks_cap(ctx, n * 32);
+          const int rmax = pw[p].Rp;
+          constexpr int CPLU = 16 / (int)sizeof(S);
+          const int64_t ng = (d + CPLU - 1) / CPLU;
+          const size_t ushm = (size_t)ng * (CPLU * rmax + 4) * sizeof(float);
+          const bool usm = ushm <= 100 * 1024;
+          const int xu_blocks = ctx->num_sms * 2;
 #define RS_XU(RM)                                                                                                    \
   do {                                                                                                               \
     if (usm) {                                                                                                       \
@@ -483,15 +614,24 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
           else RS_XU(32);
 #undef RS_XU
           RS_LAUNCH_CHECK(ctx);
-          const int cb = (int)((d + 255) / 256);
-          const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 4 / cb, (n + 63) / 64));
+          const int cpw = 32 * (64 / rmax);   // columns per block of the transposed product
+          const int cb = (int)((d + cpw - 1) / cpw);
+          const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 6 / cb, (n + 255) / 256));
           const int64_t rpc = (n + nch - 1) / nch;
           float* part = static_cast<float*>(rs_scratch(ctx, SCR_BPART, (size_t)nch * d * R * sizeof(float)));
           if (!part) return RS_ENOMEM;
           dim3 g2((unsigned)nch, (unsigned)cb);
-          if (R <= 8) skinny_xtr_kernel<S, 8><<<g2, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part);
-          else if (R <= 16) skinny_xtr_kernel<S, 16><<<g2, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part);
-          else skinny_xtr_kernel<S, 32><<<g2, 256, 0, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part);
+          constexpr size_t rshm = 8 * 64 * 32 * sizeof(float);
+#define RS_XTR(RM)                                                                                                 \
+  do {                                                                                                             \
+    RS_CUDA_TRY(cudaFuncSetAttribute(skinny_xtr_kernel<S, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                     (int)rshm));                                                                  \
+    skinny_xtr_kernel<S, RM><<<g2, 256, rshm, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part);         \
+  } while (0)
+          if (rmax == 8) RS_XTR(8);
+          else if (rmax == 16) RS_XTR(16);
+          else RS_XTR(32);
+#undef RS_XTR
           RS_LAUNCH_CHECK(ctx);
           skinny_reduce_kernel<<<blocks_cap(ctx, d * R), 256, 0, ctx->stream>>>(part, nch, d * R, 1.0 / (double)n,
                                                                                 pw[p].G);
@@ -517,9 +657,26 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
     }
     RS_TRY(index_stream_batched(ctx, idx_dev, idx_off_dev, nc, total_steps, (uint32_t)s));
     RS_TRY(epoch_prep_batched<S, float>(ctx, jobs_dev + par * (size_t)nc, blk_off_dev, nc, total_blocks));
-    for (auto& g : groups)
-      RS_TRY(epoch_chain_batched<S, float>(ctx, jobs_dev + par * (size_t)nc + g.first, g.second,
-                                           P[C[order[g.first]].problem].X.d));
+    // the width groups' inner loops run side by side: group 0 on the solver's stream, the others
+    // on side streams forked from and joined back into it
+    const int nside = std::min<int>((int)groups.size() - 1, (int)side.s.size());
+    if (nside > 0) {
+      RS_CUDA_TRY(cudaEventRecord(side.fork, ctx->stream));
+      for (int i = 0; i < nside; ++i) RS_CUDA_TRY(cudaStreamWaitEvent(side.s[i], side.fork, 0));
+    }
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      const auto& g = groups[gi];
+      cudaStream_t main_stream = ctx->stream;
+      if (nside > 0 && gi > 0) ctx->stream = side.s[(gi - 1) % nside];
+      const int grc = epoch_chain_batched<S, float>(ctx, jobs_dev + par * (size_t)nc + g.first, g.second,
+                                                    P[C[order[g.first]].problem].X.d);
+      ctx->stream = main_stream;
+      if (grc != RS_OK) return grc;
+    }
+    for (int i = 0; i < nside; ++i) {
+      RS_CUDA_TRY(cudaEventRecord(side.join[i], side.s[i]));
+      RS_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, side.join[i], 0));
+    }
     if (nsnap) {
       bmap_kernel<<<nsnap, 256, 0, ctx->stream>>>(snap_dev + par * (size_t)std::max(1, nsnap), s, ctx->d_status);
       RS_LAUNCH_CHECK(ctx);

@@ -401,9 +401,7 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   // (which read rows j, j+1, .., j+TPC-1 in the update) on distinct shared-memory banks
   constexpr int ZS = CW + chain_zpad(TPC, CPW, (int)sizeof(S));
   S* Zs = reinterpret_cast<S*>(ch_sh);                     // [STAGES][B][ZS]
-  T* Rs = reinterpret_cast<T*>(Zs + (size_t)STAGES * B * ZS);   // [STAGES][B][B]  (Rt layout: [l][j])
-  T* Cs = Rs + (size_t)STAGES * B * B;                     // [STAGES][B]
-  T* recv = Cs + (size_t)STAGES * B;                       // [2][kCsMax][B] partial dots from each rank
+  T* recv = reinterpret_cast<T*>(Zs + (size_t)STAGES * B * ZS);   // [2][kCsMax][B] partial dots from each rank
   // running sum of the iterates (epoch average) as a compensated (Kahan) pair in T: on GB300 a
   // double add sits on the critical path of every block with a long latency
   T* Ssum = recv + 2 * kCsMax * B;                         // [CW]
@@ -961,8 +959,7 @@ size_t chain_smem(int qn, int stages, int nt) {
   const int CW = 32 * qn;
   const int TPC = std::max(1, nt / CW);
   const int ZS = CW + chain_zpad(TPC, 32 / TPC, (int)sizeof(S));
-  return (size_t)stages * kBlk * ZS * sizeof(S) + (size_t)stages * kBlk * kBlk * sizeof(T) +
-         (size_t)stages * kBlk * sizeof(T) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + 2 * (size_t)CW * sizeof(T) +
+  return (size_t)stages * kBlk * ZS * sizeof(S) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + 2 * (size_t)CW * sizeof(T) +
          2 * (size_t)CW * sizeof(T) + (2 + nt / kBlk) * (size_t)kBlk * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
          (size_t)stages * kBlk * sizeof(float) + 2 * sizeof(uint64_t) + 64;
 }
@@ -985,7 +982,7 @@ int choose_threads() {
 }
 
 template <typename S, typename T>
-ChainPlan plan_chain(int64_t d, int cs) {
+ChainPlan plan_chain(int64_t d, int cs, size_t cap = 200 * 1024) {
   ChainPlan p;
   const int nt = choose_threads();
   if (cs < 1 || cs > kCsMax || (cs & (cs - 1))) return p;
@@ -994,7 +991,7 @@ ChainPlan plan_chain(int64_t d, int cs) {
   if (!qn) return p;
   for (int st = 4; st >= 2; --st) {
     const size_t shm = chain_smem<S, T>(qn, st, nt);
-    if (shm <= 200 * 1024) {
+    if (shm <= cap) {
       p.nt = nt;
       p.cs = cs;
       p.qn = qn;
@@ -1405,8 +1402,13 @@ int epoch_chain_batched(rs_ctx* ctx, const ChainJob<S, T>* jobs, int nj, int64_t
     }
     if (rc != RS_EUNSUPPORTED) return rc;
   }
+  // many chains side by side: a ring small enough for two chain blocks per SM (the inner loop is
+  // latency-bound, so two interleave), unless RS_BATCH_CHAIN_SMEM (KB; 0 = no limit) says otherwise
+  size_t cap = 110 * 1024;
+  if (const char* env = std::getenv("RS_BATCH_CHAIN_SMEM")) cap = std::atoi(env) > 0 ? (size_t)std::atoi(env) * 1024 : 0;
   for (int cs = choose_batch_cluster(d); cs >= 1; cs /= 2) {
-    const ChainPlan pl = plan_chain<S, T>(d, cs);
+    ChainPlan pl = cap ? plan_chain<S, T>(d, cs, cap) : ChainPlan{};
+    if (!pl.cs) pl = plan_chain<S, T>(d, cs);
     if (!pl.cs) continue;
     int rc = RS_EUNSUPPORTED;
 #define RS_CHAIN(ST, QN)                                                                  \
