@@ -25,7 +25,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_RPART, SCR_COUNT
 };
 
 struct rs_ctx {
@@ -232,6 +232,9 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
 bool umma_enabled();
 int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, const float* col_scale, float* C,
                  int64_t ldc);
+// Z (bfloat16) = X - P V^T for bfloat16 X (umma.cu), P n x k and V d x k float with row stride k,
+// k <= 128; RS_EUNSUPPORTED when the tensor path cannot run.
+int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, int64_t k, rs_matrix* Z);
 
 // ------------------------------------------------ batched inner loops (many chains per launch)
 

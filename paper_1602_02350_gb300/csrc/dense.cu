@@ -896,7 +896,14 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
     RS_TRY(launch_gemm<T, S, T>(ctx, n, k, d, 1.0, Xd, X->ld, 1, V, k, 1, 0.0, nullptr, 0, P, k, a));
   else if (rc_p != RS_OK)
     return rc_p;
-  RS_TRY(launch_gemm<T, T, SZ, S>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
+  int rc_z = RS_EUNSUPPORTED;
+  if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<SZ, __nv_bfloat16>::value &&
+                std::is_same<T, float>::value)
+    if (rc_p == RS_OK) rc_z = umma_resid(ctx, X, P, V, k, Xt);
+  if (rc_z == RS_EUNSUPPORTED)
+    RS_TRY(launch_gemm<T, T, SZ, S>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
+  else if (rc_z != RS_OK)
+    return rc_z;
   // Z[n:n+d] = I - V diag(a) V^T   (the rows b_j = M e_j)
   scale_cols_kernel<T><<<blocks_for(ctx, d * k), 256, 0, ctx->stream>>>(V, d, (int)k, a, Va);
   RS_LAUNCH_CHECK(ctx);

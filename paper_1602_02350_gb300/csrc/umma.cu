@@ -425,6 +425,228 @@ __global__ void __launch_bounds__(128, 4) umma_prep_kernel(const __grid_constant
   }
 }
 
+// ------------------------------------------------------------------ components Z = X - P V^T
+// The data rows of the preconditioned components (Eq. (11)): Z = X M = X - P V^T with P =
+// X V diag(a) (n x k) and V (d x k), for bfloat16 X and Z.  P and V are split into three
+// bfloat16 parts each (P = P0 + P1 + P2, V likewise) and the six products P_a V_b^T with
+// a + b <= 2 accumulate in FP32 in tensor memory, which keeps the product to about 2^-24
+// relative (the dropped terms are below 2^-27).
+//
+// One CTA per 128-row block, persistent over the 64-column output tiles, 192 threads: warp 0
+// lane 0 loads (TMA, 128-byte swizzle) the block's P parts once and, per tile, the V parts (ring of
+// BST stages) and the 128 x 64 tile of X (two buffers); warp 1 lane 0 issues tcgen05.mma (M = 128,
+// N = 64, K = 16) into one of two tensor-memory accumulators, so the next tile's products run while
+// warps 2-5 drain the previous one: each of those threads owns one row of the tile, reads its 64
+// accumulator columns (tcgen05.ld) and its row of X from shared memory, rounds X - P V^T to
+// bfloat16 into a swizzled staging tile, and one thread stores the tile with a TMA bulk store.
+// Every wait is bounded (status flag on timeout).
+constexpr int RT_ROWS = 128, RT_COLS = 64;
+constexpr uint32_t RT_A_TILE = 128 * 128;   // 128 rows x 64 bfloat16
+constexpr uint32_t RT_B_TILE = 64 * 128;    // 64 rows x 64 bfloat16
+constexpr uint32_t RT_X_TILE = 128 * 128;   // 128 rows x 64 bfloat16
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(cta_smem_addr(src))
+               : "memory");
+}
+
+template <int KC>
+constexpr size_t resid_smem_bytes() {
+  return (size_t)3 * KC * RT_A_TILE + (size_t)(KC == 1 ? 2 : 1) * 3 * KC * RT_B_TILE + 4 * (size_t)RT_X_TILE + 1024;
+}
+
+template <int KC>
+__global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                            const __grid_constant__ CUtensorMap tmB,
+                                                            const __grid_constant__ CUtensorMap tmX,
+                                                            const __grid_constant__ CUtensorMap tmZ, int64_t d,
+                                                            int64_t np, int64_t dp, int* status) {
+  constexpr int BST = KC == 1 ? 2 : 1;
+  constexpr uint32_t A_BYTES = 3 * KC * RT_A_TILE;
+  constexpr uint32_t B_STAGE = 3 * KC * RT_B_TILE;
+  extern __shared__ unsigned char rt_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(rt_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* As = base;
+  unsigned char* Bs = As + A_BYTES;
+  unsigned char* Xs = Bs + BST * B_STAGE;
+  unsigned char* Zs = Xs + 2 * RT_X_TILE;
+  __shared__ uint64_t a_full, b_full[BST], b_empty[BST], x_full[2], x_empty[2], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_holder;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * RT_ROWS;
+  const int ntiles = (int)((d + RT_COLS - 1) / RT_COLS);
+  if (threadIdx.x == 0) {
+    mbar_init_cta(&a_full, 1);
+    for (int s = 0; s < BST; ++s) {
+      mbar_init_cta(&b_full[s], 1);
+      mbar_init_cta(&b_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init_cta(&x_full[s], 1);
+      mbar_init_cta(&x_empty[s], 4);
+      mbar_init_cta(&acc_full[s], 1);
+      mbar_init_cta(&acc_empty[s], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(cta_smem_addr(&tmem_holder)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {   // producer
+      mbar_expect_tx_cta(&a_full, A_BYTES);
+      for (int pa = 0; pa < 3; ++pa)
+        for (int kc = 0; kc < KC; ++kc)
+          tma_load_2d(As + (pa * KC + kc) * RT_A_TILE, &tmA, kc * 64, (int)(pa * np) + row0, &a_full);
+      for (int t = 0; t < ntiles; ++t) {
+        const int sb = t % BST, u = t / BST;
+        if (u >= 1 && !mbar_wait_bounded(&b_empty[sb], (uint32_t)((u - 1) & 1), kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
+        mbar_expect_tx_cta(&b_full[sb], B_STAGE);
+        unsigned char* bst = Bs + sb * B_STAGE;
+        for (int pb = 0; pb < 3; ++pb)
+          for (int kc = 0; kc < KC; ++kc)
+            tma_load_2d(bst + (pb * KC + kc) * RT_B_TILE, &tmB, kc * 64, (int)(pb * dp) + t * RT_COLS, &b_full[sb]);
+        const int sx = t & 1, ux = t >> 1;
+        if (ux >= 1 && !mbar_wait_bounded(&x_empty[sx], (uint32_t)((ux - 1) & 1), kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
+        mbar_expect_tx_cta(&x_full[sx], RT_X_TILE);
+        tma_load_2d(Xs + sx * RT_X_TILE, &tmX, t * RT_COLS, row0, &x_full[sx]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      if (!mbar_wait_bounded(&a_full, 0u, kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
+      const uint32_t sa = cta_smem_addr(As);
+      for (int t = 0; t < ntiles; ++t) {
+        const int sb = t % BST, u = t / BST, ab = t & 1, ua = t >> 1;
+        if (!mbar_wait_bounded(&b_full[sb], (uint32_t)(u & 1), kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
+        if (ua >= 1 && !mbar_wait_bounded(&acc_empty[ab], (uint32_t)((ua - 1) & 1), kUmmaWait))
+          atomicOr(status, STATUS_TIMEOUT);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t sbb = cta_smem_addr(Bs + sb * B_STAGE);
+        const uint32_t dt = tmem + (uint32_t)(ab * RT_COLS);
+        uint32_t accum = 0;
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const int pa = c < 3 ? 0 : (c < 5 ? 1 : 2);      // (0,0) (0,1) (0,2) (1,0) (1,1) (2,0)
+            const int pb = c < 3 ? c : (c < 5 ? c - 3 : 0);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t da = smem_desc_sw128(sa + (pa * KC + kc) * RT_A_TILE + kk * 32);
+              const uint64_t db = smem_desc_sw128(sbb + (pb * KC + kc) * RT_B_TILE + kk * 32);
+              asm volatile(
+                  "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(dt),
+                  "l"(da), "l"(db), "r"(kPrepIdesc), "r"(accum)
+                  : "memory");
+              accum = 1;
+            }
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         cta_smem_addr(&b_empty[sb]))
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         cta_smem_addr(&acc_full[ab]))
+                     : "memory");
+      }
+    }
+  } else {   // epilogue: warps 2..5, thread = row r of the tile (tensor-memory lane r)
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    const bool lead = warp == 2 && lane == 0;
+    for (int t = 0; t < ntiles; ++t) {
+      const int ab = t & 1, ua = t >> 1;
+      bool ok = mbar_wait_bounded(&acc_full[ab], (uint32_t)(ua & 1), kUmmaWait);
+      ok = mbar_wait_bounded(&x_full[ab], (uint32_t)(ua & 1), kUmmaWait) && ok;
+      if (!ok) atomicOr(status, STATUS_TIMEOUT);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      uint32_t v[64];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * RT_COLS + 32 * h);
+        uint32_t* w = v + 32 * h;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
+              "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15]),
+              "=r"(w[16]), "=r"(w[17]), "=r"(w[18]), "=r"(w[19]), "=r"(w[20]), "=r"(w[21]), "=r"(w[22]), "=r"(w[23]),
+              "=r"(w[24]), "=r"(w[25]), "=r"(w[26]), "=r"(w[27]), "=r"(w[28]), "=r"(w[29]), "=r"(w[30]), "=r"(w[31])
+            : "r"(taddr)
+            : "memory");
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&acc_empty[ab]);
+      // the staging tile of tile t - 2 has been read by its bulk store
+      if (lead) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");
+      const unsigned char* xr = Xs + ab * RT_X_TILE + r * 128;
+      unsigned char* zr = Zs + ab * RT_X_TILE + r * 128;
+#pragma unroll
+      for (int u8 = 0; u8 < 8; ++u8) {
+        const int off = (u8 ^ (r & 7)) << 4;
+        const uint4 xw = *reinterpret_cast<const uint4*>(xr + off);
+        const uint32_t xs4[4] = {xw.x, xw.y, xw.z, xw.w};
+        uint32_t zw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float x0 = __uint_as_float(xs4[e] << 16), x1 = __uint_as_float(xs4[e] & 0xFFFF0000u);
+          const __nv_bfloat16 z0 = __float2bfloat16_rn(x0 - __uint_as_float(v[8 * u8 + 2 * e]));
+          const __nv_bfloat16 z1 = __float2bfloat16_rn(x1 - __uint_as_float(v[8 * u8 + 2 * e + 1]));
+          zw[e] = (uint32_t)__bfloat16_as_ushort(z0) | ((uint32_t)__bfloat16_as_ushort(z1) << 16);
+        }
+        *reinterpret_cast<uint4*>(zr + off) = make_uint4(zw[0], zw[1], zw[2], zw[3]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&x_empty[ab]);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");
+      if (lead) {
+        tma_store_2d(&tmZ, Zs + ab * RT_X_TILE, t * RT_COLS, row0);
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+      }
+    }
+    if (lead) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128) : "memory");
+  }
+}
+
+// src (rows x k float, row stride lds) -> out (3 x rows_pad x kp bfloat16): part p holds
+// bf16(src - part 0 - .. - part p-1), zero beyond rows and k
+__global__ void split3_rows_kernel(const float* __restrict__ src, int64_t rows, int k, int64_t lds, int64_t rows_pad,
+                                   int kp, __nv_bfloat16* __restrict__ out) {
+  const int64_t total = rows_pad * kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / kp;
+    const int c = (int)(e % kp);
+    float r = (i < rows && c < k) ? src[i * lds + c] : 0.0f;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(r);
+      out[(int64_t)p * total + e] = h;
+      r -= __bfloat162float(h);
+    }
+  }
+}
+
 // W (K x N float, row-major) -> parts (NSPLIT x kp x ldp bfloat16): part p row j = column j of
 // W_p, W = W0 + W1 + W2 with W_{p} = bf16(W - W_0 - .. - W_{p-1}); rows j >= N are zero
 __global__ void split_transpose_kernel(const float* __restrict__ W, int K, int N, int kp, int ldp,
@@ -492,6 +714,52 @@ int umma_prep(rs_ctx* ctx, const ChainJob<__nv_bfloat16, float>& one, const Chai
   RS_CUDA_TRY(cudaFuncSetAttribute(umma_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   umma_prep_kernel<<<(unsigned)total_blocks, 128, shm, ctx->stream>>>(one, jobs, blk_off, nj, ctx->d_status);
   RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
+}
+
+// Z (bfloat16 rows, n x d) = X - P V^T for bfloat16 X, P (n x k float, row stride k), V (d x k
+// float, row stride k), k <= 128, on tensor cores.  RS_EUNSUPPORTED when the tensor path is off or
+// cannot run (the caller uses the CUDA-core product).
+int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, int64_t k, rs_matrix* Z) {
+  if (!umma_enabled() || !encode_fn()) return RS_EUNSUPPORTED;
+  const char* env = std::getenv("RS_UMMA_RESID");
+  if (env && env[0] == '0') return RS_EUNSUPPORTED;
+  const int64_t n = X->n, d = X->d;
+  if (k < 1 || k > 128 || n < 1 || d < 1 || n > 0x7FFFFF00LL / 3 || d > 0x7FFFFF00LL / 3) return RS_EUNSUPPORTED;
+  const int kp = k <= 64 ? 64 : 128;
+  const int64_t np = (n + RT_ROWS - 1) / RT_ROWS * RT_ROWS, dp = (d + RT_COLS - 1) / RT_COLS * RT_COLS;
+  __nv_bfloat16* parts = static_cast<__nv_bfloat16*>(
+      rs_scratch(ctx, SCR_RPART, (size_t)3 * (np + dp) * kp * sizeof(__nv_bfloat16)));
+  if (!parts) return RS_ENOMEM;
+  __nv_bfloat16* vparts = parts + (size_t)3 * np * kp;
+  const int sb = ctx->num_sms * 8;
+  split3_rows_kernel<<<(unsigned)std::min<int64_t>((np * kp + 255) / 256, sb), 256, 0, ctx->stream>>>(
+      P, n, (int)k, k, np, kp, parts);
+  RS_LAUNCH_CHECK(ctx);
+  split3_rows_kernel<<<(unsigned)std::min<int64_t>((dp * kp + 255) / 256, sb), 256, 0, ctx->stream>>>(
+      V, d, (int)k, k, dp, kp, vparts);
+  RS_LAUNCH_CHECK(ctx);
+  CUtensorMap mA, mB, mX, mZ;
+  RS_TRY(make_map(&mA, parts, kp, 3 * np, kp, RT_ROWS));
+  RS_TRY(make_map(&mB, vparts, kp, 3 * dp, kp, RT_COLS));
+  RS_TRY(make_map(&mX, X->data, d, n, X->ld, RT_ROWS));
+  RS_TRY(make_map(&mZ, Z->data, d, n, Z->ld, RT_ROWS));
+  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  const unsigned grid = (unsigned)(np / RT_ROWS);
+  if (kp == 64) {
+    constexpr size_t shm = resid_smem_bytes<1>();
+    RS_CUDA_TRY(cudaFuncSetAttribute(umma_resid_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    umma_resid_kernel<1><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, ctx->d_status);
+  } else {
+    constexpr size_t shm = resid_smem_bytes<2>();
+    RS_CUDA_TRY(cudaFuncSetAttribute(umma_resid_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    umma_resid_kernel<2><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, ctx->d_status);
+  }
+  RS_LAUNCH_CHECK(ctx);
+  int st = 0;
+  RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (st & STATUS_TIMEOUT) return rs_fail(RS_ETIMEOUT, "tensor-core components: a bounded wait gave up");
   return RS_OK;
 }
 

@@ -18,8 +18,12 @@ pytestmark = pytest.mark.gpu
 BF16_UNIT = 2.0 ** -8   # unit roundoff of bfloat16 (8 significand bits)
 
 
-@pytest.mark.parametrize("n,d,k", [(1, 8, 1), (257, 40, 5), (4096, 256, 16), (65536, 1024, 64)])
-def test_precondition_bf16_matches_oracle(rsctx, n, d, k):
+@pytest.mark.parametrize("n,d,k", [(1, 8, 1), (257, 40, 5), (4096, 256, 16), (65536, 1024, 64), (3000, 520, 70),
+                                   (130, 2048, 128), (700, 136, 129)])
+@pytest.mark.parametrize("tc", ["1", "0"])
+def test_precondition_bf16_matches_oracle(rsctx, monkeypatch, n, d, k, tc):
+    """X - P V^T on tensor cores (tcgen05, k <= 128) and on CUDA cores."""
+    monkeypatch.setenv("RS_UMMA_RESID", tc)
     X = torch.from_numpy(synth.random_matrix(n, d, n + d, scale=1.0 / np.sqrt(d))).to(torch.bfloat16)
     V = torch.from_numpy(synth.random_orthonormal(d, k, d)).float()
     s2 = synth.random_sigma2(k, k)
