@@ -171,30 +171,40 @@ __global__ void __launch_bounds__(256) skinny_xu_kernel(const S* __restrict__ X,
     float acc[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
-    for (int64_t g = lane; g < ng; g += 32) {
-      const int64_t c = g * CPL;
-      float xv[RW][CPL];
+    // two column groups per step, all of their loads issued before the arithmetic (more bytes in
+    // flight per warp); the second group of the last step may lie beyond the row
+    for (int64_t g0 = lane; g0 < ng; g0 += 64) {
+      float xv[2][RW][CPL];
 #pragma unroll
-      for (int rr = 0; rr < RW; ++rr) {
-        if (i0 + rr < n) ld_cols<CPL>(X + (i0 + rr) * ld, c, d, xv[rr]);
-        else
+      for (int h = 0; h < 2; ++h) {
+        const int64_t c = (g0 + 32 * h) * CPL;
 #pragma unroll
-          for (int e = 0; e < CPL; ++e) xv[rr][e] = 0.0f;
+        for (int rr = 0; rr < RW; ++rr) {
+          if (i0 + rr < n && c < d) ld_cols<CPL>(X + (i0 + rr) * ld, c, d, xv[h][rr]);
+          else
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) xv[h][rr][e] = 0.0f;
+        }
       }
-      const float4* u4 = USM ? reinterpret_cast<const float4*>(us + g * USTR)
-                             : reinterpret_cast<const float4*>(U + c * RMAX);
 #pragma unroll
-      for (int e = 0; e < CPL; ++e) {
-        if (!USM && c + e >= d) break;
+      for (int h = 0; h < 2; ++h) {
+        const int64_t g = g0 + 32 * h, c = g * CPL;
+        if (g >= ng) break;
+        const float4* u4 = USM ? reinterpret_cast<const float4*>(us + g * USTR)
+                               : reinterpret_cast<const float4*>(U + c * RMAX);
 #pragma unroll
-        for (int q = 0; q < RMAX / 4; ++q) {
-          const float4 u = u4[e * (RMAX / 4) + q];
+        for (int e = 0; e < CPL; ++e) {
+          if (!USM && c + e >= d) break;
 #pragma unroll
-          for (int rr = 0; rr < RW; ++rr) {
-            acc[rr * RMAX + 4 * q] = fmaf(xv[rr][e], u.x, acc[rr * RMAX + 4 * q]);
-            acc[rr * RMAX + 4 * q + 1] = fmaf(xv[rr][e], u.y, acc[rr * RMAX + 4 * q + 1]);
-            acc[rr * RMAX + 4 * q + 2] = fmaf(xv[rr][e], u.z, acc[rr * RMAX + 4 * q + 2]);
-            acc[rr * RMAX + 4 * q + 3] = fmaf(xv[rr][e], u.w, acc[rr * RMAX + 4 * q + 3]);
+          for (int q = 0; q < RMAX / 4; ++q) {
+            const float4 u = u4[e * (RMAX / 4) + q];
+#pragma unroll
+            for (int rr = 0; rr < RW; ++rr) {
+              acc[rr * RMAX + 4 * q] = fmaf(xv[h][rr][e], u.x, acc[rr * RMAX + 4 * q]);
+              acc[rr * RMAX + 4 * q + 1] = fmaf(xv[h][rr][e], u.y, acc[rr * RMAX + 4 * q + 1]);
+              acc[rr * RMAX + 4 * q + 2] = fmaf(xv[h][rr][e], u.z, acc[rr * RMAX + 4 * q + 2]);
+              acc[rr * RMAX + 4 * q + 3] = fmaf(xv[h][rr][e], u.w, acc[rr * RMAX + 4 * q + 3]);
+            }
           }
         }
       }
@@ -210,7 +220,7 @@ __global__ void __launch_bounds__(256) skinny_xu_kernel(const S* __restrict__ X,
 // 32 CPL columns (CPL = 64 / RMAX per lane, 64 accumulators); its 8 warps take interleaved rows,
 // then the warps' sums are added in warp order through shared memory (64 KB).
 template <typename S, int RMAX>
-__global__ void __launch_bounds__(256) skinny_xtr_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
+__global__ void __launch_bounds__(256, 2) skinny_xtr_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
                                                          const float* __restrict__ Rm, int R, int64_t rows_per_chunk,
                                                          float* __restrict__ part) {
   constexpr int CPL = 64 / RMAX;
@@ -226,21 +236,37 @@ __global__ void __launch_bounds__(256) skinny_xtr_kernel(const S* __restrict__ X
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) acc[e][r] = 0.0f;
   if (c < d) {
-    for (int64_t i = i0 + warp; i < i1; i += 8) {
-      float xv[CPL];
-      ld_cols<CPL>(X + i * ld, c, d, xv);
-      const float4* rr = reinterpret_cast<const float4*>(Rm + i * RMAX);
+    // two rows per step (rows i and i + 8 of the chunk), loads issued first
+    constexpr int UR = 2;
+    for (int64_t i = i0 + warp; i < i1; i += 8 * UR) {
+      float xv[UR][CPL];
+      float4 rq[UR][RMAX / 4];
 #pragma unroll
-      for (int q = 0; q < RMAX / 4; ++q) {
-        const float4 rq = rr[q];
+      for (int u = 0; u < UR; ++u) {
+        const int64_t iu = i + 8 * u;
+        if (iu < i1) {
+          ld_cols<CPL>(X + iu * ld, c, d, xv[u]);
+          const float4* rr = reinterpret_cast<const float4*>(Rm + iu * RMAX);
 #pragma unroll
-        for (int e = 0; e < CPL; ++e) {
-          acc[e][4 * q] = fmaf(xv[e], rq.x, acc[e][4 * q]);
-          acc[e][4 * q + 1] = fmaf(xv[e], rq.y, acc[e][4 * q + 1]);
-          acc[e][4 * q + 2] = fmaf(xv[e], rq.z, acc[e][4 * q + 2]);
-          acc[e][4 * q + 3] = fmaf(xv[e], rq.w, acc[e][4 * q + 3]);
+          for (int q = 0; q < RMAX / 4; ++q) rq[u][q] = rr[q];
+        } else {
+#pragma unroll
+          for (int e = 0; e < CPL; ++e) xv[u][e] = 0.0f;
+#pragma unroll
+          for (int q = 0; q < RMAX / 4; ++q) rq[u][q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
       }
+#pragma unroll
+      for (int u = 0; u < UR; ++u)
+#pragma unroll
+        for (int q = 0; q < RMAX / 4; ++q)
+#pragma unroll
+          for (int e = 0; e < CPL; ++e) {
+            acc[e][4 * q] = fmaf(xv[u][e], rq[u][q].x, acc[e][4 * q]);
+            acc[e][4 * q + 1] = fmaf(xv[u][e], rq[u][q].y, acc[e][4 * q + 1]);
+            acc[e][4 * q + 2] = fmaf(xv[u][e], rq[u][q].z, acc[e][4 * q + 2]);
+            acc[e][4 * q + 3] = fmaf(xv[u][e], rq[u][q].w, acc[e][4 * q + 3]);
+          }
     }
   }
 #pragma unroll

@@ -433,12 +433,13 @@ __global__ void __launch_bounds__(128, 4) umma_prep_kernel(const __grid_constant
 // relative (the dropped terms are below 2^-27).
 //
 // One CTA per 128-row block, persistent over the 64-column output tiles, 192 threads: warp 0
-// lane 0 loads (TMA, 128-byte swizzle) the block's P parts once and, per tile, the V parts (ring of
-// BST stages) and the 128 x 64 tile of X (two buffers); warp 1 lane 0 issues tcgen05.mma (M = 128,
-// N = 64, K = 16) into one of two tensor-memory accumulators, so the next tile's products run while
-// warps 2-5 drain the previous one: each of those threads owns one row of the tile, reads its 64
-// accumulator columns (tcgen05.ld) and its row of X from shared memory, rounds X - P V^T to
-// bfloat16 into a swizzled staging tile, and one thread stores the tile with a TMA bulk store.
+// lane 0 loads (TMA, 128-byte swizzle) the block's P parts once and streams the V parts in K
+// chunks of 64 through a ring of NB entries, and the 128 x 64 tiles of X into two buffers; warp 1
+// lane 0 issues tcgen05.mma (M = 128, N = 64, K = 16) into one of two tensor-memory accumulators,
+// so the next tile's products run while warps 2-5 drain the previous one: each of those threads
+// owns one row of the tile, reads its 64 accumulator columns (tcgen05.ld) and its row of X,
+// writes the bfloat16 rounding of X - P V^T over that row in place (same swizzled layout), and one
+// thread stores the tile with a TMA bulk store, after which the buffer takes the next X tile.
 // Every wait is bounded (status flag on timeout).
 constexpr int RT_ROWS = 128, RT_COLS = 64;
 constexpr uint32_t RT_A_TILE = 128 * 128;   // 128 rows x 64 bfloat16
@@ -452,9 +453,10 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
                : "memory");
 }
 
+template <int KC> __host__ __device__ constexpr int resid_ring() { return KC == 1 ? 4 : 3; }
 template <int KC>
 constexpr size_t resid_smem_bytes() {
-  return (size_t)3 * KC * RT_A_TILE + (size_t)(KC == 1 ? 2 : 1) * 3 * KC * RT_B_TILE + 4 * (size_t)RT_X_TILE + 1024;
+  return (size_t)3 * KC * RT_A_TILE + (size_t)resid_ring<KC>() * 3 * RT_B_TILE + 2 * (size_t)RT_X_TILE + 1024;
 }
 
 template <int KC>
@@ -463,29 +465,28 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
                                                             const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmZ, int64_t d,
                                                             int64_t np, int64_t dp, int* status) {
-  constexpr int BST = KC == 1 ? 2 : 1;
+  constexpr int NB = resid_ring<KC>();
   constexpr uint32_t A_BYTES = 3 * KC * RT_A_TILE;
-  constexpr uint32_t B_STAGE = 3 * KC * RT_B_TILE;
+  constexpr uint32_t B_ENTRY = 3 * RT_B_TILE;   // the three V parts of one K chunk
   extern __shared__ unsigned char rt_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(rt_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* As = base;
   unsigned char* Bs = As + A_BYTES;
-  unsigned char* Xs = Bs + BST * B_STAGE;
-  unsigned char* Zs = Xs + 2 * RT_X_TILE;
-  __shared__ uint64_t a_full, b_full[BST], b_empty[BST], x_full[2], x_empty[2], acc_full[2], acc_empty[2];
+  unsigned char* XZ = Bs + NB * B_ENTRY;
+  __shared__ uint64_t a_full, b_full[NB], b_empty[NB], x_full[2], x_empty[2], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_holder;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = blockIdx.x * RT_ROWS;
   const int ntiles = (int)((d + RT_COLS - 1) / RT_COLS);
   if (threadIdx.x == 0) {
     mbar_init_cta(&a_full, 1);
-    for (int s = 0; s < BST; ++s) {
+    for (int s = 0; s < NB; ++s) {
       mbar_init_cta(&b_full[s], 1);
       mbar_init_cta(&b_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init_cta(&x_full[s], 1);
-      mbar_init_cta(&x_empty[s], 4);
+      mbar_init_cta(&x_empty[s], 1);
       mbar_init_cta(&acc_full[s], 1);
       mbar_init_cta(&acc_empty[s], 4);
     }
@@ -509,17 +510,19 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
         for (int kc = 0; kc < KC; ++kc)
           tma_load_2d(As + (pa * KC + kc) * RT_A_TILE, &tmA, kc * 64, (int)(pa * np) + row0, &a_full);
       for (int t = 0; t < ntiles; ++t) {
-        const int sb = t % BST, u = t / BST;
-        if (u >= 1 && !mbar_wait_bounded(&b_empty[sb], (uint32_t)((u - 1) & 1), kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
-        mbar_expect_tx_cta(&b_full[sb], B_STAGE);
-        unsigned char* bst = Bs + sb * B_STAGE;
-        for (int pb = 0; pb < 3; ++pb)
-          for (int kc = 0; kc < KC; ++kc)
-            tma_load_2d(bst + (pb * KC + kc) * RT_B_TILE, &tmB, kc * 64, (int)(pb * dp) + t * RT_COLS, &b_full[sb]);
+        for (int kc = 0; kc < KC; ++kc) {
+          const int c = t * KC + kc, e = c % NB, u = c / NB;
+          if (u >= 1 && !mbar_wait_bounded(&b_empty[e], (uint32_t)((u - 1) & 1), kUmmaWait))
+            atomicOr(status, STATUS_TIMEOUT);
+          mbar_expect_tx_cta(&b_full[e], B_ENTRY);
+          for (int pb = 0; pb < 3; ++pb)
+            tma_load_2d(Bs + e * B_ENTRY + pb * RT_B_TILE, &tmB, kc * 64, (int)(pb * dp) + t * RT_COLS, &b_full[e]);
+        }
         const int sx = t & 1, ux = t >> 1;
-        if (ux >= 1 && !mbar_wait_bounded(&x_empty[sx], (uint32_t)((ux - 1) & 1), kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
+        if (ux >= 1 && !mbar_wait_bounded(&x_empty[sx], (uint32_t)((ux - 1) & 1), kUmmaWait))
+          atomicOr(status, STATUS_TIMEOUT);
         mbar_expect_tx_cta(&x_full[sx], RT_X_TILE);
-        tma_load_2d(Xs + sx * RT_X_TILE, &tmX, t * RT_COLS, row0, &x_full[sx]);
+        tma_load_2d(XZ + sx * RT_X_TILE, &tmX, t * RT_COLS, row0, &x_full[sx]);
       }
     }
   } else if (warp == 1) {
@@ -527,35 +530,35 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
       if (!mbar_wait_bounded(&a_full, 0u, kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
       const uint32_t sa = cta_smem_addr(As);
       for (int t = 0; t < ntiles; ++t) {
-        const int sb = t % BST, u = t / BST, ab = t & 1, ua = t >> 1;
-        if (!mbar_wait_bounded(&b_full[sb], (uint32_t)(u & 1), kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
+        const int ab = t & 1, ua = t >> 1;
         if (ua >= 1 && !mbar_wait_bounded(&acc_empty[ab], (uint32_t)((ua - 1) & 1), kUmmaWait))
           atomicOr(status, STATUS_TIMEOUT);
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t sbb = cta_smem_addr(Bs + sb * B_STAGE);
         const uint32_t dt = tmem + (uint32_t)(ab * RT_COLS);
-        uint32_t accum = 0;
+        for (int kc = 0; kc < KC; ++kc) {
+          const int c = t * KC + kc, e = c % NB, u = c / NB;
+          if (!mbar_wait_bounded(&b_full[e], (uint32_t)(u & 1), kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t sbb = cta_smem_addr(Bs + e * B_ENTRY);
 #pragma unroll
-        for (int kc = 0; kc < KC; ++kc)
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const int pa = c < 3 ? 0 : (c < 5 ? 1 : 2);      // (0,0) (0,1) (0,2) (1,0) (1,1) (2,0)
-            const int pb = c < 3 ? c : (c < 5 ? c - 3 : 0);
+          for (int q = 0; q < 6; ++q) {
+            const int pa = q < 3 ? 0 : (q < 5 ? 1 : 2);      // (0,0) (0,1) (0,2) (1,0) (1,1) (2,0)
+            const int pb = q < 3 ? q : (q < 5 ? q - 3 : 0);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t da = smem_desc_sw128(sa + (pa * KC + kc) * RT_A_TILE + kk * 32);
-              const uint64_t db = smem_desc_sw128(sbb + (pb * KC + kc) * RT_B_TILE + kk * 32);
+              const uint64_t db = smem_desc_sw128(sbb + pb * RT_B_TILE + kk * 32);
+              const uint32_t accum = (kc | q | kk) != 0;
               asm volatile(
-                  "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(dt),
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
                   "l"(da), "l"(db), "r"(kPrepIdesc), "r"(accum)
                   : "memory");
-              accum = 1;
             }
           }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         cta_smem_addr(&b_empty[sb]))
-                     : "memory");
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           cta_smem_addr(&b_empty[e]))
+                       : "memory");
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                          cta_smem_addr(&acc_full[ab]))
                      : "memory");
@@ -590,11 +593,7 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_cta(&acc_empty[ab]);
-      // the staging tile of tile t - 2 has been read by its bulk store
-      if (lead) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
-      asm volatile("bar.sync 1, 128;\n" ::: "memory");
-      const unsigned char* xr = Xs + ab * RT_X_TILE + r * 128;
-      unsigned char* zr = Zs + ab * RT_X_TILE + r * 128;
+      unsigned char* xr = XZ + ab * RT_X_TILE + r * 128;
 #pragma unroll
       for (int u8 = 0; u8 < 8; ++u8) {
         const int off = (u8 ^ (r & 7)) << 4;
@@ -608,15 +607,16 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
           const __nv_bfloat16 z1 = __float2bfloat16_rn(x1 - __uint_as_float(v[8 * u8 + 2 * e + 1]));
           zw[e] = (uint32_t)__bfloat16_as_ushort(z0) | ((uint32_t)__bfloat16_as_ushort(z1) << 16);
         }
-        *reinterpret_cast<uint4*>(zr + off) = make_uint4(zw[0], zw[1], zw[2], zw[3]);
+        *reinterpret_cast<uint4*>(xr + off) = make_uint4(zw[0], zw[1], zw[2], zw[3]);
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive_cta(&x_empty[ab]);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       asm volatile("bar.sync 1, 128;\n" ::: "memory");
       if (lead) {
-        tma_store_2d(&tmZ, Zs + ab * RT_X_TILE, t * RT_COLS, row0);
+        tma_store_2d(&tmZ, XZ + ab * RT_X_TILE, t * RT_COLS, row0);
         asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        // the buffer takes the next X tile once the store has read it
+        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        mbar_arrive_cta(&x_empty[ab]);
       }
     }
     if (lead) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
