@@ -263,7 +263,10 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
         if (q < k) {
           const TW apq = A[p * LD + q];
           const TW app = A[p * LD + p], aqq = A[q * LD + q];
-          const TW thr = fmax(rel * sqrt(fabs(app * aqq)), abs_floor);
+          // below a few rounding units of the larger diagonal entry a rotation only stirs
+          // rounding noise (graded spectra would otherwise rotate until the sweep limit)
+          const TW noise = TW(4) * (sizeof(TW) == 8 ? TW(0x1p-53) : TW(0x1p-24)) * fmax(fabs(app), fabs(aqq));
+          const TW thr = fmax(fmax(rel * sqrt(fabs(app * aqq)), abs_floor), noise);
           if (fabs(apq) > thr) {
             const TW theta = (aqq - app) / (TW(2) * apq);
             const TW t = (theta >= TW(0) ? TW(1) : TW(-1)) / (fabs(theta) + sqrt(theta * theta + TW(1)));

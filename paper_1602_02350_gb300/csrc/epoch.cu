@@ -1235,21 +1235,56 @@ __global__ void __launch_bounds__(256) epoch_c_kernel(const S* __restrict__ Z, i
                                                       const T* __restrict__ mu, const T* __restrict__ Rt,
                                                       T* __restrict__ cvec, const float* __restrict__ rsc) {
   constexpr int B = kBlk;
+  constexpr int EU = 16 / (int)sizeof(S);   // elements per 16-byte unit of a row
+  extern __shared__ float4 ec_sh4[];
+  T* mus = reinterpret_cast<T*>(ec_sh4);    // mu, zero-padded to whole units
   __shared__ T h[B];
   const int64_t b = blockIdx.x, t0 = b * B;
   const int Bb = (int)min64(B, m - t0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int l = warp; l < B; l += nw) {
-    T s = T(0);
-    int64_t ri = 0;
-    if (l < Bb) {
-      ri = min64((int64_t)idx[t0 + l], N - 1);
-      const S* row = Z + ri * ld;
-      for (int64_t c = lane; c < d; c += 32) s = fma(cvt<T>(row[c]), mu[c], s);
+  const int64_t nu = (d + EU - 1) / EU;
+  for (int64_t e = threadIdx.x; e < nu * EU; e += blockDim.x) mus[e] = e < d ? mu[e] : T(0);
+  __syncthreads();
+  // h_l = z_l^T mu: a warp takes two rows at a time, 16-byte loads of both issued together
+  for (int l0 = warp; l0 < B; l0 += 2 * nw) {
+    int64_t ri[2];
+    const S* row[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int l = l0 + k * nw;
+      ri[k] = l < Bb ? min64((int64_t)idx[t0 + l], N - 1) : -1;
+      row[k] = ri[k] >= 0 ? Z + ri[k] * ld : nullptr;
     }
-    s = warp_sum(s);
-    if (IsFp8<S>::value && l < Bb) s *= (T)rsc[ri];
-    if (lane == 0) h[l] = s;
+    T s[2] = {T(0), T(0)};
+    for (int64_t u = lane; u < nu; u += 32) {
+      const int64_t c0 = u * EU;
+      S v[2][EU];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (!row[k]) {
+#pragma unroll
+          for (int e = 0; e < EU; ++e) v[k][e] = S(0.0f);
+        } else if (c0 + EU <= d) {
+          *reinterpret_cast<uint4*>(v[k]) = *reinterpret_cast<const uint4*>(row[k] + c0);
+        } else {
+#pragma unroll
+          for (int e = 0; e < EU; ++e) v[k][e] = c0 + e < d ? row[k][c0 + e] : S(0.0f);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < EU; ++e) {
+        const T me = mus[c0 + e];
+        s[0] = fma(cvt<T>(v[0][e]), me, s[0]);
+        s[1] = fma(cvt<T>(v[1][e]), me, s[1]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      T t = warp_sum(s[k]);
+      const int l = l0 + k * nw;
+      if (IsFp8<S>::value && ri[k] >= 0) t *= (T)rsc[ri[k]];
+      if (lane == 0 && l < B) h[l] = ri[k] >= 0 ? t : T(0);
+    }
   }
   __syncthreads();
   if (threadIdx.x < B) {
@@ -1286,8 +1321,12 @@ int epoch_finish_t(rs_ctx* ctx, const rs_matrix* Z, const uint32_t* idx, int64_t
   const S* Zd = static_cast<const S*>(Z->data);
   const int64_t N = Z->n, d = Z->d;
   const int64_t nblk = (m + kBlk - 1) / kBlk;
-  epoch_c_kernel<S, T><<<(unsigned)nblk, 256, 0, ctx->stream>>>(Zd, N, Z->ld, d, idx, m, eta, mu, Rt, cv,
-                                                                 Z->row_scale);
+  constexpr int EU = 16 / (int)sizeof(S);
+  const size_t cshm = (size_t)((d + EU - 1) / EU) * EU * sizeof(T);
+  if (cshm > 48 * 1024)
+    RS_CUDA_TRY(cudaFuncSetAttribute(epoch_c_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
+  epoch_c_kernel<S, T><<<(unsigned)nblk, 256, cshm, ctx->stream>>>(Zd, N, Z->ld, d, idx, m, eta, mu, Rt, cv,
+                                                                    Z->row_scale);
   RS_LAUNCH_CHECK(ctx);
   for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
     const ChainPlan pl = plan_chain<S, T>(d, cs);
