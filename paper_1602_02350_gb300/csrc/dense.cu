@@ -136,11 +136,30 @@ __global__ void __launch_bounds__(256) gram_kernel(int64_t rows, int64_t Ma, int
   }
 }
 
-__global__ void reduce_chunks_kernel(const double* part, int64_t nchunks, int64_t count, double alpha, double* G) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int64_t c = 0; c < nchunks; ++c) s += part[c * count + e];
-    G[e] = alpha * s;
+// G[e] = alpha * sum over the chunks of part[c][e]: 32 entries per block, the chunks split over
+// 8 warps (two interleaved partial sums each), then the warps' sums in warp order (deterministic;
+// short dependent chains of double adds, which are slow on this GPU)
+__global__ void __launch_bounds__(256) reduce_chunks_kernel(const double* part, int64_t nchunks, int64_t count,
+                                                            double alpha, double* G) {
+  __shared__ double sh[8][33];
+  const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  double s0 = 0.0, s1 = 0.0;
+  if (e < count) {
+    int64_t c = g;
+    for (; c + 8 < nchunks; c += 16) {
+      s0 += part[c * count + e];
+      s1 += part[(c + 8) * count + e];
+    }
+    for (; c < nchunks; c += 8) s0 += part[c * count + e];
+  }
+  sh[g][lane] = s0 + s1;
+  __syncthreads();
+  if (g == 0 && e < count) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sh[w][lane];
+    G[e] = alpha * t;
   }
 }
 
@@ -383,21 +402,48 @@ __global__ void identity_rows_kernel(T* Z, int64_t d, int64_t ld) {   // T: stor
 template <typename S, typename T>
 __global__ void row_beta_kernel(const S* Z, int64_t N, int64_t n, int64_t d, int64_t ld, double lam, T* beta,
                                 double* part) {
+  // a warp takes two rows at a time; lanes read 16-byte units (rows are 16-byte aligned)
+  constexpr int EU = 16 / (int)sizeof(S);
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double acc_blk = 0.0;
   const double gd = (double)N / (double)n, gr = lam * (double)N;
-  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
-    T s = T(0);
-    for (int64_t c = lane; c < d; c += 32) {
-      const T v = cvt<T>(Z[i * ld + c]);
-      s = fma(v, v, s);
+  const int64_t nu = (d + EU - 1) / EU;
+  for (int64_t i0 = ((int64_t)blockIdx.x * nw + warp) * 2; i0 < N; i0 += (int64_t)gridDim.x * nw * 2) {
+    T s[2] = {T(0), T(0)};
+    for (int64_t u = lane; u < nu; u += 32) {
+      const int64_t c0 = u * EU;
+      S v[2][EU];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int64_t i = i0 + k;
+        if (i >= N) {
+#pragma unroll
+          for (int e = 0; e < EU; ++e) v[k][e] = S(0.0f);
+        } else if (c0 + EU <= d) {
+          *reinterpret_cast<uint4*>(v[k]) = *reinterpret_cast<const uint4*>(Z + i * ld + c0);
+        } else {
+#pragma unroll
+          for (int e = 0; e < EU; ++e) v[k][e] = c0 + e < d ? Z[i * ld + c0 + e] : S(0.0f);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int e = 0; e < EU; ++e) {
+          const T x = cvt<T>(v[k][e]);
+          s[k] = fma(x, x, s[k]);
+        }
     }
-    s = warp_sum(s);
-    const double b = (i < n ? gd : gr) * (double)s;
-    if (lane == 0) {
-      beta[i] = (T)b;
-      acc_blk += b;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int64_t i = i0 + k;
+      const T t = warp_sum(s[k]);
+      if (i < N && lane == 0) {
+        const double b = (i < n ? gd : gr) * (double)t;
+        beta[i] = (T)b;
+        acc_blk += b;
+      }
     }
   }
   if (lane == 0) sh[warp] = acc_blk;
@@ -409,12 +455,12 @@ __global__ void row_beta_kernel(const S* Z, int64_t N, int64_t n, int64_t d, int
   }
 }
 
+// out = scale * sum of part[0..np): lane-strided partial sums, then a fixed shuffle tree
 __global__ void sum_parts_kernel(const double* part, int np, double scale, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int p = 0; p < np; ++p) s += part[p];
-    *out = s * scale;
-  }
+  double s = 0.0;
+  for (int p = threadIdx.x; p < np; p += 32) s += part[p];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) *out = s * scale;
 }
 
 // w[c] = wt[c] - sum_j V[c][j] a_j t_j with t = V^T wt (double)
@@ -671,7 +717,9 @@ int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, 
   dim3 grid((unsigned)((Nb + 63) / 64), (unsigned)((Ma + 63) / 64), (unsigned)nchunks);
   gram_kernel<TA, TB, TACC><<<grid, 256, 0, ctx->stream>>>(rows, Ma, Nb, A, lda, B, ldb, rpc, part);
   RS_LAUNCH_CHECK(ctx);
-  reduce_chunks_kernel<<<blocks_for(ctx, Ma * Nb), 256, 0, ctx->stream>>>(part, nchunks, Ma * Nb, alpha, G);
+  const int64_t rblocks = (Ma * Nb + 31) / 32;
+  if (rblocks > 0x7FFFFFFF) return rs_fail(RS_EINVAL, "gram: output too large");
+  reduce_chunks_kernel<<<(unsigned)rblocks, 256, 0, ctx->stream>>>(part, nchunks, Ma * Nb, alpha, G);
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
 }
