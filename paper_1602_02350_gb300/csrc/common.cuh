@@ -25,7 +25,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_RPART, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_RPART, SCR_XPART, SCR_COUNT
 };
 
 struct rs_ctx {
@@ -35,6 +35,12 @@ struct rs_ctx {
   int64_t launches = 0;
   ScratchSlot slots[SCR_COUNT];
   int* d_status = nullptr;     // device status word (bit flags, see STATUS_*)
+  // public calls entered (rs_enter); the bfloat16 parts of a float X kept in SCR_XPART are reused
+  // only within the call that formed them (X cannot change during one call)
+  uint64_t call_gen = 0;
+  const void* xp_src = nullptr;
+  int64_t xp_n = 0, xp_d = 0, xp_ld = 0;
+  uint64_t xp_gen = ~uint64_t(0);
 };
 
 enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
@@ -227,8 +233,9 @@ int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, 
 
 int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W);
 
-// tcgen05 product for bfloat16 data (umma.cu): C = X W diag(col_scale), X M x K bfloat16 rows, W K x N
-// float (N <= 256), C float; RS_EUNSUPPORTED when the tensor path cannot run (caller falls back).
+// tcgen05 product (umma.cu): C = X W diag(col_scale), X M x K bfloat16 or float rows (float rows are
+// split into three bfloat16 parts first), W K x N float (N <= 256), C float; RS_EUNSUPPORTED when
+// the tensor path cannot run (caller falls back).
 bool umma_enabled();
 int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, const float* col_scale, float* C,
                  int64_t ldc);

@@ -23,6 +23,7 @@ int rs_enter(rs_ctx* ctx) {
   int cur = -1;
   RS_CUDA_TRY(cudaGetDevice(&cur));
   if (cur != ctx->device) RS_CUDA_TRY(cudaSetDevice(ctx->device));
+  ++ctx->call_gen;
   return RS_OK;
 }
 

@@ -855,9 +855,10 @@ static int ritz_t(rs_ctx* ctx, const rs_matrix* X, const T* Q, int64_t kq, int64
   double* Wd = static_cast<double*>(rs_scratch(ctx, SCR_W, kq * kq * sizeof(double)));
   T* Wt = static_cast<T*>(rs_scratch(ctx, SCR_ADIAG, kq * kq * sizeof(T)));
   if (!B || !G || !ev || !Wd || !Wt) return RS_ENOMEM;
-  // B = X Q (n x kq), G = B^T B / n   (bfloat16 data: X Q on the tensor cores)
+  // B = X Q (n x kq), G = B^T B / n   (bfloat16 or float data: X Q on the tensor cores)
   int rc_b = RS_EUNSUPPORTED;
-  if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<T, float>::value)
+  if constexpr ((std::is_same<S, __nv_bfloat16>::value || std::is_same<S, float>::value) &&
+                std::is_same<T, float>::value)
     if (umma_enabled()) rc_b = umma_gemm_xw(ctx, X, Q, kq, nullptr, B, kq);
   if (rc_b == RS_EUNSUPPORTED)
     RS_TRY(launch_gemm<T, S, T>(ctx, n, kq, d, 1.0, static_cast<const S*>(X->data), X->ld, 1, Q, kq, 1, 0.0, nullptr, 0,
@@ -939,9 +940,10 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
   adiag_kernel<T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(sigma2, (int)k, lam, a);
   RS_LAUNCH_CHECK(ctx);
   const S* Xd = static_cast<const S*>(X->data);
-  // P = X V diag(a);  Z[0:n] = X - P V^T   (bfloat16 data: X V on the tensor cores)
+  // P = X V diag(a);  Z[0:n] = X - P V^T   (bfloat16 or float data: X V on the tensor cores)
   int rc_p = RS_EUNSUPPORTED;
-  if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<T, float>::value)
+  if constexpr ((std::is_same<S, __nv_bfloat16>::value || std::is_same<S, float>::value) &&
+                std::is_same<T, float>::value)
     if (umma_enabled()) rc_p = umma_gemm_xw(ctx, X, V, k, a, P, k);
   if (rc_p == RS_EUNSUPPORTED)
     RS_TRY(launch_gemm<T, S, T>(ctx, n, k, d, 1.0, Xd, X->ld, 1, V, k, 1, 0.0, nullptr, 0, P, k, a));

@@ -714,7 +714,13 @@ static int solve_proposed_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, 
   int32_t k = 0, fb = 0;
   double em = 0.0;
   int64_t m = 0;
-  RS_TRY(rs_propose(ctx, theta, norm, s2h, p->lambda, n, d, trc, &k, &em, &m, &fb));
+  {
+    // rs_propose is a public entry (it opens a new call generation); it does not touch X, so the
+    // bfloat16 parts of X formed by the sketch stay valid for the preconditioner below
+    const uint64_t gen = ctx->call_gen;
+    RS_TRY(rs_propose(ctx, theta, norm, s2h, p->lambda, n, d, trc, &k, &em, &m, &fb));
+    ctx->call_gen = gen;
+  }
   T* Vk = static_cast<T*>(rs_scratch(ctx, SCR_VK, d * k * es));
   const int64_t ldz = (d * (int64_t)zs + 15) / 16 * 16 / (int64_t)zs;
   ZS* Zbuf = static_cast<ZS*>(rs_scratch(ctx, SCR_Z, (size_t)N * ldz * zs));

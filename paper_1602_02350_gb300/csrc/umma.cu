@@ -1,9 +1,10 @@
-// Tensor-core (tcgen05) product of bfloat16 data with a float matrix: C = X W diag(s), X (M x K,
-// bfloat16, row-major), W (K x N, float), C (M x N, float).  This is the X V contraction of the
-// preconditioner (Eq. (11)) and the X Q product of the Rayleigh-Ritz step (Alg. 2) for bfloat16
-// data.  W is split into three bfloat16 parts, W = W0 + W1 + W2 (W1 = bf16(W - W0), ...), so the
-// three accumulating products reproduce the float W to about 2^-24 relative; X is exact in
-// bfloat16.  Accumulation is FP32 in tensor memory.
+// Tensor-core (tcgen05) product of bfloat16 or float data with a float matrix: C = X W diag(s), X
+// (M x K, row-major), W (K x N, float), C (M x N, float).  This is the X V contraction of the
+// preconditioner (Eq. (11)) and the X Q product of the Rayleigh-Ritz step (Alg. 2).  W is split
+// into three bfloat16 parts, W = W0 + W1 + W2 (W1 = bf16(W - W0), ...), so the accumulating
+// products reproduce the float W to about 2^-24 relative; bfloat16 X is exact, float X is split
+// the same way into X0 + X1 + X2 and the six products X_a W_b with a + b <= 2 are accumulated
+// (the dropped ones are below 2^-27).  Accumulation is FP32 in tensor memory.
 //
 // One CTA per 128 x 128 output tile, 128 threads: warp 0 allocates 128 tensor-memory columns and
 // (lane 0) produces: TMA (cp.async.bulk.tensor, 128-byte swizzle) loads of the 128 x 64 X tile and
@@ -22,10 +23,16 @@
 
 namespace {
 
-constexpr int UM = 128, UN = 128, UK = 64, UST = 3, NSPLIT = 3;
-constexpr uint32_t A_BYTES = UM * UK * 2;               // 16 KB
-constexpr uint32_t B_BYTES = UN * UK * 2;               // 16 KB per W part
-constexpr uint32_t STAGE_BYTES = A_BYTES + NSPLIT * B_BYTES;
+constexpr int UM = 128, UK = 64, NSPLIT = 3;
+constexpr uint32_t A_BYTES = UM * UK * 2;               // 16 KB per X part
+// NA = 1: bfloat16 X; NA = 3: float X split into three bfloat16 parts.  UN = 64 or 128 output
+// columns per tile (W part tiles of UN x 64); as many ring stages as fit in 217 KB, at most 4.
+template <int NA, int UN> __host__ __device__ constexpr uint32_t xw_stage_bytes() {
+  return NA * A_BYTES + NSPLIT * (uint32_t)(UN * UK * 2);
+}
+template <int NA, int UN> __host__ __device__ constexpr int xw_stages() {
+  return (int)(216u * 1024u / xw_stage_bytes<NA, UN>()) < 4 ? (int)(216u * 1024u / xw_stage_bytes<NA, UN>()) : 4;
+}
 constexpr long long kUmmaWait = 2000000000LL;
 
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
@@ -40,8 +47,10 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: f32 accumulate, bf16 A and B, both K-major, N = 128, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+// instruction descriptor: f32 accumulate, bf16 A and B, both K-major, N = UN, M = 128
+template <int UN> __host__ __device__ constexpr uint32_t xw_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+}
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
@@ -51,10 +60,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+template <int NA, int UN>
 __global__ void __launch_bounds__(128, 1) umma_xw_kernel(const __grid_constant__ CUtensorMap tmX,
                                                          const __grid_constant__ CUtensorMap tmW, int64_t M, int K,
                                                          int N, int kp, const float* __restrict__ col_scale,
                                                          float* __restrict__ C, int64_t ldc, int* status) {
+  constexpr int UST = xw_stages<NA, UN>();
+  constexpr uint32_t STAGE_BYTES = xw_stage_bytes<NA, UN>();
+  constexpr uint32_t B_BYTES = UN * UK * 2;
+  constexpr uint32_t kIdesc = xw_idesc<UN>();
   extern __shared__ unsigned char um_raw[];
   // the swizzled tiles need 1024-byte alignment
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(um_raw) + 1023) & ~uintptr_t(1023));
@@ -98,8 +112,9 @@ __global__ void __launch_bounds__(128, 1) umma_xw_kernel(const __grid_constant__
       if (abort_flag) break;
       unsigned char* st = base + (size_t)s * STAGE_BYTES;
       mbar_expect_tx_cta(&full[s], STAGE_BYTES);
-      tma_load_2d(st, &tmX, kb * UK, (int)m0, &full[s]);
-      for (int p = 0; p < NSPLIT; ++p) tma_load_2d(st + A_BYTES + p * B_BYTES, &tmW, kb * UK, p * kp + n0, &full[s]);
+      for (int a = 0; a < NA; ++a) tma_load_2d(st + a * A_BYTES, &tmX, kb * UK, (int)(a * M + m0), &full[s]);
+      for (int p = 0; p < NSPLIT; ++p)
+        tma_load_2d(st + NA * A_BYTES + p * B_BYTES, &tmW, kb * UK, p * kp + n0, &full[s]);
       issued_last[s] = u;
     }
     for (int s = 0; s < UST; ++s)   // every issued copy lands before the CTA moves on
@@ -115,13 +130,17 @@ __global__ void __launch_bounds__(128, 1) umma_xw_kernel(const __grid_constant__
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t sa = cta_smem_addr(base + (size_t)s * STAGE_BYTES);
+      // products X_a W_b with a + b <= 2 (NA = 1: a = 0)
+      constexpr int NPROD = NA == 1 ? 3 : 6;
 #pragma unroll
       for (int kk = 0; kk < UK / 16; ++kk) {
-        const uint64_t da = smem_desc_sw128(sa + kk * 32);
 #pragma unroll
-        for (int p = 0; p < NSPLIT; ++p) {
-          const uint64_t db = smem_desc_sw128(sa + A_BYTES + p * B_BYTES + kk * 32);
-          const uint32_t accum = (kb | kk | p) != 0;
+        for (int q = 0; q < NPROD; ++q) {
+          const int a = q < 3 ? 0 : (q < 5 ? 1 : 2);
+          const int p = q < 3 ? q : (q < 5 ? q - 3 : 0);
+          const uint64_t da = smem_desc_sw128(sa + a * A_BYTES + kk * 32);
+          const uint64_t db = smem_desc_sw128(sa + NA * A_BYTES + p * B_BYTES + kk * 32);
+          const uint32_t accum = (kb | kk | q) != 0;
           asm volatile(
               "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
@@ -629,6 +648,37 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
   }
 }
 
+// Float rows (16-byte aligned, row stride lds) -> three bfloat16 parts (3 x rows x kp, kp a multiple
+// of 8), part p = bf16(x - part 0 - .. - part p-1), zero beyond k; 8 elements per thread
+__global__ void split3_x_kernel(const float* __restrict__ src, int64_t rows, int64_t k, int64_t lds, int64_t kp,
+                                __nv_bfloat16* __restrict__ out) {
+  const int64_t units = kp / 8, total = rows * units;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / units, c0 = (e % units) * 8;
+    float v[8];
+    const float* r = src + i * lds + c0;
+    if (c0 + 8 <= k) {
+      const float4 a = *reinterpret_cast<const float4*>(r), b = *reinterpret_cast<const float4*>(r + 4);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = c0 + q < k ? r[q] : 0.0f;
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v[2 * q]), hi = __float2bfloat16_rn(v[2 * q + 1]);
+        v[2 * q] -= __bfloat162float(lo);
+        v[2 * q + 1] -= __bfloat162float(hi);
+        w[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+      }
+      *reinterpret_cast<uint4*>(out + (int64_t)p * rows * kp + i * kp + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
 // src (rows x k float, row stride lds) -> out (3 x rows_pad x kp bfloat16): part p holds
 // bf16(src - part 0 - .. - part p-1), zero beyond rows and k
 __global__ void split3_rows_kernel(const float* __restrict__ src, int64_t rows, int k, int64_t lds, int64_t rows_pad,
@@ -769,24 +819,58 @@ int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, con
                  int64_t ldc) {
   const int64_t M = X->n, K = X->d;
   if (N < 1 || N > 256 || K < 1) return RS_EUNSUPPORTED;
+  if (X->dtype != RS_BF16 && X->dtype != RS_F32) return RS_EUNSUPPORTED;
   if (!encode_fn()) return RS_EUNSUPPORTED;
+  const bool f32 = X->dtype == RS_F32;
+  const int UN = N <= 64 ? 64 : 128;
   const int kp = (int)((N + UN - 1) / UN * UN);
   const int ldp = (int)((K + 7) / 8 * 8);        // 16-byte rows
-  __nv_bfloat16* parts =
-      static_cast<__nv_bfloat16*>(rs_scratch(ctx, SCR_UMMA, (size_t)NSPLIT * kp * ldp * sizeof(__nv_bfloat16)));
+  // float data: X = X0 + X1 + X2 in bfloat16 parts (about 2^-24 relative), at most 8 GB of parts
+  const size_t xparts = f32 ? (size_t)NSPLIT * M * ldp * sizeof(__nv_bfloat16) : 0;
+  if (f32 && (xparts > ((size_t)8 << 30) || 3 * M > 0x7FFFFF00LL)) return RS_EUNSUPPORTED;
+  const size_t wparts = (size_t)NSPLIT * kp * ldp * sizeof(__nv_bfloat16);
+  __nv_bfloat16* parts = static_cast<__nv_bfloat16*>(rs_scratch(ctx, SCR_UMMA, wparts));
   if (!parts) return RS_ENOMEM;
   split_transpose_kernel<<<(unsigned)std::min<int64_t>(((int64_t)kp * ldp + 255) / 256, ctx->num_sms * 8), 256, 0,
                            ctx->stream>>>(W, (int)K, (int)N, kp, ldp, parts);
   RS_LAUNCH_CHECK(ctx);
   CUtensorMap mx, mw;
-  RS_TRY(make_map(&mx, X->data, K, M, X->ld, UM));
+  if (f32) {
+    const bool cached = ctx->xp_gen == ctx->call_gen && ctx->xp_src == X->data && ctx->xp_n == M &&
+                        ctx->xp_d == K && ctx->xp_ld == X->ld && ctx->slots[SCR_XPART].bytes >= xparts;
+    __nv_bfloat16* xp = static_cast<__nv_bfloat16*>(rs_scratch(ctx, SCR_XPART, xparts));
+    if (!xp) return RS_ENOMEM;
+    if (!cached) {
+      split3_x_kernel<<<(unsigned)std::min<int64_t>((M * (ldp / 8) + 255) / 256, ctx->num_sms * 8), 256, 0,
+                        ctx->stream>>>(static_cast<const float*>(X->data), M, K, X->ld, ldp, xp);
+      RS_LAUNCH_CHECK(ctx);
+      ctx->xp_src = X->data;
+      ctx->xp_n = M;
+      ctx->xp_d = K;
+      ctx->xp_ld = X->ld;
+      ctx->xp_gen = ctx->call_gen;
+    }
+    RS_TRY(make_map(&mx, xp, K, 3 * M, ldp, UM));
+  } else {
+    RS_TRY(make_map(&mx, X->data, K, M, X->ld, UM));
+  }
   RS_TRY(make_map(&mw, parts, K, (int64_t)NSPLIT * kp, ldp, UN));
-  const size_t shm = (size_t)UST * STAGE_BYTES + 1024;
-  RS_CUDA_TRY(cudaFuncSetAttribute(umma_xw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 grid((unsigned)((M + UM - 1) / UM), (unsigned)(kp / UN));
-  if (grid.x > 0x7FFFFFFF) return rs_fail(RS_EINVAL, "umma gemm: too many row tiles");
+  if ((M + UM - 1) / UM > 0x7FFFFFFF) return rs_fail(RS_EINVAL, "umma gemm: too many row tiles");
   RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-  umma_xw_kernel<<<grid, 128, shm, ctx->stream>>>(mx, mw, M, (int)K, (int)N, kp, col_scale, C, ldc, ctx->d_status);
+#define RS_XW(NA_, UN_)                                                                                       \
+  do {                                                                                                        \
+    constexpr size_t shm = (size_t)xw_stages<NA_, UN_>() * xw_stage_bytes<NA_, UN_>() + 1024;                 \
+    RS_CUDA_TRY(cudaFuncSetAttribute(umma_xw_kernel<NA_, UN_>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                     (int)shm));                                                              \
+    umma_xw_kernel<NA_, UN_><<<grid, 128, shm, ctx->stream>>>(mx, mw, M, (int)K, (int)N, kp, col_scale, C, ldc, \
+                                                               ctx->d_status);                                \
+  } while (0)
+  if (f32 && UN == 64) RS_XW(3, 64);
+  else if (f32) RS_XW(3, 128);
+  else if (UN == 64) RS_XW(1, 64);
+  else RS_XW(1, 128);
+#undef RS_XW
   RS_LAUNCH_CHECK(ctx);
   int st = 0;
   RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

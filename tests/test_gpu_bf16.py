@@ -176,6 +176,7 @@ def test_bf16_x_times_v_both_paths(rsctx, monkeypatch, umma, n, d, k):
     """X V for bfloat16 data on the tensor cores (tcgen05, V split into three bfloat16 parts) and
     on CUDA cores give the oracle's components to the same tolerance."""
     monkeypatch.setenv("RS_UMMA", umma)
+    monkeypatch.setenv("RS_UMMA_RESID", umma)
     X = torch.from_numpy(synth.random_matrix(n, d, 3 * n + d, scale=1.0 / np.sqrt(d))).to(torch.bfloat16)
     V = torch.from_numpy(synth.random_orthonormal(d, k, d + 5)).float()
     s2 = synth.random_sigma2(k, k + 3)
@@ -186,3 +187,22 @@ def test_bf16_x_times_v_both_paths(rsctx, monkeypatch, umma, n, d, k):
     Xt, B = precond.transform(X.double().numpy(), M)
     scale = np.abs(X.double().numpy()).max() * (1 + np.sqrt(k))
     assert np.all(np.abs(Zg[:n] - Xt) <= BF16_UNIT * np.abs(Xt) + 4e-6 * scale)
+
+
+@pytest.mark.parametrize("umma", ["1", "0"])
+@pytest.mark.parametrize("n,d,k", [(1, 8, 1), (300, 72, 5), (4097, 256, 16), (20000, 1024, 130), (65536, 1024, 64)])
+def test_f32_x_times_v_both_paths(rsctx, monkeypatch, umma, n, d, k):
+    """X V and X Q for float data on the tensor cores (X and W each split into three bfloat16
+    parts, six products) and on CUDA cores: float components to FP32 accuracy, and the
+    Rayleigh-Ritz step (Alg. 2) on the same data."""
+    monkeypatch.setenv("RS_UMMA", umma)
+    X = torch.from_numpy(synth.random_matrix(n, d, 5 * n + d, scale=1.0 / np.sqrt(d))).float()
+    V = torch.from_numpy(synth.random_orthonormal(d, k, d + 7)).float()
+    s2 = synth.random_sigma2(k, k + 1)
+    lam = 1e-4
+    Z, _, _ = rs.rs_precondition(rsctx, cuda_rows(X), V.cuda(), torch.from_numpy(s2).cuda(), lam)
+    Zg = Z.cpu().double().numpy()
+    M = precond.m_matrix(V.double().numpy(), s2, lam)
+    Xt, _ = precond.transform(X.double().numpy(), M)
+    scale = np.abs(X.double().numpy()).max() * (1 + np.sqrt(k))
+    np.testing.assert_allclose(Zg[:n], Xt, rtol=0, atol=2e-6 * scale)
