@@ -171,36 +171,37 @@ __global__ void convert_from_double_kernel(const double* in, int64_t count, T* o
 
 // ------------------------------------------------------------------ Cholesky-QR
 // Lower Cholesky factor L of the k x k double matrix G (G = L L^T, right-looking, one block) and
-// its inverse L^{-1} (column c by forward substitution, one thread per column), written as T.
-// L and the inverse live in shared memory when they fit (buf = nullptr), else in buf (2 k^2 doubles).
-template <typename T>
-__global__ void chol_inv_kernel(const double* G, int k, double* buf, T* Linv_out, int* status) {
-  extern __shared__ double ci_sh[];
+// its inverse L^{-1} (column c by forward substitution, one thread per column), computed in C and
+// written as T.  L and the inverse live in shared memory when they fit (buf = nullptr), else in buf.
+template <typename T, typename C>
+__global__ void chol_inv_kernel(const double* G, int k, C* buf, T* Linv_out, int* status) {
+  extern __shared__ __align__(16) unsigned char ci_raw[];
+  C* ci_sh = reinterpret_cast<C*>(ci_raw);
   // rows padded to k + 1: column accesses by consecutive threads spread over the banks
   const int LD = k + 1;
-  double* L = buf ? buf : ci_sh;
-  double* Xi = L + (size_t)k * LD;
-  double* dinv = Xi + (size_t)k * LD;
+  C* L = buf ? buf : ci_sh;
+  C* Xi = L + (size_t)k * LD;
+  C* dinv = Xi + (size_t)k * LD;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < k * k; e += nt) {
     const int r = e / k, c = e % k;
-    L[r * LD + c] = G[e];
-    Xi[r * LD + c] = 0.0;
+    L[r * LD + c] = (C)G[e];
+    Xi[r * LD + c] = C(0);
   }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
     if (tid == 0) {
-      double v = L[j * LD + j];
-      if (!(v > 0.0) || !isfinite(v)) {
+      C v = L[j * LD + j];
+      if (!(v > C(0)) || !isfinite(v)) {
         atomicOr(status, 4);
-        v = 1.0;
+        v = C(1);
       }
-      const double r = sqrt(v);
+      const C r = sqrt(v);
       L[j * LD + j] = r;
-      dinv[j] = 1.0 / r;
+      dinv[j] = C(1) / r;
     }
     __syncthreads();
-    const double rj = dinv[j];
+    const C rj = dinv[j];
     for (int i = j + 1 + tid; i < k; i += nt) L[i * LD + j] *= rj;
     __syncthreads();
     const int w = k - j - 1;
@@ -214,7 +215,7 @@ __global__ void chol_inv_kernel(const double* G, int k, double* buf, T* Linv_out
   for (int c = tid; c < k; c += nt) {
     Xi[c * LD + c] = dinv[c];
     for (int i = c + 1; i < k; ++i) {
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      C s0 = C(0), s1 = C(0), s2 = C(0), s3 = C(0);
       int p = c;
       for (; p + 3 < i; p += 4) {
         s0 = fma(L[i * LD + p], Xi[p * LD + c], s0);
@@ -803,12 +804,19 @@ static int orthonormalize_t(rs_ctx* ctx, const T* Y, int64_t d, int64_t k, T* Q)
     if (!buf) return RS_ENOMEM;
   }
   const size_t shm = smem ? bytes : 0;
-  RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   const T* src = Y;
   for (int pass = 0; pass < 2; ++pass) {
     T* dst = pass == 0 ? tmp : Q;
     RS_TRY(launch_gram<T>(ctx, d, k, k, src, k, src, k, 1.0, G));
-    chol_inv_kernel<T><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Linv, ctx->d_status);
+    // the first factorisation sees cond(Y)^2 and runs in double; the second one factors the Gram
+    // matrix of an already orthonormal-to-rounding basis (condition ~1) in the storage type
+    // (double work is slow on this GPU)
+    if (pass == 0)
+      chol_inv_kernel<T, double><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Linv, ctx->d_status);
+    else
+      chol_inv_kernel<T, T><<<1, 256, shm, ctx->stream>>>(G, (int)k, reinterpret_cast<T*>(buf), Linv, ctx->d_status);
     RS_LAUNCH_CHECK(ctx);
     // Q = Y L^{-T}: B(p, j) = Linv[j][p]
     RS_TRY(launch_gemm<T>(ctx, d, k, k, 1.0, src, k, 1, Linv, 1, k, 0.0, nullptr, 0, dst, k, nullptr));
