@@ -216,71 +216,145 @@ __global__ void __launch_bounds__(256) skinny_xu_kernel(const S* __restrict__ X,
   }
 }
 
-// part[chunk][c][r] = sum over the chunk's rows of X[i][c] Rm[i][r] (r < R).  A block covers
-// 32 CPL columns (CPL = 64 / RMAX per lane, 64 accumulators); its 8 warps take interleaved rows,
-// then the warps' sums are added in warp order through shared memory (64 KB).
+// part[chunk][c][r] = sum over the chunk's rows of X[i][c] Rm[i][r] (r < R), per 32 CPL columns
+// (CPL = 64 / RMAX per lane, 64 accumulators).
+// The same transposed pass fed by bulk copies: a producer warp streams tiles of 16 row slices
+// (32 CPL columns each) and the matching 16 rows of Rm into an 8-stage shared-memory ring
+// (cp.async.bulk, bytes counted on mbarriers, bounded waits); 8 consumer warps take two rows of
+// each tile, then the warps' sums are added in warp order (the ring's memory is reused).
+constexpr int kXtrRows = 16, kXtrStages = 8;
+constexpr long long kXtrWait = 2000000000LL;
 template <typename S, int RMAX>
-__global__ void __launch_bounds__(256, 2) skinny_xtr_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
-                                                         const float* __restrict__ Rm, int R, int64_t rows_per_chunk,
-                                                         float* __restrict__ part) {
+constexpr size_t xtr_bulk_smem() {
+  constexpr size_t ring = (size_t)kXtrStages * kXtrRows * (32 * (64 / RMAX) * sizeof(S) + RMAX * sizeof(float));
+  constexpr size_t red = (size_t)8 * 64 * 32 * sizeof(float);
+  return ring > red ? ring : red;
+}
+template <typename S, int RMAX>
+__global__ void __launch_bounds__(288) skinny_xtr_bulk_kernel(const S* __restrict__ X, int64_t n, int64_t d, int64_t ld,
+                                                              const float* __restrict__ Rm, int R,
+                                                              int64_t rows_per_chunk, float* __restrict__ part,
+                                                              int* status) {
   constexpr int CPL = 64 / RMAX;
   constexpr int CPW = 32 * CPL;
-  extern __shared__ float4 red4[];
-  float* red = reinterpret_cast<float*>(red4);   // [8][CPL * RMAX][32]
+  constexpr uint32_t XROW = CPW * sizeof(S);
+  constexpr uint32_t XST = kXtrRows * XROW;
+  constexpr uint32_t ST = XST + kXtrRows * RMAX * sizeof(float);
+  extern __shared__ __align__(128) unsigned char xb_sh[];
+  __shared__ uint64_t full[kXtrStages], empty[kXtrStages];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t c = (int64_t)blockIdx.y * CPW + lane * CPL;
+  const int64_t cb0 = (int64_t)blockIdx.y * CPW;
   const int64_t i0 = (int64_t)blockIdx.x * rows_per_chunk, i1 = min64(n, i0 + rows_per_chunk);
+  const int64_t ntile = i1 > i0 ? (i1 - i0 + kXtrRows - 1) / kXtrRows : 0;
+  // whole 16-byte units: a row slice is read up to the next 16-byte boundary, which lies inside
+  // the row stride; staged columns >= d only reach accumulators that are never written
+  const uint32_t xbytes = (uint32_t)((min64(CPW, d - cb0) * (int64_t)sizeof(S) + 15) / 16 * 16);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kXtrStages; ++s) {
+      mbar_init_cta(&full[s], 1);
+      mbar_init_cta(&empty[s], 8);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
   float acc[CPL][RMAX];
 #pragma unroll
   for (int e = 0; e < CPL; ++e)
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) acc[e][r] = 0.0f;
-  if (c < d) {
-    // two rows per step (rows i and i + 8 of the chunk), loads issued first
-    constexpr int UR = 2;
-    for (int64_t i = i0 + warp; i < i1; i += 8 * UR) {
-      float xv[UR][CPL];
-      float4 rq[UR][RMAX / 4];
+  if (warp == 8) {
+    if (lane == 0) {   // producer
+      int64_t last_use[kXtrStages];
+      for (int s = 0; s < kXtrStages; ++s) last_use[s] = -1;
+      for (int64_t t = 0; t < ntile; ++t) {
+        const int s = (int)(t % kXtrStages);
+        const int64_t u = t / kXtrStages;
+        if (u >= 1 && !mbar_wait_bounded(&empty[s], (uint32_t)((u - 1) & 1), kXtrWait)) {
+          atomicOr(status, STATUS_TIMEOUT);
+          break;
+        }
+        const int64_t r0 = i0 + t * kXtrRows;
+        const int rows = (int)min64(kXtrRows, i1 - r0);
+        unsigned char* st = xb_sh + (size_t)s * ST;
+        mbar_expect_tx_cta(&full[s], (uint32_t)rows * xbytes + (uint32_t)rows * RMAX * (uint32_t)sizeof(float));
+        for (int r = 0; r < rows; ++r) bulk_copy_g2s(st + r * XROW, X + (r0 + r) * ld + cb0, xbytes, &full[s]);
+        bulk_copy_g2s(st + XST, Rm + r0 * RMAX, (uint32_t)rows * RMAX * (uint32_t)sizeof(float), &full[s]);
+        last_use[s] = u;
+      }
+      for (int s = 0; s < kXtrStages; ++s)   // every issued copy lands before the ring is reused
+        if (last_use[s] >= 0 && !mbar_wait_bounded(&full[s], (uint32_t)(last_use[s] & 1), kXtrWait))
+          atomicOr(status, STATUS_TIMEOUT);
+    }
+  } else {   // consumers: warp w takes rows 2w and 2w + 1 of each tile
+    for (int64_t t = 0; t < ntile; ++t) {
+      const int s = (int)(t % kXtrStages);
+      const int64_t u = t / kXtrStages;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)(u & 1), kXtrWait)) {
+        if (lane == 0) atomicOr(status, STATUS_TIMEOUT);
+        break;
+      }
+      const int rows = (int)min64(kXtrRows, i1 - (i0 + t * kXtrRows));
+      const unsigned char* st = xb_sh + (size_t)s * ST;
 #pragma unroll
-      for (int u = 0; u < UR; ++u) {
-        const int64_t iu = i + 8 * u;
-        if (iu < i1) {
-          ld_cols<CPL>(X + iu * ld, c, d, xv[u]);
-          const float4* rr = reinterpret_cast<const float4*>(Rm + iu * RMAX);
+      for (int h = 0; h < 2; ++h) {
+        const int rr = 2 * warp + h;
+        if (rr < rows) {
+          float xv[CPL];
+          const S* xs = reinterpret_cast<const S*>(st + rr * XROW) + lane * CPL;
+          if constexpr (sizeof(S) == 2) {
+            uint32_t w[CPL / 2];
+            if constexpr (CPL == 8) {
+              const uint4 q = *reinterpret_cast<const uint4*>(xs);
+              w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
+            } else if constexpr (CPL == 4) {
+              const uint2 q = *reinterpret_cast<const uint2*>(xs);
+              w[0] = q.x; w[1] = q.y;
+            } else {
+              w[0] = *reinterpret_cast<const uint32_t*>(xs);
+            }
 #pragma unroll
-          for (int q = 0; q < RMAX / 4; ++q) rq[u][q] = rr[q];
-        } else {
+            for (int k = 0; k < CPL / 2; ++k) {
+              xv[2 * k] = __uint_as_float(w[k] << 16);
+              xv[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+            }
+          } else {
 #pragma unroll
-          for (int e = 0; e < CPL; ++e) xv[u][e] = 0.0f;
+            for (int e = 0; e < CPL; ++e) xv[e] = (float)xs[e];
+          }
+          const float4* rq4 = reinterpret_cast<const float4*>(st + XST + rr * RMAX * sizeof(float));
 #pragma unroll
-          for (int q = 0; q < RMAX / 4; ++q) rq[u][q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          for (int q = 0; q < RMAX / 4; ++q) {
+            const float4 rq = rq4[q];
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) {
+              acc[e][4 * q] = fmaf(xv[e], rq.x, acc[e][4 * q]);
+              acc[e][4 * q + 1] = fmaf(xv[e], rq.y, acc[e][4 * q + 1]);
+              acc[e][4 * q + 2] = fmaf(xv[e], rq.z, acc[e][4 * q + 2]);
+              acc[e][4 * q + 3] = fmaf(xv[e], rq.w, acc[e][4 * q + 3]);
+            }
+          }
         }
       }
-#pragma unroll
-      for (int u = 0; u < UR; ++u)
-#pragma unroll
-        for (int q = 0; q < RMAX / 4; ++q)
-#pragma unroll
-          for (int e = 0; e < CPL; ++e) {
-            acc[e][4 * q] = fmaf(xv[u][e], rq[u][q].x, acc[e][4 * q]);
-            acc[e][4 * q + 1] = fmaf(xv[u][e], rq[u][q].y, acc[e][4 * q + 1]);
-            acc[e][4 * q + 2] = fmaf(xv[u][e], rq[u][q].z, acc[e][4 * q + 2]);
-            acc[e][4 * q + 3] = fmaf(xv[u][e], rq[u][q].w, acc[e][4 * q + 3]);
-          }
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&empty[s]);
     }
   }
+  __syncthreads();
+  float* red = reinterpret_cast<float*>(xb_sh);   // [8][CPL * RMAX][32]
+  if (warp < 8) {
 #pragma unroll
-  for (int e = 0; e < CPL; ++e)
+    for (int e = 0; e < CPL; ++e)
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) red[((warp * CPL + e) * RMAX + r) * 32 + lane] = acc[e][r];
+      for (int r = 0; r < RMAX; ++r) red[((warp * CPL + e) * RMAX + r) * 32 + lane] = acc[e][r];
+  }
   __syncthreads();
   for (int k = threadIdx.x; k < CPL * RMAX * 32; k += blockDim.x) {
-    float s = 0.0f;
+    float sum = 0.0f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) s += red[w * CPL * RMAX * 32 + k];
+    for (int w = 0; w < 8; ++w) sum += red[w * CPL * RMAX * 32 + k];
     const int L = k % 32, er = k / 32, e = er / RMAX, r = er % RMAX;
-    const int64_t col = (int64_t)blockIdx.y * CPW + L * CPL + e;
-    if (col < d && r < R) part[((int64_t)blockIdx.x * d + col) * R + r] = s;
+    const int64_t col = cb0 + L * CPL + e;
+    if (col < d && r < R) part[((int64_t)blockIdx.x * d + col) * R + r] = sum;
   }
 }
 
@@ -623,6 +697,14 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
           const size_t ushm = (size_t)ng * (CPLU * rmax + 4) * sizeof(float);
           const bool usm = ushm <= 100 * 1024;
           const int xu_blocks = ctx->num_sms * 2;
+          // bfloat16 data: R = X U on the tensor cores (U split in three bfloat16 parts), then - y
+          int rc_xu = RS_EUNSUPPORTED;
+          if constexpr (std::is_same<S, __nv_bfloat16>::value)
+            if (umma_enabled()) rc_xu = umma_gemm_xw(ctx, &X, pw[p].U, rmax, nullptr, pw[p].Rm, rmax, false);
+          if (rc_xu != RS_OK && rc_xu != RS_EUNSUPPORTED) return rc_xu;
+          if (rc_xu == RS_OK) {
+            sub_labels_kernel<<<blocks_cap(ctx, n * rmax), 256, 0, ctx->stream>>>(pw[p].Rm, n, rmax, P[p].y);
+          } else {
 #define RS_XU(RM)                                                                                                    \
   do {                                                                                                               \
     if (usm) {                                                                                                       \
@@ -639,20 +721,23 @@ int solve_batched_body(rs_ctx* ctx, const rs_problem* P, int np, const rs_chain*
           else if (rmax == 16) RS_XU(16);
           else RS_XU(32);
 #undef RS_XU
+          }
           RS_LAUNCH_CHECK(ctx);
           const int cpw = 32 * (64 / rmax);   // columns per block of the transposed product
           const int cb = (int)((d + cpw - 1) / cpw);
-          const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 6 / cb, (n + 255) / 256));
-          const int64_t rpc = (n + nch - 1) / nch;
+          // row chunks: about two CTAs per SM in all, whole tiles of 16 rows
+          const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 2 / cb, (n + 255) / 256));
+          const int64_t rpc = ((n + nch - 1) / nch + 15) / 16 * 16;
           float* part = static_cast<float*>(rs_scratch(ctx, SCR_BPART, (size_t)nch * d * R * sizeof(float)));
           if (!part) return RS_ENOMEM;
           dim3 g2((unsigned)nch, (unsigned)cb);
-          constexpr size_t rshm = 8 * 64 * 32 * sizeof(float);
 #define RS_XTR(RM)                                                                                                 \
   do {                                                                                                             \
-    RS_CUDA_TRY(cudaFuncSetAttribute(skinny_xtr_kernel<S, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+    constexpr size_t rshm = xtr_bulk_smem<S, RM>();                                                               \
+    RS_CUDA_TRY(cudaFuncSetAttribute(skinny_xtr_bulk_kernel<S, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                      (int)rshm));                                                                  \
-    skinny_xtr_kernel<S, RM><<<g2, 256, rshm, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part);         \
+    skinny_xtr_bulk_kernel<S, RM><<<g2, 288, rshm, ctx->stream>>>(Xd, n, d, X.ld, pw[p].Rm, (int)R, rpc, part,    \
+                                                                   ctx->d_status);                                 \
   } while (0)
           if (rmax == 8) RS_XTR(8);
           else if (rmax == 16) RS_XTR(16);

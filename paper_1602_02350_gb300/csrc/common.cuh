@@ -237,8 +237,10 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
 // split into three bfloat16 parts first), W K x N float (N <= 256), C float; RS_EUNSUPPORTED when
 // the tensor path cannot run (caller falls back).
 bool umma_enabled();
+// sync_check = false: no status reset and no synchronisation (usable inside a stream capture; the
+// caller checks the status word afterwards).
 int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, const float* col_scale, float* C,
-                 int64_t ldc);
+                 int64_t ldc, bool sync_check = true);
 // Z (bfloat16) = X - P V^T for bfloat16 X (umma.cu), P n x k and V d x k float with row stride k,
 // k <= 128; RS_EUNSUPPORTED when the tensor path cannot run.
 int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, int64_t k, rs_matrix* Z);

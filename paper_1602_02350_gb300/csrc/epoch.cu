@@ -1230,7 +1230,7 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
 namespace {
 
 template <typename S, typename T>
-__global__ void __launch_bounds__(256) epoch_c_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
+__global__ void __launch_bounds__(512) epoch_c_kernel(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
                                                       const uint32_t* __restrict__ idx, int64_t m, double eta,
                                                       const T* __restrict__ mu, const T* __restrict__ Rt,
                                                       T* __restrict__ cvec, const float* __restrict__ rsc) {
@@ -1325,7 +1325,7 @@ int epoch_finish_t(rs_ctx* ctx, const rs_matrix* Z, const uint32_t* idx, int64_t
   const size_t cshm = (size_t)((d + EU - 1) / EU) * EU * sizeof(T);
   if (cshm > 48 * 1024)
     RS_CUDA_TRY(cudaFuncSetAttribute(epoch_c_kernel<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
-  epoch_c_kernel<S, T><<<(unsigned)nblk, 256, cshm, ctx->stream>>>(Zd, N, Z->ld, d, idx, m, eta, mu, Rt, cv,
+  epoch_c_kernel<S, T><<<(unsigned)nblk, 512, cshm, ctx->stream>>>(Zd, N, Z->ld, d, idx, m, eta, mu, Rt, cv,
                                                                     Z->row_scale);
   RS_LAUNCH_CHECK(ctx);
   for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {

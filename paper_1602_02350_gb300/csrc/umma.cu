@@ -816,7 +816,7 @@ int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, 
 // C (M x N, float, ldc) = X (bfloat16 rows, M x K) W (K x N, float) diag(col_scale); N <= 256.
 // RS_EUNSUPPORTED if the tensor-map encoder is unavailable (the caller then uses CUDA cores).
 int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, const float* col_scale, float* C,
-                 int64_t ldc) {
+                 int64_t ldc, bool sync_check) {
   const int64_t M = X->n, K = X->d;
   if (N < 1 || N > 256 || K < 1) return RS_EUNSUPPORTED;
   if (X->dtype != RS_BF16 && X->dtype != RS_F32) return RS_EUNSUPPORTED;
@@ -857,7 +857,7 @@ int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, con
   RS_TRY(make_map(&mw, parts, K, (int64_t)NSPLIT * kp, ldp, UN));
   dim3 grid((unsigned)((M + UM - 1) / UM), (unsigned)(kp / UN));
   if ((M + UM - 1) / UM > 0x7FFFFFFF) return rs_fail(RS_EINVAL, "umma gemm: too many row tiles");
-  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  if (sync_check) RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
 #define RS_XW(NA_, UN_)                                                                                       \
   do {                                                                                                        \
     constexpr size_t shm = (size_t)xw_stages<NA_, UN_>() * xw_stage_bytes<NA_, UN_>() + 1024;                 \
@@ -872,6 +872,7 @@ int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, con
   else RS_XW(1, 128);
 #undef RS_XW
   RS_LAUNCH_CHECK(ctx);
+  if (!sync_check) return RS_OK;   // inside a captured sequence: the caller reads the status word later
   int st = 0;
   RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));

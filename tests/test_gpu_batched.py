@@ -111,3 +111,21 @@ def test_batched_rejects_bad_input(rsctx, small_batch):
     with pytest.raises(rs.RsError):
         rs.rs_solve_batched(rsctx, [(Xb, torch.zeros(100, device="cuda"), 2)], [dict(problem=0, lam=1e-3)], 2,
                             refine=False)
+
+
+@pytest.mark.parametrize("nchains", [12, 20])
+def test_batched_many_chains_per_problem(rsctx, nchains):
+    """More than 8 chains on one problem (the refined-gradient passes run with 16 or 32 columns):
+    every chain agrees with the one-chain path on the same sketch, components and streams."""
+    X, y, _, _ = _problem(3000, 256, 1.5, 41, torch.bfloat16)
+    lams = [10.0 ** (-2 - 2 * j / (nchains - 1)) for j in range(nchains)]
+    chains = [dict(problem=0, lam=lam, eta_mult=1.0, m=1500, seed=j) for j, lam in enumerate(lams)]
+    epochs = 3
+    ws, _, _ = rs.rs_solve_batched(rsctx, [(X, y, 16)], chains, epochs, sketch_seed=5)
+    V, s2 = rs.rs_sketch(rsctx, X, 16, 5)
+    for ch, w in zip(chains[:: max(1, nchains // 4)], ws[:: max(1, nchains // 4)]):
+        Z, beta, _ = rs.rs_precondition(rsctx, X, V, s2, ch["lam"])
+        w1, _ = rs.rs_svrg_solve(rsctx, Z, y, V, s2, ch["lam"], epochs, ch["seed"], beta=beta, m=ch["m"],
+                                 eta_mult=1.0, X=X, refine=True)
+        err = (w - w1).norm().item() / w1.norm().item()
+        assert err <= 1e-4, (ch, err)
