@@ -136,6 +136,120 @@ __global__ void __launch_bounds__(256) gram_kernel(int64_t rows, int64_t Ma, int
   }
 }
 
+// The same split-K product for float accumulation with 16-byte loads: a 64 x 64 output tile per
+// CTA, 32 rows per step staged in shared memory (double-buffered: the next step's tiles are loaded
+// into registers while this step's products run).  Rows of A and B must be 16-byte aligned (the
+// caller checks); a 16-byte unit that crosses the matrix edge is read element by element.
+template <typename TA>
+__device__ __forceinline__ void gram_unit_load(const TA* __restrict__ M, int64_t ld, int64_t r, int64_t r1, int64_t c,
+                                               int64_t ncol, float* v) {
+  constexpr int E = 16 / (int)sizeof(TA);
+  if (r >= r1 || c >= ncol) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = 0.0f;
+    return;
+  }
+  const TA* p = M + r * ld + c;
+  if (c + E <= ncol) {
+    if constexpr (sizeof(TA) == 2) {
+      const uint4 q = *reinterpret_cast<const uint4*>(p);
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+      }
+    } else {
+      const float4 q = *reinterpret_cast<const float4*>(p);
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = c + e < ncol ? cvt<float>(p[e]) : 0.0f;
+  }
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(256) gram_vec_kernel(int64_t rows, int64_t Ma, int64_t Nb, const TA* __restrict__ A,
+                                                       int64_t lda, const float* __restrict__ B, int64_t ldb,
+                                                       int64_t rows_per_chunk, double* part) {
+  constexpr int BT = 64, BK = 32, LDS = BT + 4;
+  constexpr int EA = 16 / (int)sizeof(TA), UA = BK * BT / EA / 256;   // A units per thread (1 or 2)
+  constexpr int UB = BK * BT / 4 / 256;                                 // B units per thread (2)
+  __shared__ __align__(16) float As[2][BK][LDS];
+  __shared__ __align__(16) float Bs[2][BK][LDS];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t i0 = (int64_t)blockIdx.y * BT, j0 = (int64_t)blockIdx.x * BT;
+  const int64_t r0 = (int64_t)blockIdx.z * rows_per_chunk, r1 = min64(rows, r0 + rows_per_chunk);
+  float va[UA][EA], vb[UB][4];
+  auto load = [&](int64_t rr) {
+#pragma unroll
+    for (int q = 0; q < UA; ++q) {
+      const int u = tid + 256 * q, kk = u / (BT / EA), cc = (u % (BT / EA)) * EA;
+      gram_unit_load<TA>(A, lda, rr + kk, r1, i0 + cc, Ma, va[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < UB; ++q) {
+      const int u = tid + 256 * q, kk = u / (BT / 4), cc = (u % (BT / 4)) * 4;
+      gram_unit_load<float>(B, ldb, rr + kk, r1, j0 + cc, Nb, vb[q]);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < UA; ++q) {
+      const int u = tid + 256 * q, kk = u / (BT / EA), cc = (u % (BT / EA)) * EA;
+#pragma unroll
+      for (int e = 0; e < EA; e += 4)
+        *reinterpret_cast<float4*>(&As[buf][kk][cc + e]) = make_float4(va[q][e], va[q][e + 1], va[q][e + 2], va[q][e + 3]);
+    }
+#pragma unroll
+    for (int q = 0; q < UB; ++q) {
+      const int u = tid + 256 * q, kk = u / (BT / 4), cc = (u % (BT / 4)) * 4;
+      *reinterpret_cast<float4*>(&Bs[buf][kk][cc]) = make_float4(vb[q][0], vb[q][1], vb[q][2], vb[q][3]);
+    }
+  };
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  int buf = 0;
+  if (r0 < r1) {
+    load(r0);
+    store(0);
+  }
+  __syncthreads();
+  for (int64_t rr = r0; rr < r1; rr += BK) {
+    const bool more = rr + BK < r1;
+    if (more) load(rr + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  double* out = part + (int64_t)blockIdx.z * Ma * Nb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gi = i0 + ty * 4 + i;
+    if (gi >= Ma) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gj = j0 + tx * 4 + j;
+      if (gj < Nb) out[gi * Nb + gj] = (double)acc[i][j];
+    }
+  }
+}
+
 // G[e] = alpha * sum over the chunks of part[c][e]: 32 entries per block, the chunks split over
 // 8 warps (two interleaved partial sums each), then the warps' sums in warp order (deterministic;
 // short dependent chains of double adds, which are slow on this GPU)
@@ -732,7 +846,16 @@ int launch_gram(rs_ctx* ctx, int64_t rows, int64_t Ma, int64_t Nb, const TA* A, 
   if (!part) return RS_ENOMEM;
   if (nchunks > 65535) return rs_fail(RS_EINVAL, "gram: too many row chunks");
   dim3 grid((unsigned)((Nb + 63) / 64), (unsigned)((Ma + 63) / 64), (unsigned)nchunks);
-  gram_kernel<TA, TB, TACC><<<grid, 256, 0, ctx->stream>>>(rows, Ma, Nb, A, lda, B, ldb, rpc, part);
+  bool vec = false;
+  if constexpr (std::is_same<TACC, float>::value && std::is_same<TB, float>::value)
+    vec = (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0 &&
+          (lda * (int64_t)sizeof(TA)) % 16 == 0 && (ldb * (int64_t)sizeof(TB)) % 16 == 0;
+  if (vec) {
+    if constexpr (std::is_same<TACC, float>::value && std::is_same<TB, float>::value)
+      gram_vec_kernel<TA><<<grid, 256, 0, ctx->stream>>>(rows, Ma, Nb, A, lda, B, ldb, rpc, part);
+  } else {
+    gram_kernel<TA, TB, TACC><<<grid, 256, 0, ctx->stream>>>(rows, Ma, Nb, A, lda, B, ldb, rpc, part);
+  }
   RS_LAUNCH_CHECK(ctx);
   const int64_t rblocks = (Ma * Nb + 31) / 32;
   if (rblocks > 0x7FFFFFFF) return rs_fail(RS_EINVAL, "gram: output too large");
