@@ -241,8 +241,9 @@ bool umma_enabled();
 // caller checks the status word afterwards).
 int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, const float* col_scale, float* C,
                  int64_t ldc, bool sync_check = true);
-// Z (bfloat16) = X - P V^T for bfloat16 X (umma.cu), P n x k and V d x k float with row stride k,
-// k <= 128; RS_EUNSUPPORTED when the tensor path cannot run.
+// Z (bfloat16) = X - P V^T (umma.cu) for bfloat16 X (k <= 128) or float X whose bfloat16 parts the
+// same call has formed for X V (k <= 64), P n x k and V d x k float with row stride k;
+// RS_EUNSUPPORTED when the tensor path cannot run.
 int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, int64_t k, rs_matrix* Z);
 
 // ------------------------------------------------ batched inner loops (many chains per launch)

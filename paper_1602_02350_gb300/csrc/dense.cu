@@ -390,7 +390,11 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
     __syncthreads();
     for (int r = 0; r < K - 1; ++r) {
       for (int i = tid; i < K / 2; i += nt) {
-        auto pos = [&](int j) { return j == 0 ? 0 : ((j - 1 + r) % (K - 1)) + 1; };
+        auto pos = [&](int j) {   // round-robin seat of player j in round r (j - 1 + r < 2 (K - 1))
+          if (j == 0) return 0;
+          const int v = j - 1 + r;
+          return (v >= K - 1 ? v - (K - 1) : v) + 1;
+        };
         int p = pos(i), q = pos(K - 1 - i);
         if (p > q) { int t = p; p = q; q = t; }
         TW c = TW(1), s = TW(0);
@@ -406,7 +410,7 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
             const TW t = (theta >= TW(0) ? TW(1) : TW(-1)) / (fabs(theta) + sqrt(theta * theta + TW(1)));
             c = TW(1) / sqrt(t * t + TW(1));
             s = t * c;
-            atomicAdd(&rotations, 1);
+            rotations = 1;   // any rotation in this sweep (every writer stores the same value)
           }
         }
         pp[i] = p; qq[i] = q; cc[i] = c; ss[i] = s;
@@ -1097,8 +1101,8 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
   else if (rc_p != RS_OK)
     return rc_p;
   int rc_z = RS_EUNSUPPORTED;
-  if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<SZ, __nv_bfloat16>::value &&
-                std::is_same<T, float>::value)
+  if constexpr ((std::is_same<S, __nv_bfloat16>::value || std::is_same<S, float>::value) &&
+                std::is_same<SZ, __nv_bfloat16>::value && std::is_same<T, float>::value)
     if (rc_p == RS_OK) rc_z = umma_resid(ctx, X, P, V, k, Xt);
   if (rc_z == RS_EUNSUPPORTED)
     RS_TRY(launch_gemm<T, T, SZ, S>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));

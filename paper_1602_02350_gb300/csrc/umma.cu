@@ -472,19 +472,24 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
                : "memory");
 }
 
-template <int KC> __host__ __device__ constexpr int resid_ring() { return KC == 1 ? 4 : 3; }
-template <int KC>
+// XP = 1: bfloat16 X tiles; XP = 3: float X given as its three bfloat16 parts (rows a n .. a n + n - 1
+// of the parts' map), summed in float in the epilogue (K chunks: KC = 1 only, two ring entries).
+template <int KC, int XP = 1> __host__ __device__ constexpr int resid_ring() {
+  return XP == 3 ? 2 : (KC == 1 ? 4 : 3);
+}
+template <int KC, int XP = 1>
 constexpr size_t resid_smem_bytes() {
-  return (size_t)3 * KC * RT_A_TILE + (size_t)resid_ring<KC>() * 3 * RT_B_TILE + 2 * (size_t)RT_X_TILE + 1024;
+  return (size_t)3 * KC * RT_A_TILE + (size_t)resid_ring<KC, XP>() * 3 * RT_B_TILE + 2 * (size_t)XP * RT_X_TILE +
+         1024;
 }
 
-template <int KC>
+template <int KC, int XP = 1>
 __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constant__ CUtensorMap tmA,
                                                             const __grid_constant__ CUtensorMap tmB,
                                                             const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmZ, int64_t d,
-                                                            int64_t np, int64_t dp, int* status) {
-  constexpr int NB = resid_ring<KC>();
+                                                            int64_t np, int64_t dp, int64_t n_rows, int* status) {
+  constexpr int NB = resid_ring<KC, XP>();
   constexpr uint32_t A_BYTES = 3 * KC * RT_A_TILE;
   constexpr uint32_t B_ENTRY = 3 * RT_B_TILE;   // the three V parts of one K chunk
   extern __shared__ unsigned char rt_raw[];
@@ -540,8 +545,9 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
         const int sx = t & 1, ux = t >> 1;
         if (ux >= 1 && !mbar_wait_bounded(&x_empty[sx], (uint32_t)((ux - 1) & 1), kUmmaWait))
           atomicOr(status, STATUS_TIMEOUT);
-        mbar_expect_tx_cta(&x_full[sx], RT_X_TILE);
-        tma_load_2d(XZ + sx * RT_X_TILE, &tmX, t * RT_COLS, row0, &x_full[sx]);
+        mbar_expect_tx_cta(&x_full[sx], XP * RT_X_TILE);
+        for (int a = 0; a < XP; ++a)
+          tma_load_2d(XZ + (sx * XP + a) * RT_X_TILE, &tmX, t * RT_COLS, (int)(a * n_rows) + row0, &x_full[sx]);
       }
     }
   } else if (warp == 1) {
@@ -612,18 +618,29 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_cta(&acc_empty[ab]);
-      unsigned char* xr = XZ + ab * RT_X_TILE + r * 128;
+      unsigned char* xr = XZ + ab * XP * RT_X_TILE + r * 128;
 #pragma unroll
       for (int u8 = 0; u8 < 8; ++u8) {
         const int off = (u8 ^ (r & 7)) << 4;
-        const uint4 xw = *reinterpret_cast<const uint4*>(xr + off);
-        const uint32_t xs4[4] = {xw.x, xw.y, xw.z, xw.w};
+        float xv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xv[e] = 0.0f;
+        // float X: x = x0 + x1 + x2 (the first two parts add exactly), summed from the smallest part
+#pragma unroll
+        for (int a = XP - 1; a >= 0; --a) {
+          const uint4 xw = *reinterpret_cast<const uint4*>(xr + a * RT_X_TILE + off);
+          const uint32_t xs4[4] = {xw.x, xw.y, xw.z, xw.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            xv[2 * e] += __uint_as_float(xs4[e] << 16);
+            xv[2 * e + 1] += __uint_as_float(xs4[e] & 0xFFFF0000u);
+          }
+        }
         uint32_t zw[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float x0 = __uint_as_float(xs4[e] << 16), x1 = __uint_as_float(xs4[e] & 0xFFFF0000u);
-          const __nv_bfloat16 z0 = __float2bfloat16_rn(x0 - __uint_as_float(v[8 * u8 + 2 * e]));
-          const __nv_bfloat16 z1 = __float2bfloat16_rn(x1 - __uint_as_float(v[8 * u8 + 2 * e + 1]));
+          const __nv_bfloat16 z0 = __float2bfloat16_rn(xv[2 * e] - __uint_as_float(v[8 * u8 + 2 * e]));
+          const __nv_bfloat16 z1 = __float2bfloat16_rn(xv[2 * e + 1] - __uint_as_float(v[8 * u8 + 2 * e + 1]));
           zw[e] = (uint32_t)__bfloat16_as_ushort(z0) | ((uint32_t)__bfloat16_as_ushort(z1) << 16);
         }
         *reinterpret_cast<uint4*>(xr + off) = make_uint4(zw[0], zw[1], zw[2], zw[3]);
@@ -631,7 +648,7 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       asm volatile("bar.sync 1, 128;\n" ::: "memory");
       if (lead) {
-        tma_store_2d(&tmZ, XZ + ab * RT_X_TILE, t * RT_COLS, row0);
+        tma_store_2d(&tmZ, XZ + ab * XP * RT_X_TILE, t * RT_COLS, row0);
         asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
         // the buffer takes the next X tile once the store has read it
         asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
@@ -767,8 +784,9 @@ int umma_prep(rs_ctx* ctx, const ChainJob<__nv_bfloat16, float>& one, const Chai
   return RS_OK;
 }
 
-// Z (bfloat16 rows, n x d) = X - P V^T for bfloat16 X, P (n x k float, row stride k), V (d x k
-// float, row stride k), k <= 128, on tensor cores.  RS_EUNSUPPORTED when the tensor path is off or
+// Z (bfloat16 rows, n x d) = X - P V^T for bfloat16 X (k <= 128) or float X whose bfloat16 parts
+// this call has formed (k <= 64), P (n x k float, row stride k), V (d x k float, row stride k), on
+// tensor cores.  RS_EUNSUPPORTED when the tensor path is off or
 // cannot run (the caller uses the CUDA-core product).
 int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, int64_t k, rs_matrix* Z) {
   if (!umma_enabled() || !encode_fn()) return RS_EUNSUPPORTED;
@@ -777,6 +795,17 @@ int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, 
   const int64_t n = X->n, d = X->d;
   if (k < 1 || k > 128 || n < 1 || d < 1 || n > 0x7FFFFF00LL / 3 || d > 0x7FFFFF00LL / 3) return RS_EUNSUPPORTED;
   const int kp = k <= 64 ? 64 : 128;
+  // float X: only with the three bfloat16 parts of this X formed earlier in the same call (the
+  // tensor-core X V product leaves them in SCR_XPART), and k <= 64
+  const bool f32 = X->dtype == RS_F32;
+  const int64_t ldx = (d + 7) / 8 * 8;
+  if (f32) {
+    const bool cached = ctx->xp_gen == ctx->call_gen && ctx->xp_src == X->data && ctx->xp_n == n &&
+                        ctx->xp_d == d && ctx->xp_ld == X->ld;
+    if (!cached || kp != 64) return RS_EUNSUPPORTED;
+  } else if (X->dtype != RS_BF16) {
+    return RS_EUNSUPPORTED;
+  }
   const int64_t np = (n + RT_ROWS - 1) / RT_ROWS * RT_ROWS, dp = (d + RT_COLS - 1) / RT_COLS * RT_COLS;
   __nv_bfloat16* parts = static_cast<__nv_bfloat16*>(
       rs_scratch(ctx, SCR_RPART, (size_t)3 * (np + dp) * kp * sizeof(__nv_bfloat16)));
@@ -792,19 +821,22 @@ int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, 
   CUtensorMap mA, mB, mX, mZ;
   RS_TRY(make_map(&mA, parts, kp, 3 * np, kp, RT_ROWS));
   RS_TRY(make_map(&mB, vparts, kp, 3 * dp, kp, RT_COLS));
-  RS_TRY(make_map(&mX, X->data, d, n, X->ld, RT_ROWS));
+  if (f32) RS_TRY(make_map(&mX, ctx->slots[SCR_XPART].ptr, d, 3 * n, ldx, RT_ROWS));
+  else RS_TRY(make_map(&mX, X->data, d, n, X->ld, RT_ROWS));
   RS_TRY(make_map(&mZ, Z->data, d, n, Z->ld, RT_ROWS));
   RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   const unsigned grid = (unsigned)(np / RT_ROWS);
-  if (kp == 64) {
-    constexpr size_t shm = resid_smem_bytes<1>();
-    RS_CUDA_TRY(cudaFuncSetAttribute(umma_resid_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    umma_resid_kernel<1><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, ctx->d_status);
-  } else {
-    constexpr size_t shm = resid_smem_bytes<2>();
-    RS_CUDA_TRY(cudaFuncSetAttribute(umma_resid_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    umma_resid_kernel<2><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, ctx->d_status);
-  }
+#define RS_RESID(KC_, XP_)                                                                                    \
+  do {                                                                                                        \
+    constexpr size_t shm = resid_smem_bytes<KC_, XP_>();                                                      \
+    RS_CUDA_TRY(cudaFuncSetAttribute(umma_resid_kernel<KC_, XP_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)shm));                                                              \
+    umma_resid_kernel<KC_, XP_><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, n, ctx->d_status); \
+  } while (0)
+  if (f32) RS_RESID(1, 3);
+  else if (kp == 64) RS_RESID(1, 1);
+  else RS_RESID(2, 1);
+#undef RS_RESID
   RS_LAUNCH_CHECK(ctx);
   int st = 0;
   RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -135,9 +135,12 @@ def test_bf16_svrg_solve_requires_data_for_refinement(rsctx, bf16_problem):
     assert torch.isfinite(w).all()
 
 
-@pytest.mark.parametrize("n,d,k", [(257, 40, 5), (65536, 1024, 64)])
-def test_bf16_components_from_float_data(rsctx, n, d, k):
-    """Float data, bfloat16 components: each z_i is formed in float and rounded once."""
+@pytest.mark.parametrize("n,d,k", [(257, 40, 5), (3000, 520, 60), (65536, 1024, 64), (2000, 256, 100)])
+@pytest.mark.parametrize("tc", ["1", "0"])
+def test_bf16_components_from_float_data(rsctx, monkeypatch, n, d, k, tc):
+    """Float data, bfloat16 components: each z_i is formed in float and rounded once (tensor-core
+    path from the bfloat16 parts of X for k <= 64, and CUDA cores)."""
+    monkeypatch.setenv("RS_UMMA", tc)
     X = torch.from_numpy(synth.random_matrix(n, d, n + 2 * d, scale=1.0 / np.sqrt(d))).float()
     V = torch.from_numpy(synth.random_orthonormal(d, k, d + 1)).float()
     s2 = synth.random_sigma2(k, k + 1)
