@@ -682,11 +682,11 @@ __global__ void sumsq_kernel(const TS* X, int64_t n, int64_t d, int64_t ld, doub
 }
 
 __global__ void trace_finish_kernel(const double* part, int np, double inv_n, double* out) {
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int p = 0; p < np; ++p) t += part[p];
-    *out = t * inv_n;
-  }
+  // lane-strided partial sums, then a fixed shuffle tree (one warp)
+  double t = 0.0;
+  for (int p = threadIdx.x; p < np; p += 32) t += part[p];
+  t = warp_sum(t);
+  if (threadIdx.x == 0) *out = t * inv_n;
 }
 
 // w = M x = x - V diag(a) V^T x in one block (a_j = 1 - D'_j from sigma2): partial sums of V^T x by
@@ -702,25 +702,9 @@ __global__ void __launch_bounds__(1024) map_fused_kernel(const T* __restrict__ V
   const int G = nt / k;                    // row groups (k <= 256 so G >= 4)
   const int j = tid % k, g = tid / k;
   if (g < G) {
-    // eight independent loads in flight per step (V and x come from L2; a load-to-use chain per
-    // element would serialise their latencies)
-    A s0 = A(0), s1 = A(0);
-    int64_t c = g;
-    for (; c + 7 * (int64_t)G < d; c += 8 * (int64_t)G) {
-      A v[8], xv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        v[u] = (A)V[(c + u * (int64_t)G) * k + j];
-        xv[u] = (A)x[c + u * (int64_t)G];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        s0 += v[u] * xv[u];
-        s1 += v[u + 1] * xv[u + 1];
-      }
-    }
-    for (; c < d; c += G) s0 += (A)V[c * k + j] * (A)x[c];
-    part[g * k + j] = s0 + s1;
+    A s = A(0);
+    for (int64_t c = g; c < d; c += G) s += (A)V[c * k + j] * (A)x[c];
+    part[g * k + j] = s;
   }
   __syncthreads();
   if (tid < k) {

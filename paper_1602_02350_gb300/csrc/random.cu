@@ -97,6 +97,59 @@ __global__ void cs_place_kernel(const int32_t* bucket, int64_t n, int64_t s, int
   }
 }
 
+// Float rows (16-byte aligned) with float sums: one warp per bucket, 1024 columns per pass, each
+// lane holding 8 float4 accumulators, so the 8 16-byte loads of a row are in flight together.
+__global__ void cs_gather_f32_kernel(const float* __restrict__ X, int64_t ld, int64_t d, int64_t s, int64_t nchunks,
+                                     const uint64_t* __restrict__ incl, const uint32_t* __restrict__ cnt,
+                                     const int32_t* __restrict__ perm, const float* __restrict__ sign,
+                                     float* __restrict__ SX, int64_t ld_sx) {
+  const int warps = blockDim.x / 32;
+  const int lane = threadIdx.x & 31;
+  for (int64_t h = blockIdx.x * (int64_t)warps + threadIdx.x / 32; h < s; h += (int64_t)gridDim.x * warps) {
+    const int64_t first = h * nchunks, last = h * nchunks + nchunks - 1;
+    const uint64_t start = incl[first] - cnt[first];
+    const uint64_t end = incl[last];
+    for (int64_t c0 = 0; c0 < d; c0 += 1024) {
+      float4 acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      for (uint64_t p = start; p < end; ++p) {
+        const int64_t i = perm[p];
+        const float sg = sign[i];
+        const float* row = X + i * ld;
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int64_t col = c0 + (q * 32 + lane) * 4;
+          if (col + 4 <= d) {
+            v[q] = *reinterpret_cast<const float4*>(row + col);
+          } else {
+            v[q].x = col < d ? row[col] : 0.0f;
+            v[q].y = col + 1 < d ? row[col + 1] : 0.0f;
+            v[q].z = col + 2 < d ? row[col + 2] : 0.0f;
+            v[q].w = col + 3 < d ? row[col + 3] : 0.0f;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          acc[q].x += sg * v[q].x;
+          acc[q].y += sg * v[q].y;
+          acc[q].z += sg * v[q].z;
+          acc[q].w += sg * v[q].w;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t col = c0 + (q * 32 + lane) * 4;
+        const float a[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (col + e < d) SX[h * ld_sx + col + e] = a[e];
+      }
+    }
+  }
+}
+
 // One warp per bucket: SX[h] = sum over its rows (in increasing row index) of sign * x.
 template <typename T, typename TS>
 __global__ void cs_gather_kernel(const TS* X, int64_t ld, int64_t d, int64_t s, int64_t nchunks,
@@ -364,7 +417,9 @@ static int countsketch_t(rs_ctx* ctx, const rs_matrix* X, uint64_t seed, int64_t
   int32_t* bucket = bucket_out ? bucket_out : static_cast<int32_t*>(rs_scratch(ctx, SCR_BUCKET, n * 4));
   T* sign = sign_out ? sign_out : static_cast<T*>(rs_scratch(ctx, SCR_SIGN, n * sizeof(T)));
   if (!bucket || !sign) return RS_ENOMEM;
-  const int64_t R = 4096;
+  // rows per chunk of the stable placement: one warp walks a chunk in order, so shorter chunks
+  // shorten that serial walk (more counters to scan, which is cheap)
+  const int64_t R = 1024;
   const int64_t nchunks = (n + R - 1) / R;
   const int64_t slots = s * nchunks;
   uint32_t* cnt = static_cast<uint32_t*>(rs_scratch(ctx, SCR_CNT, slots * 4));
@@ -390,8 +445,12 @@ static int countsketch_t(rs_ctx* ctx, const rs_matrix* X, uint64_t seed, int64_t
           static_cast<const double*>(X->data), X->ld, d, s, nchunks, incl, cnt, perm, sign, SX, ld_sx);
       break;
     case RS_F32:
-      cs_gather_kernel<T, float><<<(unsigned)g, 32 * warps, 0, ctx->stream>>>(
-          static_cast<const float*>(X->data), X->ld, d, s, nchunks, incl, cnt, perm, sign, SX, ld_sx);
+      if constexpr (std::is_same<T, float>::value)
+        cs_gather_f32_kernel<<<(unsigned)g, 32 * warps, 0, ctx->stream>>>(
+            static_cast<const float*>(X->data), X->ld, d, s, nchunks, incl, cnt, perm, sign, SX, ld_sx);
+      else
+        cs_gather_kernel<T, float><<<(unsigned)g, 32 * warps, 0, ctx->stream>>>(
+            static_cast<const float*>(X->data), X->ld, d, s, nchunks, incl, cnt, perm, sign, SX, ld_sx);
       break;
     case RS_BF16:
       cs_gather_kernel<T, __nv_bfloat16><<<(unsigned)g, 32 * warps, 0, ctx->stream>>>(

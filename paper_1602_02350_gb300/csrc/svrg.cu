@@ -359,9 +359,10 @@ __global__ void row_beta_only_kernel(const S* Z, int64_t N, int64_t n, int64_t d
 template <typename T>
 __global__ void mean_kernel(const T* v, int64_t N, double* out) {
   __shared__ double sh[32];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += (double)v[i];
-  s = warp_sum(s);
+  // per-thread sums in T (a few dozen terms each; double adds are slow on this GPU), then double
+  T st = T(0);
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) st += v[i];
+  double s = warp_sum((double)st);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
