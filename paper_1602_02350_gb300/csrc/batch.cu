@@ -46,26 +46,65 @@ __device__ __forceinline__ double map_input(const MapJob& J, int64_t c) {
   return x;
 }
 
-// one block per job: t = V^T x (threads over the k columns), then y = x - V (a .* t)
+// one block per job: t = V^T x, then y = x - V (a .* t), in float (as the one-problem solver's maps;
+// double arithmetic is slow on this GPU).  x (formed in double from its parts, stored as float) is
+// staged in shared memory; t by (column, row group) partial sums combined in group order; y with a
+// warp per eight rows, lanes along the row (coalesced reads of V), one shuffle sum per row.
+constexpr int kMapMaxD = 4096;
 __global__ void __launch_bounds__(256) bmap_kernel(const MapJob* __restrict__ jobs, int64_t epoch, int* status) {
-  __shared__ double t[256];
+  __shared__ float xs[kMapMaxD];
+  __shared__ float part[256];
+  __shared__ float tv[256];
   const MapJob J = jobs[blockIdx.x];
-  for (int j = threadIdx.x; j < J.k; j += blockDim.x) {
-    double s = 0.0;
-    for (int64_t c = 0; c < J.d; ++c) s = fma((double)J.V[c * J.k + j], map_input(J, c), s);
-    t[j] = s * (double)J.a[j];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int k = J.k;
+  const int64_t d = J.d;
+  for (int64_t c = tid; c < d; c += nt) xs[c] = (float)map_input(J, c);
+  __syncthreads();
+  const int G = nt / k;   // row groups (k <= 256)
+  const int j = tid % k, g = tid / k;
+  if (g < G) {
+    float s0 = 0.0f, s1 = 0.0f;
+    int64_t c = g;
+    for (; c + G < d; c += 2 * (int64_t)G) {
+      s0 = fmaf(J.V[c * k + j], xs[c], s0);
+      s1 = fmaf(J.V[(c + G) * k + j], xs[c + G], s1);
+    }
+    if (c < d) s0 = fmaf(J.V[c * k + j], xs[c], s0);
+    part[g * k + j] = s0 + s1;
+  }
+  __syncthreads();
+  if (tid < k) {
+    float t = 0.0f;
+    for (int q = 0; q < G; ++q) t += part[q * k + tid];   // fixed order
+    tv[tid] = t * J.a[tid];
   }
   __syncthreads();
   bool bad = false;
   float* y = J.y + epoch * J.y_epoch_stride;
-  for (int64_t c = threadIdx.x; c < J.d; c += blockDim.x) {
-    const float* v = J.V + c * J.k;
-    double s = 0.0;
-    for (int j = 0; j < J.k; ++j) s = fma((double)v[j], t[j], s);
-    const float out = (float)(map_input(J, c) - s);
-    y[c * J.y_ld] = out;
-    if (J.y2) J.y2[c] = out;
-    if (J.check && !isfinite(out)) bad = true;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int64_t c0 = (int64_t)warp * 8; c0 < d; c0 += (int64_t)nw * 8) {
+    float sr[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      sr[r] = 0.0f;
+      const int64_t c = c0 + r;
+      if (c < d)
+        for (int q = lane; q < k; q += 32) sr[r] = fmaf(J.V[c * k + q], tv[q], sr[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sr[r] = warp_sum(sr[r]);
+    if (lane < 8 && c0 + lane < d) {
+      float sl = sr[0];
+#pragma unroll
+      for (int r = 1; r < 8; ++r)
+        if (lane == r) sl = sr[r];
+      const int64_t c = c0 + lane;
+      const float out = xs[c] - sl;
+      y[c * J.y_ld] = out;
+      if (J.y2) J.y2[c] = out;
+      if (J.check && !isfinite(out)) bad = true;
+    }
   }
   if (bad) atomicOr(status, STATUS_NONFINITE);
 }
