@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -191,8 +192,10 @@ def run_rs(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    cpath = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-    os.makedirs(os.path.dirname(cpath), exist_ok=True)
+    # raw nvidia-smi samples of the timed region (summarised in the JSON line); RS_CLOCKS_DIR keeps them
+    cdir = os.environ.get("RS_CLOCKS_DIR") or tempfile.gettempdir()
+    cpath = os.path.join(cdir, f"clocks_rank{rank}.csv")
+    os.makedirs(cdir, exist_ok=True)
     sampler, fh = _clock_sampler(cpath)
     time.sleep(0.3)
     ms_plain, w_plain = _time_steps(plain_step, args.steps, stream)
