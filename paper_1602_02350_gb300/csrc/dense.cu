@@ -574,6 +574,44 @@ __global__ void row_beta_kernel(const S* Z, int64_t N, int64_t n, int64_t d, int
   }
 }
 
+// beta_i with the data rows' squared norms already formed (rowsq, by the tensor-core components
+// kernel): a thread per data row, a warp per regulariser row (read from Z), and the block's sum
+// of beta in double for the mean.
+template <typename S, typename T>
+__global__ void row_beta_sq_kernel(const float* __restrict__ rowsq, const S* Z, int64_t N, int64_t n, int64_t d,
+                                   int64_t ld, double lam, T* beta, double* part) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double gd = (double)N / (double)n, gr = lam * (double)N;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double b = gd * (double)rowsq[i];
+    beta[i] = (T)b;
+    acc += b;
+  }
+  for (int64_t i = n + (int64_t)blockIdx.x * nw + warp; i < N; i += (int64_t)gridDim.x * nw) {
+    T s = T(0);
+    for (int64_t c = lane; c < d; c += 32) {
+      const T v = cvt<T>(Z[i * ld + c]);
+      s = fma(v, v, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      const double b = gr * (double)s;
+      beta[i] = (T)b;
+      acc += b;
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) sh[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
 // out = scale * sum of part[0..np): lane-strided partial sums, then a fixed shuffle tree
 __global__ void sum_parts_kernel(const double* part, int np, double scale, double* out) {
   double s = 0.0;
@@ -1085,9 +1123,14 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
   else if (rc_p != RS_OK)
     return rc_p;
   int rc_z = RS_EUNSUPPORTED;
+  float* rowsq = nullptr;   // squared norms of the data rows of Z, formed by the tensor-core kernel
   if constexpr ((std::is_same<S, __nv_bfloat16>::value || std::is_same<S, float>::value) &&
                 std::is_same<SZ, __nv_bfloat16>::value && std::is_same<T, float>::value)
-    if (rc_p == RS_OK) rc_z = umma_resid(ctx, X, P, V, k, Xt);
+    if (rc_p == RS_OK) {
+      rowsq = static_cast<float*>(rs_scratch(ctx, SCR_ROWSQ, n * sizeof(float)));
+      if (!rowsq) return RS_ENOMEM;
+      rc_z = umma_resid(ctx, X, P, V, k, Xt, rowsq);
+    }
   if (rc_z == RS_EUNSUPPORTED)
     RS_TRY(launch_gemm<T, T, SZ, S>(ctx, n, d, k, -1.0, P, k, 1, V, 1, k, 1.0, Xd, X->ld, Z, ldz, nullptr));
   else if (rc_z != RS_OK)
@@ -1103,7 +1146,10 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
   const int blocks = blocks_for(ctx, N * 32);
   double* part = static_cast<double*>(rs_scratch(ctx, SCR_MISC, (blocks + 1) * sizeof(double)));
   if (!part) return RS_ENOMEM;
-  row_beta_kernel<SZ, T><<<blocks, 256, 0, ctx->stream>>>(Z, N, n, d, ldz, lam, beta, part);
+  if (rc_z == RS_OK && rowsq)
+    row_beta_sq_kernel<SZ, T><<<blocks, 256, 0, ctx->stream>>>(rowsq, Z, N, n, d, ldz, lam, beta, part);
+  else
+    row_beta_kernel<SZ, T><<<blocks, 256, 0, ctx->stream>>>(Z, N, n, d, ldz, lam, beta, part);
   RS_LAUNCH_CHECK(ctx);
   if (beta_hat) {
     sum_parts_kernel<<<1, 32, 0, ctx->stream>>>(part, blocks, 1.0 / (double)N, part + blocks);

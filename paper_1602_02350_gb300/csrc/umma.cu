@@ -488,7 +488,8 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
                                                             const __grid_constant__ CUtensorMap tmB,
                                                             const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmZ, int64_t d,
-                                                            int64_t np, int64_t dp, int64_t n_rows, int* status) {
+                                                            int64_t np, int64_t dp, int64_t n_rows,
+                                                            float* __restrict__ rowsq, int* status) {
   constexpr int NB = resid_ring<KC, XP>();
   constexpr uint32_t A_BYTES = 3 * KC * RT_A_TILE;
   constexpr uint32_t B_ENTRY = 3 * RT_B_TILE;   // the three V parts of one K chunk
@@ -593,6 +594,7 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
     const int q = warp & 3;
     const int r = q * 32 + lane;
     const bool lead = warp == 2 && lane == 0;
+    float sq = 0.0f;   // squared norm of this row of the stored (rounded) components
     for (int t = 0; t < ntiles; ++t) {
       const int ab = t & 1, ua = t >> 1;
       bool ok = mbar_wait_bounded(&acc_full[ab], (uint32_t)(ua & 1), kUmmaWait);
@@ -642,6 +644,9 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
           const __nv_bfloat16 z0 = __float2bfloat16_rn(xv[2 * e] - __uint_as_float(v[8 * u8 + 2 * e]));
           const __nv_bfloat16 z1 = __float2bfloat16_rn(xv[2 * e + 1] - __uint_as_float(v[8 * u8 + 2 * e + 1]));
           zw[e] = (uint32_t)__bfloat16_as_ushort(z0) | ((uint32_t)__bfloat16_as_ushort(z1) << 16);
+          const float f0 = __bfloat162float(z0), f1 = __bfloat162float(z1);
+          sq = fmaf(f0, f0, sq);
+          sq = fmaf(f1, f1, sq);
         }
         *reinterpret_cast<uint4*>(xr + off) = make_uint4(zw[0], zw[1], zw[2], zw[3]);
       }
@@ -656,6 +661,9 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
       }
     }
     if (lead) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+    // columns beyond d entered as zeros (TMA fills out-of-range X with zeros, and the MMA products
+    // there vanish), so sq is the full squared norm of the stored row
+    if (rowsq && row0 + r < n_rows) rowsq[row0 + r] = sq;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -786,9 +794,10 @@ int umma_prep(rs_ctx* ctx, const ChainJob<__nv_bfloat16, float>& one, const Chai
 
 // Z (bfloat16 rows, n x d) = X - P V^T for bfloat16 X (k <= 128) or float X whose bfloat16 parts
 // this call has formed (k <= 64), P (n x k float, row stride k), V (d x k float, row stride k), on
-// tensor cores.  RS_EUNSUPPORTED when the tensor path is off or
+// tensor cores; rowsq (optional, n floats) receives the squared norms of the stored rows.  RS_EUNSUPPORTED when the tensor path is off or
 // cannot run (the caller uses the CUDA-core product).
-int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, int64_t k, rs_matrix* Z) {
+int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, int64_t k, rs_matrix* Z,
+               float* rowsq) {
   if (!umma_enabled() || !encode_fn()) return RS_EUNSUPPORTED;
   const char* env = std::getenv("RS_UMMA_RESID");
   if (env && env[0] == '0') return RS_EUNSUPPORTED;
@@ -831,7 +840,8 @@ int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, 
     constexpr size_t shm = resid_smem_bytes<KC_, XP_>();                                                      \
     RS_CUDA_TRY(cudaFuncSetAttribute(umma_resid_kernel<KC_, XP_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      (int)shm));                                                              \
-    umma_resid_kernel<KC_, XP_><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, n, ctx->d_status); \
+    umma_resid_kernel<KC_, XP_><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, n, rowsq,         \
+                                                                  ctx->d_status);                             \
   } while (0)
   if (f32) RS_RESID(1, 3);
   else if (kp == 64) RS_RESID(1, 1);
