@@ -206,6 +206,8 @@ int rs_full_gradient(rs_ctx* ctx, const rs_matrix* Z, const void* y, int64_t n, 
  * Same arguments and result as rs_full_gradient (mu is written on ``cuda_stream``, a
  * cudaStream_t, NULL = legacy default stream, on the caller's current device); the same kernels
  * run, so results match rs_full_gradient.
+ *   - Z must be RS_F32 or RS_F64 (y, w, mu of the same type); RS_BF16 and RS_FP8E4M3 rows return
+ *     RS_EINVAL before anything is launched (rs_full_gradient takes them).
  *   - Limit: d <= 1024 for RS_F32 and d <= 512 for RS_F64 rows; larger d returns RS_EINVAL.
  *   - The first call on each device resolves the array's device address (once per device, with
  *     that device current); make that first call before any stream capture.

@@ -963,6 +963,10 @@ extern "C" int rs_full_gradient_static(void* cuda_stream, const rs_matrix* Z, co
                                        const void* w, void* mu) {
   RS_CHECK_ARG(Z && y && w && mu, "rs_full_gradient_static: null argument");
   RS_TRY(check_components(Z, n));
+  // only float and double rows have a kernel here; a BF16 (or FP8) Z would be read at the wrong
+  // element size, so it is refused before anything is launched
+  RS_CHECK_ARG(Z->dtype == RS_F64 || Z->dtype == RS_F32,
+               "rs_full_gradient_static: Z must be RS_F64 or RS_F32 (RS_BF16 / RS_FP8E4M3 rows: use rs_full_gradient)");
   RS_CHECK_ARG(lambda > 0.0, "rs_full_gradient_static: lambda must be positive");
   int dev = 0;
   RS_CUDA_TRY(cudaGetDevice(&dev));

@@ -59,3 +59,21 @@ def test_static_entry_rejects_rows_beyond_its_limit(rsctx):
     with pytest.raises(rs.RsError) as e:
         rs.rs_full_gradient_static(Z, y, n, 1e-3, w, out=torch.empty(d, device="cuda"))
     assert e.value.code == 1 and "maximum" in str(e.value)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float8_e4m3fn])
+def test_static_entry_refuses_narrow_rows_before_launching(rsctx, dtype):
+    """BF16 / FP8 rows have no kernel in the allocation-free entry: the call must return RS_EINVAL
+    from its host-side checks and leave mu untouched (no kernel ran)."""
+    n, d = 256, 64
+    Z = torch.zeros(n + d, d, dtype=dtype, device="cuda")
+    y = torch.zeros(n, device="cuda")
+    w = torch.zeros(d, device="cuda")
+    mu = torch.full((d,), float("nan"), device="cuda")
+    with pytest.raises(rs.RsError) as e:
+        rs.rs_full_gradient_static(Z, y, n, 1e-3, w, out=mu)
+    assert e.value.code == 1
+    if dtype == torch.bfloat16:
+        assert "RS_F32" in str(e.value)
+    torch.cuda.synchronize()
+    assert torch.isnan(mu).all()
