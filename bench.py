@@ -1,18 +1,21 @@
 """Benchmark: time to 1e-6 relative suboptimality of sketched-preconditioned SVRG (Alg. 3) on one GB300.
 
-Workload: n = 65536, d = 1024 FP32 rows with power-law spectrum j^-2 in a random basis,
-y = X w_gen + 0.05 N(0,1), lambda = 1e-5, CountSketch (s = 4096) then Gaussian sketch.
-One step = one full solve from the device-resident (X, y) to w, every epoch needed to reach 1e-6.
+Default workload (the largest single-GPU configuration): n = 2^20, d = 4096, spectrum j^-1.2 with
+the leading 20 directions x100 in a random basis, y = X w_gen + 0.05 N(0,1), lambda = 1e-6,
+Gaussian sketch of rank k = 256.  One step = one full solve from the device-resident (X, y) to w,
+every epoch needed to reach 1e-6 (epochs calibrated once, untimed, against the FP64
+normal-equation minimiser).
 
-  chosen form (the reported value): rs_solve_proposed -- rank-64 sketch, tr(C), the trained
-    proposal network picks (k, eta, m), BF16 components with snapshot gradients refined on the
-    FP32 data;
-  plain form (alongside): rs_solve -- FP32 components, k = 64, m = 2n, eta = 1/beta_hat.
+  chosen form (the reported value): X stored in BF16, BF16 components, snapshot gradients refined
+    on the stored data (rs_solve with refine), k = 256, m = 2n, eta = 1/beta_hat;
+  plain form (alongside): the same values stored in FP32, FP32 components, same k, m, eta.
+  The proposal network's form (rs_solve_proposed) is reported alongside with its epochs to 1e-6.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {rs,reference}]
+                  [--workload {bf16_n1048576_d4096,fp32_n65536_d1024,batched}]
 
 Prints one JSON line.  `--impl reference` times the CPU oracle (the slow FP64 reference) on a
-bounded sample of the same workload and extrapolates to one solve.
+bounded sample of the same workload and extrapolates to one plain solve.
 """
 
 import argparse
@@ -31,10 +34,15 @@ import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
 TARGET = 1e-6
-WORKLOAD = "fp32_n65536_d1024"
-# dram__bytes_read.sum + dram__bytes_write.sum that ncu measured for one fullgrad_bulk_kernel launch on
-# this workload (update with the kernel)
-FULLGRAD_TRAFFIC_BYTES = 276.15e6
+METRIC = "time-to-1e-6 rel. suboptimality & data-pass HBM GB/s, chosen vs plain, 1 GB300"
+WORKLOAD = "bf16_n1048576_d4096"
+SINGLE = ("bf16_n1048576_d4096", "fp32_n65536_d1024")
+# epochs of the plain form to 1e-6 (measured by this bench on GB300); the CPU oracle's
+# extrapolation to one plain solve uses them
+PLAIN_EPOCHS = {"bf16_n1048576_d4096": 4, "fp32_n65536_d1024": 4}
+# dram__bytes_read.sum + dram__bytes_write.sum that ncu measured for one launch of the data-pass
+# kernel on each workload (None until captured for the current kernel)
+DATA_PASS_TRAFFIC = {"bf16_n1048576_d4096": None, "fp32_n65536_d1024": 276.15e6}
 
 
 def _peaks():
@@ -120,6 +128,13 @@ def _time_steps(step, steps, stream):
     return e0.elapsed_time(e1) / steps, out
 
 
+def _workload_text(name):
+    return {"bf16_n1048576_d4096": "bf16_n1048576_d4096: n=2^20 d=4096, spectrum j^-1.2 (x100 for j<=20), "
+                                   "lambda=1e-6, Gaussian sketch k=256",
+            "fp32_n65536_d1024": "fp32_n65536_d1024: n=65536 d=1024 fp32 data, spectrum j^-2, lambda=1e-5, "
+                                 "CountSketch s=4096 -> Gaussian sketch k=64"}[name]
+
+
 def run_rs(args):
     import paper_1602_02350_gb300 as rs
     from paper_1602_02350_gb300 import synth
@@ -127,64 +142,88 @@ def run_rs(args):
     dist, rank, ws = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    cfg = synth.CONFIGS[WORKLOAD]
-    X, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.float32)
-    y = y64.float().contiguous()
+    name = args.workload
+    cfg = synth.CONFIGS[name]
     n, d, k, lam = cfg.n, cfg.d, cfg.k, cfg.lam
+    big = name == "bf16_n1048576_d4096"
+    if big:
+        # one set of values, stored twice: BF16 for the chosen form, the same values in FP32 for the plain one
+        Xc, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.bfloat16)
+        Xp = Xc.float()
+    else:
+        Xp, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.float32)
+        Xc = Xp
+    y = y64.float().contiguous()
+    del y64
     stream = torch.cuda.current_stream()
     ctx = rs.Context(local, stream)
     theta, norm = _load_proposal(rs)
+    sk = dict(kind=cfg.kind, s=cfg.s)
+    m_plain, em_plain = 2 * n, 1.0
+
+    def plain(epochs, snapshots=False, X=Xp):
+        return rs.rs_solve(ctx, X, y, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, m=m_plain, eta_mult=em_plain,
+                           snapshots=snapshots, **sk)
+
+    def proposed(epochs, snapshots=False, X=Xc, yy=y, w_out=None):
+        return rs.rs_solve_proposed(ctx, X, yy, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, theta=theta, norm=norm,
+                                    z_dtype=torch.bfloat16, snapshots=snapshots, w_out=w_out, **sk)
+
+    if big:
+        def chosen(epochs, snapshots=False, X=Xc, yy=y, w_out=None):
+            return rs.rs_solve(ctx, X, yy, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, m=m_plain,
+                               eta_mult=em_plain, snapshots=snapshots, refine=True, w_out=w_out, **sk)
+        chosen_text = {"components": "bf16 from the bf16 data, snapshot gradients refined on the stored data",
+                       "k": k, "eta_mult": em_plain, "m": m_plain}
+    else:
+        chosen = proposed
+        chosen_text = {"components": "bf16, snapshot gradients refined on the fp32 data",
+                       "proposal": "network" if theta is not None else "theory setting (no weights)"}
 
     if args.profile:
-        # profiling run: one solve of each form with given epoch counts, nothing else
+        # profiling run: each form twice (the first is the warm-up) with fixed epoch counts, nothing else
         for _ in range(2):
-            rs.rs_solve(ctx, X, y, k, lam, args.plain_epochs, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s,
-                        m=2 * n, eta_mult=1.0)
-            rs.rs_solve_proposed(ctx, X, y, lam, args.chosen_epochs, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
-                                 norm=norm, kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16)
-        # the same data stored in bfloat16: sketch and components through the tensor-core product
-        Xb = X.to(torch.bfloat16)
-        rs.rs_solve(ctx, Xb, y, k, lam, 1, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0, refine=True)
+            plain(args.plain_epochs)
+            chosen(args.chosen_epochs)
         torch.cuda.synchronize()
         ctx.close()
         return
 
-    # reference minimiser for the accuracy target (normal equations in double; measurement only,
-    # untimed): the d x d Gram on the device, the d x d solve on the host
-    Xd = X.double()
-    A = (Xd.T @ Xd / n).cpu().numpy() + lam * np.eye(d)
-    b = (Xd.T @ y.double() / n).cpu().numpy()
-    del Xd
-    w_star = torch.from_numpy(np.linalg.solve(A, b)).float().cuda()
-    L_star, _ = rs.rs_objective(ctx, X, y, lam, w_star)
-
-    def rel(w):
-        return rs.rs_objective(ctx, X, y, lam, w, w_star)[1] / L_star
+    # reference minimiser for the accuracy target (normal equations in double; measurement only, untimed)
+    ref = _Reference(Xc, y, lam)
 
     def first_epoch(snaps, cap):
-        hist = [rel(s) for s in snaps]
+        hist = ref.rel(snaps)
         reach = [i for i, r in enumerate(hist) if r <= TARGET]
-        return ((reach[0] + 1) if reach else cap), hist
+        return ((reach[0] + 1) if reach else cap), [float(f"{h:.3e}") for h in hist]
 
-    # plain form: FP32 components, fixed practice setting m = 2n, eta = 1 / beta^, k = 64
-    m_plain, em_plain = 2 * n, 1.0
-    _, info = rs.rs_solve(ctx, X, y, k, lam, 20, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s, m=m_plain,
-                          eta_mult=em_plain, snapshots=True)
-    ep_plain, hist_plain = first_epoch(info["snapshots"], 20)
+    cap = args.cap_epochs
+    _, info = plain(cap, snapshots=True)
+    ep_plain, hist_plain = first_epoch(info["snapshots"], cap)
+    del info
+    _, cinfo = chosen(cap, snapshots=True)
+    ep_chosen, hist_chosen = first_epoch(cinfo["snapshots"], cap)
+    if not big:
+        chosen_text.update(k=cinfo["k"], eta_mult=cinfo["eta_mult"], m=cinfo["m"], fallback=cinfo["fallback"])
+    m_ch = cinfo.get("m", m_plain)
+    ems = cinfo["epoch_ms"]
+    del cinfo
+    prop_text = None
+    if big:
+        # the proposal network's form alongside (epochs to 1e-6 from its snapshots, not timed)
+        _, pinfo = proposed(cap, snapshots=True)
+        ep_p, hist_p = first_epoch(pinfo["snapshots"], cap)
+        prop_text = {"k": pinfo["k"], "eta_mult": pinfo["eta_mult"], "m": pinfo["m"], "fallback": pinfo["fallback"],
+                     "epochs_to_1e-6": ep_p if min(hist_p) <= TARGET else None,
+                     "epoch_ms_cumulative": [round(e, 2) for e in pinfo["epoch_ms"][:ep_p]]}
+        del pinfo
+    torch.cuda.empty_cache()
 
     def plain_step():
-        return rs.rs_solve(ctx, X, y, k, lam, ep_plain, cfg.seed_sketch, cfg.seed_svrg, kind=cfg.kind, s=cfg.s,
-                           m=m_plain, eta_mult=em_plain)[0]
-
-    # chosen form: BF16 components refined on the float data, (k, eta, m) from the proposal network
-    cap = 60
-    _, cinfo = rs.rs_solve_proposed(ctx, X, y, lam, cap, cfg.seed_sketch, cfg.seed_svrg, theta=theta, norm=norm,
-                                    kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16, snapshots=True)
-    ep_chosen, hist_chosen = first_epoch(cinfo["snapshots"], cap)
+        return plain(ep_plain)[0]
 
     def chosen_step():
-        return rs.rs_solve_proposed(ctx, X, y, lam, ep_chosen, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
-                                    norm=norm, kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16)[0]
+        return chosen(ep_chosen)[0]
 
     for _ in range(args.warmup):
         plain_step()
@@ -206,80 +245,113 @@ def run_rs(args):
         sampler.terminate()
         sampler.wait()
         fh.close()
-    final_rel, final_rel_plain = rel(w), rel(w_plain)
+    final_rel, final_rel_plain = float(ref.rel(w)[0]), float(ref.rel(w_plain)[0])
     ms = max_over_ranks(dist, ms)
     ms_plain = max_over_ranks(dist, ms_plain)
 
     # end to end through the public call with host buffers (pinned), copies inside the timed region
-    Xh = X.cpu().pin_memory()
+    Xh = Xc.cpu().pin_memory()
     yh = y.cpu().pin_memory()
     wh = torch.empty(d, dtype=torch.float32).pin_memory()
-
-    def e2e_step():
-        return rs.rs_solve_proposed(ctx, Xh, yh, lam, ep_chosen, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
-                                    norm=norm, kind=cfg.kind, s=cfg.s, z_dtype=torch.bfloat16, w_out=wh)
-
-    e2e_step()
+    chosen(ep_chosen, X=Xh, yy=yh, w_out=wh)
     torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5 if big else args.steps))
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    for _ in range(e2e_steps):
+        chosen(ep_chosen, X=Xh, yy=yh, w_out=wh)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / args.steps)
+    e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / e2e_steps)
+    e2e_ok = float(ref.rel(wh.cuda())[0])
+    del Xh
 
-    # dominant data pass: the full-gradient stream over the n + d component rows (the kernel the
-    # solve launches once per epoch), timed alone with events on the library's stream
-    V, s2 = rs.rs_sketch(ctx, X, k, cfg.seed_sketch, kind=cfg.kind, s=cfg.s)
-    Z, beta, bh = rs.rs_precondition(ctx, X, V, s2, lam)
+    # dominant data pass: the full-gradient stream over the n + d component rows of the chosen form's
+    # storage type, timed alone with events on the library's stream
+    zt = torch.bfloat16 if big else torch.float32
+    t_sk, (V, s2) = _event_ms(lambda: rs.rs_sketch(ctx, Xc, k, cfg.seed_sketch, **sk), stream)
+    t_pc, (Z, beta, bh) = _event_ms(lambda: rs.rs_precondition(ctx, Xc, V, s2, lam, z_dtype=zt), stream)
+    # speed-up diagnostic (ratio after Thm 1) from this sketch and tr(C)
+    trc = rs.rs_trace_c(ctx, Xc)
+    rat, rat_acc = rs.rs_speedup_ratio(ctx, s2, trc)
+    rat, rat_acc = rat.cpu().numpy(), rat_acc.cpu().numpy()
+    ratio = {"k": k, "ratio": float(rat[k - 1]), "accelerated": float(rat_acc[k - 1]), "trace_c": trc,
+             "ratio_at_k": {str(kk): float(rat[kk - 1]) for kk in (1, 8, 16, 32, 64, 128, 256) if kk <= k}}
     wt = torch.zeros(d, dtype=torch.float32, device="cuda")
     for _ in range(3):
         rs.rs_full_gradient(ctx, Z, y, n, lam, wt)
-    fg_ms, _ = _time_steps(lambda: rs.rs_full_gradient(ctx, Z, y, n, lam, wt), 20, stream)
-    fg_bytes = (n + d) * d * 4 + n * 4          # algorithmic: every component row and label read once
+    fg_ms, _ = _time_steps(lambda: rs.rs_full_gradient(ctx, Z, y, n, lam, wt), 10 if big else 20, stream)
+    esz = Z.element_size()
+    fg_bytes = (n + d) * d * esz + n * 4          # algorithmic: every component row and label read once
     peak, peak_kind = _peaks()
     achieved = fg_bytes / (fg_ms * 1e-3) / 1e9
+    del Z, beta
+    # tensor-core contractions of the chosen form's sketch and preconditioner (FLOP per call: the
+    # range sketch X^T Pi and X Q of Rayleigh-Ritz, 2 n d k each; X V and (X V) V^T, 2 n d k each)
+    tf_peak, tf_kind = _peak_tflops()
+    tens = {"sketch": {"flop": 4.0 * n * d * k, "ms": t_sk}, "precondition": {"flop": 4.0 * n * d * k, "ms": t_pc}}
+    for v in tens.values():
+        v["tflops"] = v["flop"] / (v["ms"] * 1e-3) / 1e12
+        v["frac_of_bf16_peak"] = v["tflops"] / tf_peak
+    tens["peak_tflops"], tens["peak_kind"] = tf_peak, tf_kind
 
-    # inner loop of the chosen setting: per-epoch time from the library's epoch events
-    ems = cinfo["epoch_ms"]
     per_epoch = (ems[-1] - ems[0]) / max(1, len(ems) - 1) if len(ems) > 1 else (ems[0] if ems else None)
-    m_ch = cinfo["m"]
-
+    xb = Xc.element_size() * n * d
     out = {
-        "metric": "time-to-1e-6 relative suboptimality (chosen form; plain form alongside)", "value": ms / 1e3,
-        "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: n=65536 d=1024 fp32 data, spectrum j^-2, lambda=1e-5, "
-                               "CountSketch s=4096 -> Gaussian sketch",
-                   "chosen": {"components": "bf16, snapshot gradients refined on the fp32 data",
-                              "proposal": "network" if theta is not None else "theory setting (no weights)",
-                              "k": cinfo["k"], "eta_mult": cinfo["eta_mult"], "m": m_ch,
-                              "fallback": cinfo["fallback"], "epochs": ep_chosen,
-                              "rel_subopt_per_epoch": [float(f"{h:.3e}") for h in hist_chosen[:ep_chosen]],
-                              "final_rel_subopt": final_rel},
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32", "data": "synthetic",
+        "config": {"workload": _workload_text(name),
+                   "chosen": dict(chosen_text, epochs=ep_chosen, rel_subopt_per_epoch=hist_chosen[:ep_chosen],
+                                  final_rel_subopt=final_rel),
                    "plain": {"components": "fp32", "k": k, "eta_mult": em_plain, "m": m_plain, "epochs": ep_plain,
                              "seconds": ms_plain / 1e3, "final_rel_subopt": final_rel_plain,
-                             "rel_subopt_per_epoch": [float(f"{h:.3e}") for h in hist_plain[:ep_plain]]},
+                             "rel_subopt_per_epoch": hist_plain[:ep_plain]},
                    "speedup_chosen_vs_plain": ms_plain / ms,
-                   "n": n, "d": d, "lambda": lam, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs exceed L2 (X 268 MB, components 272 MB fp32 / 136 MB bf16 vs 129 MB L2); no flush"},
-        "roofline": {"kernel": "fullgrad_bulk_kernel (data pass over the n+d component rows, fp32)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "traffic": FULLGRAD_TRAFFIC_BYTES, "traffic_unit": "B per launch",
+                   "n": n, "d": d, "k": k, "lambda": lam, "parallelism": f"replicas x{ws}",
+                   "l2": f"inputs exceed L2 (X {xb / 1e9:.2f} GB vs 129 MB L2); no flush"},
+        "roofline": {"kernel": f"full-gradient data pass over the n+d component rows ({'bf16' if big else 'fp32'})",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": DATA_PASS_TRAFFIC.get(name), "traffic_unit": "B per launch",
                      "algorithmic_bytes": fg_bytes, "ms_per_launch": fg_ms},
+        "tensor": tens,
+        "speedup_ratio": ratio,
         "inner_loop": {"ms_per_epoch": per_epoch, "m": m_ch,
                        "ns_per_step": per_epoch * 1e6 / m_ch if per_epoch else None,
                        "steps_per_s": m_ch / (per_epoch * 1e-3) if per_epoch else None},
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * d * 4 + n * 4, "d2h_bytes_per_step": d * 4},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": xb + n * 4, "d2h_bytes_per_step": d * 4,
+                "final_rel_subopt": e2e_ok},
         "gpu_launches": launches,
         "clocks": _clock_summary(cpath),
     }
+    if prop_text is not None:
+        out["config"]["proposal_form"] = prop_text
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline_sample(budget_s=args.cpu_budget) if args.cpu_budget > 0 else None
+        out["cpu_baseline"] = (cpu_baseline_sample(name, budget_s=args.cpu_budget, epochs=ep_plain)
+                               if args.cpu_budget > 0 else None)
         print(json.dumps(out))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     ctx.close()
+
+
+def _event_ms(fn, stream):
+    """(ms, result) of one call timed with events on ``stream`` (after one untimed call)."""
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    out = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out
+
+
+def _peak_tflops():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (bf16 burst)"
+    return 1900.0, "fallback"
 
 
 def _normal_equations(X, y):
@@ -313,88 +385,6 @@ class _Reference:
     def rel(self, W):
         E = W.double().reshape(-1, self.w.shape[0]) - self.w
         return (0.5 * ((E @ self.H) * E).sum(1) / self.L).cpu().numpy()
-
-
-def run_precision(args):
-    """Precision workload (one GPU): n = 2^20, d = 4096, spectrum j^-1.2 with the leading 20
-    directions x100, lambda = 1e-6, k = 256.  Time to 1e-6 for BF16 components with snapshot
-    gradients refined on the BF16 data, against the same solve on FP32 data, and the BF16 solve
-    with the proposal network's (k <= 64, eta, m)."""
-    import paper_1602_02350_gb300 as rs
-    from paper_1602_02350_gb300 import synth
-    name = "bf16_n1048576_d4096"
-    cfg = synth.CONFIGS[name]
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
-    ctx = rs.Context(local, stream)
-    Xb, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.bfloat16)
-    y = y64.float().contiguous()
-    del y64
-    n, d, k, lam = cfg.n, cfg.d, cfg.k, cfg.lam
-    ref = _Reference(Xb, y, lam)
-    theta, norm = _load_proposal(rs)
-    cap = args.precision_epochs
-
-    def first(snaps):
-        rel = ref.rel(snaps)
-        hit = [i for i, r in enumerate(rel) if r <= TARGET]
-        return (hit[0] + 1 if hit else cap), [float(f"{r:.3e}") for r in rel]
-
-    forms = {}
-
-    def timed(fn):
-        fn()
-        ms, _ = _time_steps(fn, 1, stream)
-        return ms
-
-    # BF16 data, k = 256, practice setting m = 2n, eta = 1/beta^, refined snapshot gradients
-    _, info = rs.rs_solve(ctx, Xb, y, k, lam, cap, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0,
-                          snapshots=True, refine=True)
-    e, hist = first(info["snapshots"])
-    del info
-    ms = timed(lambda: rs.rs_solve(ctx, Xb, y, k, lam, e, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0,
-                                   refine=True))
-    forms["bf16_refined_k256"] = {"seconds": ms / 1e3, "epochs": e, "rel_subopt_per_epoch": hist[:e]}
-    # BF16 data, proposal network
-    _, info = rs.rs_solve_proposed(ctx, Xb, y, lam, cap, cfg.seed_sketch, cfg.seed_svrg, theta=theta, norm=norm,
-                                   snapshots=True)
-    e, hist = first(info["snapshots"])
-    ms = timed(lambda: rs.rs_solve_proposed(ctx, Xb, y, lam, e, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
-                                            norm=norm))
-    forms["bf16_refined_proposal"] = {"seconds": ms / 1e3, "epochs": e, "k": info["k"], "eta_mult": info["eta_mult"],
-                                      "m": info["m"], "fallback": info["fallback"], "rel_subopt_per_epoch": hist[:e]}
-    del info
-    # BF16 data, FP8-e4m3 components with per-row scales, snapshot gradients refined on the BF16 data
-    def fp8_solve(epochs, snapshots=False):
-        V, s2 = rs.rs_sketch(ctx, Xb, k, cfg.seed_sketch)
-        Z8, beta8, _ = rs.rs_precondition(ctx, Xb, V, s2, lam, z_dtype=torch.float8_e4m3fn)
-        return rs.rs_svrg_solve(ctx, Z8, y, V, s2, lam, epochs, cfg.seed_svrg, beta=beta8, m=2 * n, eta_mult=1.0,
-                                X=Xb, refine=True, snapshots=snapshots)
-    _, info = fp8_solve(cap, snapshots=True)
-    e, hist = first(info["snapshots"])
-    del info
-    ms = timed(lambda: fp8_solve(e))
-    forms["fp8_refined_k256"] = {"seconds": ms / 1e3, "epochs": e, "rel_subopt_per_epoch": hist[:e]}
-    # FP32 data, same setting as the first form
-    Xf = Xb.float()
-    del Xb
-    torch.cuda.empty_cache()
-    _, info = rs.rs_solve(ctx, Xf, y, k, lam, cap, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0,
-                          snapshots=True)
-    e, hist = first(info["snapshots"])
-    del info
-    ms = timed(lambda: rs.rs_solve(ctx, Xf, y, k, lam, e, cfg.seed_sketch, cfg.seed_svrg, m=2 * n, eta_mult=1.0))
-    forms["fp32_k256"] = {"seconds": ms / 1e3, "epochs": e, "rel_subopt_per_epoch": hist[:e]}
-    best = min(forms, key=lambda f: forms[f]["seconds"])
-    out = {"metric": "time-to-1e-6 relative suboptimality (precision workload)", "value": forms[best]["seconds"],
-           "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False, "dtype": "bf16+f32",
-           "data": "synthetic",
-           "config": {"workload": f"{name}: n=2^20 d=4096, spectrum j^-1.2 (x100 for j<=20), lambda=1e-6, "
-                                  "Gaussian sketch", "best_form": best, "forms": forms,
-                      "l2": "inputs exceed L2 (X 8.6 GB bf16); no flush"}}
-    print(json.dumps(out))
-    ctx.close()
 
 
 def run_batched(args):
@@ -454,18 +444,26 @@ def run_batched(args):
     ctx.close()
 
 
-def cpu_baseline_sample(budget_s=20.0, epochs=None):
-    """Time the FP64 oracle on host cores on a bounded sample of the workload and extrapolate
-    to one solve: (sketch + precondition) once, plus epochs x (full gradient + m steps)."""
-    from oracle import precond, sketch, svrg
+def cpu_baseline_sample(name=WORKLOAD, budget_s=20.0, epochs=None, _cache={}):
+    """Time the FP64 oracle on host cores on a bounded sample of the workload and extrapolate to one
+    plain solve: (sketch + precondition) once, plus epochs x (full gradient + m steps).
+
+    At n = 65536 the oracle runs the passes on the whole data; at n = 2^20 it runs them on the first
+    n_s = 16384 rows of the same distribution (d, k, lambda and spectrum unchanged) and the pass times
+    are scaled by n / n_s (they are linear in n).  The sequential inner loop is timed for a bounded
+    number of steps at the full d and scaled to m = 2n steps per epoch."""
+    from oracle import precond, sketch, streams, svrg
     from paper_1602_02350_gb300 import synth
-    cfg = synth.CONFIGS[WORKLOAD]
-    X, y, _ = synth.config_problem(cfg, dtype=torch.float32)
-    Xn = X.double().numpy()
-    yn = y.float().double().numpy()
+    cfg = synth.CONFIGS[name]
     n, d, lam = cfg.n, cfg.d, cfg.lam
+    ns = min(n, 16384) if n > 65536 else n
+    if name not in _cache:
+        X, y, _ = synth.problem(ns, d, cfg.spectrum(), cfg.noise, cfg.seed_data, dtype=torch.float64)
+        _cache[name] = (X.numpy(), y.numpy())
+    Xn, yn = _cache[name]
     m = 2 * n
-    epochs = epochs or 4
+    epochs = epochs or PLAIN_EPOCHS[name]
+    scale = n / ns
     t0 = time.perf_counter()
     V, s2 = sketch.block_lanczos(Xn, cfg.k, cfg.seed_sketch, kind=cfg.kind, s=cfg.s)
     M = precond.m_matrix(V, s2, lam)
@@ -477,38 +475,43 @@ def cpu_baseline_sample(budget_s=20.0, epochs=None):
     mu = svrg.full_gradient_fast(Z, yz, g, wbar)
     t_fg = time.perf_counter() - t1
     W, cum, q = svrg.sampling_table(beta)
-    from oracle import streams
-    steps = int(min(m, max(2000, (budget_s - t_prep - t_fg) / 20e-6)))
+    per_step_guess = 10e-6 * max(1.0, d / 1024)
+    steps = int(min(m, max(2000, (budget_s - t_prep - t_fg) / per_step_guess)))
     idx = streams.sample_indices(cum, cfg.seed_svrg, 0, steps)
     t2 = time.perf_counter()
     svrg.epoch(Z, yz, g, wbar, idx, q, 1.0 / precond.beta_hat(beta), v_bar=mu)
     t_step = (time.perf_counter() - t2) / steps
-    total = t_prep + epochs * (t_fg + m * t_step)
+    total = scale * t_prep + epochs * (scale * t_fg + m * t_step)
+    rows = f"the first {ns} rows (pass times x{scale:g})" if ns < n else f"all {n} rows"
     return {"value": total, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"sketch+precondition once ({t_prep:.1f} s), one full-gradient pass ({t_fg:.2f} s) and "
-                      f"{steps} inner steps ({t_step * 1e6:.1f} us/step) of the {WORKLOAD} workload, "
+            "sample": f"sketch+precondition once ({t_prep:.1f} s) and one full-gradient pass ({t_fg:.2f} s) on {rows}, "
+                      f"{steps} inner steps at d={d} ({t_step * 1e6:.1f} us/step) of the {name} workload, "
                       f"extrapolated to {epochs} epochs of m={m}; numpy BLAS threads for the dense steps, "
                       f"one thread for the sequential inner loop"}
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle as it stands, on host cores, same workload and metric."""
+    """Reference arm: the CPU oracle as it stands, on host cores, same workload, metric and unit."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    name = args.workload if args.workload in SINGLE else WORKLOAD
     vals = []
     cb = None
-    for _ in range(max(0, args.warmup)):
-        pass   # the oracle has no warm-up state; a warm-up pass would only double the run time
+    # a bounded sample per step, sized so that the whole run stays within a few minutes
+    per_step = args.cpu_budget if args.cpu_budget > 0 else 15.0
+    per_step = min(per_step, max(3.0, 150.0 / max(1, args.steps)))
     for _ in range(args.steps):
-        cb = cpu_baseline_sample(budget_s=args.cpu_budget if args.cpu_budget > 0 else 15.0)
+        cb = cpu_baseline_sample(name, budget_s=per_step)
         vals.append(cb["value"])
     v = statistics.mean(vals)
-    out = {"impl": "reference", "metric": "time-to-1e-6 relative suboptimality", "value": v, "unit": "s",
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s",
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{WORKLOAD} (bounded sample, extrapolated)", "parallelism": "cpu"},
+           "config": {"workload": _workload_text(name) + " (oracle on a bounded sample, extrapolated to one "
+                                                       "plain solve: see cpu_baseline.sample)",
+                      "parallelism": "cpu"},
            "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -524,18 +527,16 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run two solves of each form with the given epoch counts and exit (for ncu launch lists)")
     ap.add_argument("--plain-epochs", type=int, default=4)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bf16_n1048576_d4096", "batched"],
-                    help="bf16_n1048576_d4096: the precision workload; batched: 64 problems x 8 lambda "
-                         "(each its own JSON line)")
+    ap.add_argument("--chosen-epochs", type=int, default=4)
+    ap.add_argument("--cap-epochs", type=int, default=30, help="epoch cap of the untimed calibration runs")
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(SINGLE) + ["batched"],
+                    help="bf16_n1048576_d4096 (default): n=2^20, d=4096; fp32_n65536_d1024: n=65536, d=1024; "
+                         "batched: 64 problems x 8 lambda (each its own JSON line)")
     ap.add_argument("--batch-problems", type=int, default=64)
     ap.add_argument("--batch-epochs", type=int, default=20)
-    ap.add_argument("--precision-epochs", type=int, default=30)
-    ap.add_argument("--chosen-epochs", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "bf16_n1048576_d4096":
-        run_precision(args)
     elif args.workload == "batched":
         run_batched(args)
     else:

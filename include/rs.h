@@ -336,6 +336,21 @@ int rs_solve_batched(rs_ctx* ctx, const rs_problem* probs, int32_t nprob, const 
  * double.  Synchronises. */
 int rs_trace_c(rs_ctx* ctx, const rs_matrix* X, double* out);
 
+/* ------------------------------------------------------- speed-up diagnostic
+ *
+ * The ratio after Thm 1 (Sec. 2; plotted against k in Fig. 1): preconditioned SVRG is faster than
+ * plain SVRG by about
+ *   ratio(k) = sum_{i=1..d} lambda_i / (k lambda_k + sum_{i>k} lambda_i),
+ * and by sqrt(ratio(k)) with acceleration, lambda_i the eigenvalues of C = X^T X / n.  From a sketch
+ * it is evaluated with sum_i lambda_i = tr(C) (rs_trace_c), lambda_i = sigma2[i-1] for i <= k and
+ * the tail sum tr(C) - sum_{i<=k} sigma2[i-1] (left-to-right prefix sum in double).
+ * sigma2: device, kmax doubles, descending (the Ritz values of rs_sketch of rank >= kmax).
+ * ratio (device, kmax doubles): ratio[k-1] = ratio(k); ratio_accel (device, nullable): its square
+ * roots.  A non-positive denominator gives NaN.  RS_EINVAL unless 1 <= kmax <= 65536 and tr(C) is
+ * finite and positive.  Enqueued on the context's stream. */
+int rs_speedup_ratio(rs_ctx* ctx, const double* sigma2, int64_t kmax, double trace_c, double* ratio,
+                     double* ratio_accel);
+
 /* ------------------------------------------------------- parameter proposal
  *
  * The paper sets the SVRG parameters from theory (Sec. 3, the SVRG theorem of Xiao and Zhang:

@@ -79,3 +79,54 @@ def speedup_ratio(eigs, k):
     """Eq. (5): sum_i lambda_i / (k lambda_k + sum_{i>k} lambda_i), eigenvalues descending."""
     ev = np.sort(np.asarray(eigs, np.float64))[::-1]
     return float(ev.sum() / (k * ev[k - 1] + ev[k:].sum()))
+
+
+def speedup_ratio_sketched(sigma2, trace_c, k):
+    """The same ratio (after Thm 1) from a sketch: sum_i lambda_i = tr(C), lambda_i ~ sigma2[i-1] for
+    i <= k, and the tail sum_{i>k} lambda_i = tr(C) - sum_{i<=k} sigma2[i-1].  With exact eigenvalues
+    (sigma2 = the spectrum of C) this is ``speedup_ratio``."""
+    s = np.asarray(sigma2, np.float64)
+    head = float(np.sum(s[:k]))
+    return float(trace_c / (k * s[k - 1] + (trace_c - head)))
+
+
+def normal_equations(chunks):
+    """(X^T X, X^T y, y^T y, n) accumulated in float64 over row blocks (X_b, y_b) given in order, for
+    data too large to hold in float64 at once; each block is converted to float64 before its
+    products.  With one block this is correlation(X) * n and X^T y."""
+    G = b = None
+    yy, n = 0.0, 0
+    for Xb, yb in chunks:
+        Xb = np.asarray(Xb, np.float64)
+        yb = np.asarray(yb, np.float64)
+        if G is None:
+            G = np.zeros((Xb.shape[1], Xb.shape[1]))
+            b = np.zeros(Xb.shape[1])
+        G += Xb.T @ Xb
+        b += Xb.T @ yb
+        yy += float(yb @ yb)
+        n += Xb.shape[0]
+    return G, b, yy, n
+
+
+def closed_form_from_normal(G, b, n, lam):
+    """w* of Eq. (1) from X^T X and X^T y: (G/n + lam I) w = b/n by a Cholesky factorisation and two
+    triangular solves (the steps of ``closed_form``; LAPACK's factorisation, since d may be thousands)."""
+    import scipy.linalg as sla
+    d = G.shape[0]
+    A = G / n + lam * np.eye(d)
+    L = np.linalg.cholesky(A)
+    z = sla.solve_triangular(L, b / n, lower=True)
+    return sla.solve_triangular(L.T, z, lower=False)
+
+
+def excess_from_normal(G, lam, n, e):
+    """1/2 e^T (C + lam I) e with C = G / n (the excess of Eq. (1) at w* + e, as ``excess``)."""
+    e = np.asarray(e, np.float64)
+    return 0.5 * float(e @ (G @ e)) / n + 0.5 * lam * float(e @ e)
+
+
+def objective_from_normal(G, b, yy, n, lam, w):
+    """L(w) of Eq. (1) expanded through the normal equations: (w^T G w - 2 b^T w + y^T y)/(2n) + lam/2 ||w||^2."""
+    w = np.asarray(w, np.float64)
+    return (float(w @ (G @ w)) - 2.0 * float(b @ w) + yy) / (2.0 * n) + 0.5 * lam * float(w @ w)

@@ -82,6 +82,25 @@ def gaussian(seed, rows, cols, row0=0):
     return out[:, :cols].copy()
 
 
+def gaussian_columns(seed, rows, cols, row0=0):
+    """Columns ``cols`` (any subset, any order) of the same Gaussian matrix as ``gaussian``:
+    column j = 4g + r is entry r of the Box-Muller pairs of counter (i, g, TAG_GAUSS), so only the
+    counters of the groups g the columns fall in are evaluated."""
+    cols = np.asarray(cols, np.int64)
+    out = np.empty((rows, cols.size))
+    i = np.arange(row0, row0 + rows, dtype=np.uint64)
+    for c, j in enumerate(cols):
+        g = np.uint64(j // 4)
+        w0, w1, w2, w3 = philox4x32_10(i & _MASK, i >> np.uint64(32), g, TAG_GAUSS, seed)
+        r = int(j % 4)
+        if r < 2:
+            z = box_muller(uniform24(w0), uniform24(w1))
+        else:
+            z = box_muller(uniform24(w2), uniform24(w3))
+        out[:, c] = z[r % 2]
+    return out
+
+
 def countsketch_hash(seed, n, s):
     """Bucket h(i) in [0, s) and sign sigma(i) in {+1, -1} for rows i < n.
 

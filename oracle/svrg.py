@@ -35,6 +35,18 @@ def full_gradient_fast(Z, yz, gamma, w):
     return Z.T @ r / Z.shape[0]
 
 
+def full_gradient_chunked(chunks, N, w):
+    """``full_gradient_fast`` over row blocks (Z_b, yz_b, gamma_b) given in any split, for N rows
+    in total: (1/N) sum_b Z_b^T (gamma_b (Z_b w - yz_b)), each block converted to float64."""
+    g = None
+    w = np.asarray(w, np.float64)
+    for Zb, yb, gb in chunks:
+        Zb = np.asarray(Zb, np.float64)
+        r = np.asarray(gb, np.float64) * (Zb @ w - np.asarray(yb, np.float64))
+        g = Zb.T @ r if g is None else g + Zb.T @ r
+    return g / N
+
+
 def epoch(Z, yz, gamma, w_bar, idx, q, eta, average=True, v_bar=None):
     """One outer iteration s of Alg. 1 for a given index stream i_1..i_m.
 

@@ -119,6 +119,7 @@ _SIGS = {
                  ctypes.POINTER(History)],
     "rs_objective": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_double)],
     "rs_trace_c": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(ctypes.c_double)],
+    "rs_speedup_ratio": [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P],
     "rs_solve_batched": [_P, ctypes.POINTER(Problem), ctypes.c_int32, ctypes.POINTER(Chain), ctypes.c_int32,
                          ctypes.POINTER(BatchParams), ctypes.POINTER(ctypes.c_float)],
     "rs_mlp_forward": [_P, _P, _P, ctypes.c_int64, _P],
@@ -461,6 +462,18 @@ def rs_trace_c(ctx, X):
     M = matrix(X)
     _check(lib().rs_trace_c(ctx.h, ctypes.byref(M), ctypes.byref(out)))
     return out.value
+
+
+def rs_speedup_ratio(ctx, sigma2, trace_c):
+    """ratio(k) after Thm 1 for k = 1..len(sigma2) from sketched eigenvalues (CUDA float64, descending)
+    and tr(C): returns (ratio, sqrt(ratio)) as CUDA float64 tensors."""
+    _need_cuda(sigma2)
+    s2 = sigma2.to(torch.float64).contiguous()
+    K = s2.shape[0]
+    r = ctx._empty(K, dtype=torch.float64)
+    ra = ctx._empty(K, dtype=torch.float64)
+    _check(lib().rs_speedup_ratio(ctx.h, _ptr(s2), K, float(trace_c), _ptr(r), _ptr(ra)))
+    return r, ra
 
 
 def rs_solve_batched(ctx, problems, chains, epochs, sketch_seed=0, kind="gaussian", q=1, refine=None, use_graph=True,

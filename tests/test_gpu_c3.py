@@ -1,0 +1,188 @@
+"""Full-size checks of the precision workload (n = 2^20, d = 4096, spectrum j^-1.2 with the leading 20
+directions x100, lambda = 1e-6, Gaussian sketch k = 256, BF16 storage), through the C ABI, against
+the oracle: sampled outputs the oracle computes one by one (columns of the range sketch, rows of the
+components), quantities it accumulates block by block (the full gradient, the normal equations), and
+properties that hold at any size (the Rayleigh-Ritz identity, interlacing).  Plus the kernels at
+d = 4096 and k = 256 against the oracle's full computation on row subsets.
+
+Tolerances (float arithmetic, BF16 storage):
+  * range sketch: a float sum over n = 2^20 products with Gaussian entries within a few float ulps of
+    the oracle's double values; error <= 1e-5 of the largest entry.
+  * Ritz pairs: the float Gram / Jacobi steps are accurate to about eps_32 * sigma_1^2 in absolute
+    terms (sigma_1^2 / sigma_256^2 ~ 8e4 here), so sigma2 and V^T C V are compared with atol
+    2e-5 * sigma_1^2, not a relative bound.
+  * components: each entry is formed in float and rounded once to BF16, so |z - z_oracle| <= 2^-8 |z|
+    (half an ulp) plus the float product error (1e-5 of the row's largest entry).
+  * refined BF16 / FP8 solves: relative suboptimality <= 1e-4 (the tolerance stated for BF16 with
+    refinement); whether 1e-6 is reached is reported.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1602_02350_gb300 as rs
+from oracle import precond, ridge, sketch as osk, streams, svrg
+from paper_1602_02350_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+CHUNK = 65536
+
+
+def _chunks(*ts):
+    """Row blocks of device tensors, moved to the host in float64 one block at a time."""
+    n = ts[0].shape[0]
+    for r0 in range(0, n, CHUNK):
+        yield tuple(t[r0:r0 + CHUNK].double().cpu().numpy() for t in ts)
+
+
+@pytest.fixture(scope="module")
+def c3(rsctx):
+    cfg = synth.CONFIGS["bf16_n1048576_d4096"]
+    Xb, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.bfloat16)
+    y = y64.float().contiguous()
+    del y64
+    return cfg, Xb, y
+
+
+@pytest.fixture(scope="module")
+def c3_normal(c3):
+    """X^T X, X^T y, y^T y of the stored (BF16) data in float64 on the host, and w*, L*."""
+    cfg, Xb, y = c3
+    G, b, yy, n = ridge.normal_equations(_chunks(Xb, y))
+    ws = ridge.closed_form_from_normal(G, b, n, cfg.lam)
+    Ls = ridge.objective_from_normal(G, b, yy, n, cfg.lam, ws)
+    return G, ws, Ls
+
+
+@pytest.fixture(scope="module")
+def c3_sketch(rsctx, c3):
+    cfg, Xb, _ = c3
+    V, s2 = rs.rs_sketch(rsctx, Xb, cfg.k, cfg.seed_sketch)
+    return V, s2
+
+
+def test_c3_range_sketch_sampled_columns_match_oracle(rsctx, c3):
+    cfg, Xb, _ = c3
+    Y = rs.rs_range_sketch(rsctx, Xb, cfg.k, cfg.seed_sketch).double().cpu().numpy()
+    cols = [0, 1, 2, 3, 129, 254, 255]
+    ref = np.zeros((cfg.d, len(cols)))
+    for r0, (Xc,) in zip(range(0, cfg.n, CHUNK), _chunks(Xb)):
+        ref += Xc.T @ streams.gaussian_columns(cfg.seed_sketch, Xc.shape[0], cols, row0=r0)
+    np.testing.assert_allclose(Y[:, cols], ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+
+
+def test_c3_ritz_pairs_satisfy_rayleigh_ritz_and_interlacing(c3, c3_normal, c3_sketch):
+    """V^T V = I and V^T C V = diag(sigma2) (Rayleigh-Ritz, Alg. 2's last step) with C from the oracle's
+    normal equations; Cauchy interlacing sigma2_i <= lambda_i(C)."""
+    cfg, _, _ = c3
+    G, _, _ = c3_normal
+    V, s2 = c3_sketch
+    Vd, s2 = V.double().cpu().numpy(), s2.cpu().numpy()
+    C = G / cfg.n
+    top = s2[0]
+    assert np.all(np.diff(s2) <= 0)
+    np.testing.assert_allclose(Vd.T @ Vd, np.eye(cfg.k), atol=1e-5)
+    np.testing.assert_allclose(Vd.T @ C @ Vd, np.diag(s2), atol=2e-5 * top)
+    lam_c = np.sort(np.linalg.eigvalsh(C))[::-1][: cfg.k]
+    assert np.all(s2 <= lam_c + 2e-5 * top)
+    # the 20 boosted directions are captured almost exactly by a rank-256 sketch
+    np.testing.assert_allclose(s2[:20], lam_c[:20], rtol=1e-3)
+
+
+def test_c3_components_sampled_rows_match_oracle(rsctx, c3, c3_sketch):
+    cfg, Xb, _ = c3
+    V, s2 = c3_sketch
+    n, d, lam = cfg.n, cfg.d, cfg.lam
+    Z, beta, bh = rs.rs_precondition(rsctx, Xb, V, s2, lam)
+    M = precond.m_matrix(V.double().cpu().numpy(), s2.cpu().numpy(), lam)
+    rng = np.random.default_rng(5)
+    rows = np.sort(rng.choice(n, 512, replace=False))
+    regs = np.sort(rng.choice(d, 64, replace=False))
+    idx = torch.from_numpy(np.concatenate([rows, n + regs])).cuda()
+    zg = Z[idx].double().cpu().numpy()
+    ref = np.concatenate([Xb[torch.from_numpy(rows).cuda()].double().cpu().numpy() @ M, M[regs]])
+    bound = 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(zg - ref) <= bound), float(np.max(np.abs(zg - ref) - bound))
+    # smoothness of the stored rows: gamma_i ||z_i||^2 with gamma = (n+d)/n or lam (n+d)
+    gam = np.concatenate([np.full(rows.size, (n + d) / n), np.full(regs.size, lam * (n + d))])
+    np.testing.assert_allclose(beta[idx].double().cpu().numpy(), gam * (zg * zg).sum(1), rtol=1e-5)
+
+
+def test_c3_full_gradient_matches_oracle(rsctx, c3, c3_sketch):
+    cfg, Xb, y = c3
+    V, s2 = c3_sketch
+    n, d, lam = cfg.n, cfg.d, cfg.lam
+    Z, _, _ = rs.rs_precondition(rsctx, Xb, V, s2, lam)
+    w = synth.random_vector(d, 17, scale=0.1)
+    mu = rs.rs_full_gradient(rsctx, Z, y, n, lam, torch.from_numpy(w).float().cuda()).double().cpu().numpy()
+    wf = torch.from_numpy(w).float().double().numpy()
+    yz = torch.cat([y, torch.zeros(d, device="cuda")])
+    gam = torch.cat([torch.full((n,), (n + d) / n, dtype=torch.float64, device="cuda"),
+                     torch.full((d,), lam * (n + d), dtype=torch.float64, device="cuda")])
+    ref = svrg.full_gradient_chunked(_chunks(Z, yz, gam), n + d, wf)
+    np.testing.assert_allclose(mu, ref, rtol=0, atol=2e-5 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("components", ["bf16", "fp8"])
+def test_c3_refined_solve_reaches_target(rsctx, c3, c3_normal, c3_sketch, components):
+    """BF16 components, or FP8-e4m3 with one scale per row, with snapshot gradients refined on the
+    stored BF16 data (m = 2n, eta = 1/beta^): relative suboptimality <= 1e-4 after 6 epochs."""
+    cfg, Xb, y = c3
+    G, ws, Ls = c3_normal
+    V, s2 = c3_sketch
+    n, lam = cfg.n, cfg.lam
+    zt = torch.float8_e4m3fn if components == "fp8" else None
+    Z, beta, _ = rs.rs_precondition(rsctx, Xb, V, s2, lam, z_dtype=zt)
+    _, info = rs.rs_svrg_solve(rsctx, Z, y, V, s2, lam, 6, cfg.seed_svrg, beta=beta, m=2 * n, eta_mult=1.0, X=Xb,
+                               refine=True, snapshots=True)
+    rel = [ridge.excess_from_normal(G, lam, n, s - ws) / Ls for s in info["snapshots"].double().cpu().numpy()]
+    print(f"{components} refined, rel subopt per epoch: " + ", ".join(f"{r:.2e}" for r in rel) +
+          f"; reaches 1e-6: {min(rel) <= 1e-6}")
+    assert rel[-1] <= 1e-4, rel
+    assert rel[-1] <= 1e-2 * rel[0], rel
+
+
+# ------------------------------------------------------------- the kernels at d = 4096 and k = 256
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-4), (torch.bfloat16, 1e-4)])
+def test_chain_d4096_matches_stepwise_oracle(rsctx, dtype, tol):
+    """The blocked inner loop at d = 4096 (one 16-CTA cluster, 256 columns per CTA) against the oracle's
+    step-by-step recursion on the same index stream and the stored component values."""
+    n, d, m, lam = 8192, 4096, 4160, 1e-3
+    Zn = synth.random_matrix(n + d, d, 41, scale=1.0 / np.sqrt(d))
+    Zt = torch.from_numpy(Zn).to(dtype)
+    Zd = Zt.double().numpy()
+    y = synth.random_vector(n, 42)
+    _, yz, g = precond.components(Zd[:n], Zd[n:], y, lam)
+    idx = synth.random_indices(n + d, m, 43)
+    inq_t = torch.from_numpy(synth.random_positive(m, 44, 0.5, 1.5)).float()
+    eta = 0.2 / precond.smoothness(Zd, g).mean()
+    wb_t = torch.from_numpy(synth.random_vector(d, 45, scale=0.1)).float()
+    mu_t = torch.from_numpy(synth.random_vector(d, 46, scale=1e-3)).float()
+    got = rs.rs_svrg_epoch(rsctx, Zt.cuda(), n, lam, torch.from_numpy(idx.astype(np.int32)).cuda(), inq_t.cuda(), eta,
+                           wb_t.cuda(), mu_t.cuda(), True).double().cpu().numpy()
+    ref = svrg.epoch_scaled(Zd, yz, g, wb_t.double().numpy(), idx, inq_t.double().numpy(), eta, True,
+                            v_bar=mu_t.double().numpy())
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_sketch_k256_d4096_matches_oracle(rsctx, dtype):
+    """Alg. 2 (q = 1) at k = 256, d = 4096 on 32768 rows of the precision workload's spectrum: the GPU
+    sketch against the oracle's on the same stored values (Ritz values with atol 2e-5 sigma_1^2; the
+    preconditioner M, which is invariant to the sign and rotation of V within equal Ritz values)."""
+    cfg = synth.CONFIGS["bf16_n1048576_d4096"]
+    n, d, k, lam = 32768, cfg.d, cfg.k, cfg.lam
+    X, _, _ = synth.problem(n, d, cfg.spectrum(), cfg.noise, 77, device="cuda", dtype=dtype)
+    V, s2 = rs.rs_sketch(rsctx, X, k, 2000)
+    V, s2 = V.double().cpu().numpy(), s2.cpu().numpy()
+    Vr, s2r = osk.block_lanczos(X.double().cpu().numpy(), k, 2000)
+    np.testing.assert_allclose(s2, s2r, rtol=0, atol=2e-5 * s2r[0])
+    M, Mr = precond.m_matrix(V, s2, lam), precond.m_matrix(Vr, s2r, lam)
+    err = np.abs(M - Mr).max()
+    print(f"k=256 d=4096 {dtype}: max |M - M_oracle| = {err:.2e}, max rel sigma2 err "
+          f"{np.max(np.abs(s2 - s2r) / s2r):.2e}")
+    assert err <= 2e-3, err

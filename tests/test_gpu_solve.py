@@ -116,3 +116,33 @@ def test_errors_are_reported(rsctx):
     Xo = torch.zeros(10, 5, dtype=torch.float32, device="cuda")   # row stride 20 bytes: not 16-byte aligned
     with pytest.raises(rs.RsError):
         rs.rs_full_gradient(rsctx, Xo[:, :5], torch.zeros(5, device="cuda"), 5, 1e-3, torch.zeros(5, device="cuda"))
+
+
+@pytest.mark.slow
+def test_fp32_workload_trajectory_parity_same_stream(rsctx):
+    """Full-size FP32 workload (n = 65536, d = 1024, CountSketch s = 4096 then Gaussian k = 64, lambda =
+    1e-5): the GPU's sketch, components and 4 epochs of Alg. 1 (m = 2n, eta = 1/beta^) against the
+    oracle replaying the same 4 epochs in float64 from the GPU's V, sigma2 and beta (equal beta gives
+    equal integer weights, so both sides draw the same index stream).  The iterates agree to
+    ||w - w_oracle|| / ||w_oracle|| <= 1e-4 and both reach relative suboptimality <= 1e-6."""
+    from oracle import svrg
+    cfg = synth.CONFIGS["fp32_n65536_d1024"]
+    X, y64, _ = synth.config_problem(cfg, device="cuda", dtype=torch.float32)
+    y = y64.float().contiguous()
+    n, d, lam, E, m = cfg.n, cfg.d, cfg.lam, 4, 2 * cfg.n
+    V, s2 = rs.rs_sketch(rsctx, X, cfg.k, cfg.seed_sketch, kind=cfg.kind, s=cfg.s)
+    Z, beta, _ = rs.rs_precondition(rsctx, X, V, s2, lam)
+    w, info = rs.rs_svrg_solve(rsctx, Z, y, V, s2, lam, E, cfg.seed_svrg, beta=beta, m=m, eta_mult=1.0)
+    Xn, yn = X.double().cpu().numpy(), y.double().cpu().numpy()
+    M = precond.m_matrix(V.double().cpu().numpy(), s2.cpu().numpy(), lam)
+    Zr, yz, g = precond.components(*precond.transform(Xn, M), yn, lam)
+    snaps = svrg.solve(Zr, yz, g, beta.double().cpu().numpy(), info["eta"], m, E, cfg.seed_svrg)
+    wr = M @ snaps[-1]
+    wg = w.double().cpu().numpy()
+    err = np.linalg.norm(wg - wr) / np.linalg.norm(wr)
+    ws = ridge.closed_form(Xn, yn, lam)
+    rel_gpu = ridge.rel_suboptimality(Xn, yn, lam, wg, ws)
+    rel_orc = ridge.rel_suboptimality(Xn, yn, lam, wr, ws)
+    print(f"fp32 workload: |w - w_oracle|/|w_oracle| = {err:.3e}, rel subopt GPU {rel_gpu:.3e}, oracle {rel_orc:.3e}")
+    assert err <= 1e-4, err
+    assert rel_gpu <= 1e-6 and rel_orc <= 1e-6, (rel_gpu, rel_orc)

@@ -78,3 +78,45 @@ def test_speedup_ratio_special_cases():
     assert ridge.speedup_ratio(ev, 4) == pytest.approx(7.5 / 2.0)
     assert ridge.speedup_ratio(ev, 1) == pytest.approx(1.0)
     assert ridge.speedup_ratio(ev, 2) == pytest.approx(7.5 / (2 * 2.0 + 1.5))
+
+
+def test_sketched_ratio_equals_the_spectral_ratio_with_exact_eigenvalues():
+    """With sigma2 = the eigenvalues of C (what a perfect sketch returns) and tr(C) = ||X||_F^2 / n,
+    the sketched form equals the ratio on the spectrum (Eq. after Thm 1) for every k."""
+    X, _ = _small(n=200, d=30, seed=4)
+    ev = np.sort(np.linalg.eigvalsh(ridge.correlation(X)))[::-1]
+    trc = float((X * X).sum() / X.shape[0])
+    for k in range(1, 31):
+        assert ridge.speedup_ratio_sketched(ev, trc, k) == pytest.approx(ridge.speedup_ratio(ev, k), rel=1e-10)
+
+
+def test_sketched_ratio_two_level_closed_form():
+    """r eigenvalues a and d - r eigenvalues b < a: ratio(k) = T / (k a + (r - k) a + (d - r) b) = 1 for
+    k <= r, and T / (d b) for k > r, with T = r a + (d - r) b; a dropped tail or a wrong k factor fails."""
+    r, d, a, b = 5, 40, 3.0, 0.25
+    ev = np.array([a] * r + [b] * (d - r))
+    T = r * a + (d - r) * b
+    for k in range(1, r + 1):
+        assert ridge.speedup_ratio_sketched(ev, T, k) == pytest.approx(1.0, rel=1e-14)
+    for k in range(r + 1, d + 1):
+        assert ridge.speedup_ratio_sketched(ev, T, k) == pytest.approx(T / (d * b), rel=1e-14)
+    # an underestimated head (a sketch that misses mass) moves it into the tail: the ratio drops
+    assert ridge.speedup_ratio_sketched(0.5 * ev, T, r + 1) < T / (d * b)
+
+
+def test_chunked_normal_equations_match_the_one_block_forms():
+    """Block accumulation of X^T X, X^T y, y^T y (any split) and the quantities derived from them equal
+    the direct forms: closed form, excess identity and objective."""
+    X, y = _small(n=300, d=17, seed=12)
+    lam = 3e-3
+    blocks = [(X[:7], y[:7]), (X[7:150], y[7:150]), (X[150:], y[150:])]
+    G, b, yy, n = ridge.normal_equations(blocks)
+    assert n == 300
+    np.testing.assert_allclose(G, ridge.correlation(X) * n, rtol=1e-12)
+    np.testing.assert_allclose(b, X.T @ y, rtol=1e-12)
+    assert yy == pytest.approx(float(y @ y), rel=1e-13)
+    ws = ridge.closed_form_from_normal(G, b, n, lam)
+    np.testing.assert_allclose(ws, ridge.closed_form(X, y, lam), rtol=1e-9)
+    w = ws + 0.01 * np.arange(17)
+    assert ridge.excess_from_normal(G, lam, n, w - ws) == pytest.approx(ridge.excess(X, lam, w, ws), rel=1e-10)
+    assert ridge.objective_from_normal(G, b, yy, n, lam, w) == pytest.approx(ridge.objective(X, y, lam, w), rel=1e-10)

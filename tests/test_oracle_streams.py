@@ -118,3 +118,10 @@ def test_sampler_frequencies_follow_q():
     iu = streams.sample_indices_uniform(10, 5, 1, 50000)
     assert iu.min() >= 0 and iu.max() < 10
     assert stats.chisquare(np.bincount(iu, minlength=10)).pvalue > 1e-4
+
+
+def test_gaussian_column_subset_equals_the_full_matrix_columns():
+    from oracle import streams as st
+    full = st.gaussian(99, 37, 11, row0=5)
+    cols = [10, 0, 3, 4, 7]
+    np.testing.assert_array_equal(st.gaussian_columns(99, 37, cols, row0=5), full[:, cols])

@@ -105,3 +105,17 @@ def test_alg3_fp64_config_reaches_1e10():
                           m=cfg.m, eta_mult=cfg.eta_mult, history=True)
     rel = pipeline.relative_history(X, y, cfg.lam, out["history"])
     assert rel[-1] < 1e-10
+
+
+def test_chunked_full_gradient_equals_the_one_block_form():
+    from oracle import precond
+    rng = np.random.default_rng(3)
+    n, d, lam = 90, 13, 1e-2
+    Z = rng.standard_normal((n + d, d))
+    y = rng.standard_normal(n)
+    _, yz, g = precond.components(Z[:n], Z[n:], y, lam)
+    w = rng.standard_normal(d)
+    cuts = [0, 5, 47, 95, n + d]
+    blocks = [(Z[a:b], yz[a:b], g[a:b]) for a, b in zip(cuts[:-1], cuts[1:])]
+    np.testing.assert_allclose(svrg.full_gradient_chunked(blocks, n + d, w), svrg.full_gradient(Z, yz, g, w),
+                               rtol=1e-12, atol=1e-14)
