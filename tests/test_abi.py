@@ -21,8 +21,7 @@ def _declared():
 @pytest.fixture(scope="module")
 def librs():
     from paper_1602_02350_gb300 import _lib, build
-    if not os.path.exists(_lib.LIB_PATH):
-        build.build()
+    build.build()          # incremental: recompiles only sources newer than their objects
     return _lib.lib()
 
 
