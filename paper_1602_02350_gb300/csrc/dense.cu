@@ -461,6 +461,174 @@ __global__ void jacobi_kernel(const double* G, int k, TW* Ag, TW* Wg, double tol
   }
 }
 
+// Cyclic Jacobi in float on the packed lower triangle of A (k (k+1) / 2 floats in shared memory, so
+// k up to 320 fits one CTA), with the same round-robin pairing and rotation thresholds as
+// jacobi_kernel.  A round is one pass: the K/2 disjoint rotations are chosen (first barrier), then
+// every 2 x 2 block A[(p_a, q_a), (p_b, q_b)] with a >= b is rotated from both sides by one thread
+// (second barrier): the diagonal blocks take the closed form a_pp - t a_pq, a_qq + t a_pq, 0 and
+// the others R_a M R_b^T.  The eigenvectors are not formed here: every round's rotations (p, q, c, s)
+// are logged to global memory and jacobi_apply_kernel replays them onto the identity afterwards,
+// many rows in parallel.  evals0 receives the diagonal (unsorted), *nsweeps the sweeps run.
+__device__ __forceinline__ int tri_idx(int i, int j) {   // packed lower triangle, any order of (i, j)
+  return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i;
+}
+
+__global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __restrict__ G, int k, float tol,
+                                                             double floor_ulps, int max_sweeps,
+                                                             float4* __restrict__ rot_log, int* __restrict__ nsweeps,
+                                                             double* __restrict__ evals0) {
+  extern __shared__ float jp_sh[];
+  float* A = jp_sh;
+  const int K = (k + 1) & ~1;
+  const int P = K / 2;
+  __shared__ int pp[160], qq[160];
+  __shared__ float cc[160], ss[160], tt[160];
+  __shared__ double red[32];
+  __shared__ int rotations;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double fro = 0.0;
+  for (int e = tid; e < k * (k + 1) / 2; e += nt) {
+    int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (i * (i + 1) / 2 > e) --i;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    const int j = e - i * (i + 1) / 2;
+    const double g = G[(size_t)i * k + j];
+    A[e] = (float)g;
+    fro = fma(i == j ? g : 2.0 * g, g, fro);   // off-diagonal entries count twice in ||G||_F^2
+  }
+  fro = warp_sum(fro);
+  if ((tid & 31) == 0) red[tid >> 5] = fro;
+  __syncthreads();
+  if (tid == 0) {
+    double f = 0.0;
+    for (int w = 0; w < nt / 32; ++w) f += red[w];
+    red[0] = sqrt(f);
+  }
+  __syncthreads();
+  const float abs_floor = (float)(floor_ulps * red[0] * 0x1p-24);
+  const int nblocks = P * (P + 1) / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rotations = 0;
+    __syncthreads();
+    for (int r = 0; r < K - 1; ++r) {
+      float4* log_r = rot_log + ((size_t)sweep * (K - 1) + r) * P;
+      for (int i = tid; i < P; i += nt) {
+        auto pos = [&](int j) {   // round-robin seat of player j in round r
+          if (j == 0) return 0;
+          const int v = j - 1 + r;
+          return (v >= K - 1 ? v - (K - 1) : v) + 1;
+        };
+        int p = pos(i), q = pos(K - 1 - i);
+        if (p > q) { const int t2 = p; p = q; q = t2; }
+        float c = 1.0f, sn = 0.0f, t = 0.0f;
+        if (q < k) {
+          const float apq = A[tri_idx(q, p)], app = A[tri_idx(p, p)], aqq = A[tri_idx(q, q)];
+          const float noise = 4.0f * 0x1p-24f * fmaxf(fabsf(app), fabsf(aqq));
+          const float thr = fmaxf(fmaxf(tol * sqrtf(fabsf(app * aqq)), abs_floor), noise);
+          if (fabsf(apq) > thr) {
+            const float theta = (aqq - app) / (2.0f * apq);
+            t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+            c = 1.0f / sqrtf(t * t + 1.0f);
+            sn = t * c;
+            rotations = 1;
+          }
+        }
+        pp[i] = p; qq[i] = q; cc[i] = c; ss[i] = sn; tt[i] = t;
+        log_r[i] = make_float4(__int_as_float(p), __int_as_float(q), c, sn);
+      }
+      __syncthreads();
+      for (int bi = tid; bi < nblocks; bi += nt) {
+        int a = (int)((sqrtf(8.0f * (float)bi + 1.0f) - 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 > bi) --a;
+        while ((a + 1) * (a + 2) / 2 <= bi) ++a;
+        const int b = bi - a * (a + 1) / 2;
+        const int pa = pp[a], qa = qq[a], pb = pp[b], qb = qq[b];
+        if (qa >= k || qb >= k) {
+          // a dummy player (odd k): only the real rotation acts; rows/columns of the dummy do not exist
+          if (a == b || (qa >= k && qb >= k)) continue;
+        }
+        const float sa = ss[a], sb = ss[b];
+        if (sa == 0.0f && sb == 0.0f) continue;
+        if (a == b) {
+          const int ipq = tri_idx(qa, pa);
+          const float apq = A[ipq], t = tt[a];
+          A[tri_idx(pa, pa)] -= t * apq;
+          A[tri_idx(qa, qa)] += t * apq;
+          A[ipq] = 0.0f;
+          continue;
+        }
+        const float ca = cc[a], cb = cc[b];
+        // M = [A(pa, pb) A(pa, qb); A(qa, pb) A(qa, qb)], rows of a dummy player are absent
+        const bool ra = qa < k, rb = qb < k;
+        const int i00 = tri_idx(pa, pb);
+        const int i01 = rb ? tri_idx(pa, qb) : -1;
+        const int i10 = ra ? tri_idx(qa, pb) : -1;
+        const int i11 = (ra && rb) ? tri_idx(qa, qb) : -1;
+        const float m00 = A[i00], m01 = rb ? A[i01] : 0.0f, m10 = ra ? A[i10] : 0.0f, m11 = (ra && rb) ? A[i11] : 0.0f;
+        // rows (R_a): p' = c p - s q, q' = s p + c q
+        const float r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
+        const float r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
+        // columns (R_b)
+        A[i00] = cb * r00 - sb * r01;
+        if (rb) A[i01] = sb * r00 + cb * r01;
+        if (ra) A[i10] = cb * r10 - sb * r11;
+        if (ra && rb) A[i11] = sb * r10 + cb * r11;
+      }
+      __syncthreads();
+    }
+    const int done = rotations == 0;
+    __syncthreads();
+    if (done) {
+      ++sweep;
+      break;
+    }
+  }
+  if (tid == 0) *nsweeps = sweep;
+  for (int i = tid; i < k; i += nt) evals0[i] = (double)A[tri_idx(i, i)];
+}
+
+// W = product of the logged Jacobi rotations applied to the identity, in the logged order: row j
+// of W takes (w_p, w_q) <- (c w_p - s w_q, s w_p + c w_q) for every rotation.  CTA = 8 rows of W in
+// shared memory; thread (row, pair) applies one rotation of each round, rounds separated by a
+// barrier (the rotations of a round act on disjoint columns).  Wout: double, k x k row-major.
+constexpr int kJaRows = 8;
+__global__ void __launch_bounds__(1024) jacobi_apply_kernel(const float4* __restrict__ rot_log,
+                                                            const int* __restrict__ nsweeps, int k,
+                                                            double* __restrict__ Wout) {
+  extern __shared__ float ja_sh[];
+  const int K = (k + 1) & ~1, P = K / 2, LDW = k + 1;
+  const int row0 = blockIdx.x * kJaRows;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < kJaRows * LDW; e += nt) {
+    const int rr = e / LDW, c = e % LDW;
+    ja_sh[e] = (row0 + rr == c) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const int rr = tid / P, a = tid % P;
+  const bool active = rr < kJaRows && row0 + rr < k;
+  const int64_t rounds = (int64_t)(*nsweeps) * (K - 1);
+  float* wrow = ja_sh + rr * LDW;
+  float4 cur = (active && rounds > 0) ? rot_log[a] : make_float4(0.f, 0.f, 1.f, 0.f);
+  for (int64_t r = 0; r < rounds; ++r) {
+    const float4 nxt = (active && r + 1 < rounds) ? rot_log[(r + 1) * P + a] : make_float4(0.f, 0.f, 1.f, 0.f);
+    if (active && cur.w != 0.0f) {
+      const int p = __float_as_int(cur.x), q = __float_as_int(cur.y);
+      if (q < k) {
+        const float wp = wrow[p], wq = wrow[q];
+        wrow[p] = cur.z * wp - cur.w * wq;
+        wrow[q] = cur.w * wp + cur.z * wq;
+      }
+    }
+    cur = nxt;
+    __syncthreads();
+  }
+  for (int e = tid; e < kJaRows * k; e += nt) {
+    const int r2 = e / k, c = e % k;
+    if (row0 + r2 < k) Wout[(size_t)(row0 + r2) * k + c] = (double)ja_sh[r2 * LDW + c];
+  }
+}
+
 // Rayleigh quotients lambda_j = w_j^T G w_j / w_j^T w_j in double (one block per vector): turns
 // float Jacobi eigenvectors (orthonormal to ~1e-6) into eigenvalues accurate to ~1e-12.
 __global__ void rayleigh_kernel(const double* G, int k, const double* W, double* lam) {
@@ -935,6 +1103,30 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
     double* Wt = tmp;
     double* lam0 = tmp + k * k;
     double* lam1 = lam0 + k;
+    const char* env = std::getenv("RS_JACOBI_PACKED");
+    if (k >= 2 && !(env && env[0] == '0')) {
+      // packed one-pass rounds with a rotation log, eigenvectors replayed in parallel afterwards
+      constexpr int kMaxSweeps = 30;
+      const int K = (int)((k + 1) & ~int64_t(1)), P = K / 2;
+      const size_t log_bytes = (size_t)kMaxSweeps * (K - 1) * P * sizeof(float4);
+      unsigned char* lg = static_cast<unsigned char*>(rs_scratch(ctx, SCR_EIG, log_bytes + 256));
+      if (!lg) return RS_ENOMEM;
+      float4* rot_log = reinterpret_cast<float4*>(lg);
+      int* nsw = reinterpret_cast<int*>(lg + log_bytes);
+      const size_t pshm = (size_t)k * (k + 1) / 2 * sizeof(float);
+      RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+      jacobi_packed_kernel<<<1, 1024, pshm, ctx->stream>>>(G, (int)k, 1e-6f, 8.0, kMaxSweeps, rot_log, nsw, lam0);
+      RS_LAUNCH_CHECK(ctx);
+      const size_t ashm = (size_t)kJaRows * (k + 1) * sizeof(float);
+      jacobi_apply_kernel<<<(unsigned)((k + kJaRows - 1) / kJaRows), kJaRows * P, ashm, ctx->stream>>>(rot_log, nsw,
+                                                                                                       (int)k, Wt);
+      RS_LAUNCH_CHECK(ctx);
+      rayleigh_kernel<<<(unsigned)k, 128, 0, ctx->stream>>>(G, (int)k, Wt, lam1);
+      RS_LAUNCH_CHECK(ctx);
+      sort_eig_kernel<<<1, 256, 0, ctx->stream>>>(lam1, Wt, (int)k, evals, W);
+      RS_LAUNCH_CHECK(ctx);
+      return RS_OK;
+    }
     float* Ag = static_cast<float*>(g);
     if (smem) {
       RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

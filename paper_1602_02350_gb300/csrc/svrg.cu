@@ -234,6 +234,161 @@ __global__ void __launch_bounds__(32 * (kFgRows + 1)) fullgrad_bulk_kernel(const
   }
 }
 
+// Wide rows (float or bfloat16 storage, float arithmetic): column ownership.  A producer warp
+// streams tiles of R rows into a ring of shared-memory stages with cp.async.bulk (bytes counted on
+// the stage's mbarrier, bounded waits).  Each of the 256 consumer threads owns the 16-byte column
+// chunks q = tid + 256 u (u < U), keeps w and the gradient accumulators of those columns in
+// registers, and loads each staged element exactly once: it forms its partial dot products for
+// the R rows of the tile, the partials are summed across the block (shuffles, then the eight warp
+// sums in a fixed order after one named barrier), and the same registers then take
+// acc += r_i z_i.  Every column of the block's partial gradient has one owner, so no shared-memory
+// accumulation is needed.  A wait that gives up sets the status bit and every consumer leaves the
+// loop together (the decision is taken after the barrier).
+constexpr int kFcThreads = 256, kFcMaxStages = 8;
+constexpr size_t kFcSmemBudget = 200 * 1024;
+
+template <typename S, int U, int R>
+__global__ void __launch_bounds__(kFcThreads + 32, 1)
+    fullgrad_cols_kernel(const S* __restrict__ Z, int64_t N, int64_t n, int64_t d, int64_t ld,
+                         const float* __restrict__ y, float lam, const float* __restrict__ w,
+                         float* __restrict__ part, int stages, int* status) {
+  constexpr int E = 16 / (int)sizeof(S);
+  extern __shared__ __align__(128) unsigned char fc_sh[];
+  __shared__ uint64_t full[kFcMaxStages], empty[kFcMaxStages];
+  __shared__ float dpart[kFcMaxStages][kFcThreads / 32][R];
+  __shared__ int abort_flag;
+  const int64_t nch = (d + E - 1) / E;                          // 16-byte chunks per row
+  const uint32_t row_bytes = (uint32_t)(nch * 16);
+  const int64_t rstride = ((int64_t)row_bytes + 127) / 128 * 128;   // staged row stride (bytes)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (N + R - 1) / R;
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init_cta(&full[s], 1);
+      mbar_init_cta(&empty[s], kFcThreads / 32);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  float acc[U][E];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[u][e] = 0.0f;
+  if (warp == kFcThreads / 32) {
+    if (lane == 0) {   // producer
+      int64_t it = 0, last_use[kFcMaxStages];
+      for (int s = 0; s < stages; ++s) last_use[s] = -1;
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int s = (int)(it % stages);
+        const int64_t u = it / stages;
+        if (u >= 1 && !mbar_wait_bounded(&empty[s], (uint32_t)((u - 1) & 1), kFgWait)) {
+          atomicOr(status, STATUS_TIMEOUT);
+          break;
+        }
+        const int64_t r0 = t * R;
+        const int rows = (int)min64(R, N - r0);
+        mbar_expect_tx_cta(&full[s], (uint32_t)rows * row_bytes);
+        for (int r = 0; r < rows; ++r)
+          bulk_copy_g2s(fc_sh + ((int64_t)s * R + r) * rstride, Z + (r0 + r) * ld, row_bytes, &full[s]);
+        last_use[s] = u;
+      }
+      for (int s = 0; s < stages; ++s)   // every issued copy has landed before the block exits
+        if (last_use[s] >= 0 && !mbar_wait_bounded(&full[s], (uint32_t)(last_use[s] & 1), kFgWait))
+          atomicOr(status, STATUS_TIMEOUT);
+    }
+  } else {   // consumers
+    float wr[U][E];
+    // the last chunk may run past d: its extra elements get weight 0 and are masked to zero on load
+    // (the row padding need not hold finite values); chunks beyond the row are not loaded at all
+    uint4 msk[U];
+    int lim[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t q = tid + (int64_t)kFcThreads * u;
+      lim[u] = q < nch ? (int)min64(E, d - q * E) : 0;
+      uint32_t mw[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if constexpr (E == 8) {
+          mw[k] = (2 * k < lim[u] ? 0x0000FFFFu : 0u) | (2 * k + 1 < lim[u] ? 0xFFFF0000u : 0u);
+        } else {
+          mw[k] = k < lim[u] ? 0xFFFFFFFFu : 0u;
+        }
+      }
+      msk[u] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+#pragma unroll
+      for (int e = 0; e < E; ++e) wr[u][e] = e < lim[u] ? w[q * E + e] : 0.0f;
+    }
+    const float inv_n = 1.0f / (float)n;
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int s = (int)(it % stages);
+      const int64_t uu = it / stages;
+      const int64_t r0 = t * R;
+      const int rows = (int)min64(R, N - r0);
+      if (!mbar_wait_bounded(&full[s], (uint32_t)(uu & 1), kFgWait)) abort_flag = 1;
+      const unsigned char* st = fc_sh + (int64_t)s * R * rstride;
+      uint4 zr[R][U];
+      float pd[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        pd[j] = 0.0f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t q = tid + (int64_t)kFcThreads * u;
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (j < rows && lim[u] > 0) v = *reinterpret_cast<const uint4*>(st + j * rstride + q * 16);
+          v.x &= msk[u].x;
+          v.y &= msk[u].y;
+          v.z &= msk[u].z;
+          v.w &= msk[u].w;
+          zr[j][u] = v;
+          const S* sv = reinterpret_cast<const S*>(&zr[j][u]);
+#pragma unroll
+          for (int e = 0; e < E; ++e) pd[j] = fmaf(cvt<float>(sv[e]), wr[u][e], pd[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const float v = warp_sum(pd[j]);
+        if (lane == 0) dpart[s][warp][j] = v;
+      }
+      asm volatile("bar.sync 1, %0;\n" ::"r"(kFcThreads) : "memory");
+      if (abort_flag) {
+        if (lane == 0) atomicOr(status, STATUS_TIMEOUT);
+        break;
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (j < rows) {
+          float dot = 0.0f;
+#pragma unroll
+          for (int w2 = 0; w2 < kFcThreads / 32; ++w2) dot += dpart[s][w2][j];   // fixed order
+          const int64_t i = r0 + j;
+          const float r = i < n ? (dot - y[i]) * inv_n : lam * dot;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const S* sv = reinterpret_cast<const S*>(&zr[j][u]);
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[u][e] = fmaf(r, cvt<float>(sv[e]), acc[u][e]);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&empty[s]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t q = tid + (int64_t)kFcThreads * u;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e < lim[u]) part[(int64_t)blockIdx.x * d + q * E + e] = acc[u][e];
+    }
+  }
+}
+
 // mu[c] = sum over the per-block partials, 32 columns per thread block: eight interleaved
 // partial sums per column, then a fixed-order sum of the eight (deterministic).
 template <typename T>
@@ -416,7 +571,51 @@ static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t 
     }
     return RS_OK;
   }
-  // wide rows or bfloat16 storage: shared-memory accumulators
+  // wide float rows or bfloat16 storage: column-owner kernel with a bulk-copy ring
+  if constexpr (std::is_same<T, float>::value && (std::is_same<S, float>::value ||
+                                                  std::is_same<S, __nv_bfloat16>::value)) {
+    constexpr int E = 16 / (int)sizeof(S);
+    const int64_t nch = (d + E - 1) / E;
+    // rows per tile R and chunks per thread U keep R U 16-byte chunks in registers: 16 for float
+    // rows, 8 for bfloat16 rows (whose widened values take twice the registers)
+    constexpr int RU = E == 8 ? 8 : 16;
+    constexpr int UMAX = E == 8 ? 4 : 8;
+    if (nch <= (int64_t)kFcThreads * UMAX) {
+      const int U = nch <= kFcThreads ? 1 : nch <= 2 * kFcThreads ? 2 : nch <= 4 * kFcThreads ? 4 : 8;
+      const int R = RU / U;
+      const int64_t rstride = (nch * 16 + 127) / 128 * 128;
+      int stages = (int)std::min<int64_t>(kFcMaxStages, (int64_t)kFcSmemBudget / (R * rstride));
+      if (stages >= 2) {
+        const size_t shm = (size_t)stages * R * rstride;
+        const int blocks = ctx->num_sms;
+        T* part = static_cast<T*>(rs_scratch(ctx, SCR_PART2, (size_t)blocks * d * sizeof(T)));
+        if (!part) return RS_ENOMEM;
+        const S* Zd = static_cast<const S*>(Z->data);
+#define RS_FC(UU)                                                                                             \
+  do {                                                                                                        \
+    constexpr int UC = UU <= UMAX ? UU : UMAX;                                                                \
+    RS_CUDA_TRY(cudaFuncSetAttribute(fullgrad_cols_kernel<S, UC, RU / UC>,                                     \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));                  \
+    fullgrad_cols_kernel<S, UC, RU / UC><<<blocks, kFcThreads + 32, shm, ctx->stream>>>(                      \
+        Zd, N, n, d, Z->ld, y, (float)lam, w, part, stages, ctx->d_status);                                   \
+  } while (0)
+        if (U == 1) RS_FC(1);
+        else if (U == 2) RS_FC(2);
+        else if (U == 4) RS_FC(4);
+        else RS_FC(8);
+#undef RS_FC
+        RS_LAUNCH_CHECK(ctx);
+        fullgrad_reduce_kernel<T><<<(unsigned)((d + 31) / 32), 256, 0, ctx->stream>>>(part, blocks, d, mu);
+        RS_LAUNCH_CHECK(ctx);
+        if (norm2_dev) {
+          norm2_kernel<T><<<1, 256, 0, ctx->stream>>>(mu, d, norm2_dev);
+          RS_LAUNCH_CHECK(ctx);
+        }
+        return RS_OK;
+      }
+    }
+  }
+  // wider rows: shared-memory accumulators
   const size_t shm = ((size_t)((d + 3) & ~int64_t(3)) + (size_t)(threads / 32) * d) * sizeof(T);
   if (shm > 220 * 1024) return rs_fail(RS_EUNSUPPORTED, "full gradient: d = %lld too wide for on-chip accumulators", (long long)d);
   const int blocks = ctx->num_sms * (shm <= 100 * 1024 ? 2 : 1);
