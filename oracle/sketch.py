@@ -35,7 +35,7 @@ def countsketch_matrix(seed, n, s):
     return S
 
 
-def range_sketch(X, k, seed, kind="gaussian", s=0):
+def range_sketch(X, k, seed, kind="gaussian", s=0, pi_bf16=False):
     """First Krylov block A Pi of Alg. 2, up to the scalar n^{-1/2}: Y = X^T Pi (d x k).
 
     kind = "gaussian":     Pi ~ N(0,1)^{n x k}.
@@ -45,7 +45,8 @@ def range_sketch(X, k, seed, kind="gaussian", s=0):
     """
     X = np.asarray(X, np.float64)
     if kind == "gaussian":
-        return X.T @ test_matrix_gaussian(seed, X.shape[0], k)
+        Pi = test_matrix_gaussian(seed, X.shape[0], k)
+        return X.T @ (streams.round_bf16(Pi) if pi_bf16 else Pi)
     if kind == "countsketch":
         return countsketch_rows(X, seed, s).T @ streams.gaussian(seed, s, k)
     raise ValueError(kind)
@@ -81,9 +82,11 @@ def ritz(X, Q, k):
     return Q @ W[:, :k], s[:k] ** 2
 
 
-def block_lanczos(X, k, seed, q=1, kind="gaussian", s=0):
-    """Alg. 2: returns (U~_k, sigma~^2).  q = 1 is the single-pass range sketch."""
-    Y0 = range_sketch(X, k, seed, kind, s)
+def block_lanczos(X, k, seed, q=1, kind="gaussian", s=0, pi_bf16=False):
+    """Alg. 2: returns (U~_k, sigma~^2).  q = 1 is the single-pass range sketch.  ``pi_bf16``: the
+    Gaussian test matrix with its entries rounded to bfloat16 (the tensor-core sketch of bfloat16
+    data draws the same Philox / Box-Muller values and rounds them)."""
+    Y0 = range_sketch(X, k, seed, kind, s, pi_bf16)
     Q = orthonormalize(krylov_blocks(X, Y0, q))
     return ritz(X, Q, k)
 

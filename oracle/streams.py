@@ -82,8 +82,17 @@ def gaussian(seed, rows, cols, row0=0):
     return out[:, :cols].copy()
 
 
-def gaussian_columns(seed, rows, cols, row0=0):
-    """Columns ``cols`` (any subset, any order) of the same Gaussian matrix as ``gaussian``:
+def round_bf16(x):
+    """Nearest bfloat16 value (8 significant bits, ties to even) of each float64 entry, as float64:
+    x = m 2^e with m in [0.5, 1), rounded to m' = rint(256 m) / 256 (normal range)."""
+    x = np.asarray(x, np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def gaussian_columns(seed, rows, cols, row0=0, bf16=False):
+    """Columns ``cols`` (any subset, any order) of the same Gaussian matrix as ``gaussian`` (entries
+    rounded by ``round_bf16`` when ``bf16``):
     column j = 4g + r is entry r of the Box-Muller pairs of counter (i, g, TAG_GAUSS), so only the
     counters of the groups g the columns fall in are evaluated."""
     cols = np.asarray(cols, np.int64)
@@ -98,7 +107,7 @@ def gaussian_columns(seed, rows, cols, row0=0):
         else:
             z = box_muller(uniform24(w2), uniform24(w3))
         out[:, c] = z[r % 2]
-    return out
+    return round_bf16(out) if bf16 else out
 
 
 def countsketch_hash(seed, n, s):

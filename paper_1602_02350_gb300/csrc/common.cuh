@@ -25,7 +25,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_RPART, SCR_XPART, SCR_ROWSQ, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_RPART, SCR_XPART, SCR_ROWSQ, SCR_SKPART, SCR_COUNT
 };
 
 struct rs_ctx {
@@ -241,6 +241,9 @@ bool umma_enabled();
 // caller checks the status word afterwards).
 int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, const float* col_scale, float* C,
                  int64_t ldc, bool sync_check = true);
+// Y (d x k float) = X^T Pi on tensor cores for bfloat16 X (umma.cu), Pi the Gaussian test matrix of
+// Alg. 2 with its entries rounded to bfloat16; RS_EUNSUPPORTED when the tensor path cannot run.
+int umma_sketch(rs_ctx* ctx, const rs_matrix* X, uint64_t seed, int64_t k, float* Y);
 // Z (bfloat16) = X - P V^T (umma.cu) for bfloat16 X (k <= 128) or float X whose bfloat16 parts the
 // same call has formed for X V (k <= 64), P n x k and V d x k float with row stride k;
 // RS_EUNSUPPORTED when the tensor path cannot run.

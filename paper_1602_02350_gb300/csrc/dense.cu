@@ -1195,6 +1195,11 @@ static int range_sketch_t(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_param
   double* Gd = static_cast<double*>(rs_scratch(ctx, SCR_GRAM, d * k * sizeof(double)));
   if (!Gd) return RS_ENOMEM;
   if (p->kind == RS_SKETCH_GAUSSIAN) {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value && std::is_same<T, float>::value) {
+      // bfloat16 data: the contraction on tensor cores with the test matrix rounded to bfloat16
+      const int rc = umma_sketch(ctx, X, p->seed, k, Y);
+      if (rc != RS_EUNSUPPORTED) return rc;
+    }
     T* Om = static_cast<T*>(rs_scratch(ctx, SCR_OMEGA, n * k * sizeof(T)));
     if (!Om) return RS_ENOMEM;
     RS_TRY(gaussian_dispatch(ctx, p->seed, 0, n, k, dt, Om, k));

@@ -42,6 +42,24 @@ __global__ void gaussian_kernel(uint64_t seed, int64_t row0, int64_t rows, int64
   }
 }
 
+// Transposed bfloat16 test matrix for the tensor-core range sketch: out[j * ld + i] = bf16(Pi(i, j))
+// for j < k, i < n (the float Box-Muller value of entry (i, j), rounded to nearest).  Consecutive
+// threads take consecutive rows i of one group of four columns, so each of the four stores is
+// coalesced along a row of the output.
+__global__ void gaussian_t_bf16_kernel(uint64_t seed, int64_t n, int64_t k, __nv_bfloat16* out, int64_t ld) {
+  const int64_t groups = (k + 3) / 4;
+  const int64_t total = n * groups;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n;
+    const uint32_t g = (uint32_t)(e / n);
+    float z[4];
+    gauss4<float>(seed, i, g, z);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (4 * (int64_t)g + q < k) out[(4 * (int64_t)g + q) * ld + i] = __float2bfloat16_rn(z[q]);
+  }
+}
+
 // ---------------------------------------------------------------- CountSketch
 
 template <typename T>
@@ -470,6 +488,13 @@ int countsketch_dispatch(rs_ctx* ctx, const rs_matrix* X, uint64_t seed, int64_t
                                  static_cast<double*>(sign_out));
   return countsketch_t<float>(ctx, X, seed, s, static_cast<float*>(SX), ld_sx, bucket_out,
                               static_cast<float*>(sign_out));
+}
+
+int gaussian_t_bf16_dispatch(rs_ctx* ctx, uint64_t seed, int64_t n, int64_t k, __nv_bfloat16* out, int64_t ld) {
+  const int64_t work = n * ((k + 3) / 4);
+  gaussian_t_bf16_kernel<<<grid_for(ctx, work), kThreads, 0, ctx->stream>>>(seed, n, k, out, ld);
+  RS_LAUNCH_CHECK(ctx);
+  return RS_OK;
 }
 
 int gaussian_dispatch(rs_ctx* ctx, uint64_t seed, int64_t row0, int64_t rows, int64_t cols, int32_t dtype, void* out,

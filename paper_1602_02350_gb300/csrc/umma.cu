@@ -197,6 +197,189 @@ __global__ void __launch_bounds__(128, 1) umma_xw_kernel(const __grid_constant__
   }
 }
 
+// ------------------------------------------------------------------ range sketch Y = X^T Pi
+// The first Krylov block of Alg. 2, Y = X^T Pi (d x k), for bfloat16 X: a contraction over the n
+// rows.  D[c][j] = sum_i X[i][c] Pi[i][j]: the MMA's M dimension is 128 columns c of X, its K
+// dimension the rows i and its N dimension the k columns of Pi.  X tiles arrive by TMA as they
+// are stored (rows of 64 columns, 128-byte swizzle), which makes A the MN-major operand; Pi is
+// read from its transposed bfloat16 copy Pi^T (k x n), which makes B K-major.  One CTA covers
+// NT tiles of 128 columns of X and a contiguous range of rows (split K), 128 threads: warp 0
+// lane 0 produces (TMA, ring of stages holding NT x 2 X boxes and one Pi^T box), warp 1 lane 0
+// issues tcgen05.mma (M = 128, N = kp, K = 16) into NT tensor-memory accumulators, and all four
+// warps read their 32 lanes (columns c) at the end and write the CTA's partial d x k block;
+// sketch_reduce_kernel adds the partials of the row ranges in order.  Bounded waits.
+constexpr int SK_ROWS = 64;                                   // rows of X per stage (K chunk)
+constexpr uint32_t SK_XBOX = SK_ROWS * 128;                   // one 64 x 64 bfloat16 box of X
+template <int NT> __host__ __device__ constexpr uint32_t sk_stage_bytes(int kp) {
+  return (uint32_t)NT * 2 * SK_XBOX + (uint32_t)kp * 128;
+}
+
+// instruction descriptor: f32 accumulate, bf16 A and B, A MN-major (bit 15), B K-major, N, M = 128
+__host__ __device__ constexpr uint32_t sk_idesc(int kp) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(kp >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+}
+
+// MN-major, 128-byte swizzle: rows of the tile are K (64 elements of M or N each, 128 bytes), 8-row
+// groups 1024 bytes apart (stride dimension), the two 64-wide halves of M = 128 `half` bytes apart
+// (leading dimension)
+__device__ __forceinline__ uint64_t smem_desc_mn_sw128(uint32_t saddr, uint32_t half) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((half >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1) umma_sketch_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                             const __grid_constant__ CUtensorMap tmP, int64_t n,
+                                                             int64_t d, int k, int kp, int stages,
+                                                             int64_t chunks_per_cta, float* __restrict__ part,
+                                                             int* status) {
+  extern __shared__ unsigned char sk_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sk_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full[4], empty[4], done;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int abort_flag;
+  const uint32_t stage_bytes = sk_stage_bytes<NT>(kp);
+  const uint32_t idesc = sk_idesc(kp);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c0 = (int64_t)blockIdx.x * (NT * UM);
+  const int64_t nchunks = (n + SK_ROWS - 1) / SK_ROWS;
+  const int64_t q0 = (int64_t)blockIdx.y * chunks_per_cta;
+  const int64_t q1 = min64(nchunks, q0 + chunks_per_cta);
+  const int KB = (int)max64(0, q1 - q0);
+  uint32_t tcols = 32;
+  while (tcols < (uint32_t)(NT * kp)) tcols <<= 1;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init_cta(&full[s], 1);
+      mbar_init_cta(&empty[s], 1);
+    }
+    mbar_init_cta(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(cta_smem_addr(&tmem_holder)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+
+  if (threadIdx.x == 0) {   // producer
+    int issued_last[4] = {-1, -1, -1, -1};
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % stages, u = kb / stages;
+      if (u >= 1 && !mbar_wait_bounded(&empty[s], (uint32_t)((u - 1) & 1), kUmmaWait)) {
+        atomicOr(status, STATUS_TIMEOUT);
+        abort_flag = 1;
+        break;
+      }
+      if (abort_flag) break;
+      unsigned char* st = base + (size_t)s * stage_bytes;
+      const int row = (int)((q0 + kb) * SK_ROWS);
+      mbar_expect_tx_cta(&full[s], stage_bytes);
+      for (int h = 0; h < NT * 2; ++h)   // boxes of 64 columns: tile t = h / 2, half h % 2
+        tma_load_2d(st + h * SK_XBOX, &tmX, (int)(c0 + 64 * h), row, &full[s]);
+      tma_load_2d(st + NT * 2 * SK_XBOX, &tmP, row, 0, &full[s]);
+      issued_last[s] = u;
+    }
+    for (int s = 0; s < stages; ++s)
+      if (issued_last[s] >= 0 && !mbar_wait_bounded(&full[s], (uint32_t)(issued_last[s] & 1), kUmmaWait))
+        atomicOr(status, STATUS_TIMEOUT);
+  } else if (threadIdx.x == 32) {   // MMA issuer
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % stages, u = kb / stages;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)(u & 1), kUmmaWait)) {
+        atomicOr(status, STATUS_TIMEOUT);
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sa = cta_smem_addr(base + (size_t)s * stage_bytes);
+      const uint32_t sb = sa + NT * 2 * SK_XBOX;
+#pragma unroll
+      for (int kk = 0; kk < SK_ROWS / 16; ++kk) {
+        const uint64_t db = smem_desc_sw128(sb + kk * 32);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          // 16 rows of the tile: 16 x 128 bytes into its first 64-column box; the second box is
+          // SK_XBOX bytes further on
+          const uint64_t da = smem_desc_mn_sw128(sa + t * 2 * SK_XBOX + kk * 16 * 128, SK_XBOX);
+          const uint32_t accum = (kb | kk) != 0;
+          asm volatile(
+              "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem + (uint32_t)(t * kp)),
+              "l"(da), "l"(db), "r"(idesc), "r"(accum)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       cta_smem_addr(&empty[s]))
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     cta_smem_addr(&done))
+                 : "memory");
+  }
+  __syncwarp();
+  // epilogue: warp w owns accumulator lanes 32w..32w+31, i.e. columns c0 + 128 t + 32 w + lane of X
+  bool ok = KB == 0 || mbar_wait_bounded(&done, 0u, kUmmaWait);
+  if (!ok && lane == 0) atomicOr(status, STATUS_TIMEOUT);
+  ok = __all_sync(0xffffffffu, ok && !abort_flag);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  float* pout = part + (int64_t)blockIdx.y * d * k;
+  for (int t = 0; t < NT; ++t) {
+    const int64_t c = c0 + (int64_t)t * UM + warp * 32 + lane;
+    for (int j0 = 0; j0 < kp; j0 += 32) {
+      uint32_t v[32];
+      if (ok && KB > 0) {
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kp + j0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0u;   // an empty row range contributes zeros
+      }
+      if (c < d) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j0 + j < k) pout[c * k + j0 + j] = __uint_as_float(v[j]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tcols) : "memory");
+  }
+}
+
+// Y[e] = sum over the row ranges r = 0..R-1 of part[r][e], added in increasing r
+__global__ void sketch_reduce_kernel(const float* __restrict__ part, int R, int64_t count, float* __restrict__ Y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int r = 0; r < R; ++r) s += part[(int64_t)r * count + e];
+    Y[e] = s;
+  }
+}
+
 // ------------------------------------------------------------------ block preparation
 // R = (I + eta K L)^{-1} K and c = -eta R (j . h) of one block of 64 inner steps (the blocked form
 // of the inner loop of Alg. 1; K = diag(kappa) the importance weights of the sampled rows, L the
@@ -919,5 +1102,61 @@ int umma_gemm_xw(rs_ctx* ctx, const rs_matrix* X, const float* W, int64_t N, con
   RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   if (st & STATUS_TIMEOUT) return rs_fail(RS_ETIMEOUT, "tensor-core product: a bounded wait gave up");
+  return RS_OK;
+}
+
+int gaussian_t_bf16_dispatch(rs_ctx* ctx, uint64_t seed, int64_t n, int64_t k, __nv_bfloat16* out, int64_t ld);
+
+// Y (d x k float, row stride k) = X^T Pi for bfloat16 X on tensor cores, Pi the Gaussian test matrix
+// of Alg. 2 rounded to bfloat16 (Pi^T formed once per call in scratch, k x n).  RS_EUNSUPPORTED when
+// the tensor path is off or cannot run (the caller uses the CUDA-core sketch).
+int umma_sketch(rs_ctx* ctx, const rs_matrix* X, uint64_t seed, int64_t k, float* Y) {
+  if (!umma_enabled() || !encode_fn()) return RS_EUNSUPPORTED;
+  const char* env = std::getenv("RS_UMMA_SKETCH");
+  if (env && env[0] == '0') return RS_EUNSUPPORTED;
+  const int64_t n = X->n, d = X->d;
+  if (X->dtype != RS_BF16 || k < 1 || k > 256 || n < 1 || d < 1 || n > 0x7FFFFF00LL || d > 0x7FFFFF00LL)
+    return RS_EUNSUPPORTED;
+  const int kp = (int)((k + 15) / 16 * 16);
+  const int64_t ldp = (n + 7) / 8 * 8;                    // 16-byte rows of Pi^T
+  __nv_bfloat16* PiT = static_cast<__nv_bfloat16*>(rs_scratch(ctx, SCR_OMEGA, (size_t)k * ldp * sizeof(__nv_bfloat16)));
+  if (!PiT) return RS_ENOMEM;
+  RS_TRY(gaussian_t_bf16_dispatch(ctx, seed, n, k, PiT, ldp));
+  // NT column tiles per CTA (two when d allows, so each Pi^T tile feeds 256 columns), and enough
+  // row ranges to fill the GPU once
+  const int NT = d > UM ? 2 : 1;
+  const int64_t dtiles = (d + NT * UM - 1) / (NT * UM);
+  const int64_t nchunks = (n + SK_ROWS - 1) / SK_ROWS;
+  int64_t R = std::max<int64_t>(1, std::min<int64_t>(nchunks, (ctx->num_sms + dtiles - 1) / dtiles));
+  const int64_t per = (nchunks + R - 1) / R;
+  R = (nchunks + per - 1) / per;
+  if (R > 65535) return RS_EUNSUPPORTED;
+  const uint32_t sb = NT == 2 ? sk_stage_bytes<2>(kp) : sk_stage_bytes<1>(kp);
+  const int stages = (int)std::min<uint32_t>(4, (215u * 1024u) / sb);
+  if (stages < 2) return RS_EUNSUPPORTED;
+  float* part = static_cast<float*>(rs_scratch(ctx, SCR_SKPART, (size_t)R * d * k * sizeof(float)));
+  if (!part) return RS_ENOMEM;
+  CUtensorMap mx, mp;
+  RS_TRY(make_map(&mx, X->data, d, n, X->ld, SK_ROWS));
+  RS_TRY(make_map(&mp, PiT, n, k, ldp, (uint32_t)kp));
+  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  const size_t shm = (size_t)stages * sb + 1024;
+  dim3 grid((unsigned)dtiles, (unsigned)R);
+  if (NT == 2) {
+    RS_CUDA_TRY(cudaFuncSetAttribute(umma_sketch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    umma_sketch_kernel<2><<<grid, 128, shm, ctx->stream>>>(mx, mp, n, d, (int)k, kp, stages, per, part, ctx->d_status);
+  } else {
+    RS_CUDA_TRY(cudaFuncSetAttribute(umma_sketch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    umma_sketch_kernel<1><<<grid, 128, shm, ctx->stream>>>(mx, mp, n, d, (int)k, kp, stages, per, part, ctx->d_status);
+  }
+  RS_LAUNCH_CHECK(ctx);
+  const int64_t count = d * k;
+  sketch_reduce_kernel<<<(unsigned)std::min<int64_t>((count + 255) / 256, (int64_t)ctx->num_sms * 8), 256, 0,
+                         ctx->stream>>>(part, (int)R, count, Y);
+  RS_LAUNCH_CHECK(ctx);
+  int st = 0;
+  RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (st & STATUS_TIMEOUT) return rs_fail(RS_ETIMEOUT, "tensor-core range sketch: a bounded wait gave up");
   return RS_OK;
 }

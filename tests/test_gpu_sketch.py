@@ -85,3 +85,24 @@ def test_sketch_end_to_end_matches_oracle(rsctx, dtype, tol, kind, n, d, k, s, q
     M = precond.m_matrix(V, s2, 1e-4)
     Mr = precond.m_matrix(Vr, s2r, 1e-4)
     assert np.abs(M - Mr).max() < tol * 10
+
+
+@pytest.mark.parametrize("n,d,k", [(300, 70, 5), (4096, 256, 16), (5000, 300, 100), (20000, 520, 256), (64, 130, 64)])
+def test_tensor_core_range_sketch_bf16_matches_oracle(rsctx, n, d, k):
+    """bfloat16 data: Y = X^T Pi on tensor cores with Pi rounded to bfloat16 (the oracle rounds its own
+    Philox / Box-Muller values the same way); ragged n, d and k, several 128-column tiles and row
+    ranges.  The products are exact in FP32, so only the FP32 accumulation over n rows (and the rare
+    entry whose float and double Box-Muller values round to neighbouring bfloat16 values) differ."""
+    X, _ = _data(n, d, 1.5, 11, torch.bfloat16)
+    Y = rs.rs_range_sketch(rsctx, cuda_rows(X), k, 2000).cpu().double().numpy()
+    ref = osk.range_sketch(X.double().numpy(), k, 2000, pi_bf16=True)
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=3e-5 * np.abs(ref).max())
+
+
+def test_tensor_core_range_sketch_can_be_switched_off(rsctx, monkeypatch):
+    """RS_UMMA_SKETCH=0 selects the CUDA-core sketch with the float test matrix (the oracle's Pi)."""
+    monkeypatch.setenv("RS_UMMA_SKETCH", "0")
+    X, _ = _data(3000, 200, 1.5, 12, torch.bfloat16)
+    Y = rs.rs_range_sketch(rsctx, cuda_rows(X), 24, 2000).cpu().double().numpy()
+    ref = osk.range_sketch(X.double().numpy(), 24, 2000)
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=3e-5 * np.abs(ref).max())

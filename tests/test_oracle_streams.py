@@ -125,3 +125,18 @@ def test_gaussian_column_subset_equals_the_full_matrix_columns():
     full = st.gaussian(99, 37, 11, row0=5)
     cols = [10, 0, 3, 4, 7]
     np.testing.assert_array_equal(st.gaussian_columns(99, 37, cols, row0=5), full[:, cols])
+
+
+def test_round_bf16_matches_the_bit_level_rounding():
+    """Nearest-even rounding to 8 significant bits, checked against the float32 bit manipulation
+    (add 0x7FFF plus the lowest kept bit, clear the low 16 bits) on float32 inputs, ties included."""
+    from oracle import streams as st
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.standard_normal(20000), rng.standard_normal(20000) * 1e3]).astype(np.float32)
+    m = np.arange(0, 128, dtype=np.uint32)
+    ties = ((np.uint32(127 + 3) << 23) | (m << 16) | 0x8000).view(np.float32)      # exact halfway points
+    x = np.concatenate([x, ties, -ties])
+    b = x.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    ref = b.astype(np.uint32).view(np.float32).astype(np.float64)
+    np.testing.assert_array_equal(st.round_bf16(x.astype(np.float64)), ref)
