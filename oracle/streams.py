@@ -90,6 +90,18 @@ def round_bf16(x):
     return np.ldexp(np.rint(m * 256.0) / 256.0, e)
 
 
+def bf16_rounding_ties(x, margin=2.0 ** -20):
+    """(mask, ulp): entries whose float64 value lies within ``margin`` |x| of a bfloat16 rounding
+    midpoint, where a float computation of the same value (a few float ulps away) may round to the
+    neighbouring bfloat16 value, and the bfloat16 spacing at x (the size of that disagreement)."""
+    x = np.asarray(x, np.float64)
+    m, e = np.frexp(x)
+    frac = np.abs(m) * 256.0
+    dist = np.abs(frac - np.floor(frac) - 0.5)          # distance to the midpoint, in ulps
+    ulp = np.ldexp(1.0, e - 8)
+    return dist * ulp <= margin * np.abs(x), ulp
+
+
 def gaussian_columns(seed, rows, cols, row0=0, bf16=False):
     """Columns ``cols`` (any subset, any order) of the same Gaussian matrix as ``gaussian`` (entries
     rounded by ``round_bf16`` when ``bf16``):

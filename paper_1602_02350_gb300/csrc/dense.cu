@@ -1145,6 +1145,29 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
   return RS_OK;
 }
 
+// E = S - I (k x k, double)
+__global__ void minus_identity_kernel(const double* __restrict__ S, int k, double* __restrict__ E) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
+    E[e] = S[e] - (e / k == e % k ? 1.0 : 0.0);
+}
+// T = I - E / 2 + 3 E^2 / 8: the inverse square root of S = I + E to O(|E|^3)
+__global__ void inv_sqrt_series_kernel(const double* __restrict__ E, const double* __restrict__ E2, int k,
+                                       double* __restrict__ T) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
+    T[e] = (e / k == e % k ? 1.0 : 0.0) - 0.5 * E[e] + 0.375 * E2[e];
+}
+// G <- (G + G^T) / 2
+__global__ void symmetrize_kernel(double* G, int k) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e / k, j = e % k;
+    if (i < j) {
+      const double v = 0.5 * (G[i * k + j] + G[j * k + i]);
+      G[i * k + j] = v;
+      G[j * k + i] = v;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------- Alg. 2 pieces
 
 template <typename T>
@@ -1236,8 +1259,36 @@ static int ritz_t(rs_ctx* ctx, const rs_matrix* X, const T* Q, int64_t kq, int64
   else if (rc_b != RS_OK)
     return rc_b;
   RS_TRY(launch_gram<T>(ctx, n, kq, kq, B, kq, B, kq, 1.0 / (double)n, G));
-  RS_TRY(run_sym_eig(ctx, G, kq, sizeof(T) == 8 ? RS_F64 : RS_F32, ev, Wd));
-  RS_TRY(to_T<T>(ctx, Wd, kq * kq, Wt));
+  if constexpr (sizeof(T) == 4) {
+    // Q in float is orthonormal only to the rounding of its last Cholesky-QR factorisation, S = Q^T Q =
+    // I + E with |E| ~ k 2^-24, and an unaccounted E would move the smallest Ritz values by about
+    // |E| sigma_1^2.  Rayleigh-Ritz is therefore taken in the metric of the basis as stored: with
+    // T = S^{-1/2} (series to O(|E|^3), all in double) the Ritz pairs of C on span(Q) are the eigenpairs
+    // of T G T, and V = Q T W.
+    double* Sd = static_cast<double*>(rs_scratch(ctx, SCR_RITZ, (size_t)5 * kq * kq * sizeof(double)));
+    if (!Sd) return RS_ENOMEM;
+    double* Ed = Sd + kq * kq;
+    double* E2 = Ed + kq * kq;
+    double* Td = E2 + kq * kq;
+    double* Hd = Td + kq * kq;
+    const unsigned sb = (unsigned)std::min<int64_t>((kq * kq + 255) / 256, 1024);
+    RS_TRY(launch_gram<T>(ctx, d, kq, kq, Q, kq, Q, kq, 1.0, Sd));
+    minus_identity_kernel<<<sb, 256, 0, ctx->stream>>>(Sd, (int)kq, Ed);
+    RS_LAUNCH_CHECK(ctx);
+    RS_TRY(launch_gemm<double>(ctx, kq, kq, kq, 1.0, Ed, kq, 1, Ed, kq, 1, 0.0, nullptr, 0, E2, kq, nullptr));
+    inv_sqrt_series_kernel<<<sb, 256, 0, ctx->stream>>>(Ed, E2, (int)kq, Td);
+    RS_LAUNCH_CHECK(ctx);
+    RS_TRY(launch_gemm<double>(ctx, kq, kq, kq, 1.0, G, kq, 1, Td, kq, 1, 0.0, nullptr, 0, Hd, kq, nullptr));   // G T
+    RS_TRY(launch_gemm<double>(ctx, kq, kq, kq, 1.0, Td, kq, 1, Hd, kq, 1, 0.0, nullptr, 0, G, kq, nullptr));   // T G T
+    symmetrize_kernel<<<sb, 256, 0, ctx->stream>>>(G, (int)kq);
+    RS_LAUNCH_CHECK(ctx);
+    RS_TRY(run_sym_eig(ctx, G, kq, RS_F32, ev, Wd));
+    RS_TRY(launch_gemm<double>(ctx, kq, kq, kq, 1.0, Td, kq, 1, Wd, kq, 1, 0.0, nullptr, 0, Hd, kq, nullptr));  // T W
+    RS_TRY(to_T<T>(ctx, Hd, kq * kq, Wt));
+  } else {
+    RS_TRY(run_sym_eig(ctx, G, kq, RS_F64, ev, Wd));
+    RS_TRY(to_T<T>(ctx, Wd, kq * kq, Wt));
+  }
   // V = Q W[:, :k]
   RS_TRY(launch_gemm<T>(ctx, d, k, kq, 1.0, Q, kq, 1, Wt, kq, 1, 0.0, nullptr, 0, V, k, nullptr));
   RS_CUDA_TRY(cudaMemcpyAsync(sigma2, ev, k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));

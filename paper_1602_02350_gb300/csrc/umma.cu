@@ -657,25 +657,29 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
 
 // XP = 1: bfloat16 X tiles; XP = 3: float X given as its three bfloat16 parts (rows a n .. a n + n - 1
 // of the parts' map), summed in float in the epilogue (K chunks: KC = 1 only, two ring entries).
-template <int KC, int XP = 1> __host__ __device__ constexpr int resid_ring() {
+// NP = 3: P and V in three bfloat16 parts, six products (about 2^-24 relative); NP = 2 (k up to 256,
+// where three parts of P no longer fit beside the ring): two parts each and the three products with
+// a + b <= 1, about 2^-16 relative to |P| |V|^T, below half an ulp of the bfloat16 result for the
+// data the components are formed from (|P V^T| within about 2^7 of |Z|).
+template <int KC, int XP = 1, int NP = 3> __host__ __device__ constexpr int resid_ring() {
   return XP == 3 ? 2 : (KC == 1 ? 4 : 3);
 }
-template <int KC, int XP = 1>
+template <int KC, int XP = 1, int NP = 3>
 constexpr size_t resid_smem_bytes() {
-  return (size_t)3 * KC * RT_A_TILE + (size_t)resid_ring<KC, XP>() * 3 * RT_B_TILE + 2 * (size_t)XP * RT_X_TILE +
-         1024;
+  return (size_t)NP * KC * RT_A_TILE + (size_t)resid_ring<KC, XP, NP>() * NP * RT_B_TILE +
+         2 * (size_t)XP * RT_X_TILE + 1024;
 }
 
-template <int KC, int XP = 1>
+template <int KC, int XP = 1, int NP = 3>
 __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constant__ CUtensorMap tmA,
                                                             const __grid_constant__ CUtensorMap tmB,
                                                             const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmZ, int64_t d,
                                                             int64_t np, int64_t dp, int64_t n_rows,
                                                             float* __restrict__ rowsq, int* status) {
-  constexpr int NB = resid_ring<KC, XP>();
-  constexpr uint32_t A_BYTES = 3 * KC * RT_A_TILE;
-  constexpr uint32_t B_ENTRY = 3 * RT_B_TILE;   // the three V parts of one K chunk
+  constexpr int NB = resid_ring<KC, XP, NP>();
+  constexpr uint32_t A_BYTES = NP * KC * RT_A_TILE;
+  constexpr uint32_t B_ENTRY = NP * RT_B_TILE;   // the NP V parts of one K chunk
   extern __shared__ unsigned char rt_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(rt_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* As = base;
@@ -714,7 +718,7 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
   if (warp == 0) {
     if (lane == 0) {   // producer
       mbar_expect_tx_cta(&a_full, A_BYTES);
-      for (int pa = 0; pa < 3; ++pa)
+      for (int pa = 0; pa < NP; ++pa)
         for (int kc = 0; kc < KC; ++kc)
           tma_load_2d(As + (pa * KC + kc) * RT_A_TILE, &tmA, kc * 64, (int)(pa * np) + row0, &a_full);
       for (int t = 0; t < ntiles; ++t) {
@@ -723,7 +727,7 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
           if (u >= 1 && !mbar_wait_bounded(&b_empty[e], (uint32_t)((u - 1) & 1), kUmmaWait))
             atomicOr(status, STATUS_TIMEOUT);
           mbar_expect_tx_cta(&b_full[e], B_ENTRY);
-          for (int pb = 0; pb < 3; ++pb)
+          for (int pb = 0; pb < NP; ++pb)
             tma_load_2d(Bs + e * B_ENTRY + pb * RT_B_TILE, &tmB, kc * 64, (int)(pb * dp) + t * RT_COLS, &b_full[e]);
         }
         const int sx = t & 1, ux = t >> 1;
@@ -748,10 +752,12 @@ __global__ void __launch_bounds__(192, 1) umma_resid_kernel(const __grid_constan
           if (!mbar_wait_bounded(&b_full[e], (uint32_t)(u & 1), kUmmaWait)) atomicOr(status, STATUS_TIMEOUT);
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t sbb = cta_smem_addr(Bs + e * B_ENTRY);
+          constexpr int NPROD = NP == 3 ? 6 : 3;
 #pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const int pa = q < 3 ? 0 : (q < 5 ? 1 : 2);      // (0,0) (0,1) (0,2) (1,0) (1,1) (2,0)
-            const int pb = q < 3 ? q : (q < 5 ? q - 3 : 0);
+          for (int q = 0; q < NPROD; ++q) {
+            // NP = 3: (0,0) (0,1) (0,2) (1,0) (1,1) (2,0); NP = 2: (0,0) (0,1) (1,0)
+            const int pa = NP == 3 ? (q < 3 ? 0 : (q < 5 ? 1 : 2)) : (q < 2 ? 0 : 1);
+            const int pb = NP == 3 ? (q < 3 ? q : (q < 5 ? q - 3 : 0)) : (q < 2 ? q : 0);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t da = smem_desc_sw128(sa + (pa * KC + kc) * RT_A_TILE + kk * 32);
@@ -985,8 +991,8 @@ int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, 
   const char* env = std::getenv("RS_UMMA_RESID");
   if (env && env[0] == '0') return RS_EUNSUPPORTED;
   const int64_t n = X->n, d = X->d;
-  if (k < 1 || k > 128 || n < 1 || d < 1 || n > 0x7FFFFF00LL / 3 || d > 0x7FFFFF00LL / 3) return RS_EUNSUPPORTED;
-  const int kp = k <= 64 ? 64 : 128;
+  if (k < 1 || k > 256 || n < 1 || d < 1 || n > 0x7FFFFF00LL / 3 || d > 0x7FFFFF00LL / 3) return RS_EUNSUPPORTED;
+  const int kp = k <= 64 ? 64 : (k <= 128 ? 128 : 256);
   // float X: only with the three bfloat16 parts of this X formed earlier in the same call (the
   // tensor-core X V product leaves them in SCR_XPART), and k <= 64
   const bool f32 = X->dtype == RS_F32;
@@ -1018,17 +1024,18 @@ int umma_resid(rs_ctx* ctx, const rs_matrix* X, const float* P, const float* V, 
   RS_TRY(make_map(&mZ, Z->data, d, n, Z->ld, RT_ROWS));
   RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   const unsigned grid = (unsigned)(np / RT_ROWS);
-#define RS_RESID(KC_, XP_)                                                                                    \
+#define RS_RESID(KC_, XP_, NP_)                                                                               \
   do {                                                                                                        \
-    constexpr size_t shm = resid_smem_bytes<KC_, XP_>();                                                      \
-    RS_CUDA_TRY(cudaFuncSetAttribute(umma_resid_kernel<KC_, XP_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)shm));                                                              \
-    umma_resid_kernel<KC_, XP_><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, n, rowsq,         \
-                                                                  ctx->d_status);                             \
+    constexpr size_t shm = resid_smem_bytes<KC_, XP_, NP_>();                                                 \
+    RS_CUDA_TRY(cudaFuncSetAttribute(umma_resid_kernel<KC_, XP_, NP_>,                                        \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));                 \
+    umma_resid_kernel<KC_, XP_, NP_><<<grid, 192, shm, ctx->stream>>>(mA, mB, mX, mZ, d, np, dp, n, rowsq,    \
+                                                                       ctx->d_status);                        \
   } while (0)
-  if (f32) RS_RESID(1, 3);
-  else if (kp == 64) RS_RESID(1, 1);
-  else RS_RESID(2, 1);
+  if (f32) RS_RESID(1, 3, 3);
+  else if (kp == 64) RS_RESID(1, 1, 3);
+  else if (kp == 128) RS_RESID(2, 1, 3);
+  else RS_RESID(4, 1, 2);
 #undef RS_RESID
   RS_LAUNCH_CHECK(ctx);
   int st = 0;

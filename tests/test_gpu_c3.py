@@ -6,8 +6,9 @@ properties that hold at any size (the Rayleigh-Ritz identity, interlacing).  Plu
 d = 4096 and k = 256 against the oracle's full computation on row subsets.
 
 Tolerances (float arithmetic, BF16 storage):
-  * range sketch: a float sum over n = 2^20 products with Gaussian entries within a few float ulps of
-    the oracle's double values; error <= 1e-5 of the largest entry.
+  * range sketch: bfloat16 test matrix on both sides, products exact in FP32, so the FP32 accumulation
+    over the rows (3e-5 of the largest entry) plus, for the entries whose float and double Box-Muller
+    values straddle a bfloat16 rounding midpoint, one bfloat16 ulp times |x|.
   * Ritz pairs: Q comes from Cholesky-QR whose second factorisation runs in float, so Q^T Q = I + E
     with |E| ~ k u (u = 2^-24; k u = 1.5e-5 at k = 256), and V = Q W inherits it: V^T V, the Ritz
     values and V^T C V are compared with atol 4 k u (times sigma_1^2 for the values), not a relative
@@ -15,7 +16,8 @@ Tolerances (float arithmetic, BF16 storage):
   * components: each entry is formed in float and rounded once to BF16, so |z_c - z_oracle| <=
     2^-8 |z_c| (half an ulp) plus the FP32 accumulation error of P = X V (d = 4096 terms) and of
     P (I - D') V^T (k terms), bounded per entry by 16 u sum_j |v_cj| (1 - D'_j) sum_c' |x_c'| |v_c'j|
-    (16 ~ sqrt(d) / 4: random-sign accumulation, well below the worst-case d u).
+    (16 ~ sqrt(d) / 4: random-sign accumulation, well below the worst-case d u); for k > 128 the
+    product keeps two bfloat16 parts of P and V, which adds at most 3 2^-18 of the same magnitude.
   * refined BF16 / FP8 solves: relative suboptimality <= 1e-4 (the tolerance stated for BF16 with
     refinement); whether 1e-6 is reached is reported.
 """
@@ -72,9 +74,14 @@ def test_c3_range_sketch_sampled_columns_match_oracle(rsctx, c3):
     Y = rs.rs_range_sketch(rsctx, Xb, cfg.k, cfg.seed_sketch).double().cpu().numpy()
     cols = [0, 1, 2, 3, 129, 254, 255]
     ref = np.zeros((cfg.d, len(cols)))
+    allow = np.zeros((cfg.d, len(cols)))
     for r0, (Xc,) in zip(range(0, cfg.n, CHUNK), _chunks(Xb)):
-        ref += Xc.T @ streams.gaussian_columns(cfg.seed_sketch, Xc.shape[0], cols, row0=r0, bf16=True)
-    np.testing.assert_allclose(Y[:, cols], ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+        Pi = streams.gaussian_columns(cfg.seed_sketch, Xc.shape[0], cols, row0=r0)
+        ref += Xc.T @ streams.round_bf16(Pi)
+        tie, ulp = streams.bf16_rounding_ties(Pi)
+        allow += np.abs(Xc).T @ (tie * ulp)        # entries that may round the other way
+    err = np.abs(Y[:, cols] - ref)
+    assert np.all(err <= 3e-5 * np.abs(ref).max() + allow), np.max(err - allow)
 
 
 def test_c3_ritz_pairs_satisfy_rayleigh_ritz_and_interlacing(c3, c3_normal, c3_sketch):
@@ -113,7 +120,10 @@ def test_c3_components_sampled_rows_match_oracle(rsctx, c3, c3_sketch):
     a = 1.0 - np.sqrt((s2d[-1] + lam) / (s2d + lam))                      # 1 - D'_j
     mag = np.concatenate([(np.abs(Xr) @ np.abs(Vd)) * a @ np.abs(Vd).T,   # sum_j |v_cj| a_j sum |x||v_j|
                           np.abs(Vd[regs]) * a @ np.abs(Vd).T])
-    bound = 2.0 ** -8 * np.abs(ref) + 16 * 2.0 ** -24 * mag
+    # k > 128: P and V enter the tensor-core product in two bfloat16 parts each (three products), whose
+    # dropped terms are at most 3 2^-18 |P||V|^T per entry; the FP32 accumulation adds 16 u as above
+    split = 3 * 2.0 ** -18 if cfg.k > 128 else 0.0
+    bound = 2.0 ** -8 * np.abs(ref) + (split + 16 * 2.0 ** -24) * mag
     assert np.all(np.abs(zg - ref) <= bound), float(np.max(np.abs(zg - ref) - bound))
     # smoothness of the stored rows: gamma_i ||z_i||^2 with gamma = (n+d)/n or lam (n+d)
     gam = np.concatenate([np.full(rows.size, (n + d) / n), np.full(regs.size, lam * (n + d))])

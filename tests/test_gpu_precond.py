@@ -47,3 +47,27 @@ def test_map_output_matches_oracle(rsctx, dtype, tol):
     w = rs.rs_map_output(rsctx, V.cuda(), torch.from_numpy(s2).cuda(), 1e-3, wt.cuda()).cpu().double().numpy()
     ref = precond.m_matrix(V.double().numpy(), s2, 1e-3) @ wt.double().numpy()
     np.testing.assert_allclose(w, ref, rtol=0, atol=tol * 10 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n,d,k", [(3000, 520, 200), (1000, 300, 256), (4100, 1024, 129)])
+def test_bf16_components_rank_above_128(rsctx, n, d, k):
+    """BF16 data with k in (128, 256]: Z = X - P V^T on tensor cores with two bfloat16 parts of P and V.
+    Every entry is within half a bfloat16 ulp of the oracle's M x_i plus the split's dropped terms
+    (3 2^-18 |P||V|^T) and the FP32 accumulation (16 u |P||V|^T)."""
+    from oracle import precond
+    X, _, _ = synth.problem(n, d, np.arange(1, d + 1) ** -1.2, 0.1, n + k)
+    Xb = X.to(torch.bfloat16)
+    V = synth.random_orthonormal(d, k, k + 1)
+    s2 = synth.random_sigma2(k, k + 2)
+    lam = 1e-4
+    Z, beta, _ = rs.rs_precondition(rsctx, cuda_rows(Xb), torch.from_numpy(V).float().cuda(),
+                                    torch.from_numpy(s2).cuda(), lam)
+    Vf = torch.from_numpy(V).float().double().numpy()
+    M = precond.m_matrix(Vf, s2, lam)
+    Xd = Xb.double().numpy()
+    ref = Xd @ M
+    a = 1.0 - np.sqrt((s2[-1] + lam) / (s2 + lam))
+    mag = (np.abs(Xd) @ np.abs(Vf)) * a @ np.abs(Vf).T
+    zg = Z[:n].double().cpu().numpy()
+    bound = 2.0 ** -8 * np.abs(ref) + (3 * 2.0 ** -18 + 16 * 2.0 ** -24) * mag
+    assert np.all(np.abs(zg - ref) <= bound), float(np.max(np.abs(zg - ref) - bound))

@@ -140,3 +140,16 @@ def test_round_bf16_matches_the_bit_level_rounding():
     b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
     ref = b.astype(np.uint32).view(np.float32).astype(np.float64)
     np.testing.assert_array_equal(st.round_bf16(x.astype(np.float64)), ref)
+
+
+def test_bf16_rounding_ties_flags_exactly_the_near_midpoint_entries():
+    from oracle import streams as st
+    ulp = 2.0 ** -7                                   # bfloat16 spacing in [1, 2)
+    mid = 1.0 + 37.5 * ulp                            # a rounding midpoint
+    x = np.array([mid, mid * (1 + 2 ** -22), mid * (1 + 2 ** -18), 1.0 + 37 * ulp, -mid])
+    tie, step = st.bf16_rounding_ties(x)
+    assert tie.tolist() == [True, True, False, False, True]
+    np.testing.assert_array_equal(step, np.full(5, ulp))
+    # values a margin away from the midpoint round to the same neighbour on both sides of the margin
+    lo, hi = mid * (1 - 2 ** -21), mid * (1 + 2 ** -21)
+    assert st.round_bf16(np.array([lo]))[0] != st.round_bf16(np.array([hi]))[0]
