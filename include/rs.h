@@ -264,6 +264,35 @@ int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const voi
                   const double* sigma2, int64_t k, const rs_svrg_params* p, const void* w0,
                   void* w_out, rs_history* hist, double* eta_used, int64_t* m_used);
 
+/* Accelerated SVRG (the accelerated variant Thm 1 refers to; the paper names it in Sec. 1 without
+ * fixing a scheme): Catalyst (Lin, Mairal and Harchaoui, NIPS 2015) around Alg. 1 on the same
+ * components.  Outer iteration t = 1..outer minimises the proximal problem
+ *   L(w) + (kappa/2) ||w - c_{t-1}||^2
+ * with p->epochs epochs of Alg. 1 (as rs_svrg_solve with p; epoch numbers continue from p->epoch0
+ * across the outer iterations, so every epoch draws its own index stream) warm-started at the
+ * previous outer iterate.  In the component form only the regulariser rows change: their weight
+ * becomes (lambda + kappa)(n + d) and their label kappa c_j / (lambda + kappa), i.e. every snapshot
+ * gradient is shifted by -kappa M c and the smoothness constants of those rows scale by
+ * (lambda + kappa) / lambda (eta and the importance weights follow).  Then
+ *   alpha_t^2 = (1 - alpha_t) alpha_{t-1}^2 + q alpha_t,  q = lambda / (lambda + kappa),  alpha_0 = sqrt(q),
+ *   c_t = x_t + alpha_{t-1} (1 - alpha_{t-1}) / (alpha_{t-1}^2 + alpha_t) (x_t - x_{t-1}),
+ * with x_t = M w~_t in original coordinates; w_out = x_outer.
+ * cp->kappa <= 0 selects kappa = max(0, beta^ / (n + d) - lambda) (beta^ the mean smoothness of the
+ * original components; Catalyst's choice for SVRG).  beta: smoothness constants for lambda as
+ * rs_precondition writes them (nullable except for FP8 components: then recomputed from Z).
+ * hist (nullable): capacity >= outer; snapshots receives x_t, epoch_ms the cumulative time at the end
+ * of each outer iteration.  kappa_used (host, nullable).  Synchronises.  Errors as rs_svrg_solve;
+ * RS_EINVAL for outer < 1 or epochs < 1. */
+typedef struct {
+  double kappa;        /* proximal weight (<= 0: the default above) */
+  int32_t outer;       /* outer iterations */
+  int32_t reserved;
+} rs_catalyst_params;
+
+int rs_catalyst_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const void* y, const void* beta,
+                      const void* V, const double* sigma2, int64_t k, const rs_svrg_params* p,
+                      const rs_catalyst_params* cp, void* w_out, rs_history* hist, double* kappa_used);
+
 /* Alg. 3 end to end: sketch (Alg. 2), preconditioner and transformed components (Eq. (11),
  * Sec. 5.1), SVRG (Alg. 1), w_out = M w~ (Eq. (4)).  X may be RS_F64, RS_F32 or RS_BF16 (the
  * components are stored in the same type; with RS_BF16 set p->refine).  X->data, y and w_out may be HOST

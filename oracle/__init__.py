@@ -22,6 +22,7 @@ step by step:
                   n+d decomposition of Sec. 5.1, smoothness constants of Alg. 3.
 * ``svrg``      - Alg. 1 (SVRG with importance sampling) on the n+d components.
 * ``pipeline``  - Alg. 3 end to end.
+* ``catalyst``  - accelerated SVRG (Catalyst) around Alg. 1 on the same components (Sec. 1, Thm 1).
 * ``proposal``  - the theory-set parameters of Sec. 3 / Thm 1 and the parameter-proposal
                   network (forward, backpropagation, Adam) that the library trains.
 
@@ -31,4 +32,4 @@ inputs, library routines).  Functions without such a pin say
 "parity unpinned" in their docstring.
 """
 
-from . import ridge, streams, sketch, precond, svrg, pipeline, proposal  # noqa: F401
+from . import ridge, streams, sketch, precond, svrg, pipeline, proposal, catalyst  # noqa: F401

@@ -77,6 +77,10 @@ class BatchParams(ctypes.Structure):
                 ("sketch_seed", ctypes.c_uint64)]
 
 
+class CatalystParams(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("outer", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class History(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int32), ("epochs_run", ctypes.c_int32), ("snapshots", ctypes.c_void_p),
                 ("mu_norm2", ctypes.POINTER(ctypes.c_double)), ("epoch_ms", ctypes.POINTER(ctypes.c_float))]
@@ -120,6 +124,9 @@ _SIGS = {
     "rs_objective": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_double)],
     "rs_trace_c": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(ctypes.c_double)],
     "rs_speedup_ratio": [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P],
+    "rs_catalyst_solve": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(Matrix), _P, _P, _P, _P, ctypes.c_int64,
+                          ctypes.POINTER(SvrgParams), ctypes.POINTER(CatalystParams), _P, ctypes.POINTER(History),
+                          ctypes.POINTER(ctypes.c_double)],
     "rs_solve_batched": [_P, ctypes.POINTER(Problem), ctypes.c_int32, ctypes.POINTER(Chain), ctypes.c_int32,
                          ctypes.POINTER(BatchParams), ctypes.POINTER(ctypes.c_float)],
     "rs_mlp_forward": [_P, _P, _P, ctypes.c_int64, _P],
@@ -425,6 +432,25 @@ def rs_svrg_solve(ctx, Z, y, V, sigma2, lam, epochs, seed, beta=None, w0=None, e
                                ctypes.byref(mu_)))
     info = {"eta": eu.value, "m": mu_.value, "mu_norm2": list(mu2)[:epochs], "epoch_ms": list(ems)[:epochs],
             "snapshots": snaps[:epochs] if snaps is not None else None}
+    return w, info
+
+
+def rs_catalyst_solve(ctx, Z, y, V, sigma2, lam, outer, epochs, seed, kappa=0.0, beta=None, eta_mult=1.0, m=0,
+                      epoch0=0, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False, X=None, refine=False):
+    """Accelerated SVRG (Catalyst) on the components Z: ``outer`` proximal problems of ``epochs`` epochs
+    each.  Returns (w, info) with info holding kappa, the outer iterates (snapshots) and their times."""
+    d = Z.shape[1]
+    w = ctx._empty(d, dtype=V.dtype)
+    p = _svrg_params(lam, epochs, seed, 0.0, eta_mult, m, epoch0, sampling, average, refine)
+    cp = CatalystParams(float(kappa), int(outer), 0)
+    MX = matrix(X) if X is not None else None
+    h, _, ems, snaps = _history(ctx, outer, d, V.dtype, snapshots)
+    ku = ctypes.c_double(0)
+    M = matrix(Z)
+    _check(lib().rs_catalyst_solve(ctx.h, ctypes.byref(M), ctypes.byref(MX) if MX is not None else None, _ptr(y),
+                                   _ptr(beta), _ptr(V.contiguous()), _ptr(sigma2), V.shape[1], ctypes.byref(p),
+                                   ctypes.byref(cp), _ptr(w), ctypes.byref(h), ctypes.byref(ku)))
+    info = {"kappa": ku.value, "epoch_ms": list(ems)[:outer], "snapshots": snaps[:outer] if snaps is not None else None}
     return w, info
 
 

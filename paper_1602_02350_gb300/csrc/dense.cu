@@ -1023,6 +1023,7 @@ RS_GEMM_INST(double, double, double, double)
 RS_GEMM_INST(float, __nv_bfloat16, float, float)
 RS_GEMM_INST(float, float, __nv_bfloat16, __nv_bfloat16)
 RS_GEMM_INST(float, float, __nv_bfloat16, float)
+RS_GEMM_INST(double, float, float, float)
 #undef RS_GEMM_INST
 
 template <typename TA, typename TB>
@@ -1193,6 +1194,21 @@ static int orthonormalize_t(rs_ctx* ctx, const T* Y, int64_t d, int64_t k, T* Q)
     // the first factorisation sees cond(Y)^2 and runs in double; the second one factors the Gram
     // matrix of an already orthonormal-to-rounding basis (condition ~1) in the storage type
     // (double work is slow on this GPU)
+    if (pass == 0 && sizeof(T) == 4) {
+      // float Y: Y L^{-T} is also formed in double.  A float product would perturb span(Y) by about
+      // 2^-24 cond(Y)^2 (its rounding relative to |Y| |L^{-1}|, divided by the smallest singular value
+      // of Y), which for graded spectra scrambles the weakest directions of the sketch and with them
+      // the smallest Ritz values; in double the perturbation is 2^-53 cond(Y)^2.
+      double* Ld = static_cast<double*>(rs_scratch(ctx, SCR_LINVD, k * k * sizeof(double)));
+      if (!Ld) return RS_ENOMEM;
+      RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)shm));
+      chol_inv_kernel<double, double><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Ld, ctx->d_status);
+      RS_LAUNCH_CHECK(ctx);
+      RS_TRY(launch_gemm<double, T, T, T>(ctx, d, k, k, 1.0, src, k, 1, Ld, 1, k, 0.0, nullptr, 0, dst, k, nullptr));
+      src = dst;
+      continue;
+    }
     if (pass == 0)
       chol_inv_kernel<T, double><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Linv, ctx->d_status);
     else

@@ -676,16 +676,34 @@ static int check_components(const rs_matrix* Z, int64_t n, bool allow_fp8 = fals
   return RS_OK;
 }
 
+// Options of the proximal subproblems of accelerated SVRG (rs_catalyst_solve): the output map uses
+// the preconditioner's lambda (lam_pre) while p->lambda is the subproblem's regularisation; mc
+// (nullable) is subtracted from every snapshot gradient (kappa M c for the proximal centre c); the
+// final preconditioned iterate is copied to wt_out (nullable).
+template <typename T>
+struct CenterOpt {
+  double lam_pre;
+  const T* mc;
+  T* wt_out;
+};
+
+template <typename T>
+__global__ void sub_vec_kernel(T* v, const T* u, int64_t d) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x)
+    v[c] -= u[c];
+}
+
 // Alg. 1 epochs on the components Z (storage S, compute T).  With p->refine the full gradient
 // is formed on the stored data X instead (mu = M (X^T (X M w - y)/n + lam M w), storage SX), so
 // that the fixed point is exact for the data as stored even when Z is a rounded copy.
 template <typename S, typename T, typename SX>
 static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const T* y, const T* beta_in,
                         const T* V, const double* sigma2, int64_t k, const rs_svrg_params* p, const T* w0, T* w_out,
-                        rs_history* hist, double* eta_used, int64_t* m_used) {
+                        rs_history* hist, double* eta_used, int64_t* m_used, const CenterOpt<T>* opt = nullptr) {
   const int64_t N = Z->n, d = Z->d, n = N - d;
   const int32_t dt = sizeof(T) == 8 ? RS_F64 : RS_F32;
   const double lam = p->lambda;
+  const double lam_m = opt ? opt->lam_pre : lam;   // lambda of the preconditioner M (output maps)
   T* beta = const_cast<T*>(beta_in);
   if constexpr (IsFp8<S>::value) {
     if (!beta || !(p->refine && X))
@@ -777,11 +795,11 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, con
     if (refine) {
       T* u = tmp;
       T* g = tmp + d;
-      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, u));                     // u = M w
+      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam_m, dt, wa, u));                   // u = M w
       RS_TRY(full_gradient_t<SX, T>(ctx, X, y, X->n, lam, u, g, nullptr));                   // X^T (X u - y) / n
       add_ridge_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(g, u, d, lam, g);     // + lam u
       RS_LAUNCH_CHECK(ctx);
-      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, g, mu));                      // mu = M (...)
+      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam_m, dt, g, mu));                    // mu = M (...)
       if (want_norm) {
         norm2_kernel<T><<<1, 256, 0, ctx->stream>>>(mu, d, norms + s);
         RS_LAUNCH_CHECK(ctx);
@@ -789,6 +807,14 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, con
     } else {
       if constexpr (!IsFp8<S>::value)
         RS_TRY(full_gradient_t<S, T>(ctx, Z, y, n, lam, wa, mu, want_norm ? norms + s : nullptr));
+    }
+    if (opt && opt->mc) {   // proximal centre: mu -= kappa M c
+      sub_vec_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(mu, opt->mc, d);
+      RS_LAUNCH_CHECK(ctx);
+      if (want_norm) {
+        norm2_kernel<T><<<1, 256, 0, ctx->stream>>>(mu, d, norms + s);
+        RS_LAUNCH_CHECK(ctx);
+      }
     }
     RS_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, sd.ready[q], 0));
     RS_TRY(epoch_finish_t<S, T>(ctx, Z, set_idx(q), m, eta, set_rt(q), set_cv(q), wa, mu, p->average, wb));
@@ -800,10 +826,11 @@ static int svrg_solve_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, con
     }
     std::swap(wa, wb);
     if (hist && hist->snapshots && s < hist->capacity)
-      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, static_cast<T*>(hist->snapshots) + (int64_t)s * d));
+      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam_m, dt, wa, static_cast<T*>(hist->snapshots) + (int64_t)s * d));
     if (!ev.empty()) RS_CUDA_TRY(cudaEventRecord(ev[s + 1], ctx->stream));
   }
-  RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, wa, w_out));
+  RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam_m, dt, wa, w_out));
+  if (opt && opt->wt_out) RS_CUDA_TRY(cudaMemcpyAsync(opt->wt_out, wa, d * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
   // the status word was cleared by rs_sampling_weights above; epochs may have set the timeout bit
   finite_check_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(w_out, d, 1e30, ctx->d_status);
   RS_LAUNCH_CHECK(ctx);
@@ -1039,6 +1066,171 @@ int rs_svrg_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const voi
   return svrg_solve_t<float, float, float>(ctx, Z, X, static_cast<const float*>(y), static_cast<const float*>(beta),
                                            static_cast<const float*>(V), sigma2, k, p, static_cast<const float*>(w0),
                                            static_cast<float*>(w_out), hist, eta_used, m_used);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- accelerated SVRG (Catalyst)
+namespace {
+
+// beta1[i] = beta0[i] for i < n, beta0[i] f for the regulariser rows (their weight lam -> lam + kappa)
+template <typename T>
+__global__ void scale_tail_kernel(const T* b0, T* b1, int64_t N, int64_t n, double f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    b1[i] = i < n ? b0[i] : (T)((double)b0[i] * f);
+}
+// c = x + b (x - x_prev); x_prev = x; v *= s for the centre term
+template <typename T>
+__global__ void extrapolate_kernel(const T* x, T* x_prev, T* c, int64_t d, double b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
+    const T xi = x[i];
+    c[i] = xi + (T)b * (xi - x_prev[i]);
+    x_prev[i] = xi;
+  }
+}
+template <typename T>
+__global__ void scale_vec_kernel(T* v, int64_t d, double s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (T)((double)v[i] * s);
+}
+
+// Catalyst (Lin, Mairal, Harchaoui 2015) around the epochs of Alg. 1: outer iteration t solves the
+// proximal problem L(w) + kappa/2 ||w - c_{t-1}||^2 (regularisation lam + kappa; in the component
+// form only the regulariser rows change: weight (lam + kappa)(n + d), label kappa c_j / (lam + kappa),
+// which shifts every snapshot gradient by -kappa M c) with p->epochs epochs warm-started at the
+// previous outer iterate, then extrapolates c_t = x_t + b_t (x_t - x_{t-1}).
+template <typename S, typename T, typename SX>
+int catalyst_t(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const T* y, const T* beta_in, const T* V,
+               const double* sigma2, int64_t k, const rs_svrg_params* p, const rs_catalyst_params* cp, T* w_out,
+               rs_history* hist, double* kappa_used) {
+  const int64_t N = Z->n, d = Z->d, n = N - d;
+  const int32_t dt = sizeof(T) == 8 ? RS_F64 : RS_F32;
+  const double lam = p->lambda;
+  T* b0 = const_cast<T*>(beta_in);
+  if (!b0) {
+    if constexpr (IsFp8<S>::value) {
+      return rs_fail(RS_EINVAL, "rs_catalyst_solve: FP8 components need beta");
+    } else {
+      b0 = static_cast<T*>(rs_scratch(ctx, SCR_CATB, N * sizeof(T)));
+      if (!b0) return RS_ENOMEM;
+      row_beta_only_kernel<S, T><<<blocks_for(ctx, N * 32), 256, 0, ctx->stream>>>(static_cast<const S*>(Z->data), N,
+                                                                                    n, d, Z->ld, lam, b0);
+      RS_LAUNCH_CHECK(ctx);
+    }
+  }
+  double kappa = cp->kappa;
+  if (!(kappa > 0.0)) {   // the Catalyst choice for SVRG: kappa = L / N - mu with L the mean smoothness
+    double* sc = static_cast<double*>(rs_scratch(ctx, SCR_CATS, sizeof(double)));
+    if (!sc) return RS_ENOMEM;
+    mean_kernel<T><<<1, 1024, 0, ctx->stream>>>(b0, N, sc);
+    RS_LAUNCH_CHECK(ctx);
+    double bh = 0.0;
+    RS_CUDA_TRY(cudaMemcpyAsync(&bh, sc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    kappa = std::max(0.0, bh / (double)N - lam);
+  }
+  if (kappa_used) *kappa_used = kappa;
+  T* b1 = static_cast<T*>(rs_scratch(ctx, SCR_CATB2, N * sizeof(T)));
+  T* vec = static_cast<T*>(rs_scratch(ctx, SCR_CATV, 6 * d * sizeof(T)));
+  if (!b1 || !vec) return RS_ENOMEM;
+  T *wt = vec, *wt2 = vec + d, *x = vec + 2 * d, *xprev = vec + 3 * d, *c = vec + 4 * d, *mc = vec + 5 * d;
+  scale_tail_kernel<T><<<blocks_for(ctx, N), 256, 0, ctx->stream>>>(b0, b1, N, n, (lam + kappa) / lam);
+  RS_LAUNCH_CHECK(ctx);
+  RS_CUDA_TRY(cudaMemsetAsync(vec, 0, 6 * d * sizeof(T), ctx->stream));
+  const double q = lam / (lam + kappa);
+  double alpha = std::sqrt(q);
+  std::vector<cudaEvent_t> ev;
+  if (hist && hist->epoch_ms) {
+    ev.resize(cp->outer + 1);
+    for (auto& e : ev) RS_CUDA_TRY(cudaEventCreate(&e));
+    RS_CUDA_TRY(cudaEventRecord(ev[0], ctx->stream));
+  }
+  int rc = RS_OK;
+  for (int t = 0; t < cp->outer && rc == RS_OK; ++t) {
+    rs_svrg_params p2 = *p;
+    p2.lambda = lam + kappa;
+    p2.epoch0 = p->epoch0 + t * p->epochs;
+    const T* mcp = nullptr;
+    if (kappa > 0.0) {
+      RS_TRY(map_output_dispatch(ctx, V, sigma2, d, k, lam, dt, c, mc));   // M c
+      scale_vec_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(mc, d, kappa);
+      RS_LAUNCH_CHECK(ctx);
+      mcp = mc;
+    }
+    CenterOpt<T> opt{lam, mcp, wt2};
+    rc = svrg_solve_t<S, T, SX>(ctx, Z, X, y, b1, V, sigma2, k, &p2, t == 0 ? nullptr : wt, x, nullptr, nullptr,
+                                nullptr, &opt);
+    if (rc != RS_OK) break;
+    std::swap(wt, wt2);
+    const double a_prev = alpha;
+    const double bq = alpha * alpha - q;
+    alpha = 0.5 * (-bq + std::sqrt(bq * bq + 4.0 * a_prev * a_prev));
+    const double b = a_prev * (1.0 - a_prev) / (a_prev * a_prev + alpha);
+    extrapolate_kernel<T><<<blocks_for(ctx, d), 256, 0, ctx->stream>>>(x, xprev, c, d, b);
+    RS_LAUNCH_CHECK(ctx);
+    if (hist && hist->snapshots && t < hist->capacity)
+      RS_CUDA_TRY(cudaMemcpyAsync(static_cast<T*>(hist->snapshots) + (int64_t)t * d, x, d * sizeof(T),
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    if (!ev.empty()) RS_CUDA_TRY(cudaEventRecord(ev[t + 1], ctx->stream));
+  }
+  if (rc == RS_OK) RS_CUDA_TRY(cudaMemcpyAsync(w_out, x, d * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (hist) {
+    hist->epochs_run = cp->outer;
+    if (!ev.empty()) {
+      for (int t = 0; t < cp->outer && t < hist->capacity; ++t)
+        RS_CUDA_TRY(cudaEventElapsedTime(&hist->epoch_ms[t], ev[0], ev[t + 1]));
+      for (auto& e : ev) cudaEventDestroy(e);
+    }
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rs_catalyst_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const void* y, const void* beta,
+                      const void* V, const double* sigma2, int64_t k, const rs_svrg_params* p,
+                      const rs_catalyst_params* cp, void* w_out, rs_history* hist, double* kappa_used) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(Z && p && cp, "rs_catalyst_solve: null argument");
+  const int64_t n = Z->n - Z->d;
+  RS_TRY(check_components(Z, n, true));
+  RS_CHECK_ARG(y && V && sigma2 && w_out, "rs_catalyst_solve: null argument");
+  RS_CHECK_ARG(k >= 1 && k <= Z->d, "rs_catalyst_solve: k must be in [1, d]");
+  RS_CHECK_ARG(p->lambda > 0.0 && std::isfinite(cp->kappa), "rs_catalyst_solve: need lambda > 0 and a finite kappa");
+  RS_CHECK_ARG(cp->outer >= 1 && p->epochs >= 1 && p->epoch0 >= 0, "rs_catalyst_solve: need outer >= 1, epochs >= 1");
+  RS_CHECK_ARG(p->sampling == RS_SAMPLE_IMPORTANCE || p->sampling == RS_SAMPLE_UNIFORM, "rs_catalyst_solve: bad sampling");
+  if (p->refine) {
+    RS_CHECK_ARG(X != nullptr, "rs_catalyst_solve: refinement needs the stored data X");
+    RS_TRY(check_matrix(X, "rs_catalyst_solve X"));
+    RS_CHECK_ARG(X->n == n && X->d == Z->d, "rs_catalyst_solve: X must be n x d");
+    RS_CHECK_ARG(X->dtype == Z->dtype || (Z->dtype == RS_BF16 && X->dtype == RS_F32) ||
+                     (Z->dtype == RS_FP8E4M3 && (X->dtype == RS_F32 || X->dtype == RS_BF16)),
+                 "rs_catalyst_solve: X must be stored like Z (as for rs_svrg_solve)");
+  }
+  const float* yf = static_cast<const float*>(y);
+  const float* bf = static_cast<const float*>(beta);
+  const float* Vf = static_cast<const float*>(V);
+  float* wf = static_cast<float*>(w_out);
+  if (Z->dtype == RS_FP8E4M3) {
+    RS_CHECK_ARG(p->refine && X && beta, "rs_catalyst_solve: FP8 components need refine, X and beta");
+    if (X->dtype == RS_F32)
+      return catalyst_t<__nv_fp8_e4m3, float, float>(ctx, Z, X, yf, bf, Vf, sigma2, k, p, cp, wf, hist, kappa_used);
+    return catalyst_t<__nv_fp8_e4m3, float, __nv_bfloat16>(ctx, Z, X, yf, bf, Vf, sigma2, k, p, cp, wf, hist,
+                                                           kappa_used);
+  }
+  if (Z->dtype == RS_F64)
+    return catalyst_t<double, double, double>(ctx, Z, X, static_cast<const double*>(y), static_cast<const double*>(beta),
+                                              static_cast<const double*>(V), sigma2, k, p, cp,
+                                              static_cast<double*>(w_out), hist, kappa_used);
+  if (Z->dtype == RS_BF16 && p->refine && X->dtype == RS_F32)
+    return catalyst_t<__nv_bfloat16, float, float>(ctx, Z, X, yf, bf, Vf, sigma2, k, p, cp, wf, hist, kappa_used);
+  if (Z->dtype == RS_BF16)
+    return catalyst_t<__nv_bfloat16, float, __nv_bfloat16>(ctx, Z, X, yf, bf, Vf, sigma2, k, p, cp, wf, hist,
+                                                           kappa_used);
+  return catalyst_t<float, float, float>(ctx, Z, X, yf, bf, Vf, sigma2, k, p, cp, wf, hist, kappa_used);
 }
 
 int rs_solve(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp, const rs_svrg_params* p,
