@@ -444,6 +444,115 @@ def run_batched(args):
     ctx.close()
 
 
+def run_fig2(args):
+    """Sec. 6's synthetic comparison (Fig. 2 a, b) at n = 16384, d = 4096 (the paper's 4:1 shape at the
+    widest d the inner loop takes): singular values q^-1 and q^-2, unit-norm examples, lambda = 1e-8,
+    SVRG (k = 1, i.e. M = I) against sketched-preconditioned SVRG with k = 30, m = n, the step size
+    tuned per method over a grid (lowest suboptimality after the last epoch), 30 epochs.  Prints one
+    JSON line with the suboptimality L(w_t) - L* per epoch of each method next to the paper's values."""
+    import paper_1602_02350_gb300 as rs
+    from paper_1602_02350_gb300 import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ctx = rs.Context(int(os.environ.get("LOCAL_RANK", "0")), torch.cuda.current_stream())
+    n, d, lam, E = args.fig2_n, args.fig2_d, 1e-8, 30
+    grid = (0.25, 0.5, 1.0, 2.0, 4.0, 8.0)
+    # the paper's curves (Fig. 2 a, b: 5000 x 20000), epochs 1, 5, 10, 15, 20 where printed
+    paper = {1: {"SVRG": {1: 5.38e-2, 5: 2.63e-3, 10: 1.99e-3, 15: 1.74e-3, 20: 1.59e-3},
+                 "SCSVRG-k=30": {1: 7.32e-2, 5: 1.87e-3, 10: 9.48e-4, 15: 6.50e-4, 20: 4.86e-4}},
+             2: {"SVRG": {1: 6.13e-2, 5: 7.43e-5, 10: 4.74e-5, 15: 4.00e-5, 20: 3.61e-5},
+                 "SCSVRG-k=30": {1: 7.03e-2, 5: 4.69e-5, 10: 5.46e-6, 15: 1.08e-6, 20: 3.29e-7}}}
+    out = {}
+    for decay in (1, 2):
+        X, y64, _ = synth.spectrum_problem(n, d, decay, 0.1, 6000 + decay)
+        y = y64.float().contiguous()
+        ref = _Reference(X, y, lam)
+        res = {}
+        for name, k in (("SVRG", 1), ("SCSVRG-k=30", 30)):
+            V, s2 = rs.rs_sketch(ctx, X, k, 7000 + decay)
+            Z, beta, _ = rs.rs_precondition(ctx, X, V, s2, lam)
+            best = None
+            for em in grid:
+                try:
+                    _, info = rs.rs_svrg_solve(ctx, Z, y, V, s2, lam, E, 8000 + decay, beta=beta, m=n, eta_mult=em,
+                                               snapshots=True)
+                except rs.RsError:
+                    continue                           # this step size diverged
+                sub = ref.rel(info["snapshots"]) * ref.L
+                if np.all(np.isfinite(sub)) and (best is None or sub[-1] < best[1][-1]):
+                    best = (em, sub, info["epoch_ms"][-1])
+            em, sub, ms = best
+            res[name] = {"eta_mult": em, "ms_30_epochs": ms,
+                         "suboptimality": [float(f"{v:.3e}") for v in sub]}
+            del Z, beta
+        r = {e: res["SVRG"]["suboptimality"][e - 1] / res["SCSVRG-k=30"]["suboptimality"][e - 1] for e in (5, 10, 20, 30)}
+        pr = {e: paper[decay]["SVRG"][e] / paper[decay]["SCSVRG-k=30"][e] for e in (5, 10, 20)}
+        out[f"decay_{decay}"] = dict(res, svrg_over_scsvrg=r, paper_svrg_over_scsvrg=pr, paper=paper[decay],
+                                     L_star=ref.L)
+        del X, y, ref
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "suboptimality per epoch, SVRG vs sketched-preconditioned SVRG (Sec. 6, Fig. 2 a, b)",
+                      "unit": "L(w_t) - L*", "n_gpus": 1, "data": "synthetic",
+                      "config": {"workload": f"n={n} d={d} singular values q^-1 / q^-2, unit-norm rows, lambda=1e-8, "
+                                             f"k=30, m=n, eta tuned over {list(grid)} / beta^, {E} epochs"},
+                      "results": out}))
+    ctx.close()
+
+
+def run_krylov(args):
+    """Alg. 2 with q = 1, 2, 3 Krylov blocks (k = 64) on the n = 65536, d = 1024 FP32 workload and the
+    n = 2^20, d = 4096 BF16 workload: the average condition number kappa^ = tr(H) / lambda_min(H) of the
+    preconditioned Hessian H = M (C + lambda I) M (Eq. (3); measured from the double normal equations),
+    the sketch time, and the time to relative suboptimality 1e-6 of the solve (m = 2n, eta = 1/beta^)."""
+    import paper_1602_02350_gb300 as rs
+    from paper_1602_02350_gb300 import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    ctx = rs.Context(int(os.environ.get("LOCAL_RANK", "0")), stream)
+    out = {}
+    for name in ("fp32_n65536_d1024", "bf16_n1048576_d4096"):
+        cfg = synth.CONFIGS[name]
+        dt = torch.bfloat16 if name.startswith("bf16") else torch.float32
+        X, y64, _ = synth.config_problem(cfg, device="cuda", dtype=dt)
+        y = y64.float().contiguous()
+        del y64
+        n, d, lam, k = cfg.n, cfg.d, cfg.lam, 64
+        ref = _Reference(X, y, lam)
+        rows = {}
+        for q in (1, 2, 3):
+            sk = dict(kind=cfg.kind, s=cfg.s) if q == 1 else dict(kind="gaussian")
+            t_sk, (V, s2) = _event_ms(lambda: rs.rs_sketch(ctx, X, k, cfg.seed_sketch, q=q, **sk), stream)
+            Vd = V.double()
+            a = 1.0 - torch.sqrt((s2[-1] + lam) / (s2 + lam))
+            M = torch.eye(d, dtype=torch.float64, device="cuda") - (Vd * a[None, :]) @ Vd.T
+            H = M @ ref.H @ M
+            ev = torch.linalg.eigvalsh(H)
+            kappa_hat = float(torch.trace(H) / ev[0])
+            cap = 20
+            _, info = rs.rs_solve(ctx, X, y, k, lam, cap, cfg.seed_sketch, cfg.seed_svrg, q=q, m=2 * n, eta_mult=1.0,
+                                  snapshots=True, refine=dt == torch.bfloat16, **sk)
+            rel = ref.rel(info["snapshots"])
+            hit = [i for i, r in enumerate(rel) if r <= TARGET]
+            e = hit[0] + 1 if hit else None
+            secs = None
+            if e:
+                ms, _ = _event_ms(lambda: rs.rs_solve(ctx, X, y, k, lam, e, cfg.seed_sketch, cfg.seed_svrg, q=q,
+                                                      m=2 * n, eta_mult=1.0, refine=dt == torch.bfloat16, **sk),
+                                  stream)
+                secs = ms / 1e3
+            rows[f"q={q}"] = {"kappa_hat": kappa_hat, "sketch_ms": t_sk, "epochs_to_1e-6": e, "seconds_to_1e-6": secs,
+                              "sigma2_k": float(s2[-1]), "rel_subopt_per_epoch": [float(f"{r:.3e}") for r in rel[:e or cap]]}
+            del M, H
+        kap_exact = None
+        ev_c = torch.linalg.eigvalsh(ref.H)
+        kap_exact = float(torch.trace(ref.H) / ev_c[0])
+        out[name] = {"k": k, "kappa_hat_unpreconditioned": kap_exact, "by_q": rows}
+        del X, y, ref
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "kappa^ of the preconditioned problem and time to 1e-6 vs Krylov blocks q (Alg. 2)",
+                      "n_gpus": 1, "data": "synthetic", "results": out}))
+    ctx.close()
+
+
 def cpu_baseline_sample(name=WORKLOAD, budget_s=20.0, epochs=None, _cache={}):
     """Time the FP64 oracle on host cores on a bounded sample of the workload and extrapolate to one
     plain solve: (sketch + precondition) once, plus epochs x (full gradient + m steps).
@@ -529,7 +638,9 @@ def main():
     ap.add_argument("--plain-epochs", type=int, default=4)
     ap.add_argument("--chosen-epochs", type=int, default=4)
     ap.add_argument("--cap-epochs", type=int, default=30, help="epoch cap of the untimed calibration runs")
-    ap.add_argument("--workload", default=WORKLOAD, choices=list(SINGLE) + ["batched"],
+    ap.add_argument("--fig2-n", type=int, default=16384)
+    ap.add_argument("--fig2-d", type=int, default=4096)
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(SINGLE) + ["batched", "fig2", "krylov"],
                     help="bf16_n1048576_d4096 (default): n=2^20, d=4096; fp32_n65536_d1024: n=65536, d=1024; "
                          "batched: 64 problems x 8 lambda (each its own JSON line)")
     ap.add_argument("--batch-problems", type=int, default=64)
@@ -539,6 +650,10 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "fig2":
+        run_fig2(args)
+    elif args.workload == "krylov":
+        run_krylov(args)
     else:
         run_rs(args)
 

@@ -380,6 +380,15 @@ int rs_trace_c(rs_ctx* ctx, const rs_matrix* X, double* out);
 int rs_speedup_ratio(rs_ctx* ctx, const double* sigma2, int64_t kmax, double trace_c, double* ratio,
                      double* ratio_accel);
 
+/* Check of the bounded device-side waits (no counterpart in the paper).  Every wait in this
+ * library's kernels (mbarrier phases of the copy/MMA pipelines, the cluster exchange of the inner
+ * loop) gives up after a budget of clock cycles, sets a bit in the context's status word and lets
+ * the kernel return, so the call reports RS_ETIMEOUT and the context stays usable.  This entry runs
+ * one such wait on an mbarrier expecting one arrival: with complete != 0 the arrival is made and the
+ * call returns RS_OK; with complete == 0 nothing arrives, the wait gives up after budget_cycles
+ * (1 .. 4e9, about two seconds at most) and the call returns RS_ETIMEOUT.  Synchronises. */
+int rs_wait_probe(rs_ctx* ctx, int64_t budget_cycles, int32_t complete);
+
 /* ------------------------------------------------------- parameter proposal
  *
  * The paper sets the SVRG parameters from theory (Sec. 3, the SVRG theorem of Xiao and Zhang:

@@ -124,6 +124,7 @@ _SIGS = {
     "rs_objective": [_P, ctypes.POINTER(Matrix), _P, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_double)],
     "rs_trace_c": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(ctypes.c_double)],
     "rs_speedup_ratio": [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P],
+    "rs_wait_probe": [_P, ctypes.c_int64, ctypes.c_int32],
     "rs_catalyst_solve": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(Matrix), _P, _P, _P, _P, ctypes.c_int64,
                           ctypes.POINTER(SvrgParams), ctypes.POINTER(CatalystParams), _P, ctypes.POINTER(History),
                           ctypes.POINTER(ctypes.c_double)],
@@ -488,6 +489,11 @@ def rs_trace_c(ctx, X):
     M = matrix(X)
     _check(lib().rs_trace_c(ctx.h, ctypes.byref(M), ctypes.byref(out)))
     return out.value
+
+
+def rs_wait_probe(ctx, budget_cycles, complete):
+    """Run one bounded device-side wait; raises RsError(RS_ETIMEOUT) when it gives up."""
+    _check(lib().rs_wait_probe(ctx.h, int(budget_cycles), 1 if complete else 0))
 
 
 def rs_speedup_ratio(ctx, sigma2, trace_c):

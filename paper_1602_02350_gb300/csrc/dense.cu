@@ -1074,6 +1074,33 @@ static int to_T(rs_ctx* ctx, const double* in, int64_t count, T* out) {
   return RS_OK;
 }
 
+namespace {
+
+// E = S - I (k x k, double)
+__global__ void minus_identity_kernel(const double* __restrict__ S, int k, double* __restrict__ E) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
+    E[e] = S[e] - (e / k == e % k ? 1.0 : 0.0);
+}
+// T = I - E / 2 + 3 E^2 / 8: the inverse square root of S = I + E to O(|E|^3)
+__global__ void inv_sqrt_series_kernel(const double* __restrict__ E, const double* __restrict__ E2, int k,
+                                       double* __restrict__ T) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
+    T[e] = (e / k == e % k ? 1.0 : 0.0) - 0.5 * E[e] + 0.375 * E2[e];
+}
+// G <- (G + G^T) / 2
+__global__ void symmetrize_kernel(double* G, int k) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e / k, j = e % k;
+    if (i < j) {
+      const double v = 0.5 * (G[i * k + j] + G[j * k + i]);
+      G[i * k + j] = v;
+      G[j * k + i] = v;
+    }
+  }
+}
+
+}  // namespace
+
 int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* evals, double* W) {
   if (k < 1 || k > 256) return rs_fail(RS_EINVAL, "sym_eig: k = %lld outside [1, 256]", (long long)k);
   const size_t es = prec == RS_F64 ? 8 : 4;
@@ -1115,13 +1142,35 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
       float4* rot_log = reinterpret_cast<float4*>(lg);
       int* nsw = reinterpret_cast<int*>(lg + log_bytes);
       const size_t pshm = (size_t)k * (k + 1) / 2 * sizeof(float);
+      const size_t ashm = (size_t)kJaRows * (k + 1) * sizeof(float);
       RS_CUDA_TRY(cudaFuncSetAttribute(jacobi_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+      // pass 1: float Jacobi on G.  Its absolute floor (a few rounding units of ||G||) stops it from
+      // stirring rounding noise, but also leaves the small eigenvalues of a graded spectrum with only
+      // absolute accuracy.
       jacobi_packed_kernel<<<1, 1024, pshm, ctx->stream>>>(G, (int)k, 1e-6f, 8.0, kMaxSweeps, rot_log, nsw, lam0);
       RS_LAUNCH_CHECK(ctx);
-      const size_t ashm = (size_t)kJaRows * (k + 1) * sizeof(float);
       jacobi_apply_kernel<<<(unsigned)((k + kJaRows - 1) / kJaRows), kJaRows * P, ashm, ctx->stream>>>(rot_log, nsw,
                                                                                                        (int)k, Wt);
       RS_LAUNCH_CHECK(ctx);
+      // pass 2: H = W1^T G W1 formed in double is diagonal up to the first pass's rounding, so each
+      // entry in float keeps its own relative accuracy; Jacobi on H with the relative criterion alone
+      // (no absolute floor) then resolves the small eigenvalues to relative accuracy, and W = W1 W2.
+      double* aux = static_cast<double*>(rs_scratch(ctx, SCR_JAC2, (size_t)3 * k * k * sizeof(double)));
+      if (!aux) return RS_ENOMEM;
+      double* Hd = aux;
+      double* Tm = aux + k * k;
+      double* W2 = aux + 2 * k * k;
+      RS_TRY(launch_gemm<double>(ctx, k, k, k, 1.0, G, k, 1, Wt, k, 1, 0.0, nullptr, 0, Tm, k, nullptr));    // G W1
+      RS_TRY(launch_gemm<double>(ctx, k, k, k, 1.0, Wt, 1, k, Tm, k, 1, 0.0, nullptr, 0, Hd, k, nullptr));   // W1^T (G W1)
+      symmetrize_kernel<<<(unsigned)std::min<int64_t>((k * k + 255) / 256, 1024), 256, 0, ctx->stream>>>(Hd, (int)k);
+      RS_LAUNCH_CHECK(ctx);
+      jacobi_packed_kernel<<<1, 1024, pshm, ctx->stream>>>(Hd, (int)k, 1e-6f, 0.0, kMaxSweeps, rot_log, nsw, lam0);
+      RS_LAUNCH_CHECK(ctx);
+      jacobi_apply_kernel<<<(unsigned)((k + kJaRows - 1) / kJaRows), kJaRows * P, ashm, ctx->stream>>>(rot_log, nsw,
+                                                                                                       (int)k, W2);
+      RS_LAUNCH_CHECK(ctx);
+      RS_TRY(launch_gemm<double>(ctx, k, k, k, 1.0, Wt, k, 1, W2, k, 1, 0.0, nullptr, 0, Tm, k, nullptr));   // W1 W2
+      RS_CUDA_TRY(cudaMemcpyAsync(Wt, Tm, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
       rayleigh_kernel<<<(unsigned)k, 128, 0, ctx->stream>>>(G, (int)k, Wt, lam1);
       RS_LAUNCH_CHECK(ctx);
       sort_eig_kernel<<<1, 256, 0, ctx->stream>>>(lam1, Wt, (int)k, evals, W);
@@ -1144,29 +1193,6 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
   }
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
-}
-
-// E = S - I (k x k, double)
-__global__ void minus_identity_kernel(const double* __restrict__ S, int k, double* __restrict__ E) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
-    E[e] = S[e] - (e / k == e % k ? 1.0 : 0.0);
-}
-// T = I - E / 2 + 3 E^2 / 8: the inverse square root of S = I + E to O(|E|^3)
-__global__ void inv_sqrt_series_kernel(const double* __restrict__ E, const double* __restrict__ E2, int k,
-                                       double* __restrict__ T) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
-    T[e] = (e / k == e % k ? 1.0 : 0.0) - 0.5 * E[e] + 0.375 * E2[e];
-}
-// G <- (G + G^T) / 2
-__global__ void symmetrize_kernel(double* G, int k) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
-    const int i = e / k, j = e % k;
-    if (i < j) {
-      const double v = 0.5 * (G[i * k + j] + G[j * k + i]);
-      G[i * k + j] = v;
-      G[j * k + i] = v;
-    }
-  }
 }
 
 // ---------------------------------------------------------------------- Alg. 2 pieces

@@ -37,3 +37,35 @@ extern "C" int rs_speedup_ratio(rs_ctx* ctx, const double* sigma2, int64_t kmax,
   RS_LAUNCH_CHECK(ctx);
   return RS_OK;
 }
+
+// ------------------------------------------------------------------ bounded-wait check
+// Every device-side wait of this library is bounded: it gives up after a budget of clock cycles,
+// sets the timeout bit of the context's status word and lets the kernel finish, so that the host
+// reports RS_ETIMEOUT and the context stays usable.  rs_wait_probe runs that path on purpose:
+// one thread initialises an mbarrier expecting one arrival, arrives on it only if `complete`, and
+// waits for its phase with the same bounded wait the pipelined kernels use.
+namespace {
+__global__ void wait_probe_kernel(long long budget, int complete, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init_cta(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  if (complete) mbar_arrive_cta(&bar);
+  if (!mbar_wait_bounded(&bar, 0u, budget)) atomicOr(status, STATUS_TIMEOUT);
+}
+}  // namespace
+
+extern "C" int rs_wait_probe(rs_ctx* ctx, int64_t budget_cycles, int32_t complete) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(budget_cycles >= 1 && budget_cycles <= 4000000000LL,
+               "rs_wait_probe: budget must be in [1, 4e9] cycles (about two seconds)");
+  RS_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  wait_probe_kernel<<<1, 32, 0, ctx->stream>>>((long long)budget_cycles, complete ? 1 : 0, ctx->d_status);
+  RS_LAUNCH_CHECK(ctx);
+  int st = 0;
+  RS_CUDA_TRY(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (st & STATUS_TIMEOUT) return rs_fail(RS_ETIMEOUT, "rs_wait_probe: the bounded wait gave up after %lld cycles",
+                                          (long long)budget_cycles);
+  return RS_OK;
+}

@@ -110,6 +110,32 @@ def problem(n, d, spectrum, noise, seed, device="cpu", dtype=torch.float64):
     return X, y, w_gen
 
 
+def spectrum_problem(n, d, decay, noise, seed, device="cuda", dtype=torch.float32):
+    """The synthetic data of the paper's Sec. 6 at n x d: a d x n matrix with uniformly random singular
+    vectors and q-th singular value q^-decay (decay 1: linear, 2: quadratic), examples (its columns)
+    normalised to unit norm, labels y_i = w_gen^T x_i + noise N(0, 1) with w_gen ~ N(0, I_d).
+    Rows of the returned X are the examples: X = V diag(s) U^T with U (d x d) and V (n x d) orthonormal
+    (QR of seeded Gaussians, signs fixed), then each row scaled to norm 1."""
+    dev = torch.device(device)
+    U = torch.from_numpy(haar_orthogonal(d, seed + 11))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    G = torch.randn((n, d), generator=gen, device=dev, dtype=torch.float64)
+    Vq, R = torch.linalg.qr(G)
+    Vq = Vq * torch.sign(torch.diagonal(R))[None, :]
+    del G, R
+    s = torch.arange(1, d + 1, dtype=torch.float64, device=dev) ** (-float(decay))
+    X = (Vq * s[None, :]) @ U.to(dev).T
+    del Vq
+    X = X / X.norm(dim=1, keepdim=True)
+    rng = np.random.default_rng(seed)
+    w_gen = torch.from_numpy(rng.standard_normal(d)).to(dev)
+    eps = torch.randn(n, generator=gen, device=dev, dtype=torch.float64)
+    Xs = X.to(dtype)
+    y = Xs.double() @ w_gen + noise * eps
+    return Xs.contiguous(), y, w_gen
+
+
 def config_problem(cfg, device="cpu", dtype=None):
     """The data of a named configuration."""
     if dtype is None:

@@ -99,6 +99,10 @@ def test_c3_ritz_pairs_satisfy_rayleigh_ritz_and_interlacing(c3, c3_normal, c3_s
     np.testing.assert_allclose(Vd.T @ C @ Vd, np.diag(s2), atol=tol * top)
     lam_c = np.sort(np.linalg.eigvalsh(C))[::-1][: cfg.k]
     assert np.all(s2 <= lam_c + tol * top)
+    # every Ritz value, the smallest included, is the Rayleigh quotient of its own Ritz vector to
+    # relative accuracy (the eigen-solve keeps the relative accuracy of a graded spectrum)
+    rq = np.einsum("ij,ij->j", Vd, C @ Vd) / np.einsum("ij,ij->j", Vd, Vd)
+    np.testing.assert_allclose(s2, rq, rtol=1e-3)
     # a single-pass rank-256 sketch captures the 20 boosted directions to within half a percent
     assert np.all(s2[:20] >= (1 - 5e-3) * lam_c[:20]), np.max(1 - s2[:20] / lam_c[:20])
 

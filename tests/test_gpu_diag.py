@@ -55,3 +55,18 @@ def test_ratio_from_sketch_matches_oracle(rsctx, dtype, tol):
     got = r.cpu().numpy()
     assert np.all(np.abs(got - ref) <= 2 * eps_r * ref * ref + 1e-12), np.max(np.abs(got - ref) / (ref * ref))
     assert ref[31] > 5.0 * ref[0]
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(rsctx):
+    """A device-side wait that nothing completes gives up after its budget (about 2 ms here), the call
+    reports RS_ETIMEOUT (5), and the same context then runs ordinary work correctly."""
+    rs.rs_wait_probe(rsctx, 4_000_000, True)
+    with pytest.raises(rs.RsError) as e:
+        rs.rs_wait_probe(rsctx, 4_000_000, False)
+    assert e.value.code == 5 and "gave up" in str(e.value)
+    s2 = torch.tensor([4.0, 1.0], dtype=torch.float64, device="cuda")
+    r, _ = rs.rs_speedup_ratio(rsctx, s2, 6.0)
+    np.testing.assert_allclose(r.cpu().numpy(), [1.0, 6.0 / (2.0 + 1.0)], rtol=1e-15)
+    with pytest.raises(rs.RsError) as e:
+        rs.rs_wait_probe(rsctx, 0, True)
+    assert e.value.code == 1

@@ -110,3 +110,14 @@ def test_tensor_core_range_sketch_can_be_switched_off(rsctx, monkeypatch):
     Y = rs.rs_range_sketch(rsctx, cuda_rows(X), 24, 2000).cpu().double().numpy()
     ref = osk.range_sketch(X.double().numpy(), 24, 2000)
     np.testing.assert_allclose(Y, ref, rtol=0, atol=3e-5 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("k,spread", [(64, 5.0), (256, 5.0), (200, 8.0)])
+def test_sym_eig_float_keeps_relative_accuracy_of_small_eigenvalues(rsctx, k, spread):
+    """Graded spectra (eigenvalues over 10^spread) in a random basis: the float eigen-solve returns
+    every eigenvalue, the smallest included, to a relative 1e-4 (a float Jacobi with an absolute
+    floor alone would leave the small ones with absolute accuracy only)."""
+    G = synth.random_symmetric(k, k + 7, spread=spread)
+    ev, W = rs.rs_sym_eig(rsctx, torch.from_numpy(G).cuda(), rs.RS_F32)
+    ev_ref, _ = osk.sym_eig_desc(G)
+    np.testing.assert_allclose(ev.cpu().numpy(), ev_ref, rtol=1e-4)
