@@ -382,24 +382,26 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
                                            const T* __restrict__ wbar, int average, T* __restrict__ wnext,
                                            int* status, const float* __restrict__ rsc) {
   constexpr int B = kBlk;
-  constexpr int E = 16 / sizeof(T);
   constexpr int ES = 16 / sizeof(S);
   constexpr int CW = 32 * QN;               // columns owned by this block
   constexpr int NCH = CW / ES;              // 16-byte chunks per row slice
+  constexpr int CPL = NCH >= 32 ? NCH / 32 : 1;   // chunks per lane
   constexpr int NW = NT / 32;                 // warps
-  constexpr int RPW = B / NW;                 // rows of the dot product per warp
-  constexpr int H = NT / B;                   // partial sums per row of R p
-  constexpr int TPC = NT / CW > 0 ? NT / CW : 1;   // lanes per column in the update (same warp)
-  constexpr int JPT = B / TPC;                      // steps per lane in the update
-  constexpr int CPW = 32 / TPC;                     // columns per warp in the update
+  constexpr int RPW = B / NW;                 // rows of the block per warp
+  constexpr int H = NT / B;                   // threads per row of R p
   constexpr int W16 = RPW * (int)sizeof(T) / 16;    // 16-byte pieces of one warp's partials
+  static_assert(RPW * sizeof(T) % 16 == 0, "partial dots travel in 16-byte pieces");
+  static_assert(H == 4 || H == 8, "R p is split over 4 or 8 threads per row");
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) unsigned char ch_sh[];
-  // row stride of the staged slices (in S): the padding puts the TPC lanes that share a column
-  // (which read rows j, j+1, .., j+TPC-1 in the update) on distinct shared-memory banks
-  constexpr int ZS = CW + chain_zpad(TPC, CPW, (int)sizeof(S));
+  // Layout: lane L of warp w owns the 16-byte chunks q = L + 32 v (v < CPL) of this block's column
+  // slice, for the RPW rows RPW w .. RPW w + RPW - 1 of the block of steps.  It loads each of those
+  // chunks once with a 16-byte shared-memory load, uses them for its part of the dot products and
+  // keeps them in registers for the rank-B update, whose per-warp partial sums over the warp's rows
+  // are added across the warps through shared memory (fixed warp order).
+  constexpr int ZS = CW;                                   // row stride of the staged slices (in S)
   S* Zs = reinterpret_cast<S*>(ch_sh);                     // [STAGES][B][ZS]
   T* recv = reinterpret_cast<T*>(Zs + (size_t)STAGES * B * ZS);   // [2][kCsMax][B] partial dots from each rank
   // running sum of the iterates (epoch average) as a compensated (Kahan) pair in T: on GB300 a
@@ -409,14 +411,17 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   T* dl = Scmp + CW;                                       // [CW]
   T* mus = dl + CW;                                        // [CW]
   T* pv = mus + CW;                                        // [B]
-  T* av = pv + B;                                          // [B]
-  T* part4 = av + B;                                       // [H][B] partial sums of R p
-  uint32_t* srow = reinterpret_cast<uint32_t*>(part4 + H * B);   // [STAGES][B]
+  T* av = pv + B;                                          // [B]   a_j, then (B_b - j) a_j in avw
+  T* avw = av + B;                                         // [B]
+  T* redu = avw + B;                                       // [NW][CW] per-warp partial sums of the update
+  T* redw = redu + NW * CW;                                // [NW][CW] the same with the running-sum weights
+  uint32_t* srow = reinterpret_cast<uint32_t*>(redw + NW * CW);   // [STAGES][B]
   float* sscale = reinterpret_cast<float*>(srow + STAGES * B);   // [STAGES][B] row scales (FP8 codes)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sscale + STAGES * B);   // [2]
   constexpr bool F8 = IsFp8<S>::value;
   __shared__ int aborted;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool lane_on = lane < NCH;
   const int64_t c0 = (int64_t)rank * CW;
   const int cwid = (int)max64(0, min64(CW, d - c0));
   const int64_t nblk = (m + B - 1) / B;
@@ -450,16 +455,20 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   }
   __syncthreads();
 
-  // rows beyond the last step and columns beyond d are zero-filled (source size 0)
+  // rows beyond the last step and columns beyond d are zero-filled (source size 0); each thread
+  // copies exactly the chunks it reads later
   auto load_block = [&](int64_t blk) {
     const int slot = (int)(blk % STAGES);
     S* zdst = Zs + (size_t)slot * B * ZS;
     const uint32_t* rows = srow + slot * B;
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
-      const int j = warp + NW * r;
+      const int j = RPW * warp + r;
       const uint32_t row = rows[j];
-      for (int q = lane; q < NCH; q += 32) {
+#pragma unroll
+      for (int v = 0; v < CPL; ++v) {
+        const int q = lane + 32 * v;
+        if (!lane_on) continue;
         const int col = q * ES;
         int bytes = 0;
         const S* src = Z;
@@ -501,59 +510,64 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
     const float myscale = (F8 && tid < B) ? sscale[slot * B + tid] : 1.0f;   // row tid of this block
     const int Bb = (int)min64(B, m - blk * B);
     const S* zs = Zs + (size_t)slot * B * ZS;
-    // this block's R column entries and c_j go straight from L2 into registers: issued here, used
-    // after the exchange, so their latency is hidden behind the dot products
+    // this block's R entries and c_j go straight from L2 into registers: issued here, used after the
+    // exchange, so their latency is hidden behind the dot products.  Thread (j, h) with j = tid / H
+    // takes the terms l = h, h + H, ... of row j of R p.
     constexpr int RPT = B / H;   // R entries per thread
     T rreg[RPT];
     T creg = T(0);
+    const int jr = tid / H, hr = tid % H;
     {
-      const int j = tid & (B - 1), h = tid >> 6;
-      const T* rsrc = Rt + blk * (int64_t)B * B + j;
+      const T* rsrc = Rt + blk * (int64_t)B * B + jr;
 #pragma unroll
       for (int t = 0; t < RPT; ++t) {
-        const int l = h + H * t;
-        rreg[t] = l <= j ? __ldg(rsrc + l * B) : T(0);
+        const int l = hr + H * t;
+        rreg[t] = l <= jr ? __ldg(rsrc + l * B) : T(0);
       }
-      if (tid < B) creg = __ldg(cvec + blk * B + tid);
+      if (hr == 0) creg = __ldg(cvec + blk * B + jr);
     }
-    // partial p_j over this block's columns for rows 8 warp .. 8 warp + 7, pushed to every rank
+    // the warp's rows of the staged slice, 16 bytes per chunk, kept for the update
+    uint4 zr[RPW][CPL];
+    T part[RPW];
     {
-      T dv[QN];
+      T dv[CPL][ES];
 #pragma unroll
-      for (int q = 0; q < QN; ++q) dv[q] = dl[lane + 32 * q];
-      T part[RPW];
+      for (int v = 0; v < CPL; ++v)
+#pragma unroll
+        for (int e = 0; e < ES; ++e) dv[v][e] = lane_on ? dl[(lane + 32 * v) * ES + e] : T(0);
 #pragma unroll
       for (int r = 0; r < RPW; ++r) {
-        const S* zr = zs + (RPW * warp + r) * ZS + lane;
-        T s = T(0);
+        const S* zrow = zs + (RPW * warp + r) * ZS;
+        T sacc = T(0);
 #pragma unroll
-        for (int q = 0; q < QN; ++q) s = fma(cvt<T>(zr[32 * q]), dv[q], s);
-        part[r] = s;
-      }
+        for (int v = 0; v < CPL; ++v) {
+          zr[r][v] = lane_on ? *reinterpret_cast<const uint4*>(zrow + (lane + 32 * v) * ES) : make_uint4(0u, 0u, 0u, 0u);
+          const S* sv = reinterpret_cast<const S*>(&zr[r][v]);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int r = 0; r < RPW; ++r) part[r] += __shfl_xor_sync(0xffffffffu, part[r], o);
-      if (lane < CS) {
-        uint32_t pw[RPW * sizeof(T) / 4];
-#pragma unroll
-        for (int r = 0; r < RPW; ++r) {
-          if constexpr (sizeof(T) == 8) {
-            pw[2 * r] = (uint32_t)__double2loint(part[r]);
-            pw[2 * r + 1] = (uint32_t)__double2hiint(part[r]);
-          } else {
-            pw[r] = __float_as_uint(part[r]);
-          }
+          for (int e = 0; e < ES; ++e) sacc = fma(cvt<T>(sv[e]), dv[v][e], sacc);
         }
-        const uint32_t base = recv_remote + (uint32_t)(((par * kCsMax + rank) * B + RPW * warp) * sizeof(T));
-        const uint32_t rbar = par ? bar_remote1 : bar_remote0;
-#pragma unroll
-        for (int h = 0; h < W16; ++h) st_async16(base + 16 * h, rbar, pw + 4 * h);
+        part[r] = sacc;
       }
     }
-    if (tid < B) {
-      srow[slot * B + tid] = next_row;    // this slot now holds block blk + STAGES
-      if (F8) sscale[slot * B + tid] = next_scale;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) part[r] += __shfl_xor_sync(0xffffffffu, part[r], o);
+    if (lane < CS) {
+      uint32_t pw[RPW * sizeof(T) / 4];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        if constexpr (sizeof(T) == 8) {
+          pw[2 * r] = (uint32_t)__double2loint(part[r]);
+          pw[2 * r + 1] = (uint32_t)__double2hiint(part[r]);
+        } else {
+          pw[r] = __float_as_uint(part[r]);
+        }
+      }
+      const uint32_t base = recv_remote + (uint32_t)(((par * kCsMax + rank) * B + RPW * warp) * sizeof(T));
+      const uint32_t rbar = par ? bar_remote1 : bar_remote0;
+#pragma unroll
+      for (int h = 0; h < W16; ++h) st_async16(base + 16 * h, rbar, pw + 4 * h);
     }
     // wait for the CS partial vectors of this block (bounded), then p = sum over ranks
     if (!aborted) {
@@ -568,63 +582,95 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
     }
     if (tid < B) {
       const T* rv = recv + (size_t)par * kCsMax * B + tid;
-      T s = T(0);
-      for (int r = 0; r < CS; ++r) s += rv[r * B];   // rank order: identical in every block
-      pv[tid] = F8 ? s * myscale : s;
+      T sp = T(0);
+      for (int r = 0; r < CS; ++r) sp += rv[r * B];   // rank order: identical in every block
+      pv[tid] = F8 ? sp * myscale : sp;
     }
     __syncthreads();
     if (tid == 0 && blk + 2 < nblk) mbar_arm(&mbar[par], tx_per_block);   // next use: block blk + 2
-    // a = R p + c: thread (j, h) sums the terms l = h, h+H, ... <= j (R is lower triangular, zero
-    // above the diagonal, so the loop may run to the end of its group); fixed combine order below
+    // a = R p + c: the H threads of row j (adjacent lanes) sum their terms and combine by shuffles
+    // in a fixed order; R is lower triangular, so the terms beyond the diagonal are zero
     {
-      const int j = tid & (B - 1), h = tid >> 6;
       T s0 = T(0), s1 = T(0);
 #pragma unroll
       for (int t = 0; t < RPT; t += 2) {
-        s0 = fma(rreg[t], pv[h + H * t], s0);
-        if (t + 1 < RPT) s1 = fma(rreg[t + 1], pv[h + H * (t + 1)], s1);
+        s0 = fma(rreg[t], pv[hr + H * t], s0);
+        if (t + 1 < RPT) s1 = fma(rreg[t + 1], pv[hr + H * (t + 1)], s1);
       }
-      part4[h * B + j] = s0 + s1;
+      T sa = s0 + s1;
+#pragma unroll
+      for (int o = 1; o < H; o <<= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      if (hr == 0) {
+        sa += creg;
+        // FP8 codes: the update multiplies stored codes, so a_j carries row j's scale (the slot's
+        // scales are replaced only after the barrier below)
+        const T a = F8 ? sa * (T)sscale[slot * B + jr] : sa;
+        av[jr] = a;
+        avw[jr] = (T)(Bb - jr) * a;   // weight B_b - j of the running-sum term
+      }
     }
     __syncthreads();
-    if (tid < B)
+    if (tid < B) {
+      srow[slot * B + tid] = next_row;    // this slot now holds block blk + STAGES
+      if (F8) sscale[slot * B + tid] = next_scale;
+    }
+    // rank-B update of this warp's rows: u_c = sum_j a_j z_jc, w_c = sum_j (B_b - j) a_j z_jc
     {
-      T sa = creg;
+      T u[CPL][ES], w[CPL][ES];
 #pragma unroll
-      for (int hh = 0; hh < H; ++hh) sa += part4[hh * B + tid];   // fixed order
-      av[tid] = F8 ? sa * myscale : sa;   // the update multiplies stored codes
+      for (int v = 0; v < CPL; ++v)
+#pragma unroll
+        for (int e = 0; e < ES; ++e) u[v][e] = w[v][e] = T(0);
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        const int j = RPW * warp + r;
+        const T a = av[j], aw = avw[j];
+#pragma unroll
+        for (int v = 0; v < CPL; ++v) {
+          const S* sv = reinterpret_cast<const S*>(&zr[r][v]);
+#pragma unroll
+          for (int e = 0; e < ES; ++e) {
+            const T z = cvt<T>(sv[e]);
+            u[v][e] = fma(a, z, u[v][e]);
+            w[v][e] = fma(aw, z, w[v][e]);
+          }
+        }
+      }
+      if (lane_on) {
+#pragma unroll
+        for (int v = 0; v < CPL; ++v) {
+          T* du = redu + warp * CW + (lane + 32 * v) * ES;
+          T* dw = redw + warp * CW + (lane + 32 * v) * ES;
+#pragma unroll
+          for (int e = 0; e < ES; e += 16 / (int)sizeof(T)) {
+            if constexpr (sizeof(T) == 4) {
+              *reinterpret_cast<float4*>(du + e) = make_float4(u[v][e], u[v][e + 1], u[v][e + 2], u[v][e + 3]);
+              *reinterpret_cast<float4*>(dw + e) = make_float4(w[v][e], w[v][e + 1], w[v][e + 2], w[v][e + 3]);
+            } else {
+              *reinterpret_cast<double2*>(du + e) = make_double2(u[v][e], u[v][e + 1]);
+              *reinterpret_cast<double2*>(dw + e) = make_double2(w[v][e], w[v][e + 1]);
+            }
+          }
+        }
+      }
     }
     __syncthreads();
-    // rank-B update: lanes g = 0..TPC-1 of a column take steps j = g, g + TPC, ... and combine by
-    // shuffles (the padded row stride keeps their shared-memory reads on distinct banks)
-    {
-      const int c = warp * CPW + (lane % CPW), g = lane / CPW;
-      T u = T(0), w = T(0);
-      T wt = (T)(Bb - g);                       // weight B_b - j of the running-sum term
-#pragma unroll 8
-      for (int jj = 0; jj < JPT; ++jj) {
-        const int j = g + TPC * jj;
-        const T az = av[j] * cvt<T>(zs[j * ZS + c]);
-        u += az;
-        w = fma(wt, az, w);
-        wt -= T(TPC);
-      }
+    for (int c = tid; c < CW; c += NT) {
+      T uu = T(0), ww = T(0);
 #pragma unroll
-      for (int o = CPW; o < 32; o <<= 1) {
-        u += __shfl_xor_sync(0xffffffffu, u, o);
-        w += __shfl_xor_sync(0xffffffffu, w, o);
+      for (int w2 = 0; w2 < NW; ++w2) {   // fixed warp order
+        uu += redu[w2 * CW + c];
+        ww += redw[w2 * CW + c];
       }
-      if (g == 0) {
-        const T bbT = (T)Bb;
-        const T tri = (T)((Bb * (Bb + 1)) / 2);   // exact
-        const T dold = dl[c];
-        const T x = bbT * dold - et * (mus[c] * tri + w);
-        const T yk = x - Scmp[c];
-        const T tk = Ssum[c] + yk;
-        Scmp[c] = (tk - Ssum[c]) - yk;
-        Ssum[c] = tk;
-        dl[c] = dold - et * (bbT * mus[c] + u);
-      }
+      const T bbT = (T)Bb;
+      const T tri = (T)((Bb * (Bb + 1)) / 2);   // exact
+      const T dold = dl[c];
+      const T x = bbT * dold - et * (mus[c] * tri + ww);
+      const T yk = x - Scmp[c];
+      const T tk = Ssum[c] + yk;
+      Scmp[c] = (tk - Ssum[c]) - yk;
+      Ssum[c] = tk;
+      dl[c] = dold - et * (bbT * mus[c] + uu);
     }
   }
   cp_async_wait<0>();
@@ -957,10 +1003,9 @@ struct ChainPlan {
 template <typename S, typename T>
 size_t chain_smem(int qn, int stages, int nt) {
   const int CW = 32 * qn;
-  const int TPC = std::max(1, nt / CW);
-  const int ZS = CW + chain_zpad(TPC, 32 / TPC, (int)sizeof(S));
-  return (size_t)stages * kBlk * ZS * sizeof(S) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + 2 * (size_t)CW * sizeof(T) +
-         2 * (size_t)CW * sizeof(T) + (2 + nt / kBlk) * (size_t)kBlk * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
+  const int NW = nt / 32;
+  return (size_t)stages * kBlk * CW * sizeof(S) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + 4 * (size_t)CW * sizeof(T) +
+         3 * (size_t)kBlk * sizeof(T) + 2 * (size_t)NW * CW * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
          (size_t)stages * kBlk * sizeof(float) + 2 * sizeof(uint64_t) + 64;
 }
 
