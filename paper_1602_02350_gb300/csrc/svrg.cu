@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kFcThreads + 32, 1)
   constexpr int E = 16 / (int)sizeof(S);
   extern __shared__ __align__(128) unsigned char fc_sh[];
   __shared__ uint64_t full[kFcMaxStages], empty[kFcMaxStages];
-  __shared__ float dpart[kFcMaxStages][kFcThreads / 32][R];
+  __shared__ __align__(16) float dpart[kFcMaxStages][kFcThreads / 32][R];
   __shared__ int abort_flag;
   const int64_t nch = (d + E - 1) / E;                          // 16-byte chunks per row
   const uint32_t row_bytes = (uint32_t)(nch * 16);
@@ -328,6 +328,10 @@ __global__ void __launch_bounds__(kFcThreads + 32, 1)
       const int64_t uu = it / stages;
       const int64_t r0 = t * R;
       const int rows = (int)min64(R, N - r0);
+      // the tile's labels are read before waiting for its rows, so their latency overlaps the copy
+      float yv[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) yv[j] = (r0 + j < n) ? y[r0 + j] : 0.0f;
       if (!mbar_wait_bounded(&full[s], (uint32_t)(uu & 1), kFgWait)) abort_flag = 1;
       const unsigned char* st = fc_sh + (int64_t)s * R * rstride;
       uint4 zr[R][U];
@@ -360,14 +364,31 @@ __global__ void __launch_bounds__(kFcThreads + 32, 1)
         if (lane == 0) atomicOr(status, STATUS_TIMEOUT);
         break;
       }
+      float dots[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) dots[j] = 0.0f;
+#pragma unroll
+      for (int w2 = 0; w2 < kFcThreads / 32; ++w2) {   // fixed order
+        if constexpr (R % 4 == 0) {
+#pragma unroll
+          for (int j = 0; j < R; j += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(&dpart[s][w2][j]);
+            dots[j] += q.x;
+            dots[j + 1] += q.y;
+            dots[j + 2] += q.z;
+            dots[j + 3] += q.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < R; ++j) dots[j] += dpart[s][w2][j];
+        }
+      }
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         if (j < rows) {
-          float dot = 0.0f;
-#pragma unroll
-          for (int w2 = 0; w2 < kFcThreads / 32; ++w2) dot += dpart[s][w2][j];   // fixed order
+          const float dot = dots[j];
           const int64_t i = r0 + j;
-          const float r = i < n ? (dot - y[i]) * inv_n : lam * dot;
+          const float r = i < n ? (dot - yv[j]) * inv_n : lam * dot;
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const S* sv = reinterpret_cast<const S*>(&zr[j][u]);
