@@ -293,6 +293,28 @@ int rs_catalyst_solve(rs_ctx* ctx, const rs_matrix* Z, const rs_matrix* X, const
                       const void* V, const double* sigma2, int64_t k, const rs_svrg_params* p,
                       const rs_catalyst_params* cp, void* w_out, rs_history* hist, double* kappa_used);
 
+/* Autotuning of the launch layouts (no counterpart in the paper).  For components Z (storage type,
+ * width d) this times, on this GPU, every layout that fits for
+ *   - the inner-loop chain of Alg. 1: thread-block cluster size (1..16 blocks, each owning at most
+ *     256 columns), threads per block (256 or 512) and ring stages (2..4), on a probe epoch of 8192
+ *     uniformly drawn steps (one warm-up and three timed launches each);
+ *   - the full-gradient pass for RS_F32 / RS_BF16 rows: the ring stages of its bulk-copy pipeline
+ *     (2, 3, 4, 6, 8 within the shared-memory budget), one pass each (warm-up + three timed);
+ * keeps the fastest of each in the context, and later calls on this context with components of the
+ * same storage type and width use them (rs_svrg_epoch, rs_svrg_solve, rs_solve, rs_full_gradient,
+ * rs_catalyst_solve).  A second call for the same shape times nothing (report->cached = 1).
+ * Synchronises.  report (host): the chosen layout and its time per probe launch / pass. */
+typedef struct {
+  int32_t chain_cluster, chain_threads, chain_stages;
+  float chain_ms;           /* per launch of the 8192-step probe */
+  int32_t fullgrad_stages;  /* 0 when the storage type has no tunable full-gradient kernel */
+  float fullgrad_ms;        /* per pass */
+  int32_t candidates;       /* layouts timed by this call */
+  int32_t cached;           /* 1: both choices were already in the context */
+} rs_tune_report;
+
+int rs_autotune(rs_ctx* ctx, const rs_matrix* Z, int64_t n, rs_tune_report* report);
+
 /* Alg. 3 end to end: sketch (Alg. 2), preconditioner and transformed components (Eq. (11),
  * Sec. 5.1), SVRG (Alg. 1), w_out = M w~ (Eq. (4)).  X may be RS_F64, RS_F32 or RS_BF16 (the
  * components are stored in the same type; with RS_BF16 set p->refine).  X->data, y and w_out may be HOST

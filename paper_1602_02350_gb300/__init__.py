@@ -13,5 +13,5 @@ from ._lib import (  # noqa: F401
     rs_philox_words, rs_gaussian, rs_countsketch, rs_range_sketch, rs_orthonormalize, rs_sym_eig,
     rs_ritz, rs_sketch, rs_precondition, rs_map_output, rs_sampling_weights, rs_sampling_table,
     rs_index_stream, rs_full_gradient, rs_full_gradient_static, rs_svrg_epoch, rs_svrg_solve, rs_solve,
-    rs_objective, rs_trace_c, rs_speedup_ratio, rs_wait_probe, rs_catalyst_solve, rs_solve_batched, rs_solve_proposed, rs_mlp_forward, rs_mlp_train_step, rs_propose, mlp_norm, MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM,
+    rs_objective, rs_trace_c, rs_speedup_ratio, rs_wait_probe, rs_autotune, rs_catalyst_solve, rs_solve_batched, rs_solve_proposed, rs_mlp_forward, rs_mlp_train_step, rs_propose, mlp_norm, MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM,
 )

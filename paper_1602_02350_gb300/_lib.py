@@ -81,6 +81,12 @@ class CatalystParams(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_double), ("outer", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("chain_cluster", ctypes.c_int32), ("chain_threads", ctypes.c_int32), ("chain_stages", ctypes.c_int32),
+                ("chain_ms", ctypes.c_float), ("fullgrad_stages", ctypes.c_int32), ("fullgrad_ms", ctypes.c_float),
+                ("candidates", ctypes.c_int32), ("cached", ctypes.c_int32)]
+
+
 class History(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int32), ("epochs_run", ctypes.c_int32), ("snapshots", ctypes.c_void_p),
                 ("mu_norm2", ctypes.POINTER(ctypes.c_double)), ("epoch_ms", ctypes.POINTER(ctypes.c_float))]
@@ -125,6 +131,7 @@ _SIGS = {
     "rs_trace_c": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(ctypes.c_double)],
     "rs_speedup_ratio": [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P],
     "rs_wait_probe": [_P, ctypes.c_int64, ctypes.c_int32],
+    "rs_autotune": [_P, ctypes.POINTER(Matrix), ctypes.c_int64, ctypes.POINTER(TuneReport)],
     "rs_catalyst_solve": [_P, ctypes.POINTER(Matrix), ctypes.POINTER(Matrix), _P, _P, _P, _P, ctypes.c_int64,
                           ctypes.POINTER(SvrgParams), ctypes.POINTER(CatalystParams), _P, ctypes.POINTER(History),
                           ctypes.POINTER(ctypes.c_double)],
@@ -489,6 +496,15 @@ def rs_trace_c(ctx, X):
     M = matrix(X)
     _check(lib().rs_trace_c(ctx.h, ctypes.byref(M), ctypes.byref(out)))
     return out.value
+
+
+def rs_autotune(ctx, Z, n):
+    """Time the launch layouts of the inner loop and the full-gradient pass for components Z and keep
+    the fastest in the context; returns the report as a dict."""
+    r = TuneReport()
+    M = matrix(Z)
+    _check(lib().rs_autotune(ctx.h, ctypes.byref(M), n, ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in TuneReport._fields_}
 
 
 def rs_wait_probe(ctx, budget_cycles, complete):

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <cstdarg>
+#include <type_traits>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -28,6 +29,17 @@ enum ScratchId {
   SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_RPART, SCR_XPART, SCR_ROWSQ, SCR_SKPART, SCR_RITZ, SCR_CATB, SCR_CATB2, SCR_CATS, SCR_CATV, SCR_LINVD, SCR_JAC2, SCR_COUNT
 };
 
+// Launch choices measured by rs_autotune for one (kernel, storage type, width): chain = cluster
+// size, threads per block and ring stages; fullgrad = ring stages of the column-owner kernel.
+enum { TUNE_CHAIN = 1, TUNE_FULLGRAD = 2 };
+struct TuneEntry {
+  int32_t kind = 0, dtype = -1;
+  int64_t d = 0;
+  int32_t a = 0, b = 0, c = 0;
+  float ms = 0.0f;
+};
+constexpr int kTuneSlots = 32;
+
 struct rs_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -41,7 +53,30 @@ struct rs_ctx {
   const void* xp_src = nullptr;
   int64_t xp_n = 0, xp_d = 0, xp_ld = 0;
   uint64_t xp_gen = ~uint64_t(0);
+  TuneEntry tune[kTuneSlots];   // autotuner cache (rs_autotune); empty slots have kind 0
+  int ntune = 0;
 };
+
+// The cached choice for (kind, dtype, d), or nullptr.
+inline const TuneEntry* tune_find(const rs_ctx* ctx, int kind, int dtype, int64_t d) {
+  for (int i = 0; i < ctx->ntune; ++i)
+    if (ctx->tune[i].kind == kind && ctx->tune[i].dtype == dtype && ctx->tune[i].d == d) return &ctx->tune[i];
+  return nullptr;
+}
+inline void tune_put(rs_ctx* ctx, const TuneEntry& e) {
+  for (int i = 0; i < ctx->ntune; ++i)
+    if (ctx->tune[i].kind == e.kind && ctx->tune[i].dtype == e.dtype && ctx->tune[i].d == e.d) {
+      ctx->tune[i] = e;
+      return;
+    }
+  if (ctx->ntune < kTuneSlots) ctx->tune[ctx->ntune++] = e;
+  else ctx->tune[kTuneSlots - 1] = e;   // a full cache replaces its last entry
+}
+template <typename S> constexpr int32_t dtype_code() {
+  return std::is_same<S, double>::value ? RS_F64
+         : std::is_same<S, float>::value ? RS_F32
+         : std::is_same<S, __nv_bfloat16>::value ? RS_BF16 : RS_FP8E4M3;
+}
 
 enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 

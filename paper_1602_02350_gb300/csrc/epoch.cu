@@ -1027,14 +1027,14 @@ int choose_threads() {
 }
 
 template <typename S, typename T>
-ChainPlan plan_chain(int64_t d, int cs, size_t cap = 200 * 1024) {
+ChainPlan plan_chain(int64_t d, int cs, size_t cap = 200 * 1024, int nt_pick = 0, int max_st = 4) {
   ChainPlan p;
-  const int nt = choose_threads();
+  const int nt = nt_pick ? nt_pick : choose_threads();
   if (cs < 1 || cs > kCsMax || (cs & (cs - 1))) return p;
   const int64_t per = (d + cs - 1) / cs;
   int qn = per <= 64 ? 2 : (per <= 128 ? 4 : (per <= 256 ? 8 : 0));
   if (!qn) return p;
-  for (int st = 4; st >= 2; --st) {
+  for (int st = max_st; st >= 2; --st) {
     const size_t shm = chain_smem<S, T>(qn, st, nt);
     if (shm <= cap) {
       p.nt = nt;
@@ -1248,8 +1248,9 @@ int svrg_epoch_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, double lam, const u
       RS_LAUNCH_CHECK(ctx);
     }
   }
-  for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
-    const ChainPlan pl = plan_chain<S, T>(d, cs);
+  const TuneEntry* te = tune_find(ctx, TUNE_CHAIN, dtype_code<S>(), d);   // rs_autotune's choice, if any
+  for (int cs = te ? te->a : choose_cluster(d); cs >= 1; cs /= 2) {
+    const ChainPlan pl = plan_chain<S, T>(d, cs, 200 * 1024, te ? te->b : 0, te ? te->c : 4);
     if (!pl.cs) continue;
     int rc = RS_EUNSUPPORTED;
 #define RS_CHAIN(ST, QN)                                                                                          \
@@ -1373,8 +1374,9 @@ int epoch_finish_t(rs_ctx* ctx, const rs_matrix* Z, const uint32_t* idx, int64_t
   epoch_c_kernel<S, T><<<(unsigned)nblk, 512, cshm, ctx->stream>>>(Zd, N, Z->ld, d, idx, m, eta, mu, Rt, cv,
                                                                     Z->row_scale);
   RS_LAUNCH_CHECK(ctx);
-  for (int cs = choose_cluster(d); cs >= 1; cs /= 2) {
-    const ChainPlan pl = plan_chain<S, T>(d, cs);
+  const TuneEntry* te = tune_find(ctx, TUNE_CHAIN, dtype_code<S>(), d);   // rs_autotune's choice, if any
+  for (int cs = te ? te->a : choose_cluster(d); cs >= 1; cs /= 2) {
+    const ChainPlan pl = plan_chain<S, T>(d, cs, 200 * 1024, te ? te->b : 0, te ? te->c : 4);
     if (!pl.cs) continue;
     int rc = RS_EUNSUPPORTED;
 #define RS_CHAIN(ST, QN)                                                                                          \
@@ -1513,6 +1515,86 @@ template int epoch_prep_batched<__nv_bfloat16, float>(rs_ctx*, const ChainJob<__
                                                       int, int64_t);
 template int epoch_chain_batched<float, float>(rs_ctx*, const ChainJob<float, float>*, int, int64_t);
 template int epoch_chain_batched<__nv_bfloat16, float>(rs_ctx*, const ChainJob<__nv_bfloat16, float>*, int, int64_t);
+
+// ------------------------------------------------------------------ autotuning of the chain
+// Times the inner-loop chain on the components Z for every launch layout that fits (cluster size,
+// threads per block, ring stages) on a probe of m steps with the given index stream, and returns
+// the fastest.  The block matrices are zero for the probe: the chain's work does not depend on the
+// values, and zero keeps every iterate finite.
+template <typename S, typename T>
+int tune_chain_t(rs_ctx* ctx, const rs_matrix* Z, const uint32_t* idx, int64_t m, TuneEntry* best, int* tried) {
+  const int64_t N = Z->n, d = Z->d;
+  const S* Zd = static_cast<const S*>(Z->data);
+  const int64_t nblk = (m + kBlk - 1) / kBlk;
+  T* Rt = static_cast<T*>(rs_scratch(ctx, SCR_R, (size_t)nblk * kBlk * kBlk * sizeof(T)));
+  T* cv = static_cast<T*>(rs_scratch(ctx, SCR_C, (size_t)nblk * kBlk * sizeof(T)));
+  T* vec = static_cast<T*>(rs_scratch(ctx, SCR_TMPV, 3 * d * sizeof(T)));
+  if (!Rt || !cv || !vec) return RS_ENOMEM;
+  RS_CUDA_TRY(cudaMemsetAsync(Rt, 0, (size_t)nblk * kBlk * kBlk * sizeof(T), ctx->stream));
+  RS_CUDA_TRY(cudaMemsetAsync(cv, 0, (size_t)nblk * kBlk * sizeof(T), ctx->stream));
+  RS_CUDA_TRY(cudaMemsetAsync(vec, 0, 3 * d * sizeof(T), ctx->stream));
+  const T *mu = vec, *wbar = vec + d;
+  T* wnext = vec + 2 * d;
+  cudaEvent_t e0, e1;
+  RS_CUDA_TRY(cudaEventCreate(&e0));
+  RS_CUDA_TRY(cudaEventCreate(&e1));
+  best->kind = 0;
+  int rc_all = RS_OK;
+  for (int cs = 1; cs <= kCsMax && rc_all == RS_OK; cs *= 2) {
+    if ((d + cs - 1) / cs > 256) continue;
+    for (int nt : {256, 512}) {
+      int last_st = 0;
+      for (int st = 4; st >= 2; --st) {
+        const ChainPlan pl = plan_chain<S, T>(d, cs, 200 * 1024, nt, st);
+        if (!pl.cs || pl.stages == last_st) continue;
+        last_st = pl.stages;
+        float ms_sum = 0.0f;
+        int rc = RS_OK;
+        for (int rep = 0; rep < 4 && rc == RS_OK; ++rep) {   // one warm-up, three timed
+          if (rep == 1) RS_CUDA_TRY(cudaEventRecord(e0, ctx->stream));
+          rc = RS_EUNSUPPORTED;
+#define RS_TCHAIN(ST, QN, NT)                                                                                      \
+  if (pl.stages == ST && pl.qn == QN && pl.nt == NT)                                                               \
+    rc = launch_chain<S, T, ST, QN, NT>(ctx, pl, Zd, N, Z->ld, d, idx, m, Rt, cv, 0.0, mu, wbar, 1, wnext,          \
+                                        Z->row_scale);
+          RS_TCHAIN(4, 2, 256) RS_TCHAIN(4, 4, 256) RS_TCHAIN(4, 8, 256) RS_TCHAIN(3, 2, 256) RS_TCHAIN(3, 4, 256)
+          RS_TCHAIN(3, 8, 256) RS_TCHAIN(2, 2, 256) RS_TCHAIN(2, 4, 256) RS_TCHAIN(2, 8, 256)
+          RS_TCHAIN(4, 2, 512) RS_TCHAIN(4, 4, 512) RS_TCHAIN(4, 8, 512) RS_TCHAIN(3, 2, 512) RS_TCHAIN(3, 4, 512)
+          RS_TCHAIN(3, 8, 512) RS_TCHAIN(2, 2, 512) RS_TCHAIN(2, 4, 512) RS_TCHAIN(2, 8, 512)
+#undef RS_TCHAIN
+        }
+        if (rc == RS_EUNSUPPORTED) continue;   // this cluster shape cannot be placed
+        if (rc != RS_OK) {
+          rc_all = rc;
+          break;
+        }
+        RS_CUDA_TRY(cudaEventRecord(e1, ctx->stream));
+        RS_CUDA_TRY(cudaEventSynchronize(e1));
+        RS_CUDA_TRY(cudaEventElapsedTime(&ms_sum, e0, e1));
+        ++*tried;
+        const float ms = ms_sum / 3.0f;
+        if (!best->kind || ms < best->ms) {
+          best->kind = TUNE_CHAIN;
+          best->dtype = dtype_code<S>();
+          best->d = d;
+          best->a = pl.cs;
+          best->b = pl.nt;
+          best->c = pl.stages;
+          best->ms = ms;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc_all != RS_OK) return rc_all;
+  if (!best->kind) return rs_fail(RS_EUNSUPPORTED, "rs_autotune: no chain layout fits d = %lld", (long long)d);
+  return RS_OK;
+}
+template int tune_chain_t<float, float>(rs_ctx*, const rs_matrix*, const uint32_t*, int64_t, TuneEntry*, int*);
+template int tune_chain_t<double, double>(rs_ctx*, const rs_matrix*, const uint32_t*, int64_t, TuneEntry*, int*);
+template int tune_chain_t<__nv_bfloat16, float>(rs_ctx*, const rs_matrix*, const uint32_t*, int64_t, TuneEntry*, int*);
+template int tune_chain_t<__nv_fp8_e4m3, float>(rs_ctx*, const rs_matrix*, const uint32_t*, int64_t, TuneEntry*, int*);
 
 template int svrg_epoch_t<float, float>(rs_ctx*, const rs_matrix*, int64_t, double, const uint32_t*, const float*,
                                         int64_t, double, const float*, const float*, int, float*);

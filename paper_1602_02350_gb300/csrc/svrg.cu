@@ -19,6 +19,8 @@ int index_stream_dispatch(rs_ctx* ctx, const uint32_t* W, const uint64_t* cum, i
 int map_output_dispatch(rs_ctx* ctx, const void* V, const double* sigma2, int64_t d, int64_t k, double lam,
                         int32_t dtype, const void* wt, void* w);
 int sketch_dispatch(rs_ctx* ctx, const rs_matrix* X, const rs_sketch_params* p, void* V, double* sigma2);
+template <typename S, typename T>
+int tune_chain_t(rs_ctx* ctx, const rs_matrix* Z, const uint32_t* idx, int64_t m, TuneEntry* best, int* tried);   // epoch.cu
 int precondition_dispatch(rs_ctx* ctx, const rs_matrix* X, const void* V, const double* sigma2, int64_t k, double lam,
                           rs_matrix* Xt, void* beta, double* beta_hat);
 
@@ -606,6 +608,8 @@ static int full_gradient_t(rs_ctx* ctx, const rs_matrix* Z, const T* y, int64_t 
       const int R = RU / U;
       const int64_t rstride = (nch * 16 + 127) / 128 * 128;
       int stages = (int)std::min<int64_t>(kFcMaxStages, (int64_t)kFcSmemBudget / (R * rstride));
+      if (const TuneEntry* te = tune_find(ctx, TUNE_FULLGRAD, dtype_code<S>(), d))   // rs_autotune's choice
+        stages = std::min(stages, te->a);
       if (stages >= 2) {
         const size_t shm = (size_t)stages * R * rstride;
         const int blocks = ctx->num_sms;
@@ -1297,6 +1301,104 @@ int rs_solve_proposed(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_s
 }
 
 }  // extern "C"
+
+// ====================================================================== autotuning
+namespace {
+
+// Ring stages of the column-owner full-gradient kernel for float / bf16 rows: every stage count
+// that fits is timed on one pass over Z (one warm-up, three timed passes); the fastest is kept.
+template <typename S>
+int tune_fullgrad_t(rs_ctx* ctx, const rs_matrix* Z, int64_t n, TuneEntry* best, int* tried) {
+  const int64_t d = Z->d;
+  float* vec = static_cast<float*>(rs_scratch(ctx, SCR_CATV, (size_t)(n + 2 * d) * sizeof(float)));
+  if (!vec) return RS_ENOMEM;
+  RS_CUDA_TRY(cudaMemsetAsync(vec, 0, (size_t)(n + 2 * d) * sizeof(float), ctx->stream));
+  const float* y = vec;
+  const float* w = vec + n;
+  float* mu = vec + n + d;
+  cudaEvent_t e0, e1;
+  RS_CUDA_TRY(cudaEventCreate(&e0));
+  RS_CUDA_TRY(cudaEventCreate(&e1));
+  best->kind = 0;
+  int rc = RS_OK;
+  for (int st : {2, 3, 4, 6, 8}) {
+    TuneEntry probe;
+    probe.kind = TUNE_FULLGRAD;
+    probe.dtype = dtype_code<S>();
+    probe.d = d;
+    probe.a = st;
+    tune_put(ctx, probe);   // the dispatch reads the stage cap from the cache
+    for (int rep = 0; rep < 4 && rc == RS_OK; ++rep) {
+      if (rep == 1) RS_CUDA_TRY(cudaEventRecord(e0, ctx->stream));
+      rc = full_gradient_t<S, float>(ctx, Z, y, n, 1.0, w, mu, nullptr);
+    }
+    if (rc != RS_OK) break;
+    RS_CUDA_TRY(cudaEventRecord(e1, ctx->stream));
+    RS_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    RS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= 3.0f;
+    ++*tried;
+    if (!best->kind || ms < best->ms) {
+      *best = probe;
+      best->ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int rs_autotune(rs_ctx* ctx, const rs_matrix* Z, int64_t n, rs_tune_report* rep) {
+  RS_TRY(rs_enter(ctx));
+  RS_CHECK_ARG(Z && rep, "rs_autotune: null argument");
+  RS_TRY(check_components(Z, n, true));
+  const int64_t N = Z->n, d = Z->d;
+  *rep = rs_tune_report{};
+  const TuneEntry* ct = tune_find(ctx, TUNE_CHAIN, Z->dtype, d);
+  const bool fg_applies = Z->dtype == RS_F32 || Z->dtype == RS_BF16;
+  const TuneEntry* ft = fg_applies ? tune_find(ctx, TUNE_FULLGRAD, Z->dtype, d) : nullptr;
+  int tried = 0;
+  if (!ct) {
+    // probe: 8192 steps drawn uniformly over the N components
+    constexpr int64_t kProbe = 8192;
+    uint32_t* idx = static_cast<uint32_t*>(rs_scratch(ctx, SCR_IDX, kProbe * sizeof(uint32_t)));
+    void* inq = rs_scratch(ctx, SCR_INVNQ, kProbe * sizeof(double));
+    if (!idx || !inq) return RS_ENOMEM;
+    const int32_t dt = Z->dtype == RS_F64 ? RS_F64 : RS_F32;
+    RS_TRY(index_stream_dispatch(ctx, nullptr, nullptr, N, 0x5EEDull, 0, 0, kProbe, RS_SAMPLE_UNIFORM, dt, idx, inq));
+    TuneEntry best;
+    int rc;
+    if (Z->dtype == RS_F64) rc = tune_chain_t<double, double>(ctx, Z, idx, kProbe, &best, &tried);
+    else if (Z->dtype == RS_BF16) rc = tune_chain_t<__nv_bfloat16, float>(ctx, Z, idx, kProbe, &best, &tried);
+    else if (Z->dtype == RS_FP8E4M3) rc = tune_chain_t<__nv_fp8_e4m3, float>(ctx, Z, idx, kProbe, &best, &tried);
+    else rc = tune_chain_t<float, float>(ctx, Z, idx, kProbe, &best, &tried);
+    RS_TRY(rc);
+    tune_put(ctx, best);
+    ct = tune_find(ctx, TUNE_CHAIN, Z->dtype, d);
+  }
+  if (fg_applies && !ft) {
+    TuneEntry best;
+    const int rc = Z->dtype == RS_BF16 ? tune_fullgrad_t<__nv_bfloat16>(ctx, Z, n, &best, &tried)
+                                       : tune_fullgrad_t<float>(ctx, Z, n, &best, &tried);
+    RS_TRY(rc);
+    if (best.kind) tune_put(ctx, best);
+    ft = tune_find(ctx, TUNE_FULLGRAD, Z->dtype, d);
+  }
+  rep->chain_cluster = ct->a;
+  rep->chain_threads = ct->b;
+  rep->chain_stages = ct->c;
+  rep->chain_ms = ct->ms;
+  if (ft) {
+    rep->fullgrad_stages = ft->a;
+    rep->fullgrad_ms = ft->ms;
+  }
+  rep->candidates = tried;
+  rep->cached = tried == 0;
+  return RS_OK;
+}
 
 // ====================================================================== allocation-free variant
 //
