@@ -41,8 +41,10 @@ SINGLE = ("bf16_n1048576_d4096", "fp32_n65536_d1024")
 # extrapolation to one plain solve uses them
 PLAIN_EPOCHS = {"bf16_n1048576_d4096": 4, "fp32_n65536_d1024": 4}
 # dram__bytes_read.sum + dram__bytes_write.sum that ncu measured for one launch of the data-pass
-# kernel on each workload (None until captured for the current kernel)
-DATA_PASS_TRAFFIC = {"bf16_n1048576_d4096": None, "fp32_n65536_d1024": 276.15e6}
+# kernel on each workload.  n = 2^20: captured at 262144 + 4096 rows (2.1857 GB, --profile-kernel
+# fullgrad) and scaled by the rows to 2^20 + 4096 (the traffic is one read of every row).
+DATA_PASS_TRAFFIC = {"bf16_n1048576_d4096": 2.185742e9 * (1048576 + 4096) / (262144 + 4096),
+                     "fp32_n65536_d1024": 276.15e6}
 
 
 def _peaks():
@@ -420,7 +422,7 @@ def run_batched(args):
     ws, snaps, ems = rs.rs_solve_batched(ctx, probs, chains, S, sketch_seed=7, snapshots=True)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
-    reached, first = 0, []
+    reached, first, missed = 0, [], []
     for p in range(nprob):
         X, y, _ = probs[p]
         ne = _normal_equations(X, y)
@@ -431,13 +433,21 @@ def run_batched(args):
             if hit:
                 reached += 1
                 first.append(hit[0] + 1)
+            else:
+                # kappa^ = tr(H) / lambda_min(H) of the unpreconditioned problem (Eq. (3)), for context
+                H = ref_p[j].H
+                kap = float(torch.trace(H) / torch.linalg.eigvalsh(H)[0])
+                n_, d_, a_ = specs[p]
+                missed.append({"problem": p, "n": n_, "d": d_, "alpha": round(a_, 3), "lambda": lams[j],
+                               "m": chains[p * 8 + j]["m"], "final_rel_subopt": float(f"{rel[-1]:.3e}"),
+                               "kappa_hat": float(f"{kap:.3e}")})
         del ref_p
     out = {"metric": "batched solve time (64 problems x 8 lambda, one graph)", "value": secs, "unit": "s",
            "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False, "dtype": "bf16+f32",
            "data": "synthetic",
            "config": {"workload": f"{nprob} bf16 problems x 8 lambda, k=d/16, eta=1.5/beta^, m=n/4, {S} epochs",
                       "chains": len(chains), "inner_steps": steps, "inner_steps_per_s": steps / secs,
-                      "epoch_ms_cumulative": ems, "chains_reaching_1e-6": reached,
+                      "epoch_ms_cumulative": ems, "chains_reaching_1e-6": reached, "chains_not_reaching": missed,
                       "median_epochs_to_1e-6": float(np.median(first)) if first else None,
                       "data_bytes": int(sum(X.numel() * 2 for X, _, _ in probs))}}
     print(json.dumps(out))

@@ -485,6 +485,9 @@ __global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __res
   __shared__ float cc[160], ss[160], tt[160];
   __shared__ double red[32];
   __shared__ int rotations;
+  // pairs that rotate in the current round (compacted; their order does not matter, every 2 x 2 block
+  // is updated exactly once from its old values), double-buffered counts
+  __shared__ int act[160], isact[160], nact[2];
   const int tid = threadIdx.x, nt = blockDim.x;
   double fro = 0.0;
   for (int e = tid; e < k * (k + 1) / 2; e += nt) {
@@ -507,12 +510,16 @@ __global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __res
   __syncthreads();
   const float abs_floor = (float)(floor_ulps * red[0] * 0x1p-24);
   const int nblocks = P * (P + 1) / 2;
+  if (tid == 0) nact[0] = nact[1] = 0;
   int sweep = 0;
+  int rnd = 0;   // rounds run so far (selects the count buffer)
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) rotations = 0;
     __syncthreads();
-    for (int r = 0; r < K - 1; ++r) {
+    for (int r = 0; r < K - 1; ++r, ++rnd) {
       float4* log_r = rot_log + ((size_t)sweep * (K - 1) + r) * P;
+      const int cb_now = rnd & 1;
+      if (tid == 0) nact[cb_now ^ 1] = 0;   // the next round's count (the previous round read it)
       for (int i = tid; i < P; i += nt) {
         auto pos = [&](int j) {   // round-robin seat of player j in round r
           if (j == 0) return 0;
@@ -535,14 +542,28 @@ __global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __res
           }
         }
         pp[i] = p; qq[i] = q; cc[i] = c; ss[i] = sn; tt[i] = t;
+        isact[i] = sn != 0.0f;
+        if (sn != 0.0f) act[atomicAdd(&nact[cb_now], 1)] = i;
         log_r[i] = make_float4(__int_as_float(p), __int_as_float(q), c, sn);
       }
       __syncthreads();
-      for (int bi = tid; bi < nblocks; bi += nt) {
-        int a = (int)((sqrtf(8.0f * (float)bi + 1.0f) - 1.0f) * 0.5f);
-        while (a * (a + 1) / 2 > bi) --a;
-        while ((a + 1) * (a + 2) / 2 <= bi) ++a;
-        const int b = bi - a * (a + 1) / 2;
+      const int na = nact[cb_now];
+      if (na == 0) continue;   // nothing rotates in this round (uniform: read after the barrier)
+      // few rotating pairs: only the blocks of a row or column of one of them; many: every block
+      const bool compact = 4 * na <= P;
+      const int items = compact ? na * P : nblocks;
+      for (int bi = tid; bi < items; bi += nt) {
+        int a, b;
+        if (compact) {
+          a = act[bi / P];
+          b = bi % P;
+          if (isact[b] && b > a) continue;   // both rotate: the block is taken from b's list
+        } else {
+          a = (int)((sqrtf(8.0f * (float)bi + 1.0f) - 1.0f) * 0.5f);
+          while (a * (a + 1) / 2 > bi) --a;
+          while ((a + 1) * (a + 2) / 2 <= bi) ++a;
+          b = bi - a * (a + 1) / 2;
+        }
         const int pa = pp[a], qa = qq[a], pb = pp[b], qb = qq[b];
         if (qa >= k || qb >= k) {
           // a dummy player (odd k): only the real rotation acts; rows/columns of the dummy do not exist

@@ -170,12 +170,12 @@ def label_problem(ctx, spec, epochs=64):
                 t_pre=[t_pre[k] for k in K_GRID], trace_c=trc, sigma2=s2n[:64], status=status, **spec)
 
 
-def generate(ctx, count, seed=0, out=RUNS, log=print):
+def generate(ctx, count, seed=0, out=RUNS, log=print, n_range=(16384, 131072), d_choices=(256, 512, 1024, 2048)):
     rng = np.random.default_rng(seed)
     recs = []
     t0 = time.time()
     for i in range(count):
-        spec = draw_problem(rng)
+        spec = draw_problem(rng, n_range=tuple(n_range), d_choices=tuple(d_choices))
         rec = label_problem(ctx, spec)
         recs.append(rec)
         log(f"[{i + 1}/{count}] n={spec['n']} d={spec['d']} alpha={spec['alpha']:.2f} lam={spec['lam']:.1e} "
@@ -367,10 +367,14 @@ def main():
     ap.add_argument("--runs", default=RUNS)
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--eval-out", default=EVAL)
+    ap.add_argument("--n-range", type=int, nargs=2, default=[16384, 131072],
+                    help="training problems: n log-uniform in this range")
+    ap.add_argument("--d-choices", type=int, nargs="+", default=[256, 512, 1024, 2048],
+                    help="training problems: d drawn log-uniformly from these")
     args = ap.parse_args()
     ctx = rs.Context(0)
     if args.what in ("generate", "all"):
-        generate(ctx, args.count, seed=args.seed, out=args.runs)
+        generate(ctx, args.count, seed=args.seed, out=args.runs, n_range=args.n_range, d_choices=args.d_choices)
     if args.merge:
         merge_runs(args.merge, args.runs)
     if args.what in ("train", "all", "train+evaluate"):

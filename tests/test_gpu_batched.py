@@ -129,3 +129,29 @@ def test_batched_many_chains_per_problem(rsctx, nchains):
                                  eta_mult=1.0, X=X, refine=True)
         err = (w - w1).norm().item() / w1.norm().item()
         assert err <= 1e-4, (ch, err)
+
+
+def test_batched_chains_follow_the_oracle(rsctx, small_batch):
+    """Every chain of a batched call against the oracle's Alg. 1 replayed in float64 on the same
+    components (from the same sketch seed), smoothness constants (so the same integer weights and
+    index stream), step size and epoch length: ||w - w_oracle|| / ||w_oracle|| <= 1e-4 (FP32)."""
+    from oracle import precond, svrg
+    probs = small_batch
+    k, epochs = 8, 3
+    chains = [dict(problem=p, lam=lam, eta_mult=1.0, m=probs[p][0].shape[0], seed=200 + p)
+              for p in range(len(probs)) for lam in (1e-3, 3e-5)]
+    ws, _, _ = rs.rs_solve_batched(rsctx, [(X, y, k) for X, y, _, _ in probs], chains, epochs, sketch_seed=60,
+                                   refine=False)
+    for ch, w in zip(chains, ws):
+        X, y, Xn, yn = probs[ch["problem"]]
+        n = Xn.shape[0]
+        lam = ch["lam"]
+        V, s2 = rs.rs_sketch(rsctx, X, k, 60 + ch["problem"])
+        _, beta, _ = rs.rs_precondition(rsctx, X, V, s2, lam)
+        M = precond.m_matrix(V.double().cpu().numpy(), s2.cpu().numpy(), lam)
+        Zr, yz, g = precond.components(*precond.transform(Xn, M), yn, lam)
+        b = beta.double().cpu().numpy()
+        snaps = svrg.solve(Zr, yz, g, b, ch["eta_mult"] / precond.beta_hat(b), ch["m"], epochs, ch["seed"])
+        wr = M @ snaps[-1]
+        err = np.linalg.norm(w.double().cpu().numpy() - wr) / np.linalg.norm(wr)
+        assert err <= 1e-4, (ch, err)
