@@ -494,21 +494,6 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   const uint32_t bar_remote0 = map_rank(smem_u32(&mbar[0]), dst);
   const uint32_t bar_remote1 = map_rank(smem_u32(&mbar[1]), dst);
 
-  constexpr int RPT = B / H;   // R entries per thread
-  const int jr = tid / H, hr = tid % H;
-  T rreg[RPT];
-  T creg = T(0);
-  auto load_r = [&](int64_t blk) {
-    const T* rsrc = Rt + blk * (int64_t)B * B + jr;
-#pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-      const int l = hr + H * t;
-      rreg[t] = l <= jr ? __ldg(rsrc + l * B) : T(0);
-    }
-    creg = hr == 0 ? __ldg(cvec + blk * B + jr) : T(0);
-  };
-  if (nblk > 0) load_r(0);
-
   for (int64_t blk = 0; blk < nblk; ++blk) {
     // row indices are read one block ahead of when they enter the ring, so the load's latency is
     // hidden behind a whole block of steps
@@ -525,9 +510,23 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
     const float myscale = (F8 && tid < B) ? sscale[slot * B + tid] : 1.0f;   // row tid of this block
     const int Bb = (int)min64(B, m - blk * B);
     const S* zs = Zs + (size_t)slot * B * ZS;
-    // this block's R entries and c_j were loaded into registers during the previous block (rreg,
-    // creg, issued after its R p step), so their L2 latency is off the critical path.  Thread (j, h)
-    // with j = tid / H takes the terms l = h, h + H, ... of row j of R p.
+    // this block's R entries and c_j go straight from L2 into registers: issued here, used after the
+    // exchange, so their latency is hidden behind the dot products (issuing them one block earlier,
+    // during the update, measured slower: the loads then compete with the update's shared-memory
+    // traffic).  Thread (j, h) with j = tid / H takes the terms l = h, h + H, ... of row j of R p.
+    constexpr int RPT = B / H;   // R entries per thread
+    T rreg[RPT];
+    T creg = T(0);
+    const int jr = tid / H, hr = tid % H;
+    {
+      const T* rsrc = Rt + blk * (int64_t)B * B + jr;
+#pragma unroll
+      for (int t = 0; t < RPT; ++t) {
+        const int l = hr + H * t;
+        rreg[t] = l <= jr ? __ldg(rsrc + l * B) : T(0);
+      }
+      if (hr == 0) creg = __ldg(cvec + blk * B + jr);
+    }
     // the warp's rows of the staged slice, 16 bytes per chunk, kept for the update
     uint4 zr[RPW][CPL];
     T part[RPW];
@@ -602,10 +601,8 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
       T sa = s0 + s1;
 #pragma unroll
       for (int o = 1; o < H; o <<= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
-      const T cj = creg;
-      if (blk + 1 < nblk) load_r(blk + 1);   // next block's R and c, in flight during this block's update
       if (hr == 0) {
-        sa += cj;
+        sa += creg;
         // FP8 codes: the update multiplies stored codes, so a_j carries row j's scale (the slot's
         // scales are replaced only after the barrier below)
         const T a = F8 ? sa * (T)sscale[slot * B + jr] : sa;
