@@ -172,11 +172,25 @@ def run_rs(args):
                                     z_dtype=torch.bfloat16, snapshots=snapshots, w_out=w_out, **sk)
 
     if big:
-        def chosen(epochs, snapshots=False, X=Xc, yy=y, w_out=None):
-            return rs.rs_solve(ctx, X, yy, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, m=m_plain,
-                               eta_mult=em_plain, snapshots=snapshots, refine=True, w_out=w_out, **sk)
-        chosen_text = {"components": "bf16 from the bf16 data, snapshot gradients refined on the stored data",
-                       "k": k, "eta_mult": em_plain, "m": m_plain}
+        # the configured rank k; the network proposes eta and m from the first 64 Ritz values of the
+        # rank-k sketch (rs_solve_proposed with a fixed rank), unless it falls back, when the chosen
+        # form keeps the plain form's eta and m
+        probe = rs.rs_solve_proposed(ctx, Xc, y, lam, 0, cfg.seed_sketch, cfg.seed_svrg, theta=theta, norm=norm,
+                                     k_fixed=k, **sk)[1] if theta is not None else {"fallback": True}
+        if not probe["fallback"]:
+            def chosen(epochs, snapshots=False, X=Xc, yy=y, w_out=None):
+                return rs.rs_solve_proposed(ctx, X, yy, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, theta=theta,
+                                            norm=norm, snapshots=snapshots, w_out=w_out, k_fixed=k, **sk)
+            chosen_text = {"components": "bf16 from the bf16 data, snapshot gradients refined on the stored data",
+                           "k": k, "eta_mult": probe["eta_mult"], "m": probe["m"],
+                           "proposal": "network (eta, m) at the configured rank k"}
+        else:
+            def chosen(epochs, snapshots=False, X=Xc, yy=y, w_out=None):
+                return rs.rs_solve(ctx, X, yy, k, lam, epochs, cfg.seed_sketch, cfg.seed_svrg, m=m_plain,
+                                   eta_mult=em_plain, snapshots=snapshots, refine=True, w_out=w_out, **sk)
+            chosen_text = {"components": "bf16 from the bf16 data, snapshot gradients refined on the stored data",
+                           "k": k, "eta_mult": em_plain, "m": m_plain,
+                           "proposal": "plain eta and m (the network falls back on this problem)"}
     else:
         chosen = proposed
         chosen_text = {"components": "bf16, snapshot gradients refined on the fp32 data",

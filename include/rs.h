@@ -459,7 +459,9 @@ typedef struct {
 /* Propose (k, eta_mult, m) for a problem with sketched eigenvalues sigma2 (host double, 64,
  * descending: the first 64 of an Alg. 2 sketch of rank >= 64), regularisation lambda, size n x d
  * and trace_c = tr(C) = ||X||_F^2 / n.  With theta (device) and norm (host) the network runs
- * on the GPU; its proposal is k = round(2^o0) (clamped to [1, min(64, d)]), eta_mult = e^o1,
+ * on the GPU on the inputs 0.5 log(sigma2_i / sigma2_0) (i < 64), log(lambda / sigma2_0), log n,
+ * log d (invariant to the scale of X), normalised by norm and clipped to +-3; its proposal is
+ * k = round(2^o0) (clamped to [1, min(64, d)]), eta_mult = e^o1,
  * m = round(n 2^o2).  The theory setting is used instead (*used_fallback = 1) when theta is
  * NULL or an output is non-finite or outside eta_mult in [0.01, 8], m / n in [2^-8, 2^6]:
  * k minimises n d k + (kappa~(k) + n + d) d with kappa~(k) = (k sigma_k^2 + tr(C)
@@ -469,13 +471,16 @@ int rs_propose(rs_ctx* ctx, const float* theta, const rs_mlp_norm* norm, const d
                int64_t n, int64_t d, double trace_c, int32_t* k, double* eta_mult, int64_t* m,
                int32_t* used_fallback);
 
-/* Alg. 3 with proposed parameters, end to end: a rank-64 sketch of X (Alg. 2 with sp, whose k is
- * replaced by 64; d >= 64), tr(C), rs_propose (theta / norm as there; NULL = theory setting),
+/* Alg. 3 with proposed parameters, end to end: a rank-64 sketch of X (Alg. 2 with sp; sp->k <= 64
+ * is replaced by 64; d >= 64), tr(C), rs_propose (theta / norm as there; NULL = theory setting),
  * the components of Eq. (11) / Sec. 5.1 from the leading k Ritz pairs, stored as z_dtype
  * (X->dtype, or RS_BF16 for RS_F32 data: then the snapshot gradients are refined on X), and
  * p->epochs epochs of Alg. 1 with eta = eta_mult / beta^ and the proposed m (p->eta, p->eta_mult
- * and p->m are ignored).  X, y and w_out may be host pointers as in rs_solve.  k, eta_mult, m,
- * used_fallback (host, nullable) receive the parameters used.  Synchronises. */
+ * and p->m are ignored).  With sp->k > 64 the caller fixes the rank instead: the sketch has rank
+ * sp->k (<= d), its first 64 Ritz values are the network's input, the preconditioner keeps all
+ * sp->k pairs and only eta_mult and m are proposed (*k returns sp->k).  X, y and w_out may be
+ * host pointers as in rs_solve.  k, eta_mult, m, used_fallback (host, nullable) receive the
+ * parameters used.  Synchronises. */
 int rs_solve_proposed(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp,
                       const rs_svrg_params* p, const float* theta, const rs_mlp_norm* norm, int32_t z_dtype,
                       void* w_out, rs_history* hist, int32_t* k, double* eta_mult, int64_t* m,

@@ -120,6 +120,18 @@ def adam_step(theta, m, v, g, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def features(sigma2_64, lam, n, d):
     """Network input: log of the 64 leading sketched singular values (sqrt of sigma~_i^2, floored
-    at 1e-30), log lam, log n, log d."""
+    at 1e-30) and log lam, both relative to the leading value (log(s_i / s_1), log(lam / s_1^2)), then
+    log n, log d.  Scaling X by c scales every sigma~_i^2 and the lam of the equivalent problem by
+    c^2 and leaves (k, eta beta^, m) unchanged, so the input is taken invariant to it."""
     s = np.sqrt(np.maximum(np.asarray(sigma2_64, np.float64)[:64], 1e-60))
-    return np.concatenate([np.log(np.maximum(s, 1e-30)), [np.log(lam), np.log(n), np.log(d)]])
+    ls = np.log(np.maximum(s, 1e-30))
+    return np.concatenate([ls - ls[0], [np.log(lam) - 2.0 * ls[0], np.log(n), np.log(d)]])
+
+
+INPUT_CLIP = 3.0   # normalised inputs are clipped to +-INPUT_CLIP (training spreads) before the network
+
+
+def network_input(x, in_mean, in_std):
+    """(x - in_mean) / in_std, clipped to [-INPUT_CLIP, INPUT_CLIP]: a problem outside the training
+    ranges (larger n, a smaller lam) is proposed for as if at their edge instead of extrapolating."""
+    return np.clip((np.asarray(x, np.float64) - in_mean) / in_std, -INPUT_CLIP, INPUT_CLIP)

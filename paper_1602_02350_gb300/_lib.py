@@ -609,15 +609,17 @@ def rs_propose(ctx, sigma2, lam, n, d, trace_c, theta=None, norm=None):
 
 
 def rs_solve_proposed(ctx, X, y, lam, epochs, sketch_seed, svrg_seed, theta=None, norm=None, kind="gaussian", s=0,
-                      q=1, z_dtype=None, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False, w_out=None):
-    """Alg. 3 with proposed (k, eta, m).  X / y / w_out may be CUDA or (pinned) CPU tensors.
+                      q=1, z_dtype=None, sampling=RS_SAMPLE_IMPORTANCE, average=True, snapshots=False, w_out=None,
+                      k_fixed=0):
+    """Alg. 3 with proposed (k, eta, m), or with k_fixed > 64 the sketch rank fixed by the caller and
+    only (eta, m) proposed.  X / y / w_out may be CUDA or (pinned) CPU tensors.
     Returns (w, info) with info holding k, eta_mult, m, fallback and the epoch history."""
     d = X.shape[1]
     ct = torch.float64 if X.dtype == torch.float64 else torch.float32
     if w_out is None:
         w_out = ctx._empty(d, dtype=ct) if X.is_cuda else torch.empty(d, dtype=ct)
     M = Matrix(X.data_ptr(), None, X.shape[0], d, X.stride(0), _DT[X.dtype], 0)
-    sp = _sketch_params(64, sketch_seed, kind, s, q)
+    sp = _sketch_params(max(64, int(k_fixed)), sketch_seed, kind, s, q)
     zt = _DT[z_dtype] if z_dtype is not None else _DT[X.dtype]
     p = _svrg_params(lam, epochs, svrg_seed, 0.0, 0.0, 0, 0, sampling, average, refine=zt != _DT[X.dtype] or
                      X.dtype == torch.bfloat16)

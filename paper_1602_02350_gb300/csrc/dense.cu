@@ -345,6 +345,74 @@ __global__ void chol_inv_kernel(const double* G, int k, C* buf, T* Linv_out, int
   for (int e = tid; e < k * k; e += nt) Linv_out[e] = (T)Xi[(e / k) * LD + e % k];
 }
 
+// The same factorisation for k up to a few hundred with the packed lower triangle of L in shared
+// memory (row i at i (i + 1) / 2), overwritten in place by L^{-1}.  Cholesky by columns (pivot, the
+// column scaled into a contiguous buffer, rank-1 update of the trailing triangle by warp rows);
+// then the inverse by columns from the last (x = L[j+1:, j] from the buffer, x <- -L^{-1}[j+1:, j+1:]
+// x / l_jj by one warp per row with shuffle sums).  Linv_out: Tout, k x k row-major, zero above the
+// diagonal.  status bit 4 on a non-positive pivot (replaced by 1).
+template <typename C, typename Tout>
+__global__ void __launch_bounds__(1024) chol_inv_packed_kernel(const double* __restrict__ G, int k,
+                                                               Tout* __restrict__ Linv_out, int* status) {
+  extern __shared__ __align__(16) unsigned char cp_raw[];
+  C* L = reinterpret_cast<C*>(cp_raw);
+  C* col = L + (size_t)k * (k + 1) / 2;   // [k]
+  __shared__ C piv;
+  const int tid = threadIdx.x, nt = blockDim.x, nw = nt >> 5, wid = tid >> 5, ln = tid & 31;
+  auto row = [](int i) { return i * (i + 1) / 2; };
+  for (int i = wid; i < k; i += nw)
+    for (int j = ln; j <= i; j += 32) L[row(i) + j] = (C)G[(size_t)i * k + j];
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      C v = L[row(j) + j];
+      if (!(v > C(0)) || !isfinite(v)) {
+        atomicOr(status, 4);
+        v = C(1);
+      }
+      const C r = sqrt(v);
+      L[row(j) + j] = r;
+      piv = C(1) / r;
+    }
+    __syncthreads();
+    const C rj = piv;
+    for (int i = j + 1 + tid; i < k; i += nt) {
+      const C v = L[row(i) + j] * rj;
+      L[row(i) + j] = v;
+      col[i] = v;
+    }
+    __syncthreads();
+    for (int i = j + 1 + wid; i < k; i += nw) {
+      const C lij = col[i];
+      C* Li = L + row(i);
+      for (int l = j + 1 + ln; l <= i; l += 32) Li[l] = fma(-lij, col[l], Li[l]);
+    }
+    __syncthreads();
+  }
+  for (int j = k - 1; j >= 0; --j) {
+    for (int i = j + 1 + tid; i < k; i += nt) col[i] = L[row(i) + j];
+    if (tid == 0) L[row(j) + j] = C(1) / L[row(j) + j];
+    __syncthreads();
+    const C ajj = -L[row(j) + j];
+    for (int i = j + 1 + wid; i < k; i += nw) {
+      const C* Li = L + row(i);
+      C acc = C(0);
+      for (int l = j + 1 + ln; l <= i; l += 32) acc = fma(Li[l], col[l], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (ln == 0) L[row(i) + j] = ajj * acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e / k, j = e % k;
+    Linv_out[e] = j <= i ? (Tout)L[row(i) + j] : Tout(0);
+  }
+}
+
+constexpr size_t kCholPackedMax = 200 * 1024;
+template <typename C> size_t chol_packed_bytes(int64_t k) { return ((size_t)k * (k + 1) / 2 + (size_t)k) * sizeof(C); }
+
 // ------------------------------------------------------------------ Jacobi eigensolver
 // Cyclic Jacobi with round-robin pairing: each round rotates k/2 disjoint (p,q) planes at once.
 // A plane is rotated only if |a_pq| exceeds both tol sqrt|a_pp a_qq| and an absolute floor of a
@@ -509,7 +577,6 @@ __global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __res
   }
   __syncthreads();
   const float abs_floor = (float)(floor_ulps * red[0] * 0x1p-24);
-  const int nblocks = P * (P + 1) / 2;
   if (tid == 0) nact[0] = nact[1] = 0;
   int sweep = 0;
   int rnd = 0;   // rounds run so far (selects the count buffer)
@@ -549,35 +616,22 @@ __global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __res
       __syncthreads();
       const int na = nact[cb_now];
       if (na == 0) continue;   // nothing rotates in this round (uniform: read after the barrier)
-      // few rotating pairs: only the blocks of a row or column of one of them; many: every block
-      const bool compact = 4 * na <= P;
-      const int items = compact ? na * P : nblocks;
-      for (int bi = tid; bi < items; bi += nt) {
-        int a, b;
-        if (compact) {
-          a = act[bi / P];
-          b = bi % P;
-          if (isact[b] && b > a) continue;   // both rotate: the block is taken from b's list
-        } else {
-          a = (int)((sqrtf(8.0f * (float)bi + 1.0f) - 1.0f) * 0.5f);
-          while (a * (a + 1) / 2 > bi) --a;
-          while ((a + 1) * (a + 2) / 2 <= bi) ++a;
-          b = bi - a * (a + 1) / 2;
-        }
+      // every 2 x 2 block (a, b), b <= a, of the round's planes, rotated from both sides from its old values
+      auto upd = [&](int a, int b) {
         const int pa = pp[a], qa = qq[a], pb = pp[b], qb = qq[b];
         if (qa >= k || qb >= k) {
           // a dummy player (odd k): only the real rotation acts; rows/columns of the dummy do not exist
-          if (a == b || (qa >= k && qb >= k)) continue;
+          if (a == b || (qa >= k && qb >= k)) return;
         }
         const float sa = ss[a], sb = ss[b];
-        if (sa == 0.0f && sb == 0.0f) continue;
+        if (sa == 0.0f && sb == 0.0f) return;
         if (a == b) {
           const int ipq = tri_idx(qa, pa);
           const float apq = A[ipq], t = tt[a];
           A[tri_idx(pa, pa)] -= t * apq;
           A[tri_idx(qa, qa)] += t * apq;
           A[ipq] = 0.0f;
-          continue;
+          return;
         }
         const float ca = cc[a], cb = cc[b];
         // M = [A(pa, pb) A(pa, qb); A(qa, pb) A(qa, qb)], rows of a dummy player are absent
@@ -595,6 +649,20 @@ __global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __res
         if (rb) A[i01] = sb * r00 + cb * r01;
         if (ra) A[i10] = cb * r10 - sb * r11;
         if (ra && rb) A[i11] = sb * r10 + cb * r11;
+      };
+      if (4 * na <= P) {
+        // few rotating pairs: only the blocks of a row or column of one of them
+        for (int bi = tid; bi < na * P; bi += nt) {
+          const int a = act[bi / P], b = bi % P;
+          if (isact[b] && b > a) continue;   // both rotate: the block is taken from b's list
+          upd(a, b);
+        }
+      } else {
+        // every block: warp w takes the rows a = w, w + 32, ... of the triangle (equal numbers of
+        // 32-wide column passes per warp), lanes the columns b <= a
+        const int nw = nt >> 5, wid = tid >> 5, ln = tid & 31;
+        for (int a = wid; a < P; a += nw)
+          for (int b = ln; b <= a; b += 32) upd(a, b);
       }
       __syncthreads();
     }
@@ -1218,6 +1286,8 @@ int run_sym_eig(rs_ctx* ctx, const double* G, int64_t k, int32_t prec, double* e
 
 // ---------------------------------------------------------------------- Alg. 2 pieces
 
+static int read_status(rs_ctx* ctx, int* st);
+
 template <typename T>
 static int orthonormalize_t(rs_ctx* ctx, const T* Y, int64_t d, int64_t k, T* Q) {
   double* G = static_cast<double*>(rs_scratch(ctx, SCR_GRAM, k * k * sizeof(double)));
@@ -1245,21 +1315,51 @@ static int orthonormalize_t(rs_ctx* ctx, const T* Y, int64_t d, int64_t k, T* Q)
       // float Y: Y L^{-T} is also formed in double.  A float product would perturb span(Y) by about
       // 2^-24 cond(Y)^2 (its rounding relative to |Y| |L^{-1}|, divided by the smallest singular value
       // of Y), which for graded spectra scrambles the weakest directions of the sketch and with them
-      // the smallest Ritz values; in double the perturbation is 2^-53 cond(Y)^2.
+      // the smallest Ritz values; in double the perturbation is 2^-53 cond(Y)^2.  L itself only sets
+      // how orthonormal this first basis comes out (span(Y L^{-T}) = span(Y) for any invertible L),
+      // so it is factored in float on chip when its packed triangle fits (the second pass restores
+      // orthonormality), and in double when the float pivots break down (cond(Y)^2 near 2^24).
       double* Ld = static_cast<double*>(rs_scratch(ctx, SCR_LINVD, k * k * sizeof(double)));
       if (!Ld) return RS_ENOMEM;
-      RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)shm));
-      chol_inv_kernel<double, double><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Ld, ctx->d_status);
-      RS_LAUNCH_CHECK(ctx);
+      bool done = false;
+      if (chol_packed_bytes<float>(k) <= kCholPackedMax) {
+        const size_t ps = chol_packed_bytes<float>(k);
+        int st0 = 0, st = 0;
+        RS_TRY(read_status(ctx, &st0));   // the status word accumulates over the whole sketch
+        RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_packed_kernel<float, double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps));
+        chol_inv_packed_kernel<float, double><<<1, 1024, ps, ctx->stream>>>(G, (int)k, Ld, ctx->d_status);
+        RS_LAUNCH_CHECK(ctx);
+        RS_TRY(read_status(ctx, &st));
+        done = (st & 4) == 0 || (st0 & 4) != 0;
+        if (!done) RS_CUDA_TRY(cudaMemcpy(ctx->d_status, &st0, sizeof(int), cudaMemcpyHostToDevice));   // retry in double
+      }
+      if (!done) {
+        RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)shm));
+        chol_inv_kernel<double, double><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Ld, ctx->d_status);
+        RS_LAUNCH_CHECK(ctx);
+      }
       RS_TRY(launch_gemm<double, T, T, T>(ctx, d, k, k, 1.0, src, k, 1, Ld, 1, k, 0.0, nullptr, 0, dst, k, nullptr));
       src = dst;
       continue;
     }
-    if (pass == 0)
-      chol_inv_kernel<T, double><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Linv, ctx->d_status);
-    else
+    if (pass == 0) {
+      if (chol_packed_bytes<double>(k) <= kCholPackedMax) {
+        RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_packed_kernel<double, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)chol_packed_bytes<double>(k)));
+        chol_inv_packed_kernel<double, T><<<1, 1024, chol_packed_bytes<double>(k), ctx->stream>>>(G, (int)k, Linv,
+                                                                                                 ctx->d_status);
+      } else {
+        chol_inv_kernel<T, double><<<1, 256, shm, ctx->stream>>>(G, (int)k, buf, Linv, ctx->d_status);
+      }
+    } else if (chol_packed_bytes<T>(k) <= kCholPackedMax) {
+      RS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_packed_kernel<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)chol_packed_bytes<T>(k)));
+      chol_inv_packed_kernel<T, T><<<1, 1024, chol_packed_bytes<T>(k), ctx->stream>>>(G, (int)k, Linv, ctx->d_status);
+    } else {
       chol_inv_kernel<T, T><<<1, 256, shm, ctx->stream>>>(G, (int)k, reinterpret_cast<T*>(buf), Linv, ctx->d_status);
+    }
     RS_LAUNCH_CHECK(ctx);
     // Q = Y L^{-T}: B(p, j) = Linv[j][p]
     RS_TRY(launch_gemm<T>(ctx, d, k, k, 1.0, src, k, 1, Linv, 1, k, 0.0, nullptr, 0, dst, k, nullptr));

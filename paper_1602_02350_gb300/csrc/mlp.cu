@@ -9,6 +9,7 @@
 namespace {
 
 constexpr int IN = RS_MLP_IN, HID = RS_MLP_HIDDEN, OUT = RS_MLP_OUT, NP = RS_MLP_NPARAM;
+constexpr float kInputClip = 3.0f;   // normalised inputs are clipped to this many training spreads
 constexpr int OW1 = 0, OB1 = OW1 + HID * IN, OW2 = OB1 + HID, OB2 = OW2 + HID * HID, OW3 = OB2 + HID,
               OB3 = OW3 + OUT * HID;
 static_assert(OB3 + OUT == NP, "parameter layout");
@@ -268,11 +269,15 @@ int rs_propose(rs_ctx* ctx, const float* theta, const rs_mlp_norm* norm, const d
   *used_fallback = 1;
   if (!theta || !norm) return RS_OK;
   float x[IN];
-  for (int j = 0; j < 64; ++j) x[j] = (float)(0.5 * std::log(std::fmax(sigma2[j], 1e-60)));
-  x[64] = (float)std::log(lambda);
+  // log-spectrum and log lambda relative to the leading sketched value (invariant to the scale of
+  // X), log n, log d; normalised, then clipped to kInputClip training spreads
+  const double ls0 = 0.5 * std::log(std::fmax(sigma2[0], 1e-60));
+  for (int j = 0; j < 64; ++j) x[j] = (float)(0.5 * std::log(std::fmax(sigma2[j], 1e-60)) - ls0);
+  x[64] = (float)(std::log(lambda) - 2.0 * ls0);
   x[65] = (float)std::log((double)n);
   x[66] = (float)std::log((double)d);
-  for (int j = 0; j < IN; ++j) x[j] = (x[j] - norm->in_mean[j]) / norm->in_std[j];
+  for (int j = 0; j < IN; ++j)
+    x[j] = std::fmin(std::fmax((x[j] - norm->in_mean[j]) / norm->in_std[j], -kInputClip), kInputClip);
   float* io = static_cast<float*>(rs_scratch(ctx, SCR_MLP_IO, (IN + OUT) * sizeof(float)));
   if (!io) return RS_ENOMEM;
   RS_CUDA_TRY(cudaMemcpyAsync(io, x, IN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));

@@ -936,7 +936,9 @@ template <typename S, typename T, typename ZS>
 static int solve_proposed_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, const rs_sketch_params* sp,
                             const rs_svrg_params* p, const float* theta, const rs_mlp_norm* norm, void* w_out,
                             rs_history* hist, int32_t* k_out, double* eta_out, int64_t* m_out, int32_t* fb_out) {
-  const int64_t n = Xin->n, d = Xin->d, N = n + d, K = 64;
+  const int64_t n = Xin->n, d = Xin->d, N = n + d;
+  // sketch rank: 64 (the network's input) unless the caller fixes a larger preconditioner rank
+  const int64_t K = sp->k > 64 ? (int64_t)sp->k : 64;
   rs_matrix X = *Xin;
   const size_t es = sizeof(T), ss = sizeof(S), zs = sizeof(ZS);
   if (is_host_ptr(Xin->data)) {
@@ -973,6 +975,7 @@ static int solve_proposed_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, 
     RS_TRY(rs_propose(ctx, theta, norm, s2h, p->lambda, n, d, trc, &k, &em, &m, &fb));
     ctx->call_gen = gen;
   }
+  if (K > 64) k = (int32_t)K;   // fixed rank: only eta and m are proposed
   T* Vk = static_cast<T*>(rs_scratch(ctx, SCR_VK, d * k * es));
   const int64_t ldz = (d * (int64_t)zs + 15) / 16 * 16 / (int64_t)zs;
   ZS* Zbuf = static_cast<ZS*>(rs_scratch(ctx, SCR_Z, (size_t)N * ldz * zs));
@@ -1279,6 +1282,7 @@ int rs_solve_proposed(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_s
   RS_TRY(rs_enter(ctx));
   RS_CHECK_ARG(X && X->data && y && sp && p && w_out, "rs_solve_proposed: null argument");
   RS_CHECK_ARG(X->n >= 1 && X->d >= 64 && X->ld >= X->d, "rs_solve_proposed: need d >= 64 (rank-64 sketch)");
+  RS_CHECK_ARG(sp->k <= 64 || sp->k <= X->d, "rs_solve_proposed: a fixed rank k > 64 needs k <= d");
   RS_CHECK_ARG((X->ld * (int64_t)dtype_size(X->dtype)) % 16 == 0,
                "rs_solve_proposed: row stride must be a multiple of 16 bytes");
   RS_CHECK_ARG(p->lambda > 0.0 && p->epochs >= 0, "rs_solve_proposed: bad SVRG parameters");

@@ -47,16 +47,24 @@ TARGET = 1e-6
 # ------------------------------------------------------------------ problems and reference solutions
 
 def draw_problem(rng, n_range=(16384, 131072), d_choices=(256, 512, 1024, 2048), alpha=(1.0, 2.5),
-                 lam=(1e-7, 1e-3)):
+                 lam=(1e-7, 1e-3), spike_prob=0.0):
+    """A training or evaluation problem: n log-uniform, d from d_choices, spectrum j^-alpha; with
+    probability spike_prob the leading r ~ U{5..40} eigenvalues are also multiplied by s, log-uniform
+    in [10, 1000] (a few dominant directions over the power law)."""
     n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1]))) / 64) * 64)
     d = int(d_choices[int(rng.integers(len(d_choices)))])
-    return dict(n=n, d=d, alpha=float(rng.uniform(*alpha)), lam=float(math.exp(rng.uniform(math.log(lam[0]),
+    spec = dict(n=n, d=d, alpha=float(rng.uniform(*alpha)), lam=float(math.exp(rng.uniform(math.log(lam[0]),
                                                                                           math.log(lam[1])))),
-                seed=int(rng.integers(1 << 30)))
+                seed=int(rng.integers(1 << 30)), spike_r=0, spike_s=1.0)
+    if spike_prob > 0.0 and rng.uniform() < spike_prob:
+        spec["spike_r"] = int(rng.integers(5, 41))
+        spec["spike_s"] = float(math.exp(rng.uniform(math.log(10.0), math.log(1000.0))))
+    return spec
 
 
 def make_data(spec, device="cuda"):
     spectrum = np.arange(1, spec["d"] + 1, dtype=np.float64) ** -spec["alpha"]
+    spectrum[:spec.get("spike_r", 0)] *= spec.get("spike_s", 1.0)
     X, y, _ = synth.problem(spec["n"], spec["d"], spectrum, 0.05, spec["seed"], device=device, dtype=torch.float32)
     return X.contiguous(), y.float().contiguous()
 
@@ -102,6 +110,13 @@ def _timed(fn):
     return out, a.elapsed_time(b)
 
 
+def network_features(sigma2, lam, n, d):
+    """The network's input as rs_propose forms it: 0.5 log(sigma2_i / sigma2_0) for the 64 leading
+    sketched values, log(lam / sigma2_0), log n, log d (invariant to the scale of X)."""
+    ls = 0.5 * np.log(np.maximum(np.asarray(sigma2, np.float64)[:64], 1e-60))
+    return np.concatenate([ls - ls[0], [math.log(lam) - 2.0 * ls[0], math.log(n), math.log(d)]])
+
+
 def features(ctx, X, lam, seed):
     V, s2 = rs.rs_sketch(ctx, X, 64, seed)
     trc = rs.rs_trace_c(ctx, X)
@@ -116,7 +131,7 @@ def label_problem(ctx, spec, epochs=64):
     ref = Reference(X, y, lam)
     _, s2, trc = features(ctx, X, lam, spec["seed"] + 1)
     s2n = s2.cpu().numpy()
-    feat = np.concatenate([0.5 * np.log(np.maximum(s2n[:64], 1e-60)), [math.log(lam), math.log(n), math.log(d)]])
+    feat = network_features(s2n, lam, n, d)
     # measured costs on this problem: preconditioning per k, full gradient, one inner step
     t_pre = {}
     rs.rs_precondition(ctx, X, *rs.rs_sketch(ctx, X, 32, 5), lam)          # warm-up
@@ -170,19 +185,20 @@ def label_problem(ctx, spec, epochs=64):
                 t_pre=[t_pre[k] for k in K_GRID], trace_c=trc, sigma2=s2n[:64], status=status, **spec)
 
 
-def generate(ctx, count, seed=0, out=RUNS, log=print, n_range=(16384, 131072), d_choices=(256, 512, 1024, 2048)):
+def generate(ctx, count, seed=0, out=RUNS, log=print, n_range=(16384, 131072), d_choices=(256, 512, 1024, 2048),
+             spike_prob=0.0):
     rng = np.random.default_rng(seed)
     recs = []
     t0 = time.time()
     for i in range(count):
-        spec = draw_problem(rng, n_range=tuple(n_range), d_choices=tuple(d_choices))
+        spec = draw_problem(rng, n_range=tuple(n_range), d_choices=tuple(d_choices), spike_prob=spike_prob)
         rec = label_problem(ctx, spec)
         recs.append(rec)
         log(f"[{i + 1}/{count}] n={spec['n']} d={spec['d']} alpha={spec['alpha']:.2f} lam={spec['lam']:.1e} "
             f"reached={rec['reached']} target={np.round(rec['target'], 2)} ({time.time() - t0:.0f} s)")
     keys = ["features", "target", "times", "sigma2"]
     arrs = {k: np.stack([r[k] for r in recs]) for k in keys}
-    for k in ("reached", "t_step", "t_fg", "trace_c", "n", "d", "alpha", "lam", "seed"):
+    for k in ("reached", "t_step", "t_fg", "trace_c", "n", "d", "alpha", "lam", "seed", "spike_r", "spike_s"):
         arrs[k] = np.array([r[k] for r in recs])
     arrs["t_pre"] = np.array([r["t_pre"] for r in recs])
     np.savez_compressed(out, **arrs)
@@ -206,15 +222,23 @@ def soft_targets(times, n, tol=1.1):
 
 
 def merge_runs(paths, out):
+    """Concatenate run records; records made before the spiked spectra count as spike_r = 0."""
     parts = [dict(np.load(p)) for p in paths]
-    np.savez_compressed(out, **{k: np.concatenate([q[k] for q in parts]) for k in parts[0]})
+    for q in parts:
+        q.setdefault("spike_r", np.zeros(len(q["n"]), np.int64))
+        q.setdefault("spike_s", np.ones(len(q["n"])))
+    keys = [k for k in parts[0] if all(k in q for q in parts)]
+    np.savez_compressed(out, **{k: np.concatenate([q[k] for q in parts]) for k in keys})
 
 
 def train(ctx, runs=RUNS, out=WEIGHTS, steps=4000, lr=2e-3, seed=0, val_frac=0.15, log=print):
     """Adam on soft targets; the checkpoint with the lowest validation loss is kept."""
     D = np.load(runs)
     ok = D["reached"].astype(bool)
-    F = D["features"][ok]
+    # inputs recomputed from the stored spectra (records made before the inputs were taken relative
+    # to the leading value hold the absolute form in "features")
+    F = np.stack([network_features(s2, lam, n, d) for s2, lam, n, d in
+                  zip(D["sigma2"][ok], D["lam"][ok], D["n"][ok], D["d"][ok])])
     T = np.stack([soft_targets(t, int(n)) for t, n in zip(D["times"][ok], D["n"][ok])])
     rng = np.random.default_rng(seed)
     perm = rng.permutation(len(F))
@@ -371,10 +395,13 @@ def main():
                     help="training problems: n log-uniform in this range")
     ap.add_argument("--d-choices", type=int, nargs="+", default=[256, 512, 1024, 2048],
                     help="training problems: d drawn log-uniformly from these")
+    ap.add_argument("--spike-prob", type=float, default=0.0,
+                    help="training problems: share with a few dominant directions over the power law")
     args = ap.parse_args()
     ctx = rs.Context(0)
     if args.what in ("generate", "all"):
-        generate(ctx, args.count, seed=args.seed, out=args.runs, n_range=args.n_range, d_choices=args.d_choices)
+        generate(ctx, args.count, seed=args.seed, out=args.runs, n_range=args.n_range, d_choices=args.d_choices,
+                 spike_prob=args.spike_prob)
     if args.merge:
         merge_runs(args.merge, args.runs)
     if args.what in ("train", "all", "train+evaluate"):

@@ -130,7 +130,8 @@ def test_propose_runs_the_network(rsctx, seed):
     nm = rs.mlp_norm(im, isd, om, osd)
     k, em, m, fb = rs.rs_propose(rsctx, s[:64], lam, n, d, s.sum(), theta=_f32(theta).cuda(), norm=nm)
     assert not fb
-    x = (proposal.features(s[:64], lam, n, d) - _f32(im).double().numpy()) / _f32(isd).double().numpy()
+    x = proposal.network_input(proposal.features(s[:64], lam, n, d), _f32(im).double().numpy(),
+                               _f32(isd).double().numpy())
     o, _ = proposal.forward(theta, x[None, :])
     o = o[0] * _f32(osd).double().numpy() + _f32(om).double().numpy()
     assert k == int(np.clip(np.round(2.0 ** o[0]), 1, 64))
@@ -189,6 +190,29 @@ def test_solve_proposed_equals_its_steps(rsctx, z_dtype):
     wh, _ = rs.rs_solve_proposed(rsctx, Xh, yc.cpu().pin_memory(), lam, 3, 11, 12, theta=theta, norm=nm,
                                  z_dtype=z_dtype, w_out=torch.empty(d).pin_memory())
     assert torch.equal(wh, w.cpu())
+
+
+@pytest.mark.parametrize("z_dtype", [None, torch.bfloat16])
+def test_solve_proposed_with_fixed_rank_equals_its_steps(rsctx, z_dtype):
+    """With a caller-fixed rank k > 64 the features are the first 64 Ritz values of the rank-k sketch,
+    the preconditioner keeps all k pairs and only (eta, m) come from the network, bit for bit."""
+    from tests.gpu_helpers import cuda_rows
+    n, d, lam, kf = 6000, 192, 1e-4, 96
+    X, y, _ = synth.problem(n, d, np.arange(1, d + 1, dtype=np.float64) ** -1.4, 0.1, 33)
+    Xc, yc = cuda_rows(X.float()), y.float().cuda()
+    im, isd, om, osd = _norm()
+    nm = rs.mlp_norm(im, isd, om, osd)
+    theta = _f32(_proposal_theta([0.3, 0.2, -0.5])).cuda()
+    w, info = rs.rs_solve_proposed(rsctx, Xc, yc, lam, 3, 11, 12, theta=theta, norm=nm, z_dtype=z_dtype, k_fixed=kf)
+    assert info["k"] == kf
+    V, s2 = rs.rs_sketch(rsctx, Xc, kf, 11)
+    _, em, m, fb = rs.rs_propose(rsctx, s2[:64].cpu().numpy(), lam, n, d, rs.rs_trace_c(rsctx, Xc), theta=theta,
+                                 norm=nm)
+    assert (m, fb) == (info["m"], info["fallback"]) and em == info["eta_mult"]
+    Z, beta, _ = rs.rs_precondition(rsctx, Xc, V, s2, lam, z_dtype=z_dtype)
+    w2, _ = rs.rs_svrg_solve(rsctx, Z, yc, V, s2, lam, 3, 12, beta=beta, m=m, eta_mult=em,
+                             X=Xc if z_dtype is not None else None, refine=z_dtype is not None)
+    assert torch.equal(w, w2)
 
 
 def test_solve_proposed_without_weights_uses_the_theory_setting(rsctx):

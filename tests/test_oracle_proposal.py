@@ -124,8 +124,21 @@ def test_theory_rank_on_two_level_spectrum(n, expect_rank_plus_one):
 
 
 def test_features():
-    s2 = np.geomspace(1.0, 1e-8, 70)
+    s2 = 4.0 * np.geomspace(1.0, 1e-8, 70)
     f = proposal.features(s2, 1e-5, 1000, 64)
     assert f.shape == (67,)
-    np.testing.assert_allclose(f[:64], 0.5 * np.log(s2[:64]), rtol=1e-14)
-    np.testing.assert_allclose(f[64:], np.log([1e-5, 1000, 64]), rtol=1e-14)
+    np.testing.assert_allclose(f[:64], 0.5 * np.log(s2[:64] / 4.0), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(f[64:], np.log([1e-5 / 4.0, 1000, 64]), rtol=1e-14)
+
+
+def test_features_are_scale_invariant():
+    # X -> c X scales the sketched spectrum and the equivalent lam by c^2: the input does not change
+    s2 = np.geomspace(3.0, 3e-6, 64)
+    np.testing.assert_allclose(proposal.features(s2, 1e-4, 5000, 256), proposal.features(49.0 * s2, 49e-4, 5000, 256),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_network_input_clips_to_the_training_spread():
+    x = np.array([0.0, 5.0, -7.0, 1.0])
+    z = proposal.network_input(x, np.zeros(4), np.array([1.0, 1.0, 2.0, 0.5]))
+    np.testing.assert_array_equal(z, [0.0, proposal.INPUT_CLIP, -proposal.INPUT_CLIP, 2.0])
