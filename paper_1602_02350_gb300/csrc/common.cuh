@@ -26,7 +26,7 @@ enum ScratchId {
   SCR_P, SCR_ADIAG, SCR_W, SCR_CUM, SCR_IDX, SCR_INVNQ, SCR_R, SCR_C, SCR_MU, SCR_WBAR,
   SCR_WNEXT, SCR_BETA, SCR_Z, SCR_XDEV, SCR_YDEV, SCR_V, SCR_S2, SCR_WOUT, SCR_BUCKET,
   SCR_SIGN, SCR_CSR, SCR_CNT, SCR_RED, SCR_EIG, SCR_MISC, SCR_STATUS, SCR_TMPV, SCR_SIGMA, SCR_LINV,
-  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_RPART, SCR_XPART, SCR_ROWSQ, SCR_SKPART, SCR_RITZ, SCR_CATB, SCR_CATB2, SCR_CATS, SCR_CATV, SCR_LINVD, SCR_JAC2, SCR_COUNT
+  SCR_MLP_PART, SCR_MLP_IO, SCR_BATCH, SCR_VK, SCR_KT, SCR_HN, SCR_UMMA, SCR_Z8, SCR_BPART, SCR_RPART, SCR_XPART, SCR_ROWSQ, SCR_SKPART, SCR_RITZ, SCR_CATB, SCR_CATB2, SCR_CATS, SCR_CATV, SCR_LINVD, SCR_JAC2, SCR_MAPPART, SCR_COUNT
 };
 
 // Launch choices measured by rs_autotune for one (kernel, storage type, width): chain = cluster

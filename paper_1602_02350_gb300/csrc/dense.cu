@@ -1022,6 +1022,53 @@ __global__ void __launch_bounds__(1024) map_fused_kernel(const T* __restrict__ V
   }
 }
 
+// The same map over many blocks for larger d: t_j = sum_c V_cj x_c as partial sums over row ranges
+// (block b takes rows [b R, b R + R), thread j column j), a one-block combine in range order that
+// also applies a_j, then y_c = x_c - sum_j V_cj (a t)_j with one warp per row (lanes over j, fixed
+// shuffle tree).
+template <typename T>
+__global__ void __launch_bounds__(256) map_tpart_kernel(const T* __restrict__ V, int64_t d, int k, int64_t R,
+                                                        const T* __restrict__ x, T* __restrict__ part) {
+  const int64_t c0 = blockIdx.x * R, c1 = min64(d, c0 + R);
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    T s0 = T(0), s1 = T(0);
+    int64_t c = c0;
+    for (; c + 1 < c1; c += 2) {
+      s0 = fma(V[c * k + j], x[c], s0);
+      s1 = fma(V[(c + 1) * k + j], x[c + 1], s1);
+    }
+    if (c < c1) s0 = fma(V[c * k + j], x[c], s0);
+    part[(int64_t)blockIdx.x * k + j] = s0 + s1;
+  }
+}
+
+template <typename T>
+__global__ void map_tsum_kernel(const T* __restrict__ part, int P, int k, const double* __restrict__ sigma2,
+                                double lam, T* __restrict__ tv) {
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    T t = T(0);
+    for (int p = 0; p < P; ++p) t += part[(int64_t)p * k + j];   // range order
+    tv[j] = (T)(1.0 - sqrt((sigma2[k - 1] + lam) / (sigma2[j] + lam))) * t;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) map_apply_kernel(const T* __restrict__ V, int64_t d, int k,
+                                                        const T* __restrict__ tv, const T* __restrict__ x,
+                                                        T* __restrict__ y) {
+  __shared__ T ts[256];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) ts[j] = tv[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= d) return;
+  const T* v = V + c * k;
+  T s = T(0);
+  for (int j = lane; j < k; j += 32) s = fma(v[j], ts[j], s);
+  s = warp_sum(s);
+  if (lane == 0) y[c] = x[c] - s;
+}
+
 // mean of a float vector in double (one block)
 __global__ void mean_f_kernel(const float* v, int64_t N, double* out) {
   __shared__ double sh[32];
@@ -1574,8 +1621,22 @@ static int precondition_t(rs_ctx* ctx, const rs_matrix* X, const T* V, const dou
 template <typename T>
 static int map_output_t(rs_ctx* ctx, const T* V, const double* sigma2, int64_t d, int64_t k, double lam, const T* wt,
                         T* w) {
-  if (k <= 256) {   // one launch
+  if (k <= 256 && d * k <= 65536) {   // one launch
     map_fused_kernel<T, T><<<1, 1024, 0, ctx->stream>>>(V, sigma2, d, (int)k, lam, wt, w);
+    RS_LAUNCH_CHECK(ctx);
+    return RS_OK;
+  }
+  if (k <= 256) {   // larger d: many blocks (the one-block kernel is latency-bound on a few MB of V)
+    const int64_t R = 32;
+    const int P = (int)((d + R - 1) / R);
+    T* part = static_cast<T*>(rs_scratch(ctx, SCR_MAPPART, ((size_t)P * k + k) * sizeof(T)));
+    if (!part) return RS_ENOMEM;
+    T* tv = part + (size_t)P * k;
+    map_tpart_kernel<T><<<(unsigned)P, 256, 0, ctx->stream>>>(V, d, (int)k, R, wt, part);
+    RS_LAUNCH_CHECK(ctx);
+    map_tsum_kernel<T><<<1, 256, 0, ctx->stream>>>(part, P, (int)k, sigma2, lam, tv);
+    RS_LAUNCH_CHECK(ctx);
+    map_apply_kernel<T><<<(unsigned)((d + 7) / 8), 256, 0, ctx->stream>>>(V, d, (int)k, tv, wt, w);
     RS_LAUNCH_CHECK(ctx);
     return RS_OK;
   }

@@ -39,8 +39,10 @@ def test_precondition_matches_oracle(rsctx, dtype, tol, n, d, k):
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
-def test_map_output_matches_oracle(rsctx, dtype, tol):
-    d, k = 300, 20
+@pytest.mark.parametrize("d,k", [(300, 20), (4096, 256), (2050, 129)])
+def test_map_output_matches_oracle(rsctx, dtype, tol, d, k):
+    """w = M w~ (Eq. (11)); d k <= 65536 takes the one-block kernel, larger maps the many-block one
+    (with a ragged last row range at d = 2050)."""
     V = torch.from_numpy(synth.random_orthonormal(d, k, 4)).to(dtype)
     s2 = synth.random_sigma2(k, 2)
     wt = torch.from_numpy(synth.random_vector(d, 3)).to(dtype)
