@@ -659,10 +659,58 @@ __global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __res
         }
       } else {
         // every block: warp w takes the rows a = w, w + 32, ... of the triangle (equal numbers of
-        // 32-wide column passes per warp), lanes the columns b <= a
+        // 32-wide column passes per warp), lanes the columns b <= a.  A lane's columns b = lane + 32 t
+        // are the same for every row, so their planes and rotations are read once per round into
+        // registers, and each row's once per row: the block update is then shared-memory traffic on
+        // A alone.
         const int nw = nt >> 5, wid = tid >> 5, ln = tid & 31;
-        for (int a = wid; a < P; a += nw)
-          for (int b = ln; b <= a; b += 32) upd(a, b);
+        constexpr int TB = 5;   // P <= 160
+        int pbv[TB], qbv[TB];
+        float cbv[TB], sbv[TB];
+#pragma unroll
+        for (int t = 0; t < TB; ++t) {
+          const int b = ln + 32 * t;
+          const bool in = b < P;
+          pbv[t] = in ? pp[b] : 0;
+          qbv[t] = in ? qq[b] : 0;
+          cbv[t] = in ? cc[b] : 1.0f;
+          sbv[t] = in ? ss[b] : 0.0f;
+        }
+        for (int a = wid; a < P; a += nw) {
+          const int pa = pp[a], qa = qq[a];
+          const float ca = cc[a], sa = ss[a], ta = tt[a];
+          const bool ra = qa < k;
+#pragma unroll
+          for (int t = 0; t < TB; ++t) {
+            const int b = ln + 32 * t;
+            if (b > a) break;
+            const int pb = pbv[t], qb = qbv[t];
+            const float cb = cbv[t], sb = sbv[t];
+            if ((!ra || qb >= k) && (a == b || (!ra && qb >= k))) continue;   // dummy player (odd k)
+            if (sa == 0.0f && sb == 0.0f) continue;
+            if (a == b) {
+              const int ipq = tri_idx(qa, pa);
+              const float apq = A[ipq];
+              A[tri_idx(pa, pa)] -= ta * apq;
+              A[tri_idx(qa, qa)] += ta * apq;
+              A[ipq] = 0.0f;
+              continue;
+            }
+            const bool rb = qb < k;
+            const int i00 = tri_idx(pa, pb);
+            const int i01 = rb ? tri_idx(pa, qb) : -1;
+            const int i10 = ra ? tri_idx(qa, pb) : -1;
+            const int i11 = (ra && rb) ? tri_idx(qa, qb) : -1;
+            const float m00 = A[i00], m01 = rb ? A[i01] : 0.0f, m10 = ra ? A[i10] : 0.0f,
+                        m11 = (ra && rb) ? A[i11] : 0.0f;
+            const float r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
+            const float r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
+            A[i00] = cb * r00 - sb * r01;
+            if (rb) A[i01] = sb * r00 + cb * r01;
+            if (ra) A[i10] = cb * r10 - sb * r11;
+            if (ra && rb) A[i11] = sb * r10 + cb * r11;
+          }
+        }
       }
       __syncthreads();
     }

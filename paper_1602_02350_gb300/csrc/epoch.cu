@@ -375,13 +375,6 @@ __host__ __device__ constexpr int chain_zpad(int tpc, int cpw, int esize) {
   return tpc > 1 ? (cpw * esize >= 16 ? cpw : 16 / esize) : 0;
 }
 
-// The rank-B update by column ranges: warp w owns CW / NW consecutive columns of the block's slice
-// and sums them over all B rows itself (no cross-warp partial sums), when those columns are a whole
-// number of 16-byte chunks and the chunks tile a warp.
-__host__ __device__ constexpr bool chain_colsplit(int es, int cw, int nw) {
-  return cw % nw == 0 && (cw / nw) % es == 0 && (cw / nw) / es >= 1 && 32 % ((cw / nw) / es) == 0;
-}
-
 template <typename S, typename T, int STAGES, int QN, int NT>
 __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, int64_t ld, int64_t d,
                                            const uint32_t* __restrict__ idx, int64_t m, const T* __restrict__ Rt,
@@ -408,10 +401,7 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   // chunks once with a 16-byte shared-memory load, uses them for its part of the dot products and
   // keeps them in registers for the rank-B update, whose per-warp partial sums over the warp's rows
   // are added across the warps through shared memory (fixed warp order).
-  constexpr bool COLS = chain_colsplit(ES, CW, NW);
-  // row stride of the staged slices (in S): one 16-byte chunk of padding, so the column-range update
-  // (lanes on different rows, same columns) spreads its 16-byte reads over the banks
-  constexpr int ZS = CW + ES;
+  constexpr int ZS = CW;                                   // row stride of the staged slices (in S)
   S* Zs = reinterpret_cast<S*>(ch_sh);                     // [STAGES][B][ZS]
   T* recv = reinterpret_cast<T*>(Zs + (size_t)STAGES * B * ZS);   // [2][kCsMax][B] partial dots from each rank
   // running sum of the iterates (epoch average) as a compensated (Kahan) pair in T: on GB300 a
@@ -423,10 +413,9 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
   T* pv = mus + CW;                                        // [B]
   T* av = pv + B;                                          // [B]   a_j, then (B_b - j) a_j in avw
   T* avw = av + B;                                         // [B]
-  constexpr int RED = COLS ? 0 : NW * CW;
   T* redu = avw + B;                                       // [NW][CW] per-warp partial sums of the update
-  T* redw = redu + RED;                                    // [NW][CW] the same with the running-sum weights
-  uint32_t* srow = reinterpret_cast<uint32_t*>(redw + RED);   // [STAGES][B]
+  T* redw = redu + NW * CW;                                // [NW][CW] the same with the running-sum weights
+  uint32_t* srow = reinterpret_cast<uint32_t*>(redw + NW * CW);   // [STAGES][B]
   float* sscale = reinterpret_cast<float*>(srow + STAGES * B);   // [STAGES][B] row scales (FP8 codes)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sscale + STAGES * B);   // [2]
   constexpr bool F8 = IsFp8<S>::value;
@@ -626,70 +615,6 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
       srow[slot * B + tid] = next_row;    // this slot now holds block blk + STAGES
       if (F8) sscale[slot * B + tid] = next_scale;
     }
-    if constexpr (COLS) {
-      // rank-B update by column ranges: lane (g, h) of warp w takes chunk h of the warp's columns on
-      // rows g, g + G, ... (16-byte reads from the staged slice), u_c = sum_j a_j z_jc and
-      // w_c = sum_j (B_b - j) a_j z_jc; the G row groups are summed by halving exchanges that leave
-      // each lane one column of its chunk, then by plain exchanges (fixed order); the lane that owns
-      // the column updates delta and the running sum
-      constexpr int CPW = CW / NW, CHW = CPW / ES, G = 32 / CHW, RPL = B / G;
-      constexpr int GB = G == 32 ? 5 : G == 16 ? 4 : G == 8 ? 3 : G == 4 ? 2 : G == 2 ? 1 : 0;   // group bits
-      constexpr int LE = ES == 16 ? 4 : ES == 8 ? 3 : ES == 4 ? 2 : ES == 2 ? 1 : 0;
-      constexpr int SS = LE < GB ? LE : GB;                                                     // halving steps
-      const int h = lane % CHW, g = lane / CHW;
-      const int colb = warp * CPW + h * ES;
-      T u[ES], w[ES];
-#pragma unroll
-      for (int e = 0; e < ES; ++e) u[e] = w[e] = T(0);
-#pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        const int j = r * G + g;
-        const T a = av[j], aw = avw[j];
-        const uint4 raw = *reinterpret_cast<const uint4*>(zs + j * ZS + colb);
-        const S* sv = reinterpret_cast<const S*>(&raw);
-#pragma unroll
-        for (int e = 0; e < ES; ++e) {
-          const T z = cvt<T>(sv[e]);
-          u[e] = fma(a, z, u[e]);
-          w[e] = fma(aw, z, w[e]);
-        }
-      }
-      int ci = 0;
-#pragma unroll
-      for (int st = 0; st < GB; ++st) {
-        const int o = 16 >> st;
-        if (st < SS) {
-          const int half = ES >> (st + 1);
-          const bool up = (lane & o) != 0;
-#pragma unroll
-          for (int i = 0; i < half; ++i) {
-            const T su = up ? u[i] : u[i + half], sw = up ? w[i] : w[i + half];
-            const T ku = up ? u[i + half] : u[i], kw = up ? w[i + half] : w[i];
-            u[i] = ku + __shfl_xor_sync(0xffffffffu, su, o);
-            w[i] = kw + __shfl_xor_sync(0xffffffffu, sw, o);
-          }
-          if (up) ci += half;
-        } else {
-          u[0] += __shfl_xor_sync(0xffffffffu, u[0], o);
-          w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
-        }
-      }
-      constexpr int SMASK = 31 ^ ((32 >> SS) - 1);                 // lane bits of the halving steps
-      constexpr int RMASK = 31 & ~(CHW - 1) & ~SMASK;               // lane bits summed in full
-      if ((lane & RMASK) == 0) {
-        const int c = colb + ci;
-        const T uu = u[0], ww = w[0];
-        const T bbT = (T)Bb;
-        const T tri = (T)((Bb * (Bb + 1)) / 2);   // exact
-        const T dold = dl[c];
-        const T x = bbT * dold - et * (mus[c] * tri + ww);
-        const T yk = x - Scmp[c];
-        const T tk = Ssum[c] + yk;
-        Scmp[c] = (tk - Ssum[c]) - yk;
-        Ssum[c] = tk;
-        dl[c] = dold - et * (bbT * mus[c] + uu);
-      }
-    } else
     // rank-B update of this warp's rows: u_c = sum_j a_j z_jc, w_c = sum_j (B_b - j) a_j z_jc
     {
       T u[CPL][ES], w[CPL][ES];
@@ -730,7 +655,6 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
         }
       }
     }
-    if constexpr (!COLS) {
     __syncthreads();
     for (int c = tid; c < CW; c += NT) {
       T uu = T(0), ww = T(0);
@@ -748,7 +672,6 @@ __device__ __forceinline__ void chain_body(const S* __restrict__ Z, int64_t N, i
       Scmp[c] = (tk - Ssum[c]) - yk;
       Ssum[c] = tk;
       dl[c] = dold - et * (bbT * mus[c] + uu);
-    }
     }
   }
   cp_async_wait<0>();
@@ -1082,10 +1005,8 @@ template <typename S, typename T>
 size_t chain_smem(int qn, int stages, int nt) {
   const int CW = 32 * qn;
   const int NW = nt / 32;
-  const int ES = 16 / (int)sizeof(S);
-  const size_t red = chain_colsplit(ES, CW, NW) ? 0 : 2 * (size_t)NW * CW * sizeof(T);
-  return (size_t)stages * kBlk * (CW + ES) * sizeof(S) + 2 * (size_t)kCsMax * kBlk * sizeof(T) +
-         4 * (size_t)CW * sizeof(T) + 3 * (size_t)kBlk * sizeof(T) + red + (size_t)stages * kBlk * sizeof(uint32_t) +
+  return (size_t)stages * kBlk * CW * sizeof(S) + 2 * (size_t)kCsMax * kBlk * sizeof(T) + 4 * (size_t)CW * sizeof(T) +
+         3 * (size_t)kBlk * sizeof(T) + 2 * (size_t)NW * CW * sizeof(T) + (size_t)stages * kBlk * sizeof(uint32_t) +
          (size_t)stages * kBlk * sizeof(float) + 2 * sizeof(uint64_t) + 64;
 }
 
