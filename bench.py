@@ -449,8 +449,8 @@ def run_batched(args):
                 first.append(hit[0] + 1)
             else:
                 # kappa^ = tr(H) / lambda_min(H) of the unpreconditioned problem (Eq. (3)), for context
-                H = ref_p[j].H
-                kap = float(torch.trace(H) / torch.linalg.eigvalsh(H)[0])
+                H = ref_p[j].H.cpu().numpy()   # host eigensolve (measurement only)
+                kap = float(np.trace(H) / np.linalg.eigvalsh(H)[0])
                 n_, d_, a_ = specs[p]
                 missed.append({"problem": p, "n": n_, "d": d_, "alpha": round(a_, 3), "lambda": lams[j],
                                "m": chains[p * 8 + j]["m"], "final_rel_subopt": float(f"{rel[-1]:.3e}"),
