@@ -478,7 +478,9 @@ int rs_propose(rs_ctx* ctx, const float* theta, const rs_mlp_norm* norm, const d
  * p->epochs epochs of Alg. 1 with eta = eta_mult / beta^ and the proposed m (p->eta, p->eta_mult
  * and p->m are ignored).  With sp->k > 64 the caller fixes the rank instead: the sketch has rank
  * sp->k (<= d), its first 64 Ritz values are the network's input, the preconditioner keeps all
- * sp->k pairs and only eta_mult and m are proposed (*k returns sp->k).  X, y and w_out may be
+ * sp->k pairs and only eta_mult and m are proposed, m carried from the network's rank k_net to
+ * sp->k as m kappa~(sp->k) / kappa~(k_net) with kappa~ as in rs_propose from the sketch's Ritz
+ * values (*k returns sp->k).  X, y and w_out may be
  * host pointers as in rs_solve.  k, eta_mult, m, used_fallback (host, nullable) receive the
  * parameters used.  Synchronises. */
 int rs_solve_proposed(rs_ctx* ctx, const rs_matrix* X, const void* y, const rs_sketch_params* sp,

@@ -975,7 +975,23 @@ static int solve_proposed_t(rs_ctx* ctx, const rs_matrix* Xin, const void* yin, 
     RS_TRY(rs_propose(ctx, theta, norm, s2h, p->lambda, n, d, trc, &k, &em, &m, &fb));
     ctx->call_gen = gen;
   }
-  if (K > 64) k = (int32_t)K;   // fixed rank: only eta and m are proposed
+  if (K > 64) {
+    // fixed rank: only eta and m are proposed.  The network's m is for its own rank k; Thm 1 sets the
+    // epoch length in proportion to kappa~(k), so it is carried over to the fixed rank K by the
+    // ratio kappa~(K) / kappa~(k) of the sketch's own estimates
+    if (!fb) {
+      std::vector<double> s2all((size_t)K);
+      RS_CUDA_TRY(cudaMemcpy(s2all.data(), sg, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost));
+      auto kt = [&](int64_t kk) {
+        double head = 0.0;
+        for (int64_t i = 0; i < kk; ++i) head += s2all[(size_t)i];
+        return ((double)kk * s2all[(size_t)kk - 1] + (trc - head)) / p->lambda;
+      };
+      const double kn = kt(k), kf = kt(K);
+      if (kn > 0.0 && kf > 0.0) m = std::max<int64_t>(1, std::llround((double)m * kf / kn));
+    }
+    k = (int32_t)K;
+  }
   T* Vk = static_cast<T*>(rs_scratch(ctx, SCR_VK, d * k * es));
   const int64_t ldz = (d * (int64_t)zs + 15) / 16 * 16 / (int64_t)zs;
   ZS* Zbuf = static_cast<ZS*>(rs_scratch(ctx, SCR_Z, (size_t)N * ldz * zs));

@@ -206,8 +206,12 @@ def test_solve_proposed_with_fixed_rank_equals_its_steps(rsctx, z_dtype):
     w, info = rs.rs_solve_proposed(rsctx, Xc, yc, lam, 3, 11, 12, theta=theta, norm=nm, z_dtype=z_dtype, k_fixed=kf)
     assert info["k"] == kf
     V, s2 = rs.rs_sketch(rsctx, Xc, kf, 11)
-    _, em, m, fb = rs.rs_propose(rsctx, s2[:64].cpu().numpy(), lam, n, d, rs.rs_trace_c(rsctx, Xc), theta=theta,
-                                 norm=nm)
+    trc = rs.rs_trace_c(rsctx, Xc)
+    kn, em, m, fb = rs.rs_propose(rsctx, s2[:64].cpu().numpy(), lam, n, d, trc, theta=theta, norm=nm)
+    assert not fb
+    # the network's epoch length carried to the fixed rank by kappa~(k_fixed) / kappa~(k_net) (Thm 1)
+    s2n = s2.cpu().numpy()
+    m = max(1, int(np.floor(m * proposal.kappa_tilde(s2n, trc, lam, kf) / proposal.kappa_tilde(s2n, trc, lam, kn) + 0.5)))
     assert (m, fb) == (info["m"], info["fallback"]) and em == info["eta_mult"]
     Z, beta, _ = rs.rs_precondition(rsctx, Xc, V, s2, lam, z_dtype=z_dtype)
     w2, _ = rs.rs_svrg_solve(rsctx, Z, yc, V, s2, lam, 3, 12, beta=beta, m=m, eta_mult=em,
