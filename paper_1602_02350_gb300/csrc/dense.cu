@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(1024) jacobi_packed_kernel(const double* __res
         if (ra) A[i10] = cb * r10 - sb * r11;
         if (ra && rb) A[i11] = sb * r10 + cb * r11;
       };
-      if (4 * na <= P) {
+      if (2 * na <= P) {
         // few rotating pairs: only the blocks of a row or column of one of them
         for (int bi = tid; bi < na * P; bi += nt) {
           const int a = act[bi / P], b = bi % P;
